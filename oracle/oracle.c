@@ -1,0 +1,546 @@
+/*
+ * oracle.c -- sequential CPU oracle for GSP-Louvain (Sahu, "An Approach for
+ * Addressing Internally-Disconnected Communities in Louvain Algorithm",
+ * arXiv 2402.11454).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the package-level smoke check and the CPU
+ * baseline leg of the benchmark do.  It shares no code, header, table or
+ * helper with the CUDA library.
+ *
+ * Plain, slow, obviously correct: every quantity is FP64, every loop runs in
+ * vertex order on one thread, and the per-vertex "hashtable" H of the paper
+ * is a dense array indexed by community id plus a list of the ids touched.
+ * Each function names the passage of the paper it follows.
+ *
+ * Build with -ffp-contract=off so that a*b+c is never fused: the oracle then
+ * rounds identically on x86-64 and AArch64.
+ *
+ * Graph model (Section 3): undirected G(V,E,w) stored as a symmetric CSR,
+ * w_ij = w_ji > 0, self-loops allowed and stored once in their row.
+ * K_i = sum_j w_ij (self-loop included), m = sum_{i,j} w_ij / 2.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    uint32_t n;            /* |V| */
+    uint64_t nnz;          /* directed CSR entries (both directions stored) */
+    const uint64_t *off;   /* n+1 row offsets */
+    const uint32_t *tgt;   /* nnz neighbour ids */
+    const double *w;       /* nnz weights */
+} og_graph;
+
+typedef struct {
+    int max_passes;             /* MAX_PASSES, Algorithm 1 */
+    int max_iterations;         /* MAX_ITERATIONS, Algorithm 4 */
+    double tolerance;           /* tau, Algorithm 4 */
+    double tolerance_drop;      /* TOLERANCE_DROP, Algorithm 1 */
+    double aggregation_tolerance; /* tau_agg, Algorithm 1 */
+    int split;                  /* 0 none (GVE-Louvain), 1 LP, 2 LPP, 3 BFS */
+    int split_last;             /* 0 Split Pass (SP), 1 Split Last (SL) */
+    int sync;                   /* 0 asynchronous in-place moves, 1 frozen-state sweeps */
+    int singleton_rule;         /* frozen-state sweeps only: singleton -> singleton moves go to lower ids */
+} og_opts;
+
+typedef struct {
+    int passes;
+    int iterations[64];
+    uint32_t vertices[64];      /* |V'| at the start of each pass */
+    uint32_t communities[64];   /* communities after the split of each pass */
+    double modularity;
+    uint32_t final_communities;
+} og_stats;
+
+/* ------------------------------------------------------------------ */
+/* Section 3: weighted degree K_i and total weight m.                   */
+/* ------------------------------------------------------------------ */
+double og_vertex_weights(const og_graph *g, double *K)
+{
+    double two_m = 0.0;
+    for (uint32_t i = 0; i < g->n; i++) {
+        double k = 0.0;
+        for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++) k += g->w[e];
+        K[i] = k;
+        two_m += k;
+    }
+    return two_m / 2.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Equation 1, second form: Q = sum_c [ sigma_c/2m - (Sigma_c/2m)^2 ],  */
+/* sigma_c = weight of directed entries (i,j) with C_i = C_j = c,       */
+/* Sigma_c = sum of K_i over i in c.  Community ids must be < n.        */
+/* An edgeless graph (2m = 0) has Q := 0.                               */
+/* ------------------------------------------------------------------ */
+double og_modularity(const og_graph *g, const uint32_t *C)
+{
+    uint32_t n = g->n;
+    double *sigma = calloc(n ? n : 1, sizeof(double));
+    double *Sigma = calloc(n ? n : 1, sizeof(double));
+    double two_m = 0.0;
+    for (uint32_t i = 0; i < n; i++) {
+        for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++) {
+            uint32_t j = g->tgt[e];
+            Sigma[C[i]] += g->w[e];
+            if (C[i] == C[j]) sigma[C[i]] += g->w[e];
+            two_m += g->w[e];
+        }
+    }
+    double q = 0.0;
+    if (two_m > 0.0) {
+        for (uint32_t c = 0; c < n; c++) {
+            double a = Sigma[c] / two_m;
+            q += sigma[c] / two_m - a * a;
+        }
+    }
+    free(sigma);
+    free(Sigma);
+    return q;
+}
+
+/* ------------------------------------------------------------------ */
+/* Equation 2: delta-modularity of moving i from community d to c.      */
+/* K_{i->c}, K_{i->d} exclude the self-loop of i; Sigma_d includes K_i. */
+/* ------------------------------------------------------------------ */
+double og_delta_modularity(double Kic, double Kid, double Ki, double Sc, double Sd, double m)
+{
+    return (Kic - Kid) / m - Ki * (Ki + Sc - Sd) / (2.0 * m * m);
+}
+
+/* scanCommunities (Algorithm 4): H[C[j]] += w over the edges of i,      */
+/* skipping the self-loop unless self is set.  H is a dense array that  */
+/* starts at zero; every id touched for the first time is appended to   */
+/* list, and the list length is returned.                               */
+static uint32_t scan_communities(const og_graph *g, const uint32_t *C, uint32_t i, int self,
+                                 double *H, uint8_t *seen, uint32_t *list, uint32_t len)
+{
+    for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++) {
+        uint32_t j = g->tgt[e];
+        if (!self && j == i) continue;
+        uint32_t c = C[j];
+        if (!seen[c]) { seen[c] = 1; list[len++] = c; }
+        H[c] += g->w[e];
+    }
+    return len;
+}
+
+static void clear_table(double *H, uint8_t *seen, const uint32_t *list, uint32_t len)
+{
+    for (uint32_t t = 0; t < len; t++) { H[list[t]] = 0.0; seen[list[t]] = 0; }
+}
+
+/*
+ * Best move of vertex i (Algorithm 4: "best community linked to i" and its
+ * delta-modularity, by Equation 2).  Candidates are the communities c != d
+ * present in H; ties go to the lowest community id.  Returns d (no move)
+ * unless the best delta-modularity is strictly positive.  best/second
+ * receive the two largest candidate values (-inf when absent) so that a
+ * caller can tell near-ties apart.  size/singleton_rule implement the
+ * lower-id rule for a vertex alone in its community moving to another
+ * singleton community (frozen-state sweeps only).
+ */
+static uint32_t best_move(const og_graph *g, const uint32_t *C, const double *K, const double *Sigma,
+                          const uint32_t *size, int singleton_rule, double m, uint32_t i,
+                          double *H, uint8_t *seen, uint32_t *list, double *best_out, double *second_out)
+{
+    uint32_t d = C[i];
+    uint32_t len = scan_communities(g, C, i, 0, H, seen, list, 0);
+    double Kid = H[d];   /* zero when no neighbour lies in d */
+    double best = -INFINITY, second = -INFINITY;
+    uint32_t cbest = d;
+    for (uint32_t t = 0; t < len; t++) {          /* the best candidate */
+        uint32_t c = list[t];
+        if (c == d) continue;
+        double dq = og_delta_modularity(H[c], Kid, K[i], Sigma[c], Sigma[d], m);
+        if (dq > best || (dq == best && c < cbest)) { best = dq; cbest = c; }
+    }
+    for (uint32_t t = 0; t < len; t++) {          /* the runner-up */
+        uint32_t c = list[t];
+        if (c == d || c == cbest) continue;
+        double dq = og_delta_modularity(H[c], Kid, K[i], Sigma[c], Sigma[d], m);
+        if (dq > second) second = dq;
+    }
+    clear_table(H, seen, list, len);
+    if (best_out) *best_out = best;
+    if (second_out) *second_out = second;
+    if (cbest == d || !(best > 0.0)) return d;
+    if (singleton_rule && size && size[d] == 1 && size[cbest] == 1 && cbest > d) return d;
+    return cbest;
+}
+
+/*
+ * One frozen-state sweep of the local-moving phase (Algorithm 4, with every
+ * vertex reading the C and Sigma of the sweep's start).  Processes the
+ * vertices with active[i] != 0 and writes the chosen community to choice[i]
+ * (C[i] for inactive vertices or no move), plus the best and second-best
+ * candidate delta-modularity.  Nothing is applied.
+ */
+void og_move_sweep_sync(const og_graph *g, const uint32_t *C, const double *K, const double *Sigma,
+                        const uint32_t *size, int singleton_rule, double m, const uint8_t *active,
+                        uint32_t *choice, double *best, double *second)
+{
+    uint32_t n = g->n;
+    double *H = calloc(n, sizeof(double));
+    uint8_t *seen = calloc(n, 1);
+    uint32_t *list = malloc(sizeof(uint32_t) * (n ? n : 1));
+    for (uint32_t i = 0; i < n; i++) {
+        double b = -INFINITY, s = -INFINITY;
+        choice[i] = C[i];
+        if (active && !active[i]) { best[i] = b; second[i] = s; continue; }
+        choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, &s);
+        best[i] = b;
+        second[i] = s;
+    }
+    free(H); free(seen); free(list);
+}
+
+/*
+ * louvainMove (Algorithm 4).  Updates C and Sigma in place and returns l_i,
+ * the number of iterations executed (including the one that met the
+ * tolerance).  Every vertex starts unprocessed; a processed vertex is marked
+ * processed, and a vertex that moves marks its neighbours unprocessed.
+ *   sync = 0: one thread walks the unprocessed vertices in id order and each
+ *             move is applied at once (the in-place form of the paper).
+ *   sync = 1: every vertex of an iteration reads the C, Sigma and community
+ *             sizes of the iteration's start; the moves are applied after.
+ * dq_iter (optional) receives the total delta-modularity of each iteration.
+ */
+int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, double m, double tau,
+            int max_iterations, int sync, int singleton_rule, double *dq_iter)
+{
+    uint32_t n = g->n;
+    double *H = calloc(n ? n : 1, sizeof(double));
+    uint8_t *seen = calloc(n ? n : 1, 1);
+    uint32_t *list = malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint8_t *unprocessed = malloc(n ? n : 1);
+    uint8_t *next = calloc(n ? n : 1, 1);
+    uint32_t *choice = malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *size = calloc(n ? n : 1, sizeof(uint32_t));
+    memset(unprocessed, 1, n);
+    for (uint32_t i = 0; i < n; i++) size[C[i]]++;
+    int li = 0;
+    for (int it = 0; it < max_iterations; it++) {
+        double dQ = 0.0;
+        li = it + 1;
+        if (!sync) {
+            for (uint32_t i = 0; i < n; i++) {
+                if (!unprocessed[i]) continue;
+                unprocessed[i] = 0;
+                double b;
+                uint32_t c = best_move(g, C, K, Sigma, NULL, 0, m, i, H, seen, list, &b, NULL);
+                if (c == C[i]) continue;
+                Sigma[C[i]] -= K[i];
+                Sigma[c] += K[i];
+                size[C[i]]--; size[c]++;
+                C[i] = c;
+                dQ += b;
+                for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++)
+                    if (g->tgt[e] != i) unprocessed[g->tgt[e]] = 1;
+            }
+        } else {
+            memset(next, 0, n);
+            for (uint32_t i = 0; i < n; i++) {
+                choice[i] = C[i];
+                if (!unprocessed[i]) continue;
+                double b;
+                choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, NULL);
+                if (choice[i] != C[i]) dQ += b;
+            }
+            for (uint32_t i = 0; i < n; i++) {
+                if (choice[i] == C[i]) continue;
+                Sigma[C[i]] -= K[i];
+                Sigma[choice[i]] += K[i];
+                size[C[i]]--; size[choice[i]]++;
+                for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++)
+                    if (g->tgt[e] != i) next[g->tgt[e]] = 1;
+            }
+            for (uint32_t i = 0; i < n; i++) C[i] = choice[i];
+            memcpy(unprocessed, next, n);
+        }
+        if (dq_iter) dq_iter[it] = dQ;
+        if (dQ <= tau) break;
+    }
+    free(H); free(seen); free(list); free(unprocessed); free(next); free(choice); free(size);
+    return li;
+}
+
+/* ------------------------------------------------------------------ */
+/* splitDisconnectedLp (Algorithm 2).  Labels start at the vertex id;  */
+/* each vertex takes the minimum label over its same-community         */
+/* neighbours until no label changes.  prune != 0 is the LPP variant:  */
+/* only unprocessed vertices are visited, and a vertex whose label     */
+/* changed marks its same-community neighbours unprocessed.  Returns   */
+/* the number of iterations.                                           */
+/* ------------------------------------------------------------------ */
+int og_split_lp(const og_graph *g, const uint32_t *C, uint32_t *Cp, int prune)
+{
+    uint32_t n = g->n;
+    uint8_t *unprocessed = malloc(n ? n : 1);
+    for (uint32_t i = 0; i < n; i++) { unprocessed[i] = 1; Cp[i] = i; }
+    int iters = 0;
+    for (;;) {
+        uint64_t dN = 0;
+        iters++;
+        for (uint32_t i = 0; i < n; i++) {
+            if (!unprocessed[i]) continue;
+            if (prune) unprocessed[i] = 0;
+            uint32_t cmin = Cp[i];
+            for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++) {
+                uint32_t j = g->tgt[e];
+                if (C[j] == C[i] && Cp[j] < cmin) cmin = Cp[j];
+            }
+            if (cmin == Cp[i]) continue;
+            Cp[i] = cmin;
+            dN++;
+            if (prune)
+                for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++)
+                    if (C[g->tgt[e]] == C[i]) unprocessed[g->tgt[e]] = 1;
+        }
+        if (dN == 0) break;
+    }
+    free(unprocessed);
+    return iters;
+}
+
+/* bfsVisitForEach: breadth-first search from s over the vertices j with  */
+/* C[j] == c, marking vis; calls back by writing label into Cp (when Cp  */
+/* is given) and returns the number of vertices reached.                */
+static uint64_t bfs_visit(const og_graph *g, const uint32_t *C, uint32_t c, uint32_t s, uint8_t *vis,
+                          uint32_t *queue, uint32_t *Cp, uint32_t label)
+{
+    uint64_t head = 0, tail = 0;
+    vis[s] = 1;
+    queue[tail++] = s;
+    while (head < tail) {
+        uint32_t u = queue[head++];
+        if (Cp) Cp[u] = label;
+        for (uint64_t e = g->off[u]; e < g->off[u + 1]; e++) {
+            uint32_t j = g->tgt[e];
+            if (vis[j] || C[j] != c) continue;
+            vis[j] = 1;
+            queue[tail++] = j;
+        }
+    }
+    return tail;
+}
+
+/* ------------------------------------------------------------------ */
+/* splitDisconnectedBfs (Algorithm 3) with one thread: vertices are    */
+/* scanned in id order; an unvisited vertex i seeds a BFS inside its   */
+/* community C[i], labelling everything reached with C'[i] = i.  (The  */
+/* BFS condition is read as C[j] = C[i]; the printed condition compares */
+/* C[j] with itself.)  With one thread the busy flags never block.     */
+/* ------------------------------------------------------------------ */
+void og_split_bfs(const og_graph *g, const uint32_t *C, uint32_t *Cp)
+{
+    uint32_t n = g->n;
+    uint8_t *vis = calloc(n ? n : 1, 1);
+    uint32_t *queue = malloc(sizeof(uint32_t) * (n ? n : 1));
+    for (uint32_t i = 0; i < n; i++) Cp[i] = i;
+    for (uint32_t i = 0; i < n; i++) {
+        if (vis[i]) continue;
+        bfs_visit(g, C, C[i], i, vis, queue, Cp, Cp[i]);
+    }
+    free(vis); free(queue);
+}
+
+/* Renumber communities (Algorithm 1): distinct ids ranked by increasing */
+/* value become 0..k-1.  Ids must be < n.  Returns k.                   */
+uint32_t og_renumber(uint32_t n, uint32_t *C)
+{
+    uint32_t *rank = malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint8_t *used = calloc(n ? n : 1, 1);
+    for (uint32_t i = 0; i < n; i++) used[C[i]] = 1;
+    uint32_t k = 0;
+    for (uint32_t c = 0; c < n; c++) rank[c] = used[c] ? k++ : 0;
+    for (uint32_t i = 0; i < n; i++) C[i] = rank[C[i]];
+    free(rank); free(used);
+    return k;
+}
+
+/* Dendrogram lookup (Algorithm 1): C[v] <- C'[C[v]]. */
+void og_lookup(uint64_t n_top, uint32_t *C, const uint32_t *Cp)
+{
+    for (uint64_t v = 0; v < n_top; v++) C[v] = Cp[C[v]];
+}
+
+/* ------------------------------------------------------------------ */
+/* louvainAggregate (Algorithm 5).  C must be dense in [0,k).          */
+/*  1. community-vertex CSR: count, exclusive scan, scatter;            */
+/*  2. super-vertex offsets from each community's total degree;         */
+/*  3. per community, H over the edges of its members (self = true),    */
+/*     then the (d, w) pairs become the edges of super-vertex c.        */
+/* The holey CSR of the paper is compacted, and each row is emitted in  */
+/* increasing d, so that the result is canonical.  out_off has k+1      */
+/* entries; out_tgt/out_w need room for nnz entries.  Returns the       */
+/* number of super-edges.                                               */
+/* ------------------------------------------------------------------ */
+uint64_t og_aggregate(const og_graph *g, const uint32_t *C, uint32_t k,
+                      uint64_t *out_off, uint32_t *out_tgt, double *out_w)
+{
+    uint32_t n = g->n;
+    uint64_t *coff = calloc((size_t)k + 1, sizeof(uint64_t));
+    uint32_t *cverts = malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint64_t *fill = malloc(sizeof(uint64_t) * ((size_t)k + 1));
+    /* countCommunityVertices + exclusiveScan */
+    for (uint32_t i = 0; i < n; i++) coff[C[i] + 1]++;
+    for (uint32_t c = 0; c < k; c++) coff[c + 1] += coff[c];
+    memcpy(fill, coff, sizeof(uint64_t) * ((size_t)k + 1));
+    for (uint32_t i = 0; i < n; i++) cverts[fill[C[i]]++] = i;
+    /* communityTotalDegree + exclusiveScan: the super-vertex row bounds */
+    uint64_t *yoff = calloc((size_t)k + 1, sizeof(uint64_t));
+    for (uint32_t i = 0; i < n; i++) yoff[C[i] + 1] += g->off[i + 1] - g->off[i];
+    for (uint32_t c = 0; c < k; c++) yoff[c + 1] += yoff[c];
+    /* per-community hashtable; rows written gap-free and sorted */
+    double *H = calloc(k ? k : 1, sizeof(double));
+    uint8_t *seen = calloc(k ? k : 1, 1);
+    uint32_t *list = malloc(sizeof(uint32_t) * (k ? k : 1));
+    uint64_t pos = 0;
+    out_off[0] = 0;
+    for (uint32_t c = 0; c < k; c++) {
+        uint32_t len = 0;
+        for (uint64_t t = coff[c]; t < coff[c + 1]; t++)
+            len = scan_communities(g, C, cverts[t], 1, H, seen, list, len);
+        /* emit in increasing d: walk the touched ids after sorting them */
+        for (uint32_t a = 1; a < len; a++) {          /* insertion sort */
+            uint32_t x = list[a];
+            uint32_t b = a;
+            while (b > 0 && list[b - 1] > x) { list[b] = list[b - 1]; b--; }
+            list[b] = x;
+        }
+        for (uint32_t t = 0; t < len; t++) {
+            out_tgt[pos] = list[t];
+            out_w[pos] = H[list[t]];
+            pos++;
+        }
+        clear_table(H, seen, list, len);
+        out_off[c + 1] = pos;
+    }
+    free(coff); free(cverts); free(fill); free(yoff); free(H); free(seen); free(list);
+    return pos;
+}
+
+/* ------------------------------------------------------------------ */
+/* disconnectedCommunities (Algorithm 6) with one thread: S = community */
+/* sizes; the first vertex met of each community seeds a BFS inside it; */
+/* the community is flagged when fewer than S[c] vertices are reached.  */
+/* D (optional, n entries) receives the flags.  Returns how many.       */
+/* ------------------------------------------------------------------ */
+uint32_t og_disconnected(const og_graph *g, const uint32_t *C, uint8_t *D)
+{
+    uint32_t n = g->n;
+    uint64_t *S = calloc(n ? n : 1, sizeof(uint64_t));
+    uint8_t *vis = calloc(n ? n : 1, 1);
+    uint32_t *queue = malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t count = 0;
+    if (D) memset(D, 0, n);
+    for (uint32_t i = 0; i < n; i++) S[C[i]]++;
+    for (uint32_t i = 0; i < n; i++) {
+        uint32_t c = C[i];
+        if (S[c] == 0) continue;
+        uint64_t reached = bfs_visit(g, C, c, i, vis, queue, NULL, 0);
+        if (reached < S[c]) { if (D) D[c] = 1; count++; }
+        S[c] = 0;
+    }
+    free(S); free(vis); free(queue);
+    return count;
+}
+
+static void run_split(const og_graph *g, const uint32_t *C, uint32_t *Cp, int mode)
+{
+    if (mode == 1) og_split_lp(g, C, Cp, 0);
+    else if (mode == 2) og_split_lp(g, C, Cp, 1);
+    else if (mode == 3) og_split_bfs(g, C, Cp);
+    else memcpy(Cp, C, sizeof(uint32_t) * g->n);
+}
+
+/* Final numbering: communities ranked by their smallest vertex id. */
+static uint32_t canonical_numbering(uint32_t n, uint32_t *C)
+{
+    uint32_t *id = malloc(sizeof(uint32_t) * (n ? n : 1));
+    for (uint32_t c = 0; c < n; c++) id[c] = UINT32_MAX;
+    uint32_t k = 0;
+    for (uint32_t v = 0; v < n; v++) {
+        if (id[C[v]] == UINT32_MAX) id[C[v]] = k++;
+        C[v] = id[C[v]];
+    }
+    free(id);
+    return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* louvain (Algorithm 1), GSP-Louvain driver.  G is the input graph;   */
+/* C receives the final membership numbered 0..k-1 by smallest vertex   */
+/* id.  Each pass: K' = Sigma' = vertexWeights(G'), C' = identity,      */
+/* louvainMove, split (Split Pass), global convergence when l_i <= 1,   */
+/* low-shrink stop when |Gamma|/|V'| > tau_agg, renumber, dendrogram    */
+/* lookup, louvainAggregate, tau /= TOLERANCE_DROP.  A final lookup     */
+/* follows the loop.  With split_last the split runs once, on G and the */
+/* final membership.  Returns the number of passes.                     */
+/* ------------------------------------------------------------------ */
+int og_louvain(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st)
+{
+    uint32_t n = g->n;
+    for (uint32_t v = 0; v < n; v++) C[v] = v;
+    if (st) memset(st, 0, sizeof(*st));
+    /* the current graph G' (owned copies after the first aggregation) */
+    og_graph cur = *g;
+    uint64_t *own_off = NULL; uint32_t *own_tgt = NULL; double *own_w = NULL;
+    double *K = malloc(sizeof(double) * (n ? n : 1));
+    double *Sigma = malloc(sizeof(double) * (n ? n : 1));
+    uint32_t *Cp = malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *Cs = malloc(sizeof(uint32_t) * (n ? n : 1));
+    double tau = o->tolerance;
+    int passes = 0;
+    int split_each_pass = (o->split != 0 && !o->split_last);
+    for (int lp = 0; lp < o->max_passes; lp++) {
+        uint32_t nv = cur.n;
+        double m = og_vertex_weights(&cur, K);
+        memcpy(Sigma, K, sizeof(double) * nv);
+        for (uint32_t i = 0; i < nv; i++) Cp[i] = i;
+        int li = (m > 0.0) ? og_move(&cur, Cp, K, Sigma, m, tau, o->max_iterations, o->sync,
+                                     o->singleton_rule, NULL)
+                           : 0;
+        if (split_each_pass) {
+            run_split(&cur, Cp, Cs, o->split);
+            memcpy(Cp, Cs, sizeof(uint32_t) * nv);
+        }
+        passes = lp + 1;
+        /* |Gamma| = communities in C' after the split; |Gamma_old| = |V'| */
+        uint32_t *tmp = malloc(sizeof(uint32_t) * (nv ? nv : 1));
+        memcpy(tmp, Cp, sizeof(uint32_t) * nv);
+        uint32_t k = og_renumber(nv, tmp);
+        free(tmp);
+        if (st && lp < 64) { st->iterations[lp] = li; st->vertices[lp] = nv; st->communities[lp] = k; }
+        if (li <= 1) break;
+        if ((double)k / (double)nv > o->aggregation_tolerance) break;
+        k = og_renumber(nv, Cp);
+        og_lookup(n, C, Cp);
+        uint64_t *noff = malloc(sizeof(uint64_t) * ((size_t)k + 1));
+        uint32_t *ntgt = malloc(sizeof(uint32_t) * (cur.nnz ? cur.nnz : 1));
+        double *nw = malloc(sizeof(double) * (cur.nnz ? cur.nnz : 1));
+        uint64_t nnz2 = og_aggregate(&cur, Cp, k, noff, ntgt, nw);
+        free(own_off); free(own_tgt); free(own_w);
+        own_off = noff; own_tgt = ntgt; own_w = nw;
+        cur.n = k; cur.nnz = nnz2; cur.off = noff; cur.tgt = ntgt; cur.w = nw;
+        tau = tau / o->tolerance_drop;
+        /* the pass that aggregated leaves C' as identity on the new graph */
+        for (uint32_t i = 0; i < k; i++) Cp[i] = i;
+    }
+    og_lookup(n, C, Cp);
+    if (o->split != 0 && o->split_last) {
+        run_split(g, C, Cs, o->split);
+        memcpy(C, Cs, sizeof(uint32_t) * n);
+    }
+    uint32_t k = canonical_numbering(n, C);
+    if (st) {
+        st->passes = passes;
+        st->final_communities = k;
+        st->modularity = og_modularity(g, C);
+    }
+    free(own_off); free(own_tgt); free(own_w); free(K); free(Sigma); free(Cp); free(Cs);
+    return passes;
+}

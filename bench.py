@@ -1,0 +1,304 @@
+"""GSP-Louvain benchmark: edges/s of the whole method on one GB300.
+
+Default workload: R-MAT scale 22 (4.19 M vertices, edge factor 16,
+a/b/c/d = 0.57/0.19/0.19/0.05, symmetrised, deduplicated, self-loops dropped,
+unit float32 weights, seed 2), plain method (flag pruning), float32 delta-Q
+with float64 m / Sigma_tot / modularity.  A step is one full gsp_louvain call
+(all passes: local moving, split, aggregation, final modularity) on the graph
+already resident in HBM.  edges/s = directed CSR entries / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload rmat22|planted|grid|batch|rmat26]
+
+Under torchrun (N > 1) every rank runs its own replica (the method does not
+shard a single graph); value = edges of all ranks / max time over ranks.
+--impl reference times the sequential CPU oracle on a bounded R-MAT sample.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GSP-Louvain edges/s on 1 GB300"
+UNIT = "edges/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(gsp, graphgen, name):
+    """Generate the workload on the device; returns (off, tgt, w, config, extra)."""
+    if name == "rmat22":
+        off, tgt, w = gsp.gen_rmat(22, 16, seed=2)
+        cfg = {"workload": "rmat22", "scale": 22, "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05],
+               "seed": 2}
+    elif name == "rmat26":
+        off, tgt, w = gsp.gen_rmat(26, 16, seed=5)
+        cfg = {"workload": "rmat26", "scale": 26, "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05],
+               "seed": 5}
+    elif name == "planted":
+        off, tgt, w = gsp.gen_planted(n=10000, k=64, mean_degree=16, p_intra=0.8, seed=1)
+        cfg = {"workload": "planted", "vertices": 10000, "communities": 64, "mean_degree": 16,
+               "p_intra": 0.8, "seed": 1}
+    elif name == "grid":
+        off, tgt, w = gsp.gen_grid(4096, 4096, seed=3)
+        cfg = {"workload": "grid4096", "rows": 4096, "cols": 4096, "p_remove": 0.05, "p_long": 0.001,
+               "weights": [1.0, 10.0], "seed": 3}
+    else:
+        raise SystemExit("unknown workload %s" % name)
+    cfg["vertices"] = int(off.numel() - 1)
+    cfg["edges"] = int(tgt.numel())
+    return off, tgt, w, cfg
+
+
+def roofline_from(stats_list, peak_gbs, peak_kind):
+    byt = sum(sum(s["move_bytes"]) for s in stats_list)
+    ms = sum(sum(s["ms_move_kernels"]) for s in stats_list)
+    if ms <= 0:
+        return None
+    achieved = byt / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "local-moving sweep (k_move_group/k_move_block)",
+            "achieved": round(achieved, 1), "peak": peak_gbs, "peak_kind": peak_kind + " (burst copy)",
+            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": None,
+            "algorithmic_bytes_per_step": byt / max(1, len(stats_list))}
+
+
+def cpu_baseline(sample_scale=20, seed=2):
+    import oracle
+    from paper_2402_11454_gb300 import graphgen
+    off, tgt, w = graphgen.rmat(sample_scale, 16, seed=seed)
+    g = oracle.Graph(off, tgt, w.astype("float64"))
+    t0 = time.perf_counter()
+    _, st = oracle.louvain(g, oracle.LouvainOptions(sync=False))
+    dt = time.perf_counter() - t0
+    return {"value": len(tgt) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "R-MAT scale %d (edge factor 16, same a/b/c/d), %d directed edges, one sequential "
+                      "oracle run (%.1f s, Q=%.4f)" % (sample_scale, len(tgt), dt, st["modularity"]),
+            "cpu": cpu_model()}
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2402_11454_gb300 import graphgen
+    scale = args.ref_scale
+    off, tgt, w = graphgen.rmat(scale, 16, seed=2)
+    g = oracle.Graph(off, tgt, w.astype("float64"))
+    for _ in range(args.warmup):
+        oracle.louvain(g, oracle.LouvainOptions(sync=False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.louvain(g, oracle.LouvainOptions(sync=False))
+    dt = time.perf_counter() - t0
+    val = len(tgt) * args.steps / dt
+    cfg = {"workload": "rmat22", "sample": "R-MAT scale %d" % scale, "edges": int(len(tgt))}
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "R-MAT scale %d, sequential oracle, %d steps" % (scale, args.steps)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22")
+    ap.add_argument("--precision", default="mixed")
+    ap.add_argument("--split", default="bfs")
+    ap.add_argument("--move", default="async")
+    ap.add_argument("--ref-scale", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    from paper_2402_11454_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2402_11454_gb300 import graphgen, gsp
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    off, tgt, w, cfg = make_workload(gsp, graphgen, args.workload)
+    kw = dict(precision=args.precision, split=args.split, move=args.move)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MB > 129 MB L2
+
+    for _ in range(max(args.warmup, 0)):
+        C, q, st = gsp.louvain(off, tgt, w, **kw)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = gsp.kernel_launches()
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C, q, st = gsp.louvain(off, tgt, w, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(st)
+    launches = gsp.kernel_launches() - l0 - 0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    edges = cfg["edges"]
+    value = edges * args.steps * ws / (total_ms * 1e-3)
+
+    # end to end: host (pinned) buffers through the C ABI, copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        h_off = off.cpu().pin_memory()
+        h_tgt = tgt.cpu().pin_memory()
+        h_w = w.cpu().pin_memory()
+        h_C = torch.empty(off.numel() - 1, dtype=torch.int32, pin_memory=True)
+        gsp.louvain_host(h_off, h_tgt, h_w, h_C, **kw)
+        et = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gsp.louvain_host(h_off, h_tgt, h_w, h_C, **kw)
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t0)
+        e2e_s = sum(et)
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": edges * args.steps * ws / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_off.numel() * 8 + h_tgt.numel() * 4 + h_w.numel() * 4),
+               "d2h_bytes_per_step": int(h_C.numel() * 4)}
+
+    peak, kind = load_peaks()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic (device-generated R-MAT / planted / grid, seeded)",
+            "config": dict(cfg, precision=args.precision, split=args.split, move=args.move,
+                           parallelism="replicas" if ws > 1 else "single",
+                           l2="inputs larger than L2 plus a 256 MB flush between steps"),
+            "modularity": q, "communities": st["final_communities"], "passes": st["passes"],
+            "phase_ms": {"move": sum(st["ms_move"]), "split": sum(st["ms_split"]),
+                         "aggregate": sum(st["ms_aggregate"]), "other": sum(st["ms_other"]),
+                         "total": st["ms_total"]},
+            "roofline": roofline_from(stats, peak, kind), "gpu_launches": launches,
+            "clocks": clocks, "e2e": e2e}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

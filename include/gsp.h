@@ -1,0 +1,281 @@
+/*
+ * gsp.h -- C ABI of the GB300-native GSP-Louvain library (libgsp.so).
+ *
+ * GSP-Louvain (Sahu, arXiv 2402.11454) is the Louvain method of community
+ * detection with a split step after the local-moving phase of every pass,
+ * which breaks each community into its connected components so that no
+ * returned community is internally disconnected.
+ *
+ * Conventions for every entry point:
+ *  - Graphs are symmetric CSR: offsets (n+1 x uint64), targets (nnz x uint32),
+ *    weights (nnz x float32, or float64 where a gsp_wtype says so).  Both
+ *    directions of every undirected edge are stored; a self-loop is stored
+ *    once in its row.  Weights must be finite and > 0.  (Section 3: G(V,E,w),
+ *    w_ij = w_ji, unit weight for unweighted graphs.)
+ *  - Unless a parameter says "host", every pointer is a DEVICE pointer owned by
+ *    the caller; the library never frees caller memory.  Work runs on the
+ *    cudaStream_t passed as `stream` (NULL = legacy default stream); calls that
+ *    return host values synchronise that stream before returning.
+ *  - Nothing throws across the ABI.  Every call returns a gsp_status; invalid
+ *    sizes or options give GSP_ERR_INVALID before any device work; a CUDA
+ *    failure gives GSP_ERR_CUDA; gsp_last_error() returns a message.
+ *  - The library keeps one internal device workspace, grown on demand with
+ *    cudaMalloc and reused across calls.  Calls must not run concurrently
+ *    from several host threads.
+ *  - The naming clash of the paper (m = total edge weight, M = edge count) is
+ *    avoided by calling the edge count nnz.
+ */
+#ifndef GSP_H
+#define GSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GSP_OK = 0,
+    GSP_ERR_INVALID = -1,     /* bad size, pointer or option */
+    GSP_ERR_NOMEM = -2,       /* device allocation failed */
+    GSP_ERR_CUDA = -3,        /* a CUDA runtime call or kernel failed */
+    GSP_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    GSP_ERR_CAPACITY = -5     /* a fixed-size buffer was too small */
+} gsp_status;
+
+/* Split techniques of Section 4.1: none (GVE-Louvain), min-label propagation
+ * (Algorithm 2), min-label propagation with pruning (Algorithm 2, LPP), and
+ * breadth-first search (Algorithm 3). */
+typedef enum { GSP_SPLIT_NONE = 0, GSP_SPLIT_LP = 1, GSP_SPLIT_LPP = 2, GSP_SPLIT_BFS = 3 } gsp_split_mode;
+/* Split Pass (after the local-moving phase of every pass) or Split Last
+ * (once, after the passes converge); Section 4.1. */
+typedef enum { GSP_SPLIT_PASS = 0, GSP_SPLIT_LAST = 1 } gsp_split_when;
+/* Local moving (Algorithm 4): ASYNC updates memberships in place as the paper
+ * does (results depend on thread timing); SYNC lets every vertex of an
+ * iteration read the state of the iteration's start (deterministic). */
+typedef enum { GSP_MOVE_ASYNC = 0, GSP_MOVE_SYNC = 1 } gsp_move_mode;
+/* MIXED: per-community weights K_{i->c} and delta-modularity in float32,
+ * while m, Sigma_tot and modularity stay float64.  FP64: everything float64,
+ * Equation 2 evaluated term by term (the parity mode). */
+typedef enum { GSP_PREC_MIXED = 0, GSP_PREC_FP64 = 1 } gsp_precision;
+/* Vertex pruning of Algorithm 4 (processed/unprocessed flags), optionally
+ * narrowed by a learned skip predictor (a small MLP). */
+typedef enum { GSP_PRUNE_FLAGS = 0, GSP_PRUNE_LEARNED = 1 } gsp_prune_mode;
+typedef enum { GSP_W_F32 = 0, GSP_W_F64 = 1 } gsp_wtype;
+
+typedef struct {
+    int max_passes;                 /* MAX_PASSES (Algorithm 1); default 10 */
+    int max_iterations;             /* MAX_ITERATIONS (Algorithm 4); default 20 */
+    double tolerance;               /* tau (Algorithm 4); default 1e-2 */
+    double tolerance_drop;          /* TOLERANCE_DROP (Algorithm 1); default 10 */
+    double aggregation_tolerance;   /* tau_agg (Algorithm 1); default 0.8 */
+    int split;                      /* gsp_split_mode; default GSP_SPLIT_BFS */
+    int split_when;                 /* gsp_split_when; default GSP_SPLIT_PASS */
+    int move;                       /* gsp_move_mode; default GSP_MOVE_ASYNC */
+    int precision;                  /* gsp_precision; default GSP_PREC_MIXED */
+    int singleton_rule;             /* 1: a vertex alone in its community moves to another
+                                       singleton community only if that id is lower; default 1 */
+    int prune;                      /* gsp_prune_mode; default GSP_PRUNE_FLAGS */
+    const void *mlp_params;         /* device pointer to gsp_mlp_param_count() floats (learned pruning) */
+    int full_sweep_every;           /* learned pruning: every k-th iteration is a plain sweep; default 4 */
+    void *stream;                   /* cudaStream_t; NULL = default stream */
+} gsp_opts;
+
+#define GSP_MAX_PASS_STATS 32
+typedef struct {
+    int passes;
+    int iterations[GSP_MAX_PASS_STATS];          /* l_i of each pass */
+    uint32_t vertices[GSP_MAX_PASS_STATS];       /* |V'| at the start of each pass */
+    uint32_t communities[GSP_MAX_PASS_STATS];    /* communities after each pass's split */
+    uint64_t edges[GSP_MAX_PASS_STATS];          /* nnz of each pass's graph */
+    float ms_move[GSP_MAX_PASS_STATS];
+    float ms_split[GSP_MAX_PASS_STATS];
+    float ms_aggregate[GSP_MAX_PASS_STATS];
+    float ms_other[GSP_MAX_PASS_STATS];
+    uint64_t vertices_processed[GSP_MAX_PASS_STATS];  /* vertex visits of local moving */
+    uint64_t edges_scanned[GSP_MAX_PASS_STATS];       /* edge visits of local moving */
+    uint64_t vertices_skipped[GSP_MAX_PASS_STATS];    /* visits dropped by the learned predictor */
+    double move_bytes[GSP_MAX_PASS_STATS];            /* algorithmic bytes of the local-moving kernels */
+    float ms_move_kernels[GSP_MAX_PASS_STATS];        /* device time of those kernels (CUDA events) */
+    uint32_t final_communities;
+    double modularity;
+    float ms_total;
+} gsp_stats;
+
+/* Fill *o with the defaults listed in gsp_opts. */
+void gsp_default_opts(gsp_opts *o);
+const char *gsp_status_string(gsp_status s);
+/* Message of the last failing call on this thread (static storage). */
+const char *gsp_last_error(void);
+
+/*
+ * GSP-Louvain (Algorithm 1).  Input: the graph (float32 weights).  Output:
+ * membership[n] (device), each vertex's community numbered 0..k-1 in order of
+ * the smallest vertex id of each community; *modularity (host) = Equation 1
+ * of that membership on the input graph, reduced in float64; *stats (host,
+ * may be NULL).  n == 0 is GSP_ERR_INVALID.  An edgeless graph returns the
+ * identity membership and modularity 0 (2m = 0 leaves Equation 1 undefined).
+ */
+gsp_status gsp_louvain(const uint64_t *offsets, const uint32_t *targets, const float *weights,
+                       uint32_t n, uint64_t nnz, const gsp_opts *opts,
+                       uint32_t *membership, double *modularity, gsp_stats *stats);
+
+/* As gsp_louvain, but offsets/targets/weights/membership are HOST arrays: the
+ * call copies the graph to the device and the membership back. */
+gsp_status gsp_louvain_host(const uint64_t *offsets, const uint32_t *targets, const float *weights,
+                            uint32_t n, uint64_t nnz, const gsp_opts *opts,
+                            uint32_t *membership, double *modularity, gsp_stats *stats);
+
+/*
+ * Batched GSP-Louvain over num_graphs independent graphs concatenated into one
+ * CSR: graph g owns vertices [graph_vertex_offsets[g], graph_vertex_offsets[g+1])
+ * (host array of num_graphs+1 entries) and no edge crosses graphs.  Each graph
+ * keeps its own m, tolerance and convergence, as if run alone.  membership is
+ * per graph local (0..k_g-1, ordered by smallest vertex); modularity (device,
+ * num_graphs doubles) receives each graph's Equation 1 value.
+ */
+gsp_status gsp_louvain_batched(uint32_t num_graphs, const uint64_t *graph_vertex_offsets,
+                               const uint64_t *offsets, const uint32_t *targets, const float *weights,
+                               uint32_t n, uint64_t nnz, const gsp_opts *opts,
+                               uint32_t *membership, double *modularity, gsp_stats *stats);
+
+/* ---------------------------------------------------------------------------
+ * Phase entry points (each one step of Algorithm 1), for reuse and parity
+ * tests.  `wt` gives the weight type of `weights`.
+ * ------------------------------------------------------------------------- */
+
+/* Section 3: K[i] = sum_j w_ij (self-loop included), float64; *m_host =
+ * sum K / 2 (host). */
+gsp_status gsp_vertex_weights(const uint64_t *offsets, const uint32_t *targets, const void *weights,
+                              int wt, uint32_t n, uint64_t nnz, double *K, double *m_host, void *stream);
+
+/* Equation 1 (second form) for membership C (ids < n); *q_host receives Q. */
+gsp_status gsp_modularity(const uint64_t *offsets, const uint32_t *targets, const void *weights,
+                          int wt, uint32_t n, uint64_t nnz, const uint32_t *C, double *q_host,
+                          void *stream);
+
+/*
+ * One frozen-state sweep of local moving (Algorithm 4 with every vertex
+ * reading C, Sigma and the community sizes of the sweep's start).  Vertices
+ * with active[i] != 0 (active may be NULL = all) pick the best neighbouring
+ * community by Equation 2 (ties to the lowest id; a move needs a strictly
+ * positive gain; with singleton_rule a singleton moves to a singleton only
+ * toward a lower id) and choice[i] receives it (C[i] when not moving).
+ * precision is a gsp_precision.  *dq_host receives the summed gain of the
+ * moves and *moved_host their count (host pointers, may be NULL).
+ */
+gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, const void *weights,
+                          int wt, uint32_t n, uint64_t nnz, const uint32_t *C, const double *K,
+                          const double *Sigma, double m, const uint8_t *active, int precision,
+                          int singleton_rule, uint32_t *choice, double *dq_host,
+                          uint32_t *moved_host, void *stream);
+
+/*
+ * louvainMove (Algorithm 4) from membership C (in/out) and Sigma (in/out,
+ * must equal the per-community sums of K).  move is a gsp_move_mode.  Returns
+ * l_i, the iterations executed, in *iterations_host.
+ */
+gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, const void *weights,
+                          int wt, uint32_t n, uint64_t nnz, uint32_t *C, const double *K,
+                          double *Sigma, double m, double tolerance, int max_iterations, int move,
+                          int precision, int singleton_rule, int *iterations_host, void *stream);
+
+/*
+ * Split (Algorithms 2 and 3): labels[i] = the smallest vertex id of the
+ * connected component of i in the subgraph of edges (i,j) with C[i] = C[j].
+ * Every mode returns the same labels.  *k_host (may be NULL) = number of
+ * components.  mode is a gsp_split_mode other than NONE.
+ */
+gsp_status gsp_split(const uint64_t *offsets, const uint32_t *targets, uint32_t n, uint64_t nnz,
+                     const uint32_t *C, int mode, uint32_t *labels, uint32_t *k_host, void *stream);
+
+/* Renumber communities (Algorithm 1): distinct ids of C (all < n) ranked by
+ * increasing value become 0..k-1, written to C_dense; *k_host = k. */
+gsp_status gsp_renumber(uint32_t n, const uint32_t *C, uint32_t *C_dense, uint32_t *k_host,
+                        void *stream);
+
+/* Dendrogram lookup (Algorithm 1): C_top[v] = C_pass[C_top[v]] for v < n_top. */
+gsp_status gsp_lookup(uint32_t n_top, uint32_t *C_top, const uint32_t *C_pass, void *stream);
+
+/*
+ * louvainAggregate (Algorithm 5): super-vertex graph of membership C (dense,
+ * 0..k-1).  Row c of the output holds, for every community d adjacent to c,
+ * the summed weight of all edges (i,j) with C[i] = c, C[j] = d, self-loops
+ * included, in increasing d, with no gaps.  out_offsets has k+1 entries;
+ * out_targets/out_weights (float64) must hold nnz entries.  *out_nnz_host
+ * receives the super-edge count.
+ */
+gsp_status gsp_aggregate(const uint64_t *offsets, const uint32_t *targets, const void *weights,
+                         int wt, uint32_t n, uint64_t nnz, const uint32_t *C, uint32_t k,
+                         uint64_t *out_offsets, uint32_t *out_targets, double *out_weights,
+                         uint64_t *out_nnz_host, void *stream);
+
+/* disconnectedCommunities (Algorithm 6): *count_host = number of communities
+ * of C (ids < n) whose vertices are not all connected inside the community;
+ * flags (may be NULL, n bytes) receives a 1 at each such community id. */
+gsp_status gsp_count_disconnected(const uint64_t *offsets, const uint32_t *targets, uint32_t n,
+                                  uint64_t nnz, const uint32_t *C, uint8_t *flags,
+                                  uint32_t *count_host, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned vertex pruning: a 6 -> 32 -> 32 -> 1 MLP (ReLU, sigmoid output)
+ * predicting whether a vertex will move.  Parameters are one packed float32
+ * array of gsp_mlp_param_count() entries: W1[32][6], b1[32], W2[32][32],
+ * b2[32], W3[32], b3.  Features are gsp_mlp_features() rows of 6 floats.
+ * ------------------------------------------------------------------------- */
+int gsp_mlp_param_count(void);
+
+/* p[r] = sigmoid(MLP(x[r])) for r < rows; weights are rounded to bfloat16,
+ * products accumulate in float32. */
+gsp_status gsp_mlp_forward(const float *params, const float *x, uint32_t rows, float *p,
+                           void *stream);
+
+/* Mean binary cross-entropy of p against labels y (0/1 bytes) with its
+ * gradient: grad (gsp_mlp_param_count floats, overwritten) = d loss / d params
+ * at the bfloat16-rounded weights; *loss_host = the loss. */
+gsp_status gsp_mlp_backward(const float *params, const float *x, const uint8_t *y, uint32_t rows,
+                            float *grad, double *loss_host, void *stream);
+
+/* params -= lr * grad (plain SGD step, float32 master weights). */
+gsp_status gsp_mlp_sgd(float *params, const float *grad, float lr, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Seeded synthetic graphs, drawn on the device with the same counter-based
+ * SplitMix64 stream as the host generators.  Each writes a symmetric CSR
+ * (self-loops dropped, duplicate pairs merged keeping the smallest weight)
+ * into library-owned device memory valid until the next generator call or
+ * gsp_release_graph(); pointers are returned through the out arguments.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t n;
+    uint64_t nnz;
+    uint64_t *offsets;
+    uint32_t *targets;
+    float *weights;
+} gsp_device_graph;
+
+/* R-MAT: edge_factor << scale samples with quadrant thresholds t1<t2<t3 on the
+ * top 53 bits of each draw (a, a+b, a+b+c scaled by 2^53). */
+gsp_status gsp_gen_rmat(uint32_t scale, uint32_t edge_factor, uint64_t t1, uint64_t t2, uint64_t t3,
+                        uint64_t seed, gsp_device_graph *out, void *stream);
+/* Batch of planted-partition graphs (host parameter arrays of num_graphs
+ * entries: vertices, communities, edge samples, intra threshold on 53 bits,
+ * per-graph seed); one graph alone is the single planted-partition case. */
+gsp_status gsp_gen_planted_batch(uint32_t num_graphs, const uint64_t *n_g, const uint64_t *k_g,
+                                 const uint64_t *edges_g, const uint64_t *p_intra53_g,
+                                 const uint64_t *seed_g, gsp_device_graph *out, void *stream);
+/* R x Cc grid with random removal (threshold on 53 bits), floor(p_long * E)
+ * long-range pairs and weights uniform in [wlo, whi). */
+gsp_status gsp_gen_grid(uint32_t R, uint32_t Cc, uint64_t remove53, uint64_t n_long, float wlo,
+                        float whi, uint64_t seed, gsp_device_graph *out, void *stream);
+void gsp_release_graph(void);
+
+/* Number of kernels this library has launched since it was loaded (all
+ * devices, all threads); a diagnostic for counting launches in a region. */
+uint64_t gsp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSP_H */

@@ -1,0 +1,490 @@
+// aggregate.cu -- aggregation phase of GSP-Louvain (Algorithm 5,
+// louvainAggregate) on sm_103a.
+//
+//  1. community-vertex CSR: countCommunityVertices, exclusive scan, scatter;
+//  2. super-vertex row bounds: communityTotalDegree, exclusive scan (the
+//     paper's "holey" CSR with gaps);
+//  3. per community, an open-addressing table over the edges of all members
+//     (self-loops included) merges the weights per neighbouring community:
+//       total degree <= 128  : one warp, table in shared memory
+//       total degree <= 4096 : one block, table in shared memory
+//       larger               : one block, table in a global-memory pool;
+//  4. the rows are compacted (exclusive scan of the row lengths) and each row
+//     is sorted by target: warp bitonic sort (<= 32 entries), block bitonic
+//     sort in shared memory (<= 2048), and one segmented LSD radix sort for
+//     all longer rows together.
+// Weights are accumulated and stored in float64; sums of float32-exact
+// weights are exact in float64, so every merged weight is order-independent
+// and the output is canonical.
+#include "internal.cuh"
+
+namespace gsp {
+
+enum { ACLS_W = 0, ACLS_B, ACLS_L, NUM_ACLS };
+constexpr uint64_t ACLS_MAX[NUM_ACLS] = {128, 4096, ~0ull};
+enum { RCLS_W = 0, RCLS_B, RCLS_L, NUM_RCLS };
+constexpr uint64_t RCLS_MAX[NUM_RCLS] = {32, 2048, ~0ull};
+
+template <typename WT>
+__global__ void k_agg_count(const uint64_t *__restrict__ off, const uint32_t *__restrict__ Cd, uint32_t n,
+                            uint32_t *cnt, unsigned long long *cdeg) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint32_t c = Cd[v];
+        atomicAdd(cnt + c, 1u);
+        uint64_t deg = off[v + 1] - off[v];
+        if (deg) atomicAdd(cdeg + c, (unsigned long long)deg);
+    }
+}
+
+__global__ void k_agg_scatter(const uint32_t *__restrict__ Cd, uint32_t n, const uint64_t *__restrict__ coff,
+                              uint32_t *cnt, uint32_t *cverts) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint32_t c = Cd[v];
+        uint32_t pos = atomicSub(cnt + c, 1u) - 1u;
+        cverts[coff[c] + pos] = v;
+    }
+}
+
+// Classify ids 0..k-1 by a 64-bit size (entries of size 0 are left out).
+template <int NC>
+__global__ void k_cls_count(const uint64_t *__restrict__ sz, uint32_t k, const uint64_t *maxes, uint32_t *counts) {
+    __shared__ uint32_t sc[NC];
+    if (threadIdx.x < NC) sc[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x) {
+        uint64_t x = sz[c];
+        if (!x) continue;
+        int cls = 0;
+        while (cls < NC - 1 && x > maxes[cls]) cls++;
+        atomicAdd(&sc[cls], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < NC && sc[threadIdx.x]) atomicAdd(counts + threadIdx.x, sc[threadIdx.x]);
+}
+
+template <int NC>
+__global__ void k_cls_fill(const uint64_t *__restrict__ sz, uint32_t k, const uint64_t *maxes, uint32_t *cursor,
+                           uint32_t *list) {
+    int lane = threadIdx.x & 31;
+    for (uint32_t c0 = blockIdx.x * blockDim.x; c0 < k; c0 += gridDim.x * blockDim.x) {
+        uint32_t c = c0 + threadIdx.x;
+        int cls = -1;
+        if (c < k) {
+            uint64_t x = sz[c];
+            if (x) {
+                cls = 0;
+                while (cls < NC - 1 && x > maxes[cls]) cls++;
+            }
+        }
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, cls);
+        int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == leader && cls >= 0) base = atomicAdd(cursor + cls, (uint32_t)__popc(peers));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (cls >= 0) list[base + __popc(peers & ((1u << lane) - 1u))] = c;
+    }
+}
+
+struct IdClasses {
+    uint32_t *list = nullptr;
+    uint32_t start[4] = {0, 0, 0, 0};
+};
+
+template <int NC>
+static void classify_ids(const uint64_t *sz, uint32_t k, const uint64_t (&maxes)[NC], IdClasses &ic, cudaStream_t s) {
+    uint64_t *dmax = arena().get<uint64_t>(NC);
+    uint32_t *counts = arena().get<uint32_t>(2 * NC);
+    GSP_CUDA(cudaMemcpyAsync(dmax, maxes, sizeof(uint64_t) * NC, cudaMemcpyHostToDevice, s));
+    GSP_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * NC, s));
+    unsigned gr = grid_for(k, 256, 152 * 8);
+    k_cls_count<NC><<<gr, 256, 0, s>>>(sz, k, dmax, counts);
+    GSP_CHECK_LAUNCH();
+    uint32_t h[NC];
+    GSP_CUDA(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    ic.start[0] = 0;
+    for (int c = 0; c < NC; c++) ic.start[c + 1] = ic.start[c] + h[c];
+    GSP_CUDA(cudaMemcpyAsync(counts + NC, ic.start, sizeof(uint32_t) * NC, cudaMemcpyHostToDevice, s));
+    ic.list = arena().get<uint32_t>(ic.start[NC] + 1);
+    k_cls_fill<NC><<<gr, 256, 0, s>>>(sz, k, dmax, counts + NC, ic.list);
+    GSP_CHECK_LAUNCH();
+}
+
+struct AggArgs {
+    const uint64_t *off;
+    const uint32_t *tgt;
+    const void *w;
+    const uint32_t *Cd;
+    const uint64_t *coff;
+    const uint32_t *cverts;
+    const unsigned long long *cdeg;
+    const uint64_t *yoff;
+    uint32_t *htgt;
+    double *hw;
+    uint32_t *rowlen;
+    uint32_t k;
+};
+
+// Append the occupied slots of a table to row c of the holey CSR.
+__device__ __forceinline__ void emit_slot(const AggArgs &a, uint32_t c, uint32_t key, double val, bool valid,
+                                          uint32_t *cursor) {
+    uint32_t ballot = __ballot_sync(0xFFFFFFFFu, valid);
+    if (!ballot) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(ballot) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(cursor, (uint32_t)__popc(ballot));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (valid) {
+        uint64_t pos = a.yoff[c] + base + __popc(ballot & ((1u << lane) - 1u));
+        a.htgt[pos] = key;
+        a.hw[pos] = val;
+    }
+}
+
+constexpr int AGG_WCAP = 256;
+
+template <typename WT>
+__global__ void __launch_bounds__(256) k_agg_merge_warp(AggArgs a, const uint32_t *__restrict__ list, uint32_t count) {
+    __shared__ uint32_t s_keys[8][AGG_WCAP];
+    __shared__ double s_vals[8][AGG_WCAP];
+    __shared__ uint32_t s_cur[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t *keys = s_keys[wid];
+    double *vals = s_vals[wid];
+    const WT *w = static_cast<const WT *>(a.w);
+    for (uint32_t t = blockIdx.x * 8 + wid; t < count; t += gridDim.x * 8) {
+        uint32_t c = list[t];
+        uint32_t cd = (uint32_t)a.cdeg[c];
+        int logcap = ceil_log2(2 * cd);
+        if (logcap < 1) logcap = 1;
+        uint32_t cap = 1u << logcap;
+        for (uint32_t s = lane; s < cap; s += 32) { keys[s] = EMPTY; vals[s] = 0.0; }
+        if (lane == 0) s_cur[wid] = 0;
+        __syncwarp();
+        for (uint64_t q = a.coff[c]; q < a.coff[c + 1]; q++) {
+            uint32_t v = a.cverts[q];
+            uint64_t b = a.off[v], e = a.off[v + 1];
+            for (uint64_t p = b + lane; p < e; p += 32)
+                ht_add<double>(keys, vals, logcap, a.Cd[a.tgt[p]], (double)w[p]);
+        }
+        __syncwarp();
+        for (uint32_t s0 = 0; s0 < cap; s0 += 32) {
+            uint32_t s = s0 + lane;
+            uint32_t key = s < cap ? keys[s] : EMPTY;
+            emit_slot(a, c, key, s < cap ? vals[s] : 0.0, key != EMPTY, &s_cur[wid]);
+        }
+        __syncwarp();
+        if (lane == 0) a.rowlen[c] = s_cur[wid];
+        __syncwarp();
+    }
+}
+
+// One block per community; table in dynamic shared memory (CAP > 0) or the
+// global pool (CAP == 0).
+template <int CAP, typename WT>
+__global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32_t *__restrict__ list, uint32_t count,
+                                                         const uint64_t *__restrict__ pool_off, uint32_t *pool_keys,
+                                                         double *pool_vals) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    __shared__ uint32_t s_cur;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const WT *w = static_cast<const WT *>(a.w);
+    for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
+        uint32_t c = list[t];
+        uint64_t cd = a.cdeg[c];
+        uint64_t bound = cd < a.k ? cd : a.k;
+        int logcap = ceil_log2((uint32_t)(2 * bound));
+        if (logcap < 1) logcap = 1;
+        uint32_t cap = 1u << logcap;
+        uint32_t *keys;
+        double *vals;
+        if (CAP > 0) {
+            keys = reinterpret_cast<uint32_t *>(dyn_smem);
+            vals = reinterpret_cast<double *>(dyn_smem + (size_t)CAP * sizeof(uint32_t));
+        } else {
+            keys = pool_keys + pool_off[t];
+            vals = pool_vals + pool_off[t];
+        }
+        __syncthreads();
+        for (uint32_t s = threadIdx.x; s < cap; s += blockDim.x) { keys[s] = EMPTY; vals[s] = 0.0; }
+        if (threadIdx.x == 0) s_cur = 0;
+        __syncthreads();
+        uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
+        for (uint64_t q = q0 + wid; q < q1; q += nw) {
+            uint32_t v = a.cverts[q];
+            uint64_t b = a.off[v], e = a.off[v + 1];
+            for (uint64_t p = b + lane; p < e; p += 32)
+                ht_add<double>(keys, vals, logcap, a.Cd[a.tgt[p]], (double)w[p]);
+        }
+        __syncthreads();
+        for (uint32_t s0 = wid * 32; s0 < cap; s0 += blockDim.x) {
+            uint32_t s = s0 + lane;
+            uint32_t key = s < cap ? keys[s] : EMPTY;
+            emit_slot(a, c, key, s < cap ? vals[s] : 0.0, key != EMPTY, &s_cur);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) a.rowlen[c] = s_cur;
+    }
+}
+
+__global__ void k_agg_pool_caps(const unsigned long long *__restrict__ cdeg, const uint32_t *__restrict__ list,
+                                uint32_t count, uint32_t k, uint64_t *caps) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        uint64_t cd = cdeg[list[t]];
+        uint64_t bound = cd < k ? cd : k;
+        uint64_t cap = 2;
+        while (cap < 2 * bound) cap <<= 1;
+        caps[t] = cap;
+    }
+}
+
+// ------------------------------------------------------------ row sorting
+__global__ void k_rowlen64(const uint32_t *__restrict__ rowlen, uint32_t k, uint64_t *out) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x) out[c] = rowlen[c];
+}
+
+// Rows of <= 32 entries: one warp, bitonic network over the lanes.
+__global__ void k_sort_rows_warp(const uint32_t *__restrict__ list, uint32_t count, const uint64_t *__restrict__ yoff,
+                                 const uint32_t *__restrict__ htgt, const double *__restrict__ hw,
+                                 const uint64_t *__restrict__ noff, uint32_t *otgt, double *ow) {
+    const int lane = threadIdx.x & 31;
+    uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t t = warp; t < count; t += nwarps) {
+        uint32_t c = list[t];
+        uint64_t dst = noff[c];
+        uint32_t L = (uint32_t)(noff[c + 1] - dst);
+        uint64_t src = yoff[c];
+        uint32_t key = lane < L ? htgt[src + lane] : EMPTY;
+        double val = lane < L ? hw[src + lane] : 0.0;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                uint32_t ok = __shfl_xor_sync(0xFFFFFFFFu, key, j);
+                double ov = __shfl_xor_sync(0xFFFFFFFFu, val, j);
+                bool up = (lane & k) == 0;
+                bool lower = (lane & j) == 0;
+                bool take = (lower == up) ? (ok < key) : (ok > key);
+                if (take) { key = ok; val = ov; }
+            }
+        }
+        if (lane < L) { otgt[dst + lane] = key; ow[dst + lane] = val; }
+    }
+}
+
+constexpr int SORT_BCAP = 2048;
+// Rows of <= 2048 entries: one block, bitonic sort in shared memory.
+__global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t *__restrict__ list, uint32_t count,
+                                                         const uint64_t *__restrict__ yoff,
+                                                         const uint32_t *__restrict__ htgt,
+                                                         const double *__restrict__ hw,
+                                                         const uint64_t *__restrict__ noff, uint32_t *otgt,
+                                                         double *ow) {
+    __shared__ uint32_t sk[SORT_BCAP];
+    __shared__ double sv[SORT_BCAP];
+    for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
+        uint32_t c = list[t];
+        uint64_t dst = noff[c];
+        uint32_t L = (uint32_t)(noff[c + 1] - dst);
+        uint64_t src = yoff[c];
+        uint32_t P = 1u << ceil_log2(L);
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < P; x += blockDim.x) {
+            sk[x] = x < L ? htgt[src + x] : EMPTY;
+            sv[x] = x < L ? hw[src + x] : 0.0;
+        }
+        __syncthreads();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t x = threadIdx.x; x < P; x += blockDim.x) {
+                    uint32_t y = x ^ j;
+                    if (y > x) {
+                        bool up = (x & k) == 0;
+                        uint32_t kx = sk[x], ky = sk[y];
+                        if ((kx > ky) == up) {
+                            sk[x] = ky; sk[y] = kx;
+                            double tv = sv[x]; sv[x] = sv[y]; sv[y] = tv;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t x = threadIdx.x; x < L; x += blockDim.x) { otgt[dst + x] = sk[x]; ow[dst + x] = sv[x]; }
+    }
+}
+
+// Long rows: copy unsorted, and stage (row rank << kbits | target, position)
+// pairs for one segmented radix sort.
+__global__ void k_stage_long(const uint32_t *__restrict__ list, uint32_t count, const uint64_t *__restrict__ yoff,
+                             const uint32_t *__restrict__ htgt, const double *__restrict__ hw,
+                             const uint64_t *__restrict__ noff, const uint64_t *__restrict__ gpre, int kbits,
+                             uint64_t *keys, uint32_t *pos, double *wtmp) {
+    for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
+        uint32_t c = list[t];
+        uint64_t dst = noff[c];
+        uint32_t L = (uint32_t)(noff[c + 1] - dst);
+        uint64_t src = yoff[c], g = gpre[t];
+        for (uint32_t x = threadIdx.x; x < L; x += blockDim.x) {
+            keys[g + x] = ((uint64_t)t << kbits) | htgt[src + x];
+            pos[g + x] = (uint32_t)(g + x);
+            wtmp[g + x] = hw[src + x];
+        }
+    }
+}
+
+__global__ void k_unstage_long(const uint32_t *__restrict__ list, const uint64_t *__restrict__ keys,
+                               const uint32_t *__restrict__ pos, uint64_t total, const double *__restrict__ wtmp,
+                               const uint64_t *__restrict__ gpre, const uint64_t *__restrict__ noff, int kbits,
+                               uint32_t *otgt, double *ow) {
+    uint64_t mask = (1ull << kbits) - 1ull;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t key = keys[q];
+        uint32_t t = (uint32_t)(key >> kbits);
+        uint64_t dst = noff[list[t]] + (q - gpre[t]);
+        otgt[dst] = (uint32_t)(key & mask);
+        ow[dst] = wtmp[pos[q]];
+    }
+}
+
+__global__ void k_rowlen_gather(const uint32_t *__restrict__ list, uint32_t count, const uint32_t *__restrict__ rowlen,
+                                uint64_t *out) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x)
+        out[t] = rowlen[list[t]];
+}
+
+static int ceil_log2_host(uint64_t x) {
+    int b = 0;
+    while ((1ull << b) < x) b++;
+    return b;
+}
+
+
+template <typename WT>
+static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off,
+                               uint32_t *out_tgt, double *out_w, cudaStream_t s) {
+    size_t mk = arena().mark();
+    uint32_t n = g.n;
+    uint32_t *cnt = arena().get<uint32_t>(k);
+    unsigned long long *cdeg = arena().get<unsigned long long>(k);
+    uint64_t *coff = arena().get<uint64_t>((size_t)k + 1);
+    uint64_t *yoff = arena().get<uint64_t>((size_t)k + 1);
+    uint32_t *cverts = arena().get<uint32_t>(n);
+    uint32_t *rowlen = arena().get<uint32_t>(k);
+    uint32_t *htgt = arena().get<uint32_t>(g.nnz + 1);
+    double *hw = arena().get<double>(g.nnz + 1);
+    GSP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * k, s));
+    GSP_CUDA(cudaMemsetAsync(cdeg, 0, sizeof(unsigned long long) * k, s));
+    GSP_CUDA(cudaMemsetAsync(rowlen, 0, sizeof(uint32_t) * k, s));
+    unsigned gr = grid_for(n, 256);
+    k_agg_count<WT><<<gr, 256, 0, s>>>(g.off, Cd, n, cnt, cdeg);
+    GSP_CHECK_LAUNCH();
+    exclusive_scan_u32_to_u64(cnt, coff, k, s);
+    exclusive_scan_u64(reinterpret_cast<const uint64_t *>(cdeg), yoff, k, s);
+    k_agg_scatter<<<gr, 256, 0, s>>>(Cd, n, coff, cnt, cverts);
+    GSP_CHECK_LAUNCH();
+
+    IdClasses ic;
+    classify_ids<NUM_ACLS>(reinterpret_cast<const uint64_t *>(cdeg), k, ACLS_MAX, ic, s);
+    AggArgs a{g.off, g.tgt, g.w, Cd, coff, cverts, cdeg, yoff, htgt, hw, rowlen, k};
+    auto cnt_of = [&](int c) { return ic.start[c + 1] - ic.start[c]; };
+    if (cnt_of(ACLS_W)) {
+        k_agg_merge_warp<WT><<<grid_for((uint64_t)cnt_of(ACLS_W) * 32, 256, 152 * 8), 256, 0, s>>>(
+            a, ic.list + ic.start[ACLS_W], cnt_of(ACLS_W));
+        GSP_CHECK_LAUNCH();
+    }
+    if (cnt_of(ACLS_B)) {
+        constexpr int CAP = 8192;
+        constexpr size_t smem = (size_t)CAP * (sizeof(uint32_t) + sizeof(double));
+        static bool attr = false;
+        if (!attr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_block<CAP, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            attr = true;
+        }
+        k_agg_merge_block<CAP, WT><<<grid_for(cnt_of(ACLS_B), 1, 152 * 2), 256, smem, s>>>(
+            a, ic.list + ic.start[ACLS_B], cnt_of(ACLS_B), nullptr, nullptr, nullptr);
+        GSP_CHECK_LAUNCH();
+    }
+    uint32_t nl = cnt_of(ACLS_L);
+    if (nl) {
+        uint64_t *caps = arena().get<uint64_t>(nl);
+        uint64_t *poff = arena().get<uint64_t>((size_t)nl + 1);
+        k_agg_pool_caps<<<grid_for(nl, 256), 256, 0, s>>>(cdeg, ic.list + ic.start[ACLS_L], nl, k, caps);
+        GSP_CHECK_LAUNCH();
+        exclusive_scan_u64(caps, poff, nl, s);
+        uint64_t slots;
+        GSP_CUDA(cudaMemcpyAsync(&slots, poff + nl, sizeof(slots), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        uint32_t *pk = arena().get<uint32_t>(slots);
+        double *pv = arena().get<double>(slots);
+        k_agg_merge_block<0, WT><<<grid_for(nl, 1, 152 * 4), 256, 0, s>>>(a, ic.list + ic.start[ACLS_L], nl, poff,
+                                                                           pk, pv);
+        GSP_CHECK_LAUNCH();
+    }
+
+    // compact + sort rows
+    exclusive_scan_u32_to_u64(rowlen, out_off, k, s);
+    uint64_t nnz2;
+    GSP_CUDA(cudaMemcpyAsync(&nnz2, out_off + k, sizeof(nnz2), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    uint64_t *rl64 = arena().get<uint64_t>(k);
+    k_rowlen64<<<grid_for(k, 256), 256, 0, s>>>(rowlen, k, rl64);
+    GSP_CHECK_LAUNCH();
+    IdClasses rc;
+    classify_ids<NUM_RCLS>(rl64, k, RCLS_MAX, rc, s);
+    auto rcnt = [&](int c) { return rc.start[c + 1] - rc.start[c]; };
+    if (rcnt(RCLS_W)) {
+        k_sort_rows_warp<<<grid_for((uint64_t)rcnt(RCLS_W) * 32, 256, 152 * 16), 256, 0, s>>>(
+            rc.list + rc.start[RCLS_W], rcnt(RCLS_W), yoff, htgt, hw, out_off, out_tgt, out_w);
+        GSP_CHECK_LAUNCH();
+    }
+    if (rcnt(RCLS_B)) {
+        k_sort_rows_block<<<grid_for(rcnt(RCLS_B), 1, 152 * 4), 256, 0, s>>>(
+            rc.list + rc.start[RCLS_B], rcnt(RCLS_B), yoff, htgt, hw, out_off, out_tgt, out_w);
+        GSP_CHECK_LAUNCH();
+    }
+    uint32_t nlong = rcnt(RCLS_L);
+    if (nlong) {
+        const uint32_t *llist = rc.list + rc.start[RCLS_L];
+        uint64_t *lens = arena().get<uint64_t>(nlong);
+        uint64_t *gpre = arena().get<uint64_t>((size_t)nlong + 1);
+        // lengths of the long rows, in list order
+        k_rowlen_gather<<<grid_for(nlong, 256), 256, 0, s>>>(llist, nlong, rowlen, lens);
+        GSP_CHECK_LAUNCH();
+        exclusive_scan_u64(lens, gpre, nlong, s);
+        uint64_t total;
+        GSP_CUDA(cudaMemcpyAsync(&total, gpre + nlong, sizeof(total), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        GSP_REQUIRE(total < (1ull << 32), "aggregation: long rows exceed 2^32 entries");
+        int kbits = ceil_log2_host(k);
+        if (kbits < 1) kbits = 1;
+        int bits = kbits + ceil_log2_host(nlong) + 1;
+        uint64_t *keys = arena().get<uint64_t>(total);
+        uint64_t *keys2 = arena().get<uint64_t>(total);
+        uint32_t *pos = arena().get<uint32_t>(total);
+        uint32_t *pos2 = arena().get<uint32_t>(total);
+        double *wtmp = arena().get<double>(total);
+        k_stage_long<<<grid_for(nlong, 1, 152 * 4), 256, 0, s>>>(llist, nlong, yoff, htgt, hw, out_off, gpre, kbits,
+                                                                  keys, pos, wtmp);
+        GSP_CHECK_LAUNCH();
+        radix_sort_u64_u32(keys, pos, keys2, pos2, total, bits, s);
+        k_unstage_long<<<grid_for(total, 256), 256, 0, s>>>(llist, keys, pos, total, wtmp, gpre, out_off, kbits,
+                                                             out_tgt, out_w);
+        GSP_CHECK_LAUNCH();
+    }
+    arena().release(mk);
+    return nnz2;
+}
+
+uint64_t aggregate(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off, uint32_t *out_tgt,
+                   double *out_w, cudaStream_t s) {
+    if (g.wt == GSP_W_F64) return aggregate_impl<double>(g, Cd, k, out_off, out_tgt, out_w, s);
+    return aggregate_impl<float>(g, Cd, k, out_off, out_tgt, out_w, s);
+}
+
+}  // namespace gsp

@@ -1,0 +1,700 @@
+// driver.cu -- GSP-Louvain pass loop (Algorithm 1), the device workspace,
+// error reporting and the C ABI of include/gsp.h for the phase entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace gsp {
+
+// ---------------------------------------------------------------- errors
+static thread_local char g_err[512] = "";
+static unsigned long long g_launches = 0;
+void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+// ------------------------------------------------------------- workspace
+// Chunked bump allocator: chunks are cudaMalloc'd on demand and kept for the
+// next call, so a repeated call of the same size allocates nothing.
+struct ChunkArena {
+    struct Chunk {
+        char *base;
+        size_t cap;
+    };
+    std::vector<Chunk> chunks;
+    size_t cur = 0, top = 0;
+    void *alloc(size_t bytes) {
+        bytes = align_up(bytes ? bytes : 1, 256);
+        while (cur < chunks.size()) {
+            if (top + bytes <= chunks[cur].cap) {
+                void *p = chunks[cur].base + top;
+                top += bytes;
+                return p;
+            }
+            cur++;
+            top = 0;
+        }
+        size_t last = chunks.empty() ? 0 : chunks.back().cap;
+        size_t sz = std::max(bytes, std::max<size_t>(last * 2, (size_t)64 << 20));
+        char *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, sz);
+        if (e != cudaSuccess && sz > bytes) {
+            cudaGetLastError();
+            sz = bytes;
+            e = cudaMalloc(&p, sz);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device workspace: cudaMalloc(%zu) failed: %s", sz, cudaGetErrorString(e));
+            throw Error{GSP_ERR_NOMEM};
+        }
+        chunks.push_back({p, sz});
+        cur = chunks.size() - 1;
+        top = bytes;
+        return p;
+    }
+    size_t mark() const { return (cur << 40) | top; }
+    void release(size_t m) {
+        cur = m >> 40;
+        top = m & ((1ull << 40) - 1);
+    }
+    void reset() { cur = top = 0; }
+    void free_all() {
+        for (auto &k : chunks) cudaFree(k.base);
+        chunks.clear();
+        reset();
+    }
+};
+
+static ChunkArena g_work[16], g_io[16];
+static int cur_dev() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d & 15;
+}
+
+struct WorkArena : Arena {};
+static Arena g_work_facade, g_io_facade;
+Arena &arena() { return g_work_facade; }
+Arena &io_arena() { return g_io_facade; }
+static ChunkArena &backing(const Arena *a) { return a == &g_io_facade ? g_io[cur_dev()] : g_work[cur_dev()]; }
+void *Arena::alloc(size_t bytes) { return backing(this).alloc(bytes); }
+size_t Arena::mark() { return backing(this).mark(); }
+void Arena::release(size_t m) { backing(this).release(m); }
+void Arena::reset() { backing(this).reset(); }
+void Arena::free_all() { backing(this).free_all(); }
+
+// ---------------------------------------------------------- small kernels
+__global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+__global__ void k_community_sizes(const uint32_t *__restrict__ C, uint32_t n, uint32_t *size) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(size + C[i], 1u);
+}
+
+// Input check: offsets non-decreasing from 0 to nnz, targets < n, weights
+// finite and > 0 (float32 input).  flags[0] counts violations.
+__global__ void k_check_graph(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                              const float *__restrict__ w, uint32_t n, uint64_t nnz, unsigned long long *bad) {
+    unsigned long long b = 0;
+    uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = tid; i < n; i += stride)
+        if (off[i + 1] < off[i]) b++;
+    if (tid == 0 && (off[0] != 0 || off[n] != nnz)) b++;
+    for (uint64_t e = tid; e < nnz; e += stride) {
+        if (tgt[e] >= n) b++;
+        if (w) {
+            float x = w[e];
+            if (!(x > 0.0f) || isinf(x)) b++;
+        }
+    }
+    if (b) atomicAdd(bad, b);
+}
+
+static void check_graph(const uint64_t *off, const uint32_t *tgt, const float *w, uint32_t n, uint64_t nnz,
+                        cudaStream_t s) {
+    size_t mk = arena().mark();
+    unsigned long long *bad = arena().get<unsigned long long>(1);
+    GSP_CUDA(cudaMemsetAsync(bad, 0, sizeof(*bad), s));
+    k_check_graph<<<grid_for(std::max<uint64_t>(n, nnz), 256), 256, 0, s>>>(off, tgt, w, n, nnz, bad);
+    GSP_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    GSP_CUDA(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    GSP_REQUIRE(h == 0, "invalid graph: %llu violations (offsets must rise from 0 to nnz, targets < n, "
+                        "weights finite and > 0)", h);
+}
+
+__global__ void k_check_ids(const uint32_t *__restrict__ C, uint32_t n, uint32_t bound, unsigned long long *bad) {
+    unsigned long long b = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (C[i] >= bound) b++;
+    if (b) atomicAdd(bad, b);
+}
+
+// Caller-supplied ids must be < bound (community ids index arrays of that size).
+static void check_ids(const uint32_t *C, uint32_t n, uint32_t bound, const char *what, cudaStream_t s) {
+    size_t mk = arena().mark();
+    unsigned long long *bad = arena().get<unsigned long long>(1);
+    GSP_CUDA(cudaMemsetAsync(bad, 0, sizeof(*bad), s));
+    k_check_ids<<<grid_for(n, 256), 256, 0, s>>>(C, n, bound, bad);
+    GSP_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    GSP_CUDA(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    GSP_REQUIRE(h == 0, "%s: %llu ids out of range (must be < %u)", what, h, bound);
+}
+
+// ------------------------------------------------------------ move loop
+struct EventPool {
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    cudaEvent_t get() {
+        if (used == ev.size()) {
+            cudaEvent_t e;
+            GSP_CUDA(cudaEventCreate(&e));
+            ev.push_back(e);
+        }
+        return ev[used++];
+    }
+    void reset() { used = 0; }
+};
+static EventPool g_events;
+
+struct MoveLoopResult {
+    int iterations;
+    uint64_t vertices, edges, candidates, skipped;
+    double bytes;     // algorithmic bytes of the sweep kernels
+    float ms_kernels; // their device time
+};
+
+// Algorithmic bytes of one sweep (per processed vertex: list entry 4, flag 1,
+// C_i 4, two offsets 16, K_i 8, Sigma_d 8; per scanned edge: target 4, weight
+// 4 or 8, C_j 4; per candidate community: Sigma_c 8; per move: C_i 4, two
+// Sigma and two size updates 24, plus one flag byte per neighbour).
+static double sweep_bytes(const MoveCounters &h, int wt) {
+    double wb = wt == GSP_W_F64 ? 8.0 : 4.0;
+    return 41.0 * h.vertices + (8.0 + wb) * h.edges + 8.0 * h.candidates + 28.0 * h.moved + 1.0 * h.marked;
+}
+
+// louvainMove (Algorithm 4): iterate sweeps until the summed gain of a sweep
+// is <= tau or max_iterations is reached.  mb.C/Sigma/size/act hold the state.
+static MoveLoopResult move_loop(const DevGraph &g, const Classes &cl, MoveBuffers &mb, double tau, int max_it,
+                                bool sync, bool fp64, bool rule, bool learned, int full_every, cudaStream_t s) {
+    MoveLoopResult r{0, 0, 0, 0, 0, 0.0, 0.0f};
+    MoveCounters h;
+    cudaEvent_t e0 = g_events.get(), e1 = g_events.get();
+    for (int it = 0; it < max_it; it++) {
+        GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
+        if (sync) {
+            GSP_CUDA(cudaMemcpyAsync(mb.C2, mb.C, sizeof(uint32_t) * g.n, cudaMemcpyDeviceToDevice, s));
+            GSP_CUDA(cudaMemcpyAsync(mb.Sigma2, mb.Sigma, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, s));
+            GSP_CUDA(cudaMemcpyAsync(mb.size2, mb.size, sizeof(uint32_t) * g.n, cudaMemcpyDeviceToDevice, s));
+            GSP_CUDA(cudaMemsetAsync(mb.act2, 0, g.n, s));
+        }
+        bool use_pred = learned && full_every > 0 && (it % full_every) != full_every - 1;
+        GSP_CUDA(cudaEventRecord(e0, s));
+        move_sweep(g, cl, mb, sync, fp64, rule, use_pred, s);
+        GSP_CUDA(cudaEventRecord(e1, s));
+        if (sync) {
+            std::swap(mb.C, mb.C2);
+            std::swap(mb.Sigma, mb.Sigma2);
+            std::swap(mb.size, mb.size2);
+            std::swap(mb.act, mb.act2);
+        }
+        GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        float ms = 0;
+        GSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        r.ms_kernels += ms;
+        r.bytes += sweep_bytes(h, g.wt);
+        r.iterations = it + 1;
+        r.vertices += h.vertices;
+        r.edges += h.edges;
+        r.candidates += h.candidates;
+        r.skipped += h.skipped;
+        if (h.dq <= tau) break;
+    }
+    return r;
+}
+
+// Allocate the move state for a graph of n vertices (C, Sigma, size, act and,
+// for frozen-state sweeps, their next copies).
+static void alloc_move_state(MoveBuffers &mb, uint32_t n, bool sync) {
+    mb.C = arena().get<uint32_t>(n);
+    mb.Sigma = arena().get<double>(n);
+    mb.size = arena().get<uint32_t>(n);
+    mb.act = arena().get<uint8_t>(n);
+    if (sync) {
+        mb.C2 = arena().get<uint32_t>(n);
+        mb.Sigma2 = arena().get<double>(n);
+        mb.size2 = arena().get<uint32_t>(n);
+        mb.act2 = arena().get<uint8_t>(n);
+    }
+    mb.m_dev = arena().get<double>(1);
+    mb.ctr = arena().get<MoveCounters>(1);
+}
+
+static void alloc_pool(MoveBuffers &mb, const Classes &cl) {
+    mb.pool = nullptr;
+    if (cl.pool_slots) mb.pool = arena().alloc((align_up(cl.pool_slots, 64)) * (sizeof(uint32_t) + sizeof(double)));
+}
+
+// --------------------------------------------------------- GSP-Louvain run
+struct Timer {
+    cudaEvent_t a;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st) {
+        a = g_events.get();
+        GSP_CUDA(cudaEventRecord(a, s));
+    }
+    float lap() {  // ms since the previous lap
+        cudaEvent_t b = g_events.get();
+        GSP_CUDA(cudaEventRecord(b, s));
+        GSP_CUDA(cudaEventSynchronize(b));
+        float ms = 0;
+        GSP_CUDA(cudaEventElapsedTime(&ms, a, b));
+        a = b;
+        return ms;
+    }
+};
+
+void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, double *modularity_out,
+                 gsp_stats *st, cudaStream_t s) {
+    g_events.reset();
+    const uint32_t n0 = g0.n;
+    const bool sync = o.move == GSP_MOVE_SYNC;
+    const bool fp64 = o.precision == GSP_PREC_FP64;
+    const bool learned = o.prune == GSP_PRUNE_LEARNED && o.mlp_params;
+    gsp_stats local;
+    memset(&local, 0, sizeof(local));
+    Timer total(s), t(s);
+
+    MoveBuffers mb;
+    alloc_move_state(mb, n0, sync);
+    double *K = arena().get<double>(n0);
+    uint32_t *labels = arena().get<uint32_t>(n0);
+    uint32_t *Cd = arena().get<uint32_t>(n0);
+    mb.K = K;
+    mb.mlp = static_cast<const float *>(o.mlp_params);
+    if (learned) {
+        mb.feat_dq = arena().get<float>(n0);
+        mb.moved_last = arena().get<uint8_t>(n0);
+    }
+    // ping-pong buffers for the aggregated graphs (float64 weights)
+    uint64_t *goff[2];
+    uint32_t *gtgt[2];
+    double *gw[2];
+    for (int b = 0; b < 2; b++) {
+        goff[b] = arena().get<uint64_t>((size_t)n0 + 1);
+        gtgt[b] = arena().get<uint32_t>(g0.nnz + 1);
+        gw[b] = arena().get<double>(g0.nnz + 1);
+    }
+    iota_u32(membership, n0, s);
+    DevGraph cur = g0;
+    double tau = o.tolerance;
+    const bool split_pass = o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_PASS;
+    int passes = 0;
+    uint32_t *Cp = mb.C;  // membership of the current graph's vertices
+    int pb = 0;
+    for (int lp = 0; lp < o.max_passes; lp++) {
+        const uint32_t nv = cur.n;
+        size_t pass_mark = arena().mark();
+        t.lap();
+        // K' = Sigma' = vertexWeights(G'), C' = [0..|V'|), all unprocessed
+        double m = vertex_weights(cur, K, mb.m_dev, s);
+        GSP_CUDA(cudaMemcpyAsync(mb.Sigma, K, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+        iota_u32(mb.C, nv, s);
+        k_fill_u32<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
+        GSP_CHECK_LAUNCH();
+        GSP_CUDA(cudaMemsetAsync(mb.act, 1, nv, s));
+        Classes cl;
+        classify_vertices(cur, cl, s);
+        alloc_pool(mb, cl);
+        float ms_other = t.lap();
+        MoveLoopResult mr{0, 0, 0, 0, 0, 0.0, 0.0f};
+        if (m > 0.0)
+            mr = move_loop(cur, cl, mb, tau, o.max_iterations, sync, fp64, o.singleton_rule != 0, learned,
+                           o.full_sweep_every, s);
+        int li = mr.iterations;
+        Cp = mb.C;
+        float ms_move = t.lap();
+        if (split_pass) {
+            split_labels(cur, cl, Cp, o.split, labels, s);
+            Cp = labels;
+        }
+        // |Gamma| = communities after the split; |Gamma_old| = |V'|
+        uint32_t k = renumber(nv, Cp, Cd, s);
+        float ms_split = t.lap();
+        passes = lp + 1;
+        if (lp < GSP_MAX_PASS_STATS) {
+            local.iterations[lp] = li;
+            local.vertices[lp] = nv;
+            local.communities[lp] = k;
+            local.edges[lp] = cur.nnz;
+            local.ms_move[lp] = ms_move;
+            local.ms_split[lp] = ms_split;
+            local.ms_other[lp] = ms_other;
+            local.vertices_processed[lp] = mr.vertices;
+            local.edges_scanned[lp] = mr.edges;
+            local.vertices_skipped[lp] = mr.skipped;
+            local.move_bytes[lp] = mr.bytes;
+            local.ms_move_kernels[lp] = mr.ms_kernels;
+        }
+        if (li <= 1) break;                                          // globally converged
+        if ((double)k / (double)nv > o.aggregation_tolerance) break;  // low shrink
+        // renumber, dendrogram lookup, aggregate, threshold scaling
+        lookup(n0, membership, Cd, s);
+        DevGraph nxt;
+        nxt.n = k;
+        nxt.off = goff[pb];
+        nxt.tgt = gtgt[pb];
+        nxt.w = gw[pb];
+        nxt.wt = GSP_W_F64;
+        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s);
+        pb ^= 1;
+        cur = nxt;
+        tau = tau / o.tolerance_drop;
+        float ms_agg = t.lap();
+        if (lp < GSP_MAX_PASS_STATS) local.ms_aggregate[lp] = ms_agg;
+        arena().release(pass_mark);
+        iota_u32(mb.C, cur.n, s);  // C' = identity on the new graph
+        Cp = mb.C;
+    }
+    lookup(n0, membership, Cp, s);
+    if (o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_LAST) {
+        Classes cl;
+        classify_vertices(g0, cl, s);
+        split_labels(g0, cl, membership, o.split, labels, s);
+        GSP_CUDA(cudaMemcpyAsync(membership, labels, sizeof(uint32_t) * n0, cudaMemcpyDeviceToDevice, s));
+    }
+    uint32_t kf = canonical_numbering(n0, membership, s);
+    double q = modularity(g0, membership, s);
+    local.passes = passes;
+    local.final_communities = kf;
+    local.modularity = q;
+    local.ms_total = total.lap();
+    if (modularity_out) *modularity_out = q;
+    if (st) *st = local;
+}
+
+}  // namespace gsp
+
+// =============================================================== C ABI
+using namespace gsp;
+
+#define GSP_API_BEGIN try {
+#define GSP_API_END                                              \
+    return GSP_OK;                                               \
+    }                                                            \
+    catch (const gsp::Error &e) {                                \
+        return e.status;                                         \
+    }                                                            \
+    catch (...) {                                                \
+        set_error("unexpected C++ exception");                   \
+        return GSP_ERR_CUDA;                                     \
+    }
+
+static cudaStream_t S(void *p) { return static_cast<cudaStream_t>(p); }
+
+static DevGraph make_graph(const uint64_t *off, const uint32_t *tgt, const void *w, int wt, uint32_t n,
+                           uint64_t nnz) {
+    GSP_REQUIRE(n > 0, "n must be > 0");
+    GSP_REQUIRE(off != nullptr, "offsets must not be NULL");
+    GSP_REQUIRE(nnz == 0 || (tgt != nullptr && w != nullptr), "targets/weights must not be NULL");
+    GSP_REQUIRE(wt == GSP_W_F32 || wt == GSP_W_F64, "unknown weight type %d", wt);
+    DevGraph g;
+    g.n = n;
+    g.nnz = nnz;
+    g.off = off;
+    g.tgt = tgt;
+    g.w = w;
+    g.wt = wt;
+    return g;
+}
+
+static void check_opts(const gsp_opts &o) {
+    GSP_REQUIRE(o.max_passes >= 1 && o.max_passes <= 1000, "max_passes out of range");
+    GSP_REQUIRE(o.max_iterations >= 1 && o.max_iterations <= 100000, "max_iterations out of range");
+    GSP_REQUIRE(o.tolerance >= 0.0 && o.tolerance_drop > 0.0, "tolerance out of range");
+    GSP_REQUIRE(o.aggregation_tolerance > 0.0, "aggregation_tolerance must be > 0");
+    GSP_REQUIRE(o.split >= GSP_SPLIT_NONE && o.split <= GSP_SPLIT_BFS, "unknown split mode");
+    GSP_REQUIRE(o.split_when == GSP_SPLIT_PASS || o.split_when == GSP_SPLIT_LAST, "unknown split_when");
+    GSP_REQUIRE(o.move == GSP_MOVE_ASYNC || o.move == GSP_MOVE_SYNC, "unknown move mode");
+    GSP_REQUIRE(o.precision == GSP_PREC_MIXED || o.precision == GSP_PREC_FP64, "unknown precision");
+    GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS || o.prune == GSP_PRUNE_LEARNED, "unknown prune mode");
+    GSP_REQUIRE(o.prune != GSP_PRUNE_LEARNED || o.mlp_params != nullptr, "learned pruning needs mlp_params");
+}
+
+extern "C" {
+
+void gsp_default_opts(gsp_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->max_passes = 10;
+    o->max_iterations = 20;
+    o->tolerance = 1e-2;
+    o->tolerance_drop = 10.0;
+    o->aggregation_tolerance = 0.8;
+    o->split = GSP_SPLIT_BFS;
+    o->split_when = GSP_SPLIT_PASS;
+    o->move = GSP_MOVE_ASYNC;
+    o->precision = GSP_PREC_MIXED;
+    o->singleton_rule = 1;
+    o->prune = GSP_PRUNE_FLAGS;
+    o->mlp_params = nullptr;
+    o->full_sweep_every = 4;
+    o->stream = nullptr;
+}
+
+const char *gsp_status_string(gsp_status s) {
+    switch (s) {
+    case GSP_OK: return "ok";
+    case GSP_ERR_INVALID: return "invalid argument";
+    case GSP_ERR_NOMEM: return "out of device memory";
+    case GSP_ERR_CUDA: return "CUDA error";
+    case GSP_ERR_TIMEOUT: return "device wait timed out";
+    case GSP_ERR_CAPACITY: return "capacity exceeded";
+    }
+    return "unknown status";
+}
+
+const char *gsp_last_error(void) { return g_err; }
+
+uint64_t gsp_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+gsp_status gsp_louvain(const uint64_t *offsets, const uint32_t *targets, const float *weights, uint32_t n,
+                       uint64_t nnz, const gsp_opts *opts, uint32_t *membership, double *modularity,
+                       gsp_stats *stats) {
+    GSP_API_BEGIN
+    gsp_opts o;
+    if (opts) o = *opts;
+    else gsp_default_opts(&o);
+    check_opts(o);
+    GSP_REQUIRE(membership != nullptr, "membership must not be NULL");
+    DevGraph g = make_graph(offsets, targets, weights, GSP_W_F32, n, nnz);
+    cudaStream_t s = S(o.stream);
+    arena().reset();
+    check_graph(offsets, targets, weights, n, nnz, s);
+    louvain_run(g, o, membership, modularity, stats, s);
+    GSP_API_END
+}
+
+gsp_status gsp_louvain_host(const uint64_t *offsets, const uint32_t *targets, const float *weights, uint32_t n,
+                            uint64_t nnz, const gsp_opts *opts, uint32_t *membership, double *modularity,
+                            gsp_stats *stats) {
+    GSP_API_BEGIN
+    gsp_opts o;
+    if (opts) o = *opts;
+    else gsp_default_opts(&o);
+    check_opts(o);
+    GSP_REQUIRE(n > 0 && offsets && membership && (nnz == 0 || (targets && weights)), "invalid host buffers");
+    cudaStream_t s = S(o.stream);
+    io_arena().reset();
+    uint64_t *doff = io_arena().get<uint64_t>((size_t)n + 1);
+    uint32_t *dtgt = io_arena().get<uint32_t>(nnz + 1);
+    float *dw = io_arena().get<float>(nnz + 1);
+    uint32_t *dC = io_arena().get<uint32_t>(n);
+    GSP_CUDA(cudaMemcpyAsync(doff, offsets, sizeof(uint64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
+    if (nnz) {
+        GSP_CUDA(cudaMemcpyAsync(dtgt, targets, sizeof(uint32_t) * nnz, cudaMemcpyHostToDevice, s));
+        GSP_CUDA(cudaMemcpyAsync(dw, weights, sizeof(float) * nnz, cudaMemcpyHostToDevice, s));
+    }
+    DevGraph g = make_graph(doff, dtgt, dw, GSP_W_F32, n, nnz);
+    arena().reset();
+    check_graph(doff, dtgt, dw, n, nnz, s);
+    louvain_run(g, o, dC, modularity, stats, s);
+    GSP_CUDA(cudaMemcpyAsync(membership, dC, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    GSP_API_END
+}
+
+gsp_status gsp_vertex_weights(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt,
+                              uint32_t n, uint64_t nnz, double *K, double *m_host, void *stream) {
+    GSP_API_BEGIN
+    DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
+    GSP_REQUIRE(K != nullptr, "K must not be NULL");
+    arena().reset();
+    double m = vertex_weights(g, K, nullptr, S(stream));
+    if (m_host) *m_host = m;
+    GSP_API_END
+}
+
+gsp_status gsp_modularity(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
+                          uint64_t nnz, const uint32_t *C, double *q_host, void *stream) {
+    GSP_API_BEGIN
+    DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
+    GSP_REQUIRE(C != nullptr && q_host != nullptr, "C and q_host must not be NULL");
+    arena().reset();
+    check_ids(C, n, n, "membership", S(stream));
+    *q_host = modularity(g, C, S(stream));
+    GSP_API_END
+}
+
+gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
+                          uint64_t nnz, const uint32_t *C, const double *K, const double *Sigma, double m,
+                          const uint8_t *active, int precision, int singleton_rule, uint32_t *choice,
+                          double *dq_host, uint32_t *moved_host, void *stream) {
+    GSP_API_BEGIN
+    DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
+    GSP_REQUIRE(C && K && Sigma && choice, "C, K, Sigma and choice must not be NULL");
+    GSP_REQUIRE(m > 0.0, "m must be > 0");
+    GSP_REQUIRE(precision == GSP_PREC_MIXED || precision == GSP_PREC_FP64, "unknown precision");
+    cudaStream_t s = S(stream);
+    arena().reset();
+    check_ids(C, n, n, "membership", s);
+    if (nnz) check_ids(targets, (uint32_t)std::min<uint64_t>(nnz, 0xFFFFFFFFu), n, "targets", s);
+    MoveBuffers mb;
+    mb.C = const_cast<uint32_t *>(C);
+    mb.C2 = choice;
+    mb.K = K;
+    mb.Sigma = const_cast<double *>(Sigma);
+    mb.Sigma2 = arena().get<double>(n);
+    mb.size = arena().get<uint32_t>(n);
+    mb.size2 = arena().get<uint32_t>(n);
+    mb.act = arena().get<uint8_t>(n);
+    mb.act2 = arena().get<uint8_t>(n);
+    mb.m_dev = arena().get<double>(1);
+    mb.ctr = arena().get<MoveCounters>(1);
+    GSP_CUDA(cudaMemcpyAsync(mb.m_dev, &m, sizeof(double), cudaMemcpyHostToDevice, s));
+    GSP_CUDA(cudaMemcpyAsync(choice, C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    GSP_CUDA(cudaMemcpyAsync(mb.Sigma2, Sigma, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    GSP_CUDA(cudaMemsetAsync(mb.size, 0, sizeof(uint32_t) * n, s));
+    k_community_sizes<<<grid_for(n, 256), 256, 0, s>>>(C, n, mb.size);
+    GSP_CHECK_LAUNCH();
+    GSP_CUDA(cudaMemcpyAsync(mb.size2, mb.size, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    if (active) GSP_CUDA(cudaMemcpyAsync(mb.act, active, n, cudaMemcpyDeviceToDevice, s));
+    else GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
+    GSP_CUDA(cudaMemsetAsync(mb.act2, 0, n, s));
+    GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
+    Classes cl;
+    classify_vertices(g, cl, s);
+    alloc_pool(mb, cl);
+    move_sweep(g, cl, mb, true, precision == GSP_PREC_FP64, singleton_rule != 0, false, s);
+    MoveCounters h;
+    GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    if (dq_host) *dq_host = h.dq;
+    if (moved_host) *moved_host = (uint32_t)h.moved;
+    GSP_API_END
+}
+
+gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
+                          uint64_t nnz, uint32_t *C, const double *K, double *Sigma, double m, double tolerance,
+                          int max_iterations, int move, int precision, int singleton_rule, int *iterations_host,
+                          void *stream) {
+    GSP_API_BEGIN
+    DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
+    GSP_REQUIRE(C && K && Sigma, "C, K and Sigma must not be NULL");
+    GSP_REQUIRE(m > 0.0 && max_iterations >= 1, "m must be > 0 and max_iterations >= 1");
+    GSP_REQUIRE(move == GSP_MOVE_ASYNC || move == GSP_MOVE_SYNC, "unknown move mode");
+    GSP_REQUIRE(precision == GSP_PREC_MIXED || precision == GSP_PREC_FP64, "unknown precision");
+    cudaStream_t s = S(stream);
+    arena().reset();
+    g_events.reset();
+    check_ids(C, n, n, "membership", s);
+    bool sync = move == GSP_MOVE_SYNC;
+    MoveBuffers mb;
+    alloc_move_state(mb, n, sync);
+    mb.K = K;
+    GSP_CUDA(cudaMemcpyAsync(mb.m_dev, &m, sizeof(double), cudaMemcpyHostToDevice, s));
+    GSP_CUDA(cudaMemcpyAsync(mb.C, C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    GSP_CUDA(cudaMemcpyAsync(mb.Sigma, Sigma, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    GSP_CUDA(cudaMemsetAsync(mb.size, 0, sizeof(uint32_t) * n, s));
+    k_community_sizes<<<grid_for(n, 256), 256, 0, s>>>(C, n, mb.size);
+    GSP_CHECK_LAUNCH();
+    GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
+    Classes cl;
+    classify_vertices(g, cl, s);
+    alloc_pool(mb, cl);
+    MoveLoopResult r = move_loop(g, cl, mb, tolerance, max_iterations, sync, precision == GSP_PREC_FP64,
+                                 singleton_rule != 0, false, 0, s);
+    GSP_CUDA(cudaMemcpyAsync(C, mb.C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    GSP_CUDA(cudaMemcpyAsync(Sigma, mb.Sigma, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    if (iterations_host) *iterations_host = r.iterations;
+    GSP_API_END
+}
+
+gsp_status gsp_split(const uint64_t *offsets, const uint32_t *targets, uint32_t n, uint64_t nnz, const uint32_t *C,
+                     int mode, uint32_t *labels, uint32_t *k_host, void *stream) {
+    GSP_API_BEGIN
+    GSP_REQUIRE(mode == GSP_SPLIT_LP || mode == GSP_SPLIT_LPP || mode == GSP_SPLIT_BFS, "unknown split mode");
+    GSP_REQUIRE(C && labels && n > 0 && offsets && (nnz == 0 || targets), "invalid arguments");
+    DevGraph g = make_graph(offsets, targets, targets ? (const void *)targets : (const void *)offsets, GSP_W_F32, n,
+                            nnz);
+    cudaStream_t s = S(stream);
+    arena().reset();
+    check_ids(C, n, n, "membership", s);
+    Classes cl;
+    classify_vertices(g, cl, s);
+    split_labels(g, cl, C, mode, labels, s);
+    if (k_host) {
+        uint32_t *tmp = arena().get<uint32_t>(n);
+        *k_host = renumber(n, labels, tmp, s);
+    }
+    GSP_CUDA(cudaStreamSynchronize(s));
+    GSP_API_END
+}
+
+gsp_status gsp_renumber(uint32_t n, const uint32_t *C, uint32_t *C_dense, uint32_t *k_host, void *stream) {
+    GSP_API_BEGIN
+    GSP_REQUIRE(n > 0 && C && C_dense, "invalid arguments");
+    arena().reset();
+    check_ids(C, n, n, "membership", S(stream));
+    uint32_t k = renumber(n, C, C_dense, S(stream));
+    if (k_host) *k_host = k;
+    GSP_API_END
+}
+
+gsp_status gsp_lookup(uint32_t n_top, uint32_t *C_top, const uint32_t *C_pass, void *stream) {
+    GSP_API_BEGIN
+    GSP_REQUIRE(C_top && C_pass, "invalid arguments");
+    lookup(n_top, C_top, C_pass, S(stream));
+    GSP_CUDA(cudaStreamSynchronize(S(stream)));
+    GSP_API_END
+}
+
+gsp_status gsp_aggregate(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
+                         uint64_t nnz, const uint32_t *C, uint32_t k, uint64_t *out_offsets, uint32_t *out_targets,
+                         double *out_weights, uint64_t *out_nnz_host, void *stream) {
+    GSP_API_BEGIN
+    DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
+    GSP_REQUIRE(C && out_offsets && k > 0 && k <= n, "invalid arguments");
+    GSP_REQUIRE(nnz == 0 || (out_targets && out_weights), "output arrays must not be NULL");
+    arena().reset();
+    check_ids(C, n, k, "membership", S(stream));
+    uint64_t e = aggregate(g, C, k, out_offsets, out_targets, out_weights, S(stream));
+    GSP_CUDA(cudaStreamSynchronize(S(stream)));
+    if (out_nnz_host) *out_nnz_host = e;
+    GSP_API_END
+}
+
+gsp_status gsp_count_disconnected(const uint64_t *offsets, const uint32_t *targets, uint32_t n, uint64_t nnz,
+                                  const uint32_t *C, uint8_t *flags, uint32_t *count_host, void *stream) {
+    GSP_API_BEGIN
+    GSP_REQUIRE(C && n > 0 && offsets && (nnz == 0 || targets), "invalid arguments");
+    DevGraph g = make_graph(offsets, targets, targets ? (const void *)targets : (const void *)offsets, GSP_W_F32, n,
+                            nnz);
+    arena().reset();
+    check_ids(C, n, n, "membership", S(stream));
+    uint32_t c = count_disconnected(g, C, flags, S(stream));
+    if (count_host) *count_host = c;
+    GSP_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// misc.cu -- vertex weights (Section 3), modularity (Equation 1), community
+// renumbering and dendrogram lookup (Algorithm 1), the final numbering, and
+// the disconnected-community count (Algorithm 6).
+//
+// Row sums use one thread per row up to 64 entries and one block per longer
+// row.  All float64 sums here add float32-representable weights whose partial
+// sums stay exactly representable, so they do not depend on the order.
+#include "internal.cuh"
+
+namespace gsp {
+
+constexpr uint32_t SHORT_ROW = 64;
+
+__global__ void k_iota(uint32_t *p, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+void iota_u32(uint32_t *p, uint32_t n, cudaStream_t s) {
+    if (!n) return;
+    k_iota<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+    GSP_CHECK_LAUNCH();
+}
+
+// Per row i: K_i, and the intra-community part sum_{j: C_j = C_i} w_ij when C
+// is given; Sigma_c += K_i when Sig is given.  Long rows are deferred to a
+// list for the block kernel.
+template <typename WT>
+__global__ void k_row_sums(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                           const WT *__restrict__ w, uint32_t n, const uint32_t *__restrict__ C, double *K,
+                           double *Sig, double *acc /* [0]=2m, [1]=intra */, uint32_t *longlist,
+                           uint32_t *nlong) {
+    __shared__ double red[32];
+    double two_m = 0, intra = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint64_t b = off[i], e = off[i + 1];
+        if (e - b > SHORT_ROW) {
+            longlist[atomicAdd(nlong, 1u)] = i;
+            continue;
+        }
+        double k = 0, in = 0;
+        uint32_t ci = C ? C[i] : 0;
+        for (uint64_t p = b; p < e; p++) {
+            double wv = (double)w[p];
+            k += wv;
+            if (C && C[tgt[p]] == ci) in += wv;
+        }
+        if (K) K[i] = k;
+        if (Sig) atomicAdd(Sig + ci, k);
+        two_m += k;
+        intra += in;
+    }
+    two_m = block_sum(two_m, red);
+    intra = block_sum(intra, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(acc, two_m);
+        if (C) atomicAdd(acc + 1, intra);
+    }
+}
+
+template <typename WT>
+__global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                                const WT *__restrict__ w, const uint32_t *__restrict__ C, double *K, double *Sig,
+                                double *acc, const uint32_t *longlist, const uint32_t *nlong) {
+    __shared__ double red[32];
+    uint32_t cnt = *nlong;
+    for (uint32_t t = blockIdx.x; t < cnt; t += gridDim.x) {
+        uint32_t i = longlist[t];
+        uint64_t b = off[i], e = off[i + 1];
+        uint32_t ci = C ? C[i] : 0;
+        double k = 0, in = 0;
+        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+            double wv = (double)w[p];
+            k += wv;
+            if (C && C[tgt[p]] == ci) in += wv;
+        }
+        k = block_sum(k, red);
+        in = block_sum(in, red);
+        if (threadIdx.x == 0) {
+            if (K) K[i] = k;
+            if (Sig) atomicAdd(Sig + ci, k);
+            atomicAdd(acc, k);
+            if (C) atomicAdd(acc + 1, in);
+        }
+    }
+}
+
+template <typename WT>
+static void row_sums(const DevGraph &g, const uint32_t *C, double *K, double *Sig, double *acc, cudaStream_t s) {
+    size_t mk = arena().mark();
+    uint32_t *longlist = arena().get<uint32_t>(g.n + 1);
+    uint32_t *nlong = arena().get<uint32_t>(1);
+    GSP_CUDA(cudaMemsetAsync(nlong, 0, sizeof(uint32_t), s));
+    const WT *w = static_cast<const WT *>(g.w);
+    k_row_sums<WT><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, K, Sig, acc, longlist, nlong);
+    GSP_CHECK_LAUNCH();
+    k_row_sums_long<WT><<<152 * 4, 256, 0, s>>>(g.off, g.tgt, w, C, K, Sig, acc, longlist, nlong);
+    GSP_CHECK_LAUNCH();
+    arena().release(mk);
+}
+
+static void row_sums_any(const DevGraph &g, const uint32_t *C, double *K, double *Sig, double *acc, cudaStream_t s) {
+    if (g.wt == GSP_W_F64) row_sums<double>(g, C, K, Sig, acc, s);
+    else row_sums<float>(g, C, K, Sig, acc, s);
+}
+
+__global__ void k_half(const double *acc, double *m_dev) { *m_dev = acc[0] / 2.0; }
+
+double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t s) {
+    size_t mk = arena().mark();
+    double *acc = arena().get<double>(2);
+    GSP_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(double), s));
+    row_sums_any(g, nullptr, K, nullptr, acc, s);
+    if (m_dev) {
+        k_half<<<1, 1, 0, s>>>(acc, m_dev);
+        GSP_CHECK_LAUNCH();
+    }
+    double h[2];
+    GSP_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    return h[0] / 2.0;
+}
+
+__global__ void k_sum_sq(const double *Sig, uint32_t n, double *out) {
+    __shared__ double red[32];
+    double t = 0;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double x = Sig[c];
+        t += x * x;
+    }
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) atomicAdd(out, t);
+}
+
+// Equation 1, second form: Q = sum_c sigma_c / 2m - sum_c (Sigma_c / 2m)^2,
+// with sum_c sigma_c = the weight of all intra-community entries.
+double modularity(const DevGraph &g, const uint32_t *C, cudaStream_t s) {
+    size_t mk = arena().mark();
+    double *acc = arena().get<double>(4);
+    double *Sig = arena().get<double>(g.n);
+    GSP_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
+    GSP_CUDA(cudaMemsetAsync(Sig, 0, sizeof(double) * g.n, s));
+    row_sums_any(g, C, nullptr, Sig, acc, s);
+    k_sum_sq<<<grid_for(g.n, 256), 256, 0, s>>>(Sig, g.n, acc + 2);
+    GSP_CHECK_LAUNCH();
+    double h[4];
+    GSP_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    double two_m = h[0];
+    if (!(two_m > 0.0)) return 0.0;
+    return h[1] / two_m - h[2] / (two_m * two_m);
+}
+
+// ---------------------------------------------------------------- renumber
+__global__ void k_mark_used(const uint32_t *__restrict__ C, uint32_t n, uint8_t *used) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) used[C[i]] = 1;
+}
+__global__ void k_apply_rank(const uint32_t *__restrict__ C, uint32_t n, const uint32_t *__restrict__ rank,
+                             uint32_t *out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = rank[C[i]];
+}
+
+uint32_t renumber(uint32_t n, const uint32_t *C, uint32_t *C_dense, cudaStream_t s) {
+    size_t mk = arena().mark();
+    uint8_t *used = arena().get<uint8_t>(n);
+    uint32_t *rank = arena().get<uint32_t>((size_t)n + 1);
+    GSP_CUDA(cudaMemsetAsync(used, 0, n, s));
+    k_mark_used<<<grid_for(n, 256), 256, 0, s>>>(C, n, used);
+    GSP_CHECK_LAUNCH();
+    exclusive_scan_u8_to_u32(used, rank, n, s);
+    k_apply_rank<<<grid_for(n, 256), 256, 0, s>>>(C, n, rank, C_dense);
+    GSP_CHECK_LAUNCH();
+    uint32_t k;
+    GSP_CUDA(cudaMemcpyAsync(&k, rank + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    return k;
+}
+
+__global__ void k_lookup(uint32_t *Ctop, uint32_t n, const uint32_t *__restrict__ Cp) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) Ctop[i] = Cp[Ctop[i]];
+}
+void lookup(uint32_t n_top, uint32_t *C_top, const uint32_t *C_pass, cudaStream_t s) {
+    if (!n_top) return;
+    k_lookup<<<grid_for(n_top, 256), 256, 0, s>>>(C_top, n_top, C_pass);
+    GSP_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------- final numbering
+__global__ void k_first_vertex(const uint32_t *__restrict__ C, uint32_t n, uint32_t *first) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicMin(first + C[i], i);
+}
+__global__ void k_is_first(const uint32_t *__restrict__ C, uint32_t n, const uint32_t *__restrict__ first,
+                           uint8_t *flag) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = first[C[i]] == i;
+}
+__global__ void k_apply_first(uint32_t *C, uint32_t n, const uint32_t *__restrict__ first,
+                              const uint32_t *__restrict__ rank) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        C[i] = rank[first[C[i]]];
+}
+
+uint32_t canonical_numbering(uint32_t n, uint32_t *C, cudaStream_t s) {
+    size_t mk = arena().mark();
+    uint32_t *first = arena().get<uint32_t>(n);
+    uint8_t *flag = arena().get<uint8_t>(n);
+    uint32_t *rank = arena().get<uint32_t>((size_t)n + 1);
+    GSP_CUDA(cudaMemsetAsync(first, 0xFF, sizeof(uint32_t) * n, s));
+    unsigned gr = grid_for(n, 256);
+    k_first_vertex<<<gr, 256, 0, s>>>(C, n, first);
+    GSP_CHECK_LAUNCH();
+    k_is_first<<<gr, 256, 0, s>>>(C, n, first, flag);
+    GSP_CHECK_LAUNCH();
+    exclusive_scan_u8_to_u32(flag, rank, n, s);
+    k_apply_first<<<gr, 256, 0, s>>>(C, n, first, rank);
+    GSP_CHECK_LAUNCH();
+    uint32_t k;
+    GSP_CUDA(cudaMemcpyAsync(&k, rank + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    return k;
+}
+
+// ------------------------------------------ Algorithm 6 (disconnected count)
+// A community is disconnected exactly when its vertices fall in more than
+// one connected component of the intra-community subgraph.
+__global__ void k_count_roots(const uint32_t *__restrict__ C, const uint32_t *__restrict__ lab, uint32_t n,
+                              uint32_t *ncomp) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (lab[i] == i) atomicAdd(ncomp + C[i], 1u);
+}
+__global__ void k_flag_disconnected(const uint32_t *__restrict__ ncomp, uint32_t n, uint8_t *flags,
+                                    unsigned long long *count) {
+    __shared__ unsigned long long red[32];
+    unsigned long long t = 0;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        uint8_t f = ncomp[c] > 1;
+        if (flags) flags[c] = f;
+        t += f;
+    }
+    t = block_sum(t, red);
+    if (threadIdx.x == 0 && t) atomicAdd(count, t);
+}
+
+uint32_t count_disconnected(const DevGraph &g, const uint32_t *C, uint8_t *flags, cudaStream_t s) {
+    size_t mk = arena().mark();
+    uint32_t *lab = arena().get<uint32_t>(g.n);
+    uint32_t *ncomp = arena().get<uint32_t>(g.n);
+    unsigned long long *cnt = arena().get<unsigned long long>(1);
+    Classes cl;
+    classify_vertices(g, cl, s);
+    split_labels(g, cl, C, GSP_SPLIT_BFS, lab, s);
+    GSP_CUDA(cudaMemsetAsync(ncomp, 0, sizeof(uint32_t) * g.n, s));
+    GSP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    unsigned gr = grid_for(g.n, 256);
+    k_count_roots<<<gr, 256, 0, s>>>(C, lab, g.n, ncomp);
+    GSP_CHECK_LAUNCH();
+    k_flag_disconnected<<<gr, 256, 0, s>>>(ncomp, g.n, flags, cnt);
+    GSP_CHECK_LAUNCH();
+    unsigned long long h;
+    GSP_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    return (uint32_t)h;
+}
+
+}  // namespace gsp

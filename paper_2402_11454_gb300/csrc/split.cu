@@ -1,0 +1,275 @@
+// split.cu -- the split step of GSP-Louvain (Section 4.1): break every
+// community into the connected components of its intra-community edges.
+//
+//   LP  (Algorithm 2): labels start at the vertex id; every sweep each vertex
+//        takes the minimum label over its same-community neighbours, in place,
+//        until a sweep changes nothing.  Labels only decrease, so the in-place
+//        updates of concurrent threads converge to the same fixpoint.
+//   LPP (Algorithm 2 with pruning): only vertices flagged unprocessed are
+//        visited; a vertex whose label drops flags its same-community
+//        neighbours.
+//   BFS (Algorithm 3): rounds of multi-source, level-synchronous,
+//        frontier-compacted BFS.  In each round the seed of a community is its
+//        smallest unvisited vertex, found with atomicMin; vertices are claimed
+//        with atomicCAS on their label.  The busy flags of the paper's
+//        per-thread BFS become unnecessary: every community is searched from
+//        one seed per round by the whole GPU.
+// The seed of a round is the smallest vertex of its component (the smaller
+// vertices of the community are already visited, and components are
+// disjoint), so every mode yields label = smallest vertex id of the component.
+#include "internal.cuh"
+
+namespace gsp {
+
+template <typename T> __device__ __forceinline__ T ldcg_(const T *p) { return __ldcg(p); }
+__device__ __forceinline__ uint8_t ldcg_(const uint8_t *p) {
+    return (uint8_t)__ldcg(reinterpret_cast<const unsigned char *>(p));
+}
+
+// ----------------------------------------------------------------- LP / LPP
+template <int G, bool PRUNE>
+__global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                                                  const uint32_t *__restrict__ C, uint32_t *lab, uint8_t *flag,
+                                                  const uint32_t *__restrict__ list, uint32_t count,
+                                                  unsigned long long *changed) {
+    const int lane = threadIdx.x % G;
+    const unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+    const uint32_t NG = 256 / G;
+    unsigned long long ch = 0;
+    for (uint32_t idx = blockIdx.x * NG + threadIdx.x / G; idx < count; idx += gridDim.x * NG) {
+        uint32_t i = list[idx];
+        if (PRUNE) {  // one lane reads and clears the flag; the group follows
+            int go = 0;
+            if (lane == 0) {
+                go = ldcg_(flag + i);
+                if (go) flag[i] = 0;
+            }
+            if (!__shfl_sync(gmask, go, (threadIdx.x & 31) & ~(G - 1))) continue;
+        }
+        uint32_t ci = C[i];
+        uint32_t cur = ldcg_(lab + i);
+        uint32_t mn = cur;
+        uint64_t b = off[i], e = off[i + 1];
+        for (uint64_t p = b + lane; p < e; p += G) {
+            uint32_t j = tgt[p];
+            if (C[j] == ci) mn = min(mn, ldcg_(lab + j));
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(gmask, mn, o));
+        if (mn < cur) {
+            if (lane == 0) { lab[i] = mn; ch++; }
+            if (PRUNE)
+                for (uint64_t p = b + lane; p < e; p += G) {
+                    uint32_t j = tgt[p];
+                    if (C[j] == ci) flag[j] = 1;
+                }
+        }
+        __syncwarp(gmask);
+    }
+    __shared__ unsigned long long red[32];
+    ch = block_sum(ch, red);
+    if (threadIdx.x == 0 && ch) atomicAdd(changed, ch);
+}
+
+template <bool PRUNE>
+__global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                                                  const uint32_t *__restrict__ C, uint32_t *lab, uint8_t *flag,
+                                                  const uint32_t *__restrict__ list, uint32_t count,
+                                                  unsigned long long *changed) {
+    __shared__ uint32_t red[32];
+    __shared__ int s_go;
+    unsigned long long ch = 0;
+    for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
+        uint32_t i = list[idx];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int go = 1;
+            if (PRUNE) {
+                go = ldcg_(flag + i);
+                if (go) flag[i] = 0;
+            }
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) continue;
+        uint32_t ci = C[i];
+        uint32_t cur = ldcg_(lab + i);
+        uint32_t mn = cur;
+        uint64_t b = off[i], e = off[i + 1];
+        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+            uint32_t j = tgt[p];
+            if (C[j] == ci) mn = min(mn, ldcg_(lab + j));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+        __syncthreads();
+        mn = red[0];
+        for (int t = 1; t < (int)(blockDim.x >> 5); t++) mn = min(mn, red[t]);
+        if (mn < cur) {
+            if (threadIdx.x == 0) { lab[i] = mn; ch++; }
+            if (PRUNE)
+                for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+                    uint32_t j = tgt[p];
+                    if (C[j] == ci) flag[j] = 1;
+                }
+        }
+    }
+    __shared__ unsigned long long r2[32];
+    __syncthreads();
+    ch = block_sum(ch, r2);
+    if (threadIdx.x == 0 && ch) atomicAdd(changed, ch);
+}
+
+static void split_lp(const DevGraph &g, const Classes &cl, const uint32_t *C, bool prune, uint32_t *lab,
+                     cudaStream_t s) {
+    size_t mk = arena().mark();
+    uint8_t *flag = prune ? arena().get<uint8_t>(g.n) : nullptr;
+    unsigned long long *changed = arena().get<unsigned long long>(1);
+    iota_u32(lab, g.n, s);
+    if (prune) GSP_CUDA(cudaMemsetAsync(flag, 1, g.n, s));
+    auto cnt = [&](int c) { return cl.start[c + 1] - cl.start[c]; };
+    auto lst = [&](int c) { return cl.list + cl.start[c]; };
+    const unsigned maxg = 152 * 8;
+    uint32_t nbig = cl.start[NUM_CLS] - cl.start[CLS_BLOCK];
+    for (int it = 0; it < (1 << 30); it++) {
+        GSP_CUDA(cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s));
+#define LPG(G, CLS)                                                                                  \
+    if (cnt(CLS)) {                                                                                  \
+        if (prune)                                                                                   \
+            k_lp_group<G, true><<<grid_for((uint64_t)cnt(CLS) * G, 256, maxg), 256, 0, s>>>(        \
+                g.off, g.tgt, C, lab, flag, lst(CLS), cnt(CLS), changed);                            \
+        else                                                                                         \
+            k_lp_group<G, false><<<grid_for((uint64_t)cnt(CLS) * G, 256, maxg), 256, 0, s>>>(       \
+                g.off, g.tgt, C, lab, flag, lst(CLS), cnt(CLS), changed);                            \
+        GSP_CHECK_LAUNCH();                                                                          \
+    }
+        LPG(4, CLS_G4) LPG(8, CLS_G8) LPG(16, CLS_G16) LPG(32, CLS_G32)
+#undef LPG
+        if (nbig) {
+            if (prune)
+                k_lp_block<true><<<grid_for(nbig, 1, 152 * 4), 256, 0, s>>>(g.off, g.tgt, C, lab, flag,
+                                                                              lst(CLS_BLOCK), nbig, changed);
+            else
+                k_lp_block<false><<<grid_for(nbig, 1, 152 * 4), 256, 0, s>>>(g.off, g.tgt, C, lab, flag,
+                                                                               lst(CLS_BLOCK), nbig, changed);
+            GSP_CHECK_LAUNCH();
+        }
+        unsigned long long h;
+        GSP_CUDA(cudaMemcpyAsync(&h, changed, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        if (h == 0) break;
+    }
+    arena().release(mk);
+}
+
+// --------------------------------------------------------------------- BFS
+__global__ void k_bfs_seed_min(const uint32_t *__restrict__ C, const uint32_t *__restrict__ lab, uint32_t n,
+                               uint32_t *seed) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (lab[v] == EMPTY) atomicMin(seed + C[v], v);
+}
+
+// Warp-aggregated append of the lanes with `want` set; returns the slot.
+__device__ __forceinline__ void push_warp(bool want, uint32_t v, uint32_t *q, uint32_t *qn) {
+    uint32_t ballot = __ballot_sync(0xFFFFFFFFu, want);
+    if (!ballot) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(ballot) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(qn, (uint32_t)__popc(ballot));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (want) q[base + __popc(ballot & ((1u << lane) - 1u))] = v;
+}
+
+__global__ void k_bfs_seed_push(const uint32_t *__restrict__ C, uint32_t *lab, uint32_t n,
+                                const uint32_t *__restrict__ seed, uint32_t *q, uint32_t *qn) {
+    for (uint32_t v0 = blockIdx.x * blockDim.x; v0 < n; v0 += gridDim.x * blockDim.x) {
+        uint32_t v = v0 + threadIdx.x;
+        bool want = false;
+        if (v < n && lab[v] == EMPTY && seed[C[v]] == v) {
+            lab[v] = v;
+            want = true;
+        }
+        push_warp(want, v, q, qn);
+    }
+}
+
+__global__ void k_bfs_seed_reset(const uint32_t *__restrict__ C, const uint32_t *__restrict__ q,
+                                 const uint32_t *__restrict__ qn, uint32_t *seed) {
+    uint32_t cnt = *qn;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x)
+        seed[C[q[t]]] = EMPTY;
+}
+
+// One level: a warp per frontier vertex claims unvisited same-community
+// neighbours with atomicCAS and appends them to the next frontier.
+__global__ void k_bfs_expand(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                             const uint32_t *__restrict__ C, uint32_t *lab, const uint32_t *__restrict__ q,
+                             const uint32_t *__restrict__ qn, uint32_t *nq, uint32_t *nqn) {
+    uint32_t cnt = *qn;
+    int lane = threadIdx.x & 31;
+    uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t t = warp; t < cnt; t += nwarps) {
+        uint32_t u = q[t];
+        uint32_t cu = C[u], lu = ldcg_(lab + u);
+        uint64_t b = off[u], e = off[u + 1];
+        for (uint64_t p0 = b; p0 < e; p0 += 32) {
+            uint64_t p = p0 + lane;
+            bool want = false;
+            uint32_t j = 0;
+            if (p < e) {
+                j = tgt[p];
+                if (C[j] == cu && ldcg_(lab + j) == EMPTY) want = atomicCAS(lab + j, EMPTY, lu) == EMPTY;
+            }
+            push_warp(want, j, nq, nqn);
+        }
+    }
+}
+
+static void split_bfs(const DevGraph &g, const uint32_t *C, uint32_t *lab, cudaStream_t s) {
+    size_t mk = arena().mark();
+    uint32_t n = g.n;
+    uint32_t *seed = arena().get<uint32_t>(n);
+    uint32_t *qa = arena().get<uint32_t>(n);
+    uint32_t *qb = arena().get<uint32_t>(n);
+    uint32_t *cnts = arena().get<uint32_t>(2);
+    GSP_CUDA(cudaMemsetAsync(lab, 0xFF, sizeof(uint32_t) * n, s));
+    GSP_CUDA(cudaMemsetAsync(seed, 0xFF, sizeof(uint32_t) * n, s));
+    unsigned gr = grid_for(n, 256);
+    for (;;) {
+        GSP_CUDA(cudaMemsetAsync(cnts, 0, 2 * sizeof(uint32_t), s));
+        k_bfs_seed_min<<<gr, 256, 0, s>>>(C, lab, n, seed);
+        GSP_CHECK_LAUNCH();
+        k_bfs_seed_push<<<gr, 256, 0, s>>>(C, lab, n, seed, qa, cnts);
+        GSP_CHECK_LAUNCH();
+        k_bfs_seed_reset<<<gr, 256, 0, s>>>(C, qa, cnts, seed);
+        GSP_CHECK_LAUNCH();
+        uint32_t h;
+        GSP_CUDA(cudaMemcpyAsync(&h, cnts, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        if (h == 0) break;
+        uint32_t *q = qa, *nq = qb;
+        uint32_t *qn = cnts, *nqn = cnts + 1;
+        while (h) {
+            GSP_CUDA(cudaMemsetAsync(nqn, 0, sizeof(uint32_t), s));
+            k_bfs_expand<<<grid_for((uint64_t)h * 32, 256, 152 * 8), 256, 0, s>>>(g.off, g.tgt, C, lab, q, qn, nq,
+                                                                                  nqn);
+            GSP_CHECK_LAUNCH();
+            GSP_CUDA(cudaMemcpyAsync(&h, nqn, sizeof(h), cudaMemcpyDeviceToHost, s));
+            GSP_CUDA(cudaStreamSynchronize(s));
+            uint32_t *t = q; q = nq; nq = t;
+            uint32_t *tn = qn; qn = nqn; nqn = tn;
+        }
+    }
+    arena().release(mk);
+}
+
+void split_labels(const DevGraph &g, const Classes &cl, const uint32_t *C, int mode, uint32_t *labels,
+                  cudaStream_t s) {
+    if (mode == GSP_SPLIT_BFS) split_bfs(g, C, labels, s);
+    else split_lp(g, cl, C, mode == GSP_SPLIT_LPP, labels, s);
+}
+
+}  // namespace gsp

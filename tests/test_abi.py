@@ -1,0 +1,66 @@
+"""The C ABI library loads on a machine without a GPU, exports every entry
+point include/gsp.h declares, and rejects invalid arguments on the host
+before any device work.  CPU only."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2402_11454_gb300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    from paper_2402_11454_gb300 import _lib
+    return _lib.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "gsp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_binding_declares_every_symbol():
+    from paper_2402_11454_gb300 import _lib
+    assert set(declared_symbols()) == set(_lib._SIGS)
+
+
+def test_default_opts_and_strings(lib):
+    from paper_2402_11454_gb300._lib import GspOpts
+    o = GspOpts()
+    lib.gsp_default_opts(ctypes.byref(o))
+    assert (o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
+            o.aggregation_tolerance) == (10, 20, 1e-2, 10.0, 0.8)
+    assert o.split == 3 and o.split_when == 0 and o.move == 0 and o.precision == 0
+    assert lib.gsp_status_string(-1) == b"invalid argument"
+    assert lib.gsp_mlp_param_count() == 32 * 6 + 32 + 32 * 32 + 32 + 32 + 1
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    from paper_2402_11454_gb300._lib import GspOpts
+    # n = 0
+    assert lib.gsp_louvain(None, None, None, 0, 0, None, None, None, None) == -1
+    assert b"membership" in lib.gsp_last_error() or b"n must" in lib.gsp_last_error()
+    o = GspOpts()
+    lib.gsp_default_opts(ctypes.byref(o))
+    o.max_passes = 0
+    assert lib.gsp_louvain(None, None, None, 5, 0, ctypes.byref(o), None, None, None) == -1
+    assert b"max_passes" in lib.gsp_last_error()
+    lib.gsp_default_opts(ctypes.byref(o))
+    o.split = 9
+    assert lib.gsp_louvain(None, None, None, 5, 0, ctypes.byref(o), None, None, None) == -1
+    assert lib.gsp_split(None, None, 0, 0, None, 3, None, None, None) == -1
+    assert lib.gsp_renumber(0, None, None, None, None) == -1
+    assert lib.gsp_gen_rmat(0, 16, 1, 2, 3, 0, None, None) == -1

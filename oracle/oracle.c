@@ -41,7 +41,8 @@ typedef struct {
     double aggregation_tolerance; /* tau_agg, Algorithm 1 */
     int split;                  /* 0 none (GVE-Louvain), 1 LP, 2 LPP, 3 BFS */
     int split_last;             /* 0 Split Pass (SP), 1 Split Last (SL) */
-    int sync;                   /* 0 asynchronous in-place moves, 1 frozen-state sweeps */
+    int sync;                   /* 0 asynchronous in-place moves, 1 frozen-state waves */
+    int waves;                  /* frozen-state waves per iteration */
     int singleton_rule;         /* frozen-state sweeps only: singleton -> singleton moves go to lower ids */
 } og_opts;
 
@@ -204,19 +205,23 @@ void og_move_sweep_sync(const og_graph *g, const uint32_t *C, const double *K, c
  * processed, and a vertex that moves marks its neighbours unprocessed.
  *   sync = 0: one thread walks the unprocessed vertices in id order and each
  *             move is applied at once (the in-place form of the paper).
- *   sync = 1: every vertex of an iteration reads the C, Sigma and community
- *             sizes of the iteration's start; the moves are applied after.
+ *   sync = 1: the parallel loop is made deterministic by waves: the vertices
+ *             of an iteration are split into `waves` interleaved waves (vertex
+ *             i belongs to wave i mod waves), taken in order; every vertex of
+ *             a wave reads the C, Sigma and community sizes left by the
+ *             earlier waves, and the wave's moves are applied after it.
+ *             waves = 1 is the fully synchronous loop; waves = |V'| is the
+ *             one-thread loop in id order.
  * dq_iter (optional) receives the total delta-modularity of each iteration.
  */
 int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, double m, double tau,
-            int max_iterations, int sync, int singleton_rule, double *dq_iter)
+            int max_iterations, int sync, int waves, int singleton_rule, double *dq_iter)
 {
     uint32_t n = g->n;
     double *H = calloc(n ? n : 1, sizeof(double));
     uint8_t *seen = calloc(n ? n : 1, 1);
     uint32_t *list = malloc(sizeof(uint32_t) * (n ? n : 1));
     uint8_t *unprocessed = malloc(n ? n : 1);
-    uint8_t *next = calloc(n ? n : 1, 1);
     uint32_t *choice = malloc(sizeof(uint32_t) * (n ? n : 1));
     uint32_t *size = calloc(n ? n : 1, sizeof(uint32_t));
     memset(unprocessed, 1, n);
@@ -241,29 +246,33 @@ int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, doub
                     if (g->tgt[e] != i) unprocessed[g->tgt[e]] = 1;
             }
         } else {
-            memset(next, 0, n);
-            for (uint32_t i = 0; i < n; i++) {
-                choice[i] = C[i];
-                if (!unprocessed[i]) continue;
-                double b;
-                choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, NULL);
-                if (choice[i] != C[i]) dQ += b;
+            uint32_t W = waves < 1 ? 1u : (uint32_t)waves;
+            for (uint32_t wv = 0; wv < W && wv < (n ? n : 1); wv++) {
+                /* decide: every unprocessed vertex of the wave, frozen state */
+                for (uint32_t i = wv; i < n; i += W) {
+                    choice[i] = C[i];
+                    if (!unprocessed[i]) continue;
+                    unprocessed[i] = 0;
+                    double b;
+                    choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, NULL);
+                    if (choice[i] != C[i]) dQ += b;
+                }
+                /* apply the wave's moves; movers mark their neighbours */
+                for (uint32_t i = wv; i < n; i += W) {
+                    if (choice[i] == C[i]) continue;
+                    Sigma[C[i]] -= K[i];
+                    Sigma[choice[i]] += K[i];
+                    size[C[i]]--; size[choice[i]]++;
+                    for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++)
+                        if (g->tgt[e] != i) unprocessed[g->tgt[e]] = 1;
+                    C[i] = choice[i];
+                }
             }
-            for (uint32_t i = 0; i < n; i++) {
-                if (choice[i] == C[i]) continue;
-                Sigma[C[i]] -= K[i];
-                Sigma[choice[i]] += K[i];
-                size[C[i]]--; size[choice[i]]++;
-                for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++)
-                    if (g->tgt[e] != i) next[g->tgt[e]] = 1;
-            }
-            for (uint32_t i = 0; i < n; i++) C[i] = choice[i];
-            memcpy(unprocessed, next, n);
         }
         if (dq_iter) dq_iter[it] = dQ;
         if (dQ <= tau) break;
     }
-    free(H); free(seen); free(list); free(unprocessed); free(next); free(choice); free(size);
+    free(H); free(seen); free(list); free(unprocessed); free(choice); free(size);
     return li;
 }
 
@@ -501,7 +510,7 @@ int og_louvain(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st)
         double m = og_vertex_weights(&cur, K);
         memcpy(Sigma, K, sizeof(double) * nv);
         for (uint32_t i = 0; i < nv; i++) Cp[i] = i;
-        int li = (m > 0.0) ? og_move(&cur, Cp, K, Sigma, m, tau, o->max_iterations, o->sync,
+        int li = (m > 0.0) ? og_move(&cur, Cp, K, Sigma, m, tau, o->max_iterations, o->sync, o->waves,
                                      o->singleton_rule, NULL)
                            : 0;
         if (split_each_pass) {

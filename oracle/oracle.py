@@ -38,7 +38,7 @@ class _OgOpts(ctypes.Structure):
     _fields_ = [("max_passes", ctypes.c_int), ("max_iterations", ctypes.c_int),
                 ("tolerance", ctypes.c_double), ("tolerance_drop", ctypes.c_double),
                 ("aggregation_tolerance", ctypes.c_double), ("split", ctypes.c_int),
-                ("split_last", ctypes.c_int), ("sync", ctypes.c_int),
+                ("split_last", ctypes.c_int), ("sync", ctypes.c_int), ("waves", ctypes.c_int),
                 ("singleton_rule", ctypes.c_int)]
 
 
@@ -64,7 +64,7 @@ def _load():
         lib.og_move_sweep_sync.argtypes = [G, P, P, P, P, ctypes.c_int, ctypes.c_double, P, P, P, P]
         lib.og_move_sweep_sync.restype = None
         lib.og_move.argtypes = [G, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                ctypes.c_int, ctypes.c_int, P]
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
         lib.og_move.restype = ctypes.c_int
         lib.og_split_lp.argtypes = [G, P, P, ctypes.c_int]
         lib.og_split_lp.restype = ctypes.c_int
@@ -142,14 +142,15 @@ def move_sweep_sync(g, C, K, Sigma, m, active=None, singleton_rule=True):
     return choice, best, second
 
 
-def move(g, C, K, Sigma, m, tau, max_iterations=20, sync=True, singleton_rule=True):
-    """louvainMove (Algorithm 4); returns (C, Sigma, l_i, dq per iteration)."""
+def move(g, C, K, Sigma, m, tau, max_iterations=20, sync=True, singleton_rule=True, waves=1):
+    """louvainMove (Algorithm 4); returns (C, Sigma, l_i, dq per iteration).
+    sync=True runs frozen-state waves (vertex i in wave i mod waves)."""
     C = _u32(C).copy()
     K = np.ascontiguousarray(K, dtype=np.float64)
     Sigma = np.ascontiguousarray(Sigma, dtype=np.float64).copy()
     dq = np.zeros(max(max_iterations, 1), dtype=np.float64)
     li = _load().og_move(g.ref, _p(C), _p(K), _p(Sigma), m, tau, max_iterations, int(bool(sync)),
-                         int(bool(singleton_rule)), _p(dq))
+                         int(waves), int(bool(singleton_rule)), _p(dq))
     return C, Sigma, li, dq[:li]
 
 
@@ -215,6 +216,7 @@ class LouvainOptions:
     split: str = "bfs"
     split_last: bool = False
     sync: bool = True
+    waves: int = 16
     singleton_rule: bool = True
 
 
@@ -223,7 +225,7 @@ def louvain(g, opts=None):
     o = opts or LouvainOptions()
     co = _OgOpts(o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
                  o.aggregation_tolerance, SPLIT_MODES[o.split], int(o.split_last), int(o.sync),
-                 int(o.singleton_rule))
+                 int(o.waves), int(o.singleton_rule))
     C = np.zeros(g.n, dtype=np.uint32)
     st = _OgStats()
     _load().og_louvain(g.ref, ctypes.byref(co), _p(C), ctypes.byref(st))

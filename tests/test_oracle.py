@@ -223,6 +223,36 @@ def test_async_move_telescopes(seed):
     np.testing.assert_allclose(Sigma, np.bincount(C, weights=K, minlength=n), atol=1e-12)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_waves_of_one_vertex_equal_the_sequential_loop(seed):
+    """Frozen-state waves with one vertex per wave (waves = |V|, vertex i in
+    wave i) see every earlier move, which is the one-thread in-place loop of
+    Algorithm 4: both forms must give the same result bit for bit."""
+    rng = np.random.default_rng(350 + seed)
+    n = int(rng.integers(10, 80))
+    g, A = random_graph(rng, n, rng.uniform(0.05, 0.3))
+    K, m = oracle.vertex_weights(g)
+    C0 = np.arange(n, dtype=np.uint32)
+    Ca, Sa, la, dqa = oracle.move(g, C0, K, K.copy(), m, tau=1e-3, max_iterations=30, sync=False)
+    Cw, Sw, lw, dqw = oracle.move(g, C0, K, K.copy(), m, tau=1e-3, max_iterations=30, sync=True,
+                                  singleton_rule=False, waves=n)
+    assert la == lw
+    np.testing.assert_array_equal(Ca, Cw)
+    np.testing.assert_array_equal(Sa, Sw)
+    np.testing.assert_array_equal(dqa, dqw)
+
+
+@pytest.mark.parametrize("waves", [1, 4, 16])
+def test_waves_keep_sigma_and_gain_positive_first_sweep(waves):
+    off, tgt, w = graphgen.planted(n=2000, k=16, mean_degree=12, p_intra=0.8, seed=5)
+    g = oracle.Graph(off, tgt, w)
+    K, m = oracle.vertex_weights(g)
+    C, S, li, dq = oracle.move(g, np.arange(2000, dtype=np.uint32), K, K.copy(), m, tau=1e-2,
+                               sync=True, waves=waves)
+    np.testing.assert_allclose(S, np.bincount(C, weights=K, minlength=2000), atol=1e-9)
+    assert dq[0] > 0
+
+
 def test_sync_move_keeps_sigma_and_finds_cliques():
     A = ring_of_cliques(8, 5)
     g = dense_to_graph(A)

@@ -55,6 +55,10 @@ typedef enum { GSP_SPLIT_PASS = 0, GSP_SPLIT_LAST = 1 } gsp_split_when;
  * does (results depend on thread timing); SYNC lets every vertex of an
  * iteration read the state of the iteration's start (deterministic). */
 typedef enum { GSP_MOVE_ASYNC = 0, GSP_MOVE_SYNC = 1 } gsp_move_mode;
+/* SYNC splits each iteration into `waves` interleaved waves: vertex i belongs
+ * to wave i mod waves, and every vertex of a wave reads the state left by the
+ * earlier waves (waves = 1: fully synchronous; more waves approach the
+ * one-thread order). */
 /* MIXED: per-community weights K_{i->c} and delta-modularity in float32,
  * while m, Sigma_tot and modularity stay float64.  FP64: everything float64,
  * Equation 2 evaluated term by term (the parity mode). */
@@ -72,13 +76,15 @@ typedef struct {
     double aggregation_tolerance;   /* tau_agg (Algorithm 1); default 0.8 */
     int split;                      /* gsp_split_mode; default GSP_SPLIT_BFS */
     int split_when;                 /* gsp_split_when; default GSP_SPLIT_PASS */
-    int move;                       /* gsp_move_mode; default GSP_MOVE_ASYNC */
+    int move;                       /* gsp_move_mode; default GSP_MOVE_SYNC */
+    int waves;                      /* SYNC: waves per iteration, 1..64; default 16 */
     int precision;                  /* gsp_precision; default GSP_PREC_MIXED */
     int singleton_rule;             /* 1: a vertex alone in its community moves to another
                                        singleton community only if that id is lower; default 1 */
     int prune;                      /* gsp_prune_mode; default GSP_PRUNE_FLAGS */
     const void *mlp_params;         /* device pointer to gsp_mlp_param_count() floats (learned pruning) */
     int full_sweep_every;           /* learned pruning: every k-th iteration is a plain sweep; default 4 */
+    float prune_threshold;          /* learned pruning: skip a vertex when P(move) < this; default 0.5 */
     void *stream;                   /* cudaStream_t; NULL = default stream */
 } gsp_opts;
 
@@ -173,13 +179,15 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
 
 /*
  * louvainMove (Algorithm 4) from membership C (in/out) and Sigma (in/out,
- * must equal the per-community sums of K).  move is a gsp_move_mode.  Returns
- * l_i, the iterations executed, in *iterations_host.
+ * must equal the per-community sums of K).  move is a gsp_move_mode, waves
+ * the SYNC wave count (1..64).  Returns l_i, the iterations executed, in
+ * *iterations_host.
  */
 gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, const void *weights,
                           int wt, uint32_t n, uint64_t nnz, uint32_t *C, const double *K,
                           double *Sigma, double m, double tolerance, int max_iterations, int move,
-                          int precision, int singleton_rule, int *iterations_host, void *stream);
+                          int waves, int precision, int singleton_rule, int *iterations_host,
+                          void *stream);
 
 /*
  * Split (Algorithms 2 and 3): labels[i] = the smallest vertex id of the
@@ -217,6 +225,19 @@ gsp_status gsp_aggregate(const uint64_t *offsets, const uint32_t *targets, const
 gsp_status gsp_count_disconnected(const uint64_t *offsets, const uint32_t *targets, uint32_t n,
                                   uint64_t nnz, const uint32_t *C, uint8_t *flags,
                                   uint32_t *count_host, void *stream);
+
+/*
+ * Move/no-move traces of the plain method, for training the learned pruning
+ * predictor: runs gsp_louvain (opts as given; learned pruning ignored) and,
+ * for a sample of vertex visits of local moving (about one in sample_every),
+ * records the visit's 6 predictor features (taken before the visit) into
+ * features[rows][6] and whether the vertex moved into labels[rows] (device
+ * arrays of `capacity` rows).  *rows_host = rows written (<= capacity).
+ */
+gsp_status gsp_louvain_trace(const uint64_t *offsets, const uint32_t *targets, const float *weights,
+                             uint32_t n, uint64_t nnz, const gsp_opts *opts, float *features,
+                             uint8_t *labels, uint32_t capacity, uint32_t sample_every,
+                             uint32_t *rows_host);
 
 /* ---------------------------------------------------------------------------
  * Learned vertex pruning: a 6 -> 32 -> 32 -> 1 MLP (ReLU, sigmoid output)

@@ -21,9 +21,9 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory", -3: "CUDA
 class GspOpts(ctypes.Structure):
     _fields_ = [("max_passes", c_int), ("max_iterations", c_int), ("tolerance", c_dbl),
                 ("tolerance_drop", c_dbl), ("aggregation_tolerance", c_dbl), ("split", c_int),
-                ("split_when", c_int), ("move", c_int), ("precision", c_int),
+                ("split_when", c_int), ("move", c_int), ("waves", c_int), ("precision", c_int),
                 ("singleton_rule", c_int), ("prune", c_int), ("mlp_params", P),
-                ("full_sweep_every", c_int), ("stream", P)]
+                ("full_sweep_every", c_int), ("prune_threshold", c_flt), ("stream", P)]
 
 
 _N = GSP_MAX_PASS_STATS
@@ -55,7 +55,8 @@ _SIGS = {
     "gsp_move_sweep": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, P, c_dbl, P, c_int, c_int, P, P,
                                P, P]),
     "gsp_local_move": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, P, c_dbl, c_dbl, c_int, c_int,
-                               c_int, c_int, P, P]),
+                               c_int, c_int, c_int, P, P]),
+    "gsp_louvain_trace": (c_int, [P, P, P, c_u32, c_u64, P, P, P, c_u32, c_u32, P]),
     "gsp_split": (c_int, [P, P, c_u32, c_u64, P, c_int, P, P, P]),
     "gsp_renumber": (c_int, [c_u32, P, P, P, P]),
     "gsp_lookup": (c_int, [c_u32, P, P, P]),

@@ -184,38 +184,46 @@ struct MoveLoopResult {
 
 // Algorithmic bytes of one sweep (per processed vertex: list entry 4, flag 1,
 // C_i 4, two offsets 16, K_i 8, Sigma_d 8; per scanned edge: target 4, weight
-// 4 or 8, C_j 4; per candidate community: Sigma_c 8; per move: C_i 4, two
-// Sigma and two size updates 24, plus one flag byte per neighbour).
+// 4 or 8, C_j 4; per candidate community: Sigma_c 8; per move: move-list
+// entry 8 written and read, C_i 4, two Sigma and two size updates 24, plus
+// one flag byte per neighbour).
 static double sweep_bytes(const MoveCounters &h, int wt) {
     double wb = wt == GSP_W_F64 ? 8.0 : 4.0;
-    return 41.0 * h.vertices + (8.0 + wb) * h.edges + 8.0 * h.candidates + 28.0 * h.moved + 1.0 * h.marked;
+    return 41.0 * h.vertices + (8.0 + wb) * h.edges + 8.0 * h.candidates + 44.0 * h.moved + 1.0 * h.marked;
 }
 
+struct PruneCtx {
+    bool learned = false;
+    int full_every = 4;
+    float threshold = 0.5f;
+};
+
 // louvainMove (Algorithm 4): iterate sweeps until the summed gain of a sweep
-// is <= tau or max_iterations is reached.  mb.C/Sigma/size/act hold the state.
+// is <= tau or max_iterations is reached.  A sweep runs cl.W waves; in
+// frozen-state mode each wave's moves are applied before the next wave.
 static MoveLoopResult move_loop(const DevGraph &g, const Classes &cl, MoveBuffers &mb, double tau, int max_it,
-                                bool sync, bool fp64, bool rule, bool learned, int full_every, cudaStream_t s) {
+                                bool sync, bool fp64, bool rule, const PruneCtx &pr, cudaStream_t s) {
     MoveLoopResult r{0, 0, 0, 0, 0, 0.0, 0.0f};
     MoveCounters h;
     cudaEvent_t e0 = g_events.get(), e1 = g_events.get();
+    uint32_t wave_n[MAX_WAVES];
+    for (int wv = 0; wv < cl.W; wv++) {
+        wave_n[wv] = 0;
+        for (int c = 0; c < NUM_CLS; c++) wave_n[wv] += cl.count(c, wv);
+    }
     for (int it = 0; it < max_it; it++) {
         GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
-        if (sync) {
-            GSP_CUDA(cudaMemcpyAsync(mb.C2, mb.C, sizeof(uint32_t) * g.n, cudaMemcpyDeviceToDevice, s));
-            GSP_CUDA(cudaMemcpyAsync(mb.Sigma2, mb.Sigma, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, s));
-            GSP_CUDA(cudaMemcpyAsync(mb.size2, mb.size, sizeof(uint32_t) * g.n, cudaMemcpyDeviceToDevice, s));
-            GSP_CUDA(cudaMemsetAsync(mb.act2, 0, g.n, s));
-        }
-        bool use_pred = learned && full_every > 0 && (it % full_every) != full_every - 1;
+        bool pruned = pr.learned && pr.full_every > 0 && (it % pr.full_every) != pr.full_every - 1;
         GSP_CUDA(cudaEventRecord(e0, s));
-        move_sweep(g, cl, mb, sync, fp64, rule, use_pred, s);
-        GSP_CUDA(cudaEventRecord(e1, s));
-        if (sync) {
-            std::swap(mb.C, mb.C2);
-            std::swap(mb.Sigma, mb.Sigma2);
-            std::swap(mb.size, mb.size2);
-            std::swap(mb.act, mb.act2);
+        if (pruned)
+            mlp_prune(g, mb, it, max_it, pr.threshold, s);
+        for (int wv = 0; wv < cl.W; wv++) {
+            if (!wave_n[wv]) continue;
+            if (sync) GSP_CUDA(cudaMemsetAsync(mb.mv_cnt, 0, sizeof(uint32_t), s));
+            move_wave(g, cl, mb, wv, sync, fp64, rule, pruned, it, max_it, s);
+            if (sync) apply_moves(g, mb, wave_n[wv], s);
         }
+        GSP_CUDA(cudaEventRecord(e1, s));
         GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
         GSP_CUDA(cudaStreamSynchronize(s));
         float ms = 0;
@@ -232,21 +240,54 @@ static MoveLoopResult move_loop(const DevGraph &g, const Classes &cl, MoveBuffer
     return r;
 }
 
-// Allocate the move state for a graph of n vertices (C, Sigma, size, act and,
-// for frozen-state sweeps, their next copies).
-static void alloc_move_state(MoveBuffers &mb, uint32_t n, bool sync) {
+// Allocate the move state for a graph of n vertices.
+static void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.C = arena().get<uint32_t>(n);
     mb.Sigma = arena().get<double>(n);
     mb.size = arena().get<uint32_t>(n);
     mb.act = arena().get<uint8_t>(n);
-    if (sync) {
-        mb.C2 = arena().get<uint32_t>(n);
-        mb.Sigma2 = arena().get<double>(n);
-        mb.size2 = arena().get<uint32_t>(n);
-        mb.act2 = arena().get<uint8_t>(n);
-    }
+    mb.mv_vtx = arena().get<uint32_t>(n);
+    mb.mv_cmt = arena().get<uint32_t>(n);
+    mb.mv_cnt = arena().get<uint32_t>(1);
     mb.m_dev = arena().get<double>(1);
     mb.ctr = arena().get<MoveCounters>(1);
+}
+
+static void alloc_features(MoveBuffers &mb, uint32_t n) {
+    mb.feat_kept = arena().get<float>(n);
+    mb.feat_gain = arena().get<float>(n);
+    mb.moved_last = arena().get<uint8_t>(n);
+}
+
+__global__ void k_init_features(float *kept, float *gain, uint8_t *moved, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        kept[i] = 0.0f;
+        gain[i] = 1.0f;
+        moved[i] = 1;
+    }
+}
+
+__global__ void k_max_double(const double *x, uint32_t n, unsigned long long *out) {
+    unsigned long long mx = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        mx = max(mx, (unsigned long long)__double_as_longlong(x[i]));  // x >= 0: bits order as values
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+static double max_value(const double *x, uint32_t n, cudaStream_t s) {
+    size_t mk = arena().mark();
+    unsigned long long *d = arena().get<unsigned long long>(1);
+    GSP_CUDA(cudaMemsetAsync(d, 0, sizeof(*d), s));
+    k_max_double<<<grid_for(n, 256), 256, 0, s>>>(x, n, d);
+    GSP_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    GSP_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    double v;
+    memcpy(&v, &h, sizeof(v));
+    return v;
 }
 
 static void alloc_pool(MoveBuffers &mb, const Classes &cl) {
@@ -273,27 +314,43 @@ struct Timer {
     }
 };
 
+struct TraceSpec {
+    float *x = nullptr;
+    uint8_t *y = nullptr;
+    uint32_t cap = 0, every = 1;
+    uint32_t *cnt = nullptr;  // device counter
+};
+
 void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, double *modularity_out,
-                 gsp_stats *st, cudaStream_t s) {
+                 gsp_stats *st, cudaStream_t s, const TraceSpec *trace = nullptr) {
     g_events.reset();
     const uint32_t n0 = g0.n;
     const bool sync = o.move == GSP_MOVE_SYNC;
+    const int W = sync ? o.waves : 1;
     const bool fp64 = o.precision == GSP_PREC_FP64;
-    const bool learned = o.prune == GSP_PRUNE_LEARNED && o.mlp_params;
+    PruneCtx pr;
+    pr.learned = o.prune == GSP_PRUNE_LEARNED && o.mlp_params && !trace;
+    pr.full_every = o.full_sweep_every;
+    pr.threshold = o.prune_threshold;
+    const bool features = pr.learned || trace;
     gsp_stats local;
     memset(&local, 0, sizeof(local));
     Timer total(s), t(s);
 
     MoveBuffers mb;
-    alloc_move_state(mb, n0, sync);
+    alloc_move_state(mb, n0);
     double *K = arena().get<double>(n0);
     uint32_t *labels = arena().get<uint32_t>(n0);
     uint32_t *Cd = arena().get<uint32_t>(n0);
     mb.K = K;
     mb.mlp = static_cast<const float *>(o.mlp_params);
-    if (learned) {
-        mb.feat_dq = arena().get<float>(n0);
-        mb.moved_last = arena().get<uint8_t>(n0);
+    if (features) alloc_features(mb, n0);
+    if (trace) {
+        mb.trace_x = trace->x;
+        mb.trace_y = trace->y;
+        mb.trace_cnt = trace->cnt;
+        mb.trace_cap = trace->cap;
+        mb.trace_every = trace->every;
     }
     // ping-pong buffers for the aggregated graphs (float64 weights)
     uint64_t *goff[2];
@@ -322,14 +379,19 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         k_fill_u32<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
         GSP_CHECK_LAUNCH();
         GSP_CUDA(cudaMemsetAsync(mb.act, 1, nv, s));
+        if (features) {
+            k_init_features<<<grid_for(nv, 256), 256, 0, s>>>(mb.feat_kept, mb.feat_gain, mb.moved_last, nv);
+            GSP_CHECK_LAUNCH();
+            mb.max_logk = (float)log1p(max_value(K, nv, s));
+            if (!(mb.max_logk > 0.0f)) mb.max_logk = 1.0f;
+            mb.trace_salt = 0x85EBCA6Bu * (uint32_t)(lp + 1);
+        }
         Classes cl;
-        classify_vertices(cur, cl, s);
+        classify_vertices(cur, cl, W, s);
         alloc_pool(mb, cl);
         float ms_other = t.lap();
         MoveLoopResult mr{0, 0, 0, 0, 0, 0.0, 0.0f};
-        if (m > 0.0)
-            mr = move_loop(cur, cl, mb, tau, o.max_iterations, sync, fp64, o.singleton_rule != 0, learned,
-                           o.full_sweep_every, s);
+        if (m > 0.0) mr = move_loop(cur, cl, mb, tau, o.max_iterations, sync, fp64, o.singleton_rule != 0, pr, s);
         int li = mr.iterations;
         Cp = mb.C;
         float ms_move = t.lap();
@@ -378,7 +440,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     lookup(n0, membership, Cp, s);
     if (o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_LAST) {
         Classes cl;
-        classify_vertices(g0, cl, s);
+        classify_vertices(g0, cl, 1, s);
         split_labels(g0, cl, membership, o.split, labels, s);
         GSP_CUDA(cudaMemcpyAsync(membership, labels, sizeof(uint32_t) * n0, cudaMemcpyDeviceToDevice, s));
     }
@@ -435,6 +497,8 @@ static void check_opts(const gsp_opts &o) {
     GSP_REQUIRE(o.split >= GSP_SPLIT_NONE && o.split <= GSP_SPLIT_BFS, "unknown split mode");
     GSP_REQUIRE(o.split_when == GSP_SPLIT_PASS || o.split_when == GSP_SPLIT_LAST, "unknown split_when");
     GSP_REQUIRE(o.move == GSP_MOVE_ASYNC || o.move == GSP_MOVE_SYNC, "unknown move mode");
+    GSP_REQUIRE(o.waves >= 1 && o.waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
+    GSP_REQUIRE(o.prune_threshold >= 0.0f && o.prune_threshold <= 1.0f, "prune_threshold must be in [0, 1]");
     GSP_REQUIRE(o.precision == GSP_PREC_MIXED || o.precision == GSP_PREC_FP64, "unknown precision");
     GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS || o.prune == GSP_PRUNE_LEARNED, "unknown prune mode");
     GSP_REQUIRE(o.prune != GSP_PRUNE_LEARNED || o.mlp_params != nullptr, "learned pruning needs mlp_params");
@@ -452,12 +516,14 @@ void gsp_default_opts(gsp_opts *o) {
     o->aggregation_tolerance = 0.8;
     o->split = GSP_SPLIT_BFS;
     o->split_when = GSP_SPLIT_PASS;
-    o->move = GSP_MOVE_ASYNC;
+    o->move = GSP_MOVE_SYNC;
+    o->waves = 16;
     o->precision = GSP_PREC_MIXED;
     o->singleton_rule = 1;
     o->prune = GSP_PRUNE_FLAGS;
     o->mlp_params = nullptr;
     o->full_sweep_every = 4;
+    o->prune_threshold = 0.5f;
     o->stream = nullptr;
 }
 
@@ -558,33 +624,27 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
     arena().reset();
     check_ids(C, n, n, "membership", s);
     if (nnz) check_ids(targets, (uint32_t)std::min<uint64_t>(nnz, 0xFFFFFFFFu), n, "targets", s);
+    // one frozen-state wave over all vertices; decisions go to `choice`,
+    // nothing is applied (C and Sigma are only read)
     MoveBuffers mb;
-    mb.C = const_cast<uint32_t *>(C);
-    mb.C2 = choice;
+    alloc_move_state(mb, n);
     mb.K = K;
-    mb.Sigma = const_cast<double *>(Sigma);
-    mb.Sigma2 = arena().get<double>(n);
-    mb.size = arena().get<uint32_t>(n);
-    mb.size2 = arena().get<uint32_t>(n);
-    mb.act = arena().get<uint8_t>(n);
-    mb.act2 = arena().get<uint8_t>(n);
-    mb.m_dev = arena().get<double>(1);
-    mb.ctr = arena().get<MoveCounters>(1);
+    mb.choice = choice;
+    GSP_CUDA(cudaMemcpyAsync(mb.C, C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    GSP_CUDA(cudaMemcpyAsync(mb.Sigma, Sigma, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     GSP_CUDA(cudaMemcpyAsync(mb.m_dev, &m, sizeof(double), cudaMemcpyHostToDevice, s));
     GSP_CUDA(cudaMemcpyAsync(choice, C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
-    GSP_CUDA(cudaMemcpyAsync(mb.Sigma2, Sigma, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     GSP_CUDA(cudaMemsetAsync(mb.size, 0, sizeof(uint32_t) * n, s));
     k_community_sizes<<<grid_for(n, 256), 256, 0, s>>>(C, n, mb.size);
     GSP_CHECK_LAUNCH();
-    GSP_CUDA(cudaMemcpyAsync(mb.size2, mb.size, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     if (active) GSP_CUDA(cudaMemcpyAsync(mb.act, active, n, cudaMemcpyDeviceToDevice, s));
     else GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
-    GSP_CUDA(cudaMemsetAsync(mb.act2, 0, n, s));
     GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
+    GSP_CUDA(cudaMemsetAsync(mb.mv_cnt, 0, sizeof(uint32_t), s));
     Classes cl;
-    classify_vertices(g, cl, s);
+    classify_vertices(g, cl, 1, s);
     alloc_pool(mb, cl);
-    move_sweep(g, cl, mb, true, precision == GSP_PREC_FP64, singleton_rule != 0, false, s);
+    move_wave(g, cl, mb, 0, true, precision == GSP_PREC_FP64, singleton_rule != 0, false, 0, 1, s);
     MoveCounters h;
     GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
     GSP_CUDA(cudaStreamSynchronize(s));
@@ -595,13 +655,14 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
 
 gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
                           uint64_t nnz, uint32_t *C, const double *K, double *Sigma, double m, double tolerance,
-                          int max_iterations, int move, int precision, int singleton_rule, int *iterations_host,
-                          void *stream) {
+                          int max_iterations, int move, int waves, int precision, int singleton_rule,
+                          int *iterations_host, void *stream) {
     GSP_API_BEGIN
     DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
     GSP_REQUIRE(C && K && Sigma, "C, K and Sigma must not be NULL");
     GSP_REQUIRE(m > 0.0 && max_iterations >= 1, "m must be > 0 and max_iterations >= 1");
     GSP_REQUIRE(move == GSP_MOVE_ASYNC || move == GSP_MOVE_SYNC, "unknown move mode");
+    GSP_REQUIRE(waves >= 1 && waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
     GSP_REQUIRE(precision == GSP_PREC_MIXED || precision == GSP_PREC_FP64, "unknown precision");
     cudaStream_t s = S(stream);
     arena().reset();
@@ -609,7 +670,7 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
     check_ids(C, n, n, "membership", s);
     bool sync = move == GSP_MOVE_SYNC;
     MoveBuffers mb;
-    alloc_move_state(mb, n, sync);
+    alloc_move_state(mb, n);
     mb.K = K;
     GSP_CUDA(cudaMemcpyAsync(mb.m_dev, &m, sizeof(double), cudaMemcpyHostToDevice, s));
     GSP_CUDA(cudaMemcpyAsync(mb.C, C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
@@ -619,14 +680,45 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
     GSP_CHECK_LAUNCH();
     GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
     Classes cl;
-    classify_vertices(g, cl, s);
+    classify_vertices(g, cl, sync ? waves : 1, s);
     alloc_pool(mb, cl);
+    PruneCtx pr;
     MoveLoopResult r = move_loop(g, cl, mb, tolerance, max_iterations, sync, precision == GSP_PREC_FP64,
-                                 singleton_rule != 0, false, 0, s);
+                                 singleton_rule != 0, pr, s);
     GSP_CUDA(cudaMemcpyAsync(C, mb.C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     GSP_CUDA(cudaMemcpyAsync(Sigma, mb.Sigma, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     GSP_CUDA(cudaStreamSynchronize(s));
     if (iterations_host) *iterations_host = r.iterations;
+    GSP_API_END
+}
+
+gsp_status gsp_louvain_trace(const uint64_t *offsets, const uint32_t *targets, const float *weights, uint32_t n,
+                             uint64_t nnz, const gsp_opts *opts, float *features, uint8_t *labels,
+                             uint32_t capacity, uint32_t sample_every, uint32_t *rows_host) {
+    GSP_API_BEGIN
+    gsp_opts o;
+    if (opts) o = *opts;
+    else gsp_default_opts(&o);
+    o.prune = GSP_PRUNE_FLAGS;
+    check_opts(o);
+    GSP_REQUIRE(features && labels && capacity > 0 && sample_every >= 1, "invalid trace buffers");
+    DevGraph g = make_graph(offsets, targets, weights, GSP_W_F32, n, nnz);
+    cudaStream_t s = S(o.stream);
+    arena().reset();
+    check_graph(offsets, targets, weights, n, nnz, s);
+    uint32_t *membership = arena().get<uint32_t>(n);
+    TraceSpec tr;
+    tr.x = features;
+    tr.y = labels;
+    tr.cap = capacity;
+    tr.every = sample_every;
+    tr.cnt = arena().get<uint32_t>(1);
+    GSP_CUDA(cudaMemsetAsync(tr.cnt, 0, sizeof(uint32_t), s));
+    louvain_run(g, o, membership, nullptr, nullptr, s, &tr);
+    uint32_t rows = 0;
+    GSP_CUDA(cudaMemcpyAsync(&rows, tr.cnt, sizeof(rows), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    if (rows_host) *rows_host = std::min(rows, capacity);
     GSP_API_END
 }
 
@@ -641,7 +733,7 @@ gsp_status gsp_split(const uint64_t *offsets, const uint32_t *targets, uint32_t 
     arena().reset();
     check_ids(C, n, n, "membership", s);
     Classes cl;
-    classify_vertices(g, cl, s);
+    classify_vertices(g, cl, 1, s);
     split_labels(g, cl, C, mode, labels, s);
     if (k_host) {
         uint32_t *tmp = arena().get<uint32_t>(n);

@@ -13,22 +13,29 @@ struct DevGraph {
     int wt = GSP_W_F32;
 };
 
-// Degree classes of a vertex (or community) list.  Small degrees are served
-// by groups of G lanes with a shared-memory table, mid degrees by one block
-// with a shared-memory table, the largest by one block with a table in a
-// global-memory pool.
+// Degree classes of a vertex list.  Small degrees are served by groups of G
+// lanes with a shared-memory table, mid degrees by one block with a
+// shared-memory table, the largest by one block with a table in a global
+// pool.  Each class is further split into W waves (vertex v in wave v mod W):
+// the list holds key = class * W + wave in increasing order.
 enum { CLS_G4 = 0, CLS_G8, CLS_G16, CLS_G32, CLS_BLOCK, CLS_HUGE, NUM_CLS };
 constexpr uint32_t CLS_MAXDEG[NUM_CLS] = {8, 16, 32, 128, 4096, 0xFFFFFFFFu};
+constexpr int MAX_WAVES = 64;
 
 struct Classes {
-    uint32_t *list = nullptr;  // vertex ids grouped by class (class c at [start[c], start[c+1]))
-    uint32_t start[NUM_CLS + 1] = {0};
-    uint64_t *pool_off = nullptr;  // huge class: hashtable slot offsets (count+1)
+    uint32_t *list = nullptr;
+    int W = 1;
+    uint32_t start[NUM_CLS * MAX_WAVES + 1] = {0};
+    uint64_t *pool_off = nullptr;  // huge class (all waves): hashtable slot offsets
     uint64_t pool_slots = 0;
+    uint32_t begin(int cls, int wave) const { return start[cls * W + wave]; }
+    uint32_t count(int cls, int wave) const { return start[cls * W + wave + 1] - start[cls * W + wave]; }
+    uint32_t cls_begin(int cls) const { return start[cls * W]; }
+    uint32_t cls_count(int cls) const { return start[(cls + 1) * W] - start[cls * W]; }
 };
 
-// Build the class lists of g's vertices (degree 0 vertices are left out).
-void classify_vertices(const DevGraph &g, Classes &cl, cudaStream_t s);
+// Build the class/wave lists of g's vertices (degree 0 vertices are left out).
+void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s);
 
 struct MoveCounters {  // device-side accumulators of one sweep
     double dq;
@@ -41,30 +48,37 @@ struct MoveCounters {  // device-side accumulators of one sweep
 };
 
 struct MoveBuffers {
-    uint32_t *C = nullptr, *C2 = nullptr;       // membership (C2: next, frozen-state sweeps)
-    double *Sigma = nullptr, *Sigma2 = nullptr;
-    uint32_t *size = nullptr, *size2 = nullptr;
-    uint8_t *act = nullptr, *act2 = nullptr;     // unprocessed flags
+    uint32_t *C = nullptr;       // membership
+    double *Sigma = nullptr;     // community totals
+    uint32_t *size = nullptr;    // community sizes (singleton rule)
+    uint8_t *act = nullptr;      // unprocessed flags
     const double *K = nullptr;
-    double *m_dev = nullptr;                     // device copy of m
+    double *m_dev = nullptr;     // device copy of m
     MoveCounters *ctr = nullptr;
-    void *pool = nullptr;                        // huge-class hashtables
+    void *pool = nullptr;        // huge-class hashtables
+    uint32_t *mv_vtx = nullptr;  // moves decided in the current wave (frozen-state mode)
+    uint32_t *mv_cmt = nullptr;
+    uint32_t *mv_cnt = nullptr;
+    uint32_t *choice = nullptr;  // optional: decision of each vertex (single-sweep API)
     // learned pruning (optional)
     const float *mlp = nullptr;
-    float *feat_dq = nullptr;     // last delta-modularity gain seen per vertex (scaled)
+    float *feat_kept = nullptr;  // K_{i->C_i} / K_i at the vertex's last visit
+    float *feat_gain = nullptr;  // scaled best gain at the last visit
     uint8_t *moved_last = nullptr;
-    float *nbr_moved = nullptr;
+    float max_logk = 1.0f;
+    // move/no-move trace rows (optional)
+    float *trace_x = nullptr;
+    uint8_t *trace_y = nullptr;
+    uint32_t *trace_cnt = nullptr;
+    uint32_t trace_cap = 0, trace_every = 1, trace_salt = 0;
 };
 
-struct SweepResult {
-    double dq;
-    uint64_t moved, vertices, edges, candidates, skipped;
-};
-
-// One sweep over the active vertices.  sync: frozen-state (reads C/Sigma/size/act,
-// writes C2/Sigma2/size2/act2, which must hold copies of C/Sigma/size and zeros).
-void move_sweep(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
-                bool learned, cudaStream_t s);
+// One wave of a sweep over the active vertices.  sync: frozen-state wave
+// (decisions go to the move list; apply_moves() applies them); otherwise
+// in-place updates as the paper's parallel loop.
+void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, bool sync, bool fp64, bool rule,
+               bool learned, int iteration, int max_iterations, cudaStream_t s);
+void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s);
 
 struct LouvainTimers;
 
@@ -92,6 +106,25 @@ void iota_u32(uint32_t *p, uint32_t n, cudaStream_t s);
 // MLP (mlp.cu)
 constexpr int MLP_IN = 6, MLP_H = 32;
 constexpr int MLP_PARAMS = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
+
+// Inputs of the learned pruning predictor for vertex i, from the state its
+// last visit left: log-degree, log-weighted-degree (normalised by the pass
+// maximum), fraction of K_i kept inside its community, last scaled gain,
+// whether it moved, and the iteration's position in the pass.
+__device__ __forceinline__ void predictor_features(uint32_t deg, double Ki, float kept, float gain, uint8_t moved,
+                                                   float max_logk, float iter_frac, float *x) {
+    x[0] = log1pf((float)deg) * (1.0f / 16.0f);
+    x[1] = log1pf((float)Ki) / max_logk;
+    x[2] = kept;
+    x[3] = gain;
+    x[4] = (float)moved;
+    x[5] = iter_frac;
+}
+
+// Learned pruning before a sweep: active vertices whose predicted move
+// probability is below threshold are marked processed (skipped).
+void mlp_prune(const DevGraph &g, MoveBuffers &mb, int iteration, int max_iterations, float threshold,
+               cudaStream_t s);
 
 __device__ __forceinline__ int ceil_log2(uint32_t x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
 

@@ -250,7 +250,7 @@ uint32_t count_disconnected(const DevGraph &g, const uint32_t *C, uint8_t *flags
     uint32_t *ncomp = arena().get<uint32_t>(g.n);
     unsigned long long *cnt = arena().get<unsigned long long>(1);
     Classes cl;
-    classify_vertices(g, cl, s);
+    classify_vertices(g, cl, 1, s);
     split_labels(g, cl, C, GSP_SPLIT_BFS, lab, s);
     GSP_CUDA(cudaMemsetAsync(ncomp, 0, sizeof(uint32_t) * g.n, s));
     GSP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));

@@ -148,6 +148,40 @@ __global__ void k_mlp_sgd(float *params, const float *__restrict__ grad, float l
         params[i] -= lr * grad[i];
 }
 
+// Learned pruning: one thread per vertex; active vertices predicted not to
+// move are marked processed and counted as skipped.
+__global__ void k_mlp_prune(const float *__restrict__ params, const uint64_t *__restrict__ off,
+                            const double *__restrict__ K, const float *__restrict__ kept,
+                            const float *__restrict__ gain, const uint8_t *__restrict__ moved, uint8_t *act, uint32_t n,
+                            float max_logk, float iter_frac, float thr, MoveCounters *ctr) {
+    __shared__ float sp[MLP_PARAMS];
+    __shared__ unsigned long long red[32];
+    load_params_bf16(params, sp);
+    unsigned long long skipped = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!act[i]) continue;
+        uint32_t deg = (uint32_t)(off[i + 1] - off[i]);
+        if (!deg) continue;
+        float x[MLP_IN];
+        predictor_features(deg, K[i], kept[i], gain[i], moved[i], max_logk, iter_frac, x);
+        if (mlp_prob(sp, x) < thr) {
+            act[i] = 0;
+            skipped++;
+        }
+    }
+    skipped = block_sum(skipped, red);
+    if (threadIdx.x == 0 && skipped) atomicAdd(&ctr->skipped, skipped);
+}
+
+void mlp_prune(const DevGraph &g, MoveBuffers &mb, int iteration, int max_iterations, float threshold,
+               cudaStream_t s) {
+    float frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
+    k_mlp_prune<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(mb.mlp, g.off, mb.K, mb.feat_kept, mb.feat_gain,
+                                                            mb.moved_last, mb.act, g.n, mb.max_logk, frac,
+                                                            threshold, mb.ctr);
+    GSP_CHECK_LAUNCH();
+}
+
 }  // namespace gsp
 
 using namespace gsp;

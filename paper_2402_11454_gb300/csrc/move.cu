@@ -5,23 +5,26 @@
 // (self-loop excluded) into an open-addressing hashtable, scores every
 // candidate with Equation 2 and takes the argmax (ties to the lowest id);
 // it moves only on a strictly positive gain.  The work is binned by degree:
-//   groups of G = 4/8/16/32 lanes per vertex, table in shared memory;
+//   groups of G = 4/8/16/32 lanes per vertex, table in shared memory (one
+//     fused launch for the four group classes);
 //   one block per vertex, table in shared memory (degree <= 4096);
 //   one block per vertex, table in a global-memory pool (larger degrees).
 // Duplicate community keys meet in the table through atomicCAS on the key and
 // atomicAdd on the value.
 //
-// Precision: FP64 evaluates Equation 2 term by term with round-to-nearest
-// intrinsics (no fused multiply-add), exactly as written, so its choices can
-// be compared with a sequential FP64 evaluation.  MIXED accumulates K_{i->c}
-// in float32 and compares the scaled score s_c = K_{i->c} - K_i * Sigma_c / 2m
-// in float32 (m * dQ_{i:d->c} = s_c - s_d with Sigma_d taken without K_i);
-// m and Sigma stay float64.
+// Parallel semantics.  Frozen-state mode (deterministic): the vertices of a
+// sweep are split into W interleaved waves (vertex i in wave i mod W); a wave
+// reads C, Sigma and the community sizes left by the earlier waves, appends
+// its moves to a list, and apply_moves() applies them (Sigma/size atomics,
+// neighbour re-marking) before the next wave.  In-place mode: the paper's
+// parallel loop as written, every move applied at once, with L2-coherent
+// loads (ld.global.cg) for values other threads update.
 //
-// Modes: SYNC reads the state of the sweep's start and writes the next state
-// (deterministic); ASYNC reads and writes one state in place, as the
-// paper's parallel loop does, with L2-coherent loads (ld.global.cg) for
-// values other threads update.
+// Precision: FP64 evaluates Equation 2 term by term with round-to-nearest
+// intrinsics (no fused multiply-add), in the order written.  MIXED accumulates
+// K_{i->c} in float32 and compares the scaled score s_c = K_{i->c} - K_i *
+// Sigma_c / 2m in float32 (m * dQ_{i:d->c} = s_c - s_d with Sigma_d taken
+// without K_i); m and Sigma stay float64.
 #include <type_traits>
 
 #include "internal.cuh"
@@ -32,30 +35,34 @@ struct MoveArgs {
     const uint64_t *off;
     const uint32_t *tgt;
     const void *w;
-    const uint32_t *C;     // read
-    uint32_t *Cw;          // write
+    uint32_t *C;
     const double *K;
-    const double *Sig;     // read
-    double *Sigw;          // write (atomics)
-    const uint32_t *size;  // read
-    uint32_t *sizew;
-    const uint8_t *act;    // read
-    uint8_t *actw;         // write (re-marking); ASYNC: same as act
+    double *Sig;
+    uint32_t *size;
+    uint8_t *act;
     const double *m;
     MoveCounters *ctr;
     int rule;
-    // learned pruning
-    const float *mlp;
-    float *feat_dq;
+    uint32_t *mv_vtx, *mv_cmt, *mv_cnt;  // frozen-state move list
+    uint32_t *choice;                    // optional per-vertex decision
+    // last-visit features for the learned predictor (optional)
+    float *feat_kept, *feat_gain;
     uint8_t *moved_last;
-    int learned;
+    // trace rows (optional): features before the visit, label = moved
+    float *trace_x;
+    uint8_t *trace_y;
+    uint32_t *trace_cnt;
+    uint32_t trace_cap, trace_every;
+    float max_logk;
+    float iter_frac;
+    uint32_t salt;
 };
 
 template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 __device__ __forceinline__ uint8_t ldcg(const uint8_t *p) {
     return (uint8_t)__ldcg(reinterpret_cast<const unsigned char *>(p));
 }
-
+// Frozen-state waves read data that no thread writes during the launch.
 template <bool SYNC, typename T> __device__ __forceinline__ T ld_state(const T *p) {
     if constexpr (SYNC) return __ldg(p);
     else return ldcg(p);
@@ -83,7 +90,7 @@ template <> struct Score<true> {
     using S = double;
     double Ki, Kid, Sd, m;
     __device__ S score(double kic, double Sc) const { return eq2(kic, Kid, Ki, Sc, Sd, m); }
-    __device__ double gain(S best) const { return best; }           // in units of Q
+    __device__ double gain(S best) const { return best; }  // in units of Q
 };
 template <> struct Score<false> {
     using S = float;
@@ -93,8 +100,7 @@ template <> struct Score<false> {
     __device__ double gain(S best) const { return (double)(best - sd) / m; }
 };
 
-template <bool F64>
-__device__ __forceinline__ Score<F64> make_score(double Ki, double kid, double Sd, double m);
+template <bool F64> __device__ __forceinline__ Score<F64> make_score(double Ki, double kid, double Sd, double m);
 template <> __device__ __forceinline__ Score<true> make_score<true>(double Ki, double kid, double Sd, double m) {
     Score<true> s;
     s.Ki = Ki; s.Kid = kid; s.Sd = Sd; s.m = m;
@@ -104,24 +110,32 @@ template <> __device__ __forceinline__ Score<false> make_score<false>(double Ki,
     Score<false> s;
     double inv2m = 0.5 / m;
     s.kif = (float)(Ki * inv2m);
-    s.sd = (float)kid - (float)(Ki * inv2m) * (float)(Sd - Ki);
+    s.sd = (float)kid - s.kif * (float)(Sd - Ki);
     s.m = m;
     return s;
 }
 
-// Decide and apply the move of i (called by one thread).
+// Decide the move of i toward c (one thread).  Frozen-state: record it in the
+// move list; in place: apply it now.  Returns whether i moves.
 template <bool SYNC>
-__device__ __forceinline__ bool apply_move(const MoveArgs &a, uint32_t i, uint32_t d, uint32_t c, double Ki) {
+__device__ __forceinline__ bool decide_move(const MoveArgs &a, uint32_t i, uint32_t d, uint32_t c, double Ki) {
     if (c == EMPTY || c == d) return false;
     if (a.rule) {
         uint32_t sd = ld_state<SYNC>(a.size + d), sc = ld_state<SYNC>(a.size + c);
         if (sd == 1 && sc == 1 && c > d) return false;
     }
-    a.Cw[i] = c;
-    atomicAdd(a.Sigw + d, -Ki);
-    atomicAdd(a.Sigw + c, Ki);
-    atomicSub(a.sizew + d, 1u);
-    atomicAdd(a.sizew + c, 1u);
+    if (a.choice) a.choice[i] = c;
+    if constexpr (SYNC) {
+        uint32_t slot = atomicAdd(a.mv_cnt, 1u);
+        a.mv_vtx[slot] = i;
+        a.mv_cmt[slot] = c;
+    } else {
+        a.C[i] = c;
+        atomicAdd(a.Sig + d, -Ki);
+        atomicAdd(a.Sig + c, Ki);
+        atomicSub(a.size + d, 1u);
+        atomicAdd(a.size + c, 1u);
+    }
     return true;
 }
 
@@ -140,45 +154,71 @@ __device__ void flush_counters(const LocalCtr &l, MoveCounters *g) {
     unsigned long long ca = block_sum<unsigned long long>(l.candidates, su);
     unsigned long long mk = block_sum<unsigned long long>(l.marked, su);
     if (threadIdx.x == 0) {
-        if (mk) atomicAdd(&g->marked, mk);
         if (dq != 0.0) atomicAdd(&g->dq, dq);
         if (mv) atomicAdd(&g->moved, mv);
         if (vx) atomicAdd(&g->vertices, vx);
         if (ed) atomicAdd(&g->edges, ed);
         if (ca) atomicAdd(&g->candidates, ca);
+        if (mk) atomicAdd(&g->marked, mk);
     }
 }
 
+__device__ __forceinline__ void vertex_features(const MoveArgs &a, uint32_t i, uint32_t deg, double Ki, float *x) {
+    predictor_features(deg, Ki, a.feat_kept[i], a.feat_gain[i], a.moved_last[i], a.max_logk, a.iter_frac, x);
+}
+
+// After a visit: record last-visit features and, for sampled visits, a trace
+// row (features before the visit, label = moved).
+__device__ __forceinline__ void record_visit(const MoveArgs &a, uint32_t i, uint32_t deg, double Ki, double kid,
+                                             double gain, double m, int moved) {
+    if (!a.feat_kept) return;
+    if (a.trace_x && (hash32(i ^ a.salt) % a.trace_every) == 0) {
+        float x[MLP_IN];
+        vertex_features(a, i, deg, Ki, x);
+        uint32_t slot = atomicAdd(a.trace_cnt, 1u);
+        if (slot < a.trace_cap) {
+#pragma unroll
+            for (int k = 0; k < MLP_IN; k++) a.trace_x[(size_t)slot * MLP_IN + k] = x[k];
+            a.trace_y[slot] = (uint8_t)moved;
+        }
+    }
+    float kept = Ki > 0.0 ? (float)(kid / Ki) : 0.0f;
+    float g = Ki > 0.0 ? (float)(gain * m / Ki) : 0.0f;
+    a.feat_kept[i] = kept;
+    a.feat_gain[i] = fminf(fmaxf(g, -1.0f), 1.0f);
+    a.moved_last[i] = (uint8_t)moved;
+}
+
 // --------------------------------------------------------------------------
-// Groups of G lanes, one vertex per group, table of up to CAP slots per group.
+// Groups of G lanes, one vertex per group, table of up to CAP slots per group
+// (slots carved out of the block's shared buffer).
 // --------------------------------------------------------------------------
 template <int G, int CAP, typename WT, bool F64, bool SYNC>
-__global__ void __launch_bounds__(256) k_move_group(MoveArgs a, const uint32_t *__restrict__ list,
-                                                    uint32_t count) {
+__device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list, uint32_t count, uint32_t lb,
+                           uint32_t nb, unsigned char *smem) {
     using V = typename std::conditional<F64, double, float>::type;
     using SC = Score<F64>;
     using S = typename SC::S;
     constexpr int NG = 256 / G;
-    __shared__ uint32_t s_keys[NG][CAP];
-    __shared__ V s_vals[NG][CAP];
     const int lane = threadIdx.x % G;
     const int grp = threadIdx.x / G;
-    const unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    uint32_t *keys = s_keys[grp];
-    V *vals = s_vals[grp];
+    const int leader = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << leader);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(smem) + grp * CAP;
+    V *vals = reinterpret_cast<V *>(smem + (size_t)NG * CAP * sizeof(uint32_t)) + grp * CAP;
     const WT *w = static_cast<const WT *>(a.w);
     const double m = *a.m;
     LocalCtr lc;
-    for (uint32_t idx = blockIdx.x * NG + grp; idx < count; idx += gridDim.x * NG) {
+    for (uint32_t idx = lb * NG + grp; idx < count; idx += nb * NG) {
         uint32_t i = list[idx];
-        // one lane reads the flag (other threads may be re-marking it) and
-        // marks the vertex processed; the group follows its decision
+        // one lane reads the flag (other threads may re-mark it) and marks
+        // the vertex processed; the group follows its decision
         int go = 0;
         if (lane == 0) {
             go = ld_state<SYNC>(a.act + i);
-            if (!SYNC && go) a.actw[i] = 0;
+            if (go) a.act[i] = 0;
         }
-        go = __shfl_sync(gmask, go, (threadIdx.x & 31) & ~(G - 1));
+        go = __shfl_sync(gmask, go, leader);
         if (!go) continue;
         uint32_t d = ld_state<SYNC>(a.C + i);
         uint64_t b = a.off[i], e = a.off[i + 1];
@@ -202,7 +242,7 @@ __global__ void __launch_bounds__(256) k_move_group(MoveArgs a, const uint32_t *
         for (int o = G / 2; o > 0; o >>= 1) kid += __shfl_xor_sync(gmask, kid, o);
         double Ki = a.K[i];
         double Sd = ld_state<SYNC>(a.Sig + d);
-        Sd = __shfl_sync(gmask, Sd, (threadIdx.x & 31) & ~(G - 1));
+        Sd = __shfl_sync(gmask, Sd, leader);
         SC sc = make_score<F64>(Ki, (double)kid, Sd, m);
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
@@ -226,19 +266,49 @@ __global__ void __launch_bounds__(256) k_move_group(MoveArgs a, const uint32_t *
         if (lane == 0) {
             lc.vertices++;
             lc.edges += deg;
-            if (gain > 0.0) mv = apply_move<SYNC>(a, i, d, bestc, Ki);
-            if (mv) { lc.moved++; lc.dq += gain; lc.marked += deg; }
+            if (gain > 0.0) mv = decide_move<SYNC>(a, i, d, bestc, Ki);
+            if (mv) { lc.moved++; lc.dq += gain; }
+            record_visit(a, i, deg, Ki, (double)kid, gain, m, mv);
         }
-        mv = __shfl_sync(gmask, mv, (threadIdx.x & 31) & ~(G - 1));
-        if (mv) {
-            for (uint64_t p = b + lane; p < e; p += G) {
-                uint32_t j = __ldg(a.tgt + p);
-                if (j != i) a.actw[j] = 1;
+        if constexpr (!SYNC) {  // in place: movers re-mark their neighbours now
+            mv = __shfl_sync(gmask, mv, leader);
+            if (mv) {
+                if (lane == 0) lc.marked += deg;
+                for (uint64_t p = b + lane; p < e; p += G) {
+                    uint32_t j = __ldg(a.tgt + p);
+                    if (j != i) a.act[j] = 1;
+                }
             }
         }
         __syncwarp(gmask);
     }
     flush_counters(lc, a.ctr);
+}
+
+struct GroupLists {
+    const uint32_t *list[4];
+    uint32_t count[4];
+    uint32_t bstart[5];  // block ranges of the four classes
+};
+
+constexpr size_t GROUP_SMEM_F64 = 2048 * (sizeof(uint32_t) + sizeof(double));
+constexpr size_t GROUP_SMEM_F32 = 2048 * (sizeof(uint32_t) + sizeof(float));
+
+template <typename WT, bool F64, bool SYNC>
+__global__ void __launch_bounds__(256) k_move_groups(MoveArgs a, GroupLists gl) {
+    __shared__ __align__(16) unsigned char smem[F64 ? GROUP_SMEM_F64 : GROUP_SMEM_F32];
+    uint32_t b = blockIdx.x;
+    if (b < gl.bstart[1])
+        group_body<4, 16, WT, F64, SYNC>(a, gl.list[0], gl.count[0], b, gl.bstart[1], smem);
+    else if (b < gl.bstart[2])
+        group_body<8, 32, WT, F64, SYNC>(a, gl.list[1], gl.count[1], b - gl.bstart[1], gl.bstart[2] - gl.bstart[1],
+                                         smem);
+    else if (b < gl.bstart[3])
+        group_body<16, 64, WT, F64, SYNC>(a, gl.list[2], gl.count[2], b - gl.bstart[2],
+                                          gl.bstart[3] - gl.bstart[2], smem);
+    else
+        group_body<32, 256, WT, F64, SYNC>(a, gl.list[3], gl.count[3], b - gl.bstart[3],
+                                           gl.bstart[4] - gl.bstart[3], smem);
 }
 
 // --------------------------------------------------------------------------
@@ -258,7 +328,8 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
     __shared__ S red_s[32];
     __shared__ uint32_t red_c[32];
     __shared__ V red_k[32];
-    __shared__ int s_mv;
+    __shared__ int s_go, s_mv;
+    __shared__ uint32_t s_d;
     __shared__ double s_Sd;
     const WT *w = static_cast<const WT *>(a.w);
     const double m = *a.m;
@@ -270,13 +341,16 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
         __syncthreads();  // previous vertex done with the table and reductions
         if (threadIdx.x == 0) {
             int go = ld_state<SYNC>(a.act + i);
-            if (!SYNC && go) a.actw[i] = 0;
-            s_mv = go;
-            if (go) s_Sd = ld_state<SYNC>(a.Sig + ld_state<SYNC>(a.C + i));
+            if (go) a.act[i] = 0;
+            s_go = go;
+            if (go) {
+                s_d = ld_state<SYNC>(a.C + i);
+                s_Sd = ld_state<SYNC>(a.Sig + s_d);
+            }
         }
         __syncthreads();
-        if (!s_mv) continue;
-        uint32_t d = ld_state<SYNC>(a.C + i);
+        if (!s_go) continue;
+        uint32_t d = s_d;
         uint64_t b = a.off[i], e = a.off[i + 1];
         uint32_t deg = (uint32_t)(e - b);
         int logcap = ceil_log2(2 * deg);
@@ -330,22 +404,61 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
                 if (better(red_s[t], red_c[t], best, bestc)) { best = red_s[t]; bestc = red_c[t]; }
             double gain = (bestc == EMPTY) ? 0.0 : sc.gain(best);
             int mv = 0;
-            if (gain > 0.0) mv = apply_move<SYNC>(a, i, d, bestc, Ki);
+            if (gain > 0.0) mv = decide_move<SYNC>(a, i, d, bestc, Ki);
             lc.vertices++;
             lc.edges += deg;
-            if (mv) { lc.moved++; lc.dq += gain; lc.marked += deg; }
+            if (mv) { lc.moved++; lc.dq += gain; }
+            record_visit(a, i, deg, Ki, (double)kid, gain, m, mv);
             s_mv = mv;
         }
         __syncthreads();
-        if (s_mv) {
+        if (!SYNC && s_mv) {
+            if (threadIdx.x == 0) lc.marked += deg;
             for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
                 uint32_t j = __ldg(a.tgt + p);
-                if (j != i) a.actw[j] = 1;
+                if (j != i) a.act[j] = 1;
             }
         }
     }
     __syncthreads();
     flush_counters(lc, a.ctr);
+}
+
+// --------------------------------------------------------------------------
+// Apply a frozen-state wave's moves: C, Sigma and size updates (float64
+// atomics of exactly representable values, so the result does not depend on
+// their order), and re-marking of the movers' neighbours.  One warp per move.
+// --------------------------------------------------------------------------
+__global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                              const uint32_t *__restrict__ mv_vtx, const uint32_t *__restrict__ mv_cmt,
+                              const uint32_t *__restrict__ mv_cnt, const double *__restrict__ K, uint32_t *C,
+                              double *Sig, uint32_t *size, uint8_t *act, MoveCounters *ctr) {
+    uint32_t cnt = *mv_cnt;
+    int lane = threadIdx.x & 31;
+    uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long marked = 0;
+    for (uint32_t t = warp; t < cnt; t += nwarps) {
+        uint32_t i = mv_vtx[t], c = mv_cmt[t];
+        uint64_t b = off[i], e = off[i + 1];
+        if (lane == 0) {
+            uint32_t d = C[i];
+            double Ki = K[i];
+            C[i] = c;
+            atomicAdd(Sig + d, -Ki);
+            atomicAdd(Sig + c, Ki);
+            atomicSub(size + d, 1u);
+            atomicAdd(size + c, 1u);
+            marked += e - b;
+        }
+        for (uint64_t p = b + lane; p < e; p += 32) {
+            uint32_t j = tgt[p];
+            if (j != i) act[j] = 1;
+        }
+    }
+    __shared__ unsigned long long red[32];
+    marked = block_sum(marked, red);
+    if (threadIdx.x == 0 && marked) atomicAdd(&ctr->marked, marked);
 }
 
 // --------------------------------------------------------------------------
@@ -360,30 +473,32 @@ __device__ __forceinline__ int class_of(uint64_t deg) {
     return CLS_HUGE;
 }
 
-__global__ void k_classify_count(const uint64_t *__restrict__ off, uint32_t n, uint32_t *counts) {
-    __shared__ uint32_t sc[NUM_CLS];
-    if (threadIdx.x < NUM_CLS) sc[threadIdx.x] = 0;
+__global__ void k_classify_count(const uint64_t *__restrict__ off, uint32_t n, int W, uint32_t *counts) {
+    __shared__ uint32_t sc[NUM_CLS * MAX_WAVES];
+    for (int t = threadIdx.x; t < NUM_CLS * W; t += blockDim.x) sc[t] = 0;
     __syncthreads();
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint64_t deg = off[v + 1] - off[v];
-        if (deg) atomicAdd(&sc[class_of(deg)], 1u);
+        if (deg) atomicAdd(&sc[class_of(deg) * W + (int)(v % (uint32_t)W)], 1u);
     }
     __syncthreads();
-    if (threadIdx.x < NUM_CLS && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
+    for (int t = threadIdx.x; t < NUM_CLS * W; t += blockDim.x)
+        if (sc[t]) atomicAdd(&counts[t], sc[t]);
 }
 
-__global__ void k_classify_fill(const uint64_t *__restrict__ off, uint32_t n, uint32_t *cursor, uint32_t *list) {
+__global__ void k_classify_fill(const uint64_t *__restrict__ off, uint32_t n, int W, uint32_t *cursor,
+                                uint32_t *list) {
     int lane = threadIdx.x & 31;
     for (uint32_t v0 = blockIdx.x * blockDim.x; v0 < n; v0 += gridDim.x * blockDim.x) {
         uint32_t v = v0 + threadIdx.x;
         uint64_t deg = (v < n) ? off[v + 1] - off[v] : 0;
-        int cls = deg ? class_of(deg) : -1;
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, cls);
+        int key = deg ? class_of(deg) * W + (int)(v % (uint32_t)W) : -1;
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
         int leader = __ffs(peers) - 1;
         uint32_t base = 0;
-        if (lane == leader && cls >= 0) base = atomicAdd(&cursor[cls], (uint32_t)__popc(peers));
+        if (lane == leader && key >= 0) base = atomicAdd(&cursor[key], (uint32_t)__popc(peers));
         base = __shfl_sync(0xFFFFFFFFu, base, leader);
-        if (cls >= 0) list[base + __popc(peers & ((1u << lane) - 1u))] = v;
+        if (key >= 0) list[base + __popc(peers & ((1u << lane) - 1u))] = v;
     }
 }
 
@@ -398,28 +513,32 @@ __global__ void k_pool_caps(const uint64_t *__restrict__ off, const uint32_t *__
     }
 }
 
-void classify_vertices(const DevGraph &g, Classes &cl, cudaStream_t s) {
-    uint32_t *counts = arena().get<uint32_t>(2 * NUM_CLS);
-    GSP_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * NUM_CLS, s));
+void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s) {
+    GSP_REQUIRE(waves >= 1 && waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
+    const int W = waves;
+    const int NK = NUM_CLS * W;
+    cl.W = W;
+    uint32_t *counts = arena().get<uint32_t>(2 * NK);
+    GSP_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * NK, s));
     unsigned grid = grid_for(g.n, 256, 152 * 8);
-    k_classify_count<<<grid, 256, 0, s>>>(g.off, g.n, counts);
+    k_classify_count<<<grid, 256, 0, s>>>(g.off, g.n, W, counts);
     GSP_CHECK_LAUNCH();
-    uint32_t h[NUM_CLS];
-    GSP_CUDA(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
+    uint32_t h[NUM_CLS * MAX_WAVES];
+    GSP_CUDA(cudaMemcpyAsync(h, counts, sizeof(uint32_t) * NK, cudaMemcpyDeviceToHost, s));
     GSP_CUDA(cudaStreamSynchronize(s));
     cl.start[0] = 0;
-    for (int c = 0; c < NUM_CLS; c++) cl.start[c + 1] = cl.start[c] + h[c];
-    uint32_t *cursor = counts + NUM_CLS;
-    GSP_CUDA(cudaMemcpyAsync(cursor, cl.start, sizeof(uint32_t) * NUM_CLS, cudaMemcpyHostToDevice, s));
-    cl.list = arena().get<uint32_t>(cl.start[NUM_CLS] + 1);
-    k_classify_fill<<<grid, 256, 0, s>>>(g.off, g.n, cursor, cl.list);
+    for (int k = 0; k < NK; k++) cl.start[k + 1] = cl.start[k] + h[k];
+    uint32_t *cursor = counts + NK;
+    GSP_CUDA(cudaMemcpyAsync(cursor, cl.start, sizeof(uint32_t) * NK, cudaMemcpyHostToDevice, s));
+    cl.list = arena().get<uint32_t>(cl.start[NK] + 1);
+    k_classify_fill<<<grid, 256, 0, s>>>(g.off, g.n, W, cursor, cl.list);
     GSP_CHECK_LAUNCH();
-    uint32_t nh = cl.start[CLS_HUGE + 1] - cl.start[CLS_HUGE];
+    uint32_t nh = cl.cls_count(CLS_HUGE);
     cl.pool_off = arena().get<uint64_t>(nh + 1);
     cl.pool_slots = 0;
     if (nh) {
         uint64_t *caps = arena().get<uint64_t>(nh);
-        k_pool_caps<<<grid_for(nh, 256), 256, 0, s>>>(g.off, cl.list + cl.start[CLS_HUGE], nh, caps);
+        k_pool_caps<<<grid_for(nh, 256), 256, 0, s>>>(g.off, cl.list + cl.cls_begin(CLS_HUGE), nh, caps);
         GSP_CHECK_LAUNCH();
         exclusive_scan_u64(caps, cl.pool_off, nh, s);
         GSP_CUDA(cudaMemcpyAsync(&cl.pool_slots, cl.pool_off + nh, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -428,35 +547,28 @@ void classify_vertices(const DevGraph &g, Classes &cl, cudaStream_t s) {
 }
 
 // --------------------------------------------------------------------------
-// Host launcher for one sweep
+// Host launchers
 // --------------------------------------------------------------------------
 template <typename WT, bool F64, bool SYNC>
-static void launch_sweep(const Classes &cl, const MoveArgs &a, cudaStream_t s) {
-    auto cnt = [&](int c) { return cl.start[c + 1] - cl.start[c]; };
-    auto lst = [&](int c) { return cl.list + cl.start[c]; };
-    const unsigned maxg = 152 * 8;
-    if (cnt(CLS_G4)) {
-        k_move_group<4, 16, WT, F64, SYNC><<<grid_for((uint64_t)cnt(CLS_G4) * 4, 256, maxg), 256, 0, s>>>(
-            a, lst(CLS_G4), cnt(CLS_G4));
+static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t *pool_keys, void *pool_vals,
+                        cudaStream_t s) {
+    using V = typename std::conditional<F64, double, float>::type;
+    GroupLists gl;
+    const int G[4] = {4, 8, 16, 32};
+    uint32_t blocks = 0;
+    for (int c = 0; c < 4; c++) {
+        gl.list[c] = cl.list + cl.begin(c, wave);
+        gl.count[c] = cl.count(c, wave);
+        gl.bstart[c] = blocks;
+        if (gl.count[c]) blocks += grid_for((uint64_t)gl.count[c] * G[c], 256, 152 * 8);
+    }
+    gl.bstart[4] = blocks;
+    if (blocks) {
+        k_move_groups<WT, F64, SYNC><<<blocks, 256, 0, s>>>(a, gl);
         GSP_CHECK_LAUNCH();
     }
-    if (cnt(CLS_G8)) {
-        k_move_group<8, 32, WT, F64, SYNC><<<grid_for((uint64_t)cnt(CLS_G8) * 8, 256, maxg), 256, 0, s>>>(
-            a, lst(CLS_G8), cnt(CLS_G8));
-        GSP_CHECK_LAUNCH();
-    }
-    if (cnt(CLS_G16)) {
-        k_move_group<16, 64, WT, F64, SYNC><<<grid_for((uint64_t)cnt(CLS_G16) * 16, 256, maxg), 256, 0, s>>>(
-            a, lst(CLS_G16), cnt(CLS_G16));
-        GSP_CHECK_LAUNCH();
-    }
-    if (cnt(CLS_G32)) {
-        k_move_group<32, 256, WT, F64, SYNC><<<grid_for((uint64_t)cnt(CLS_G32) * 32, 256, maxg), 256, 0, s>>>(
-            a, lst(CLS_G32), cnt(CLS_G32));
-        GSP_CHECK_LAUNCH();
-    }
-    if (cnt(CLS_BLOCK)) {
-        using V = typename std::conditional<F64, double, float>::type;
+    uint32_t nb = cl.count(CLS_BLOCK, wave);
+    if (nb) {
         constexpr int CAP = 8192;
         constexpr size_t smem = (size_t)CAP * (sizeof(uint32_t) + sizeof(V));
         static bool attr = false;
@@ -465,58 +577,66 @@ static void launch_sweep(const Classes &cl, const MoveArgs &a, cudaStream_t s) {
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr = true;
         }
-        k_move_block<CAP, WT, F64, SYNC><<<grid_for(cnt(CLS_BLOCK), 1, 152 * 2), 256, smem, s>>>(
-            a, lst(CLS_BLOCK), cnt(CLS_BLOCK), nullptr, nullptr, nullptr);
+        k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, 152 * 2), 256, smem, s>>>(
+            a, cl.list + cl.begin(CLS_BLOCK, wave), nb, nullptr, nullptr, nullptr);
+        GSP_CHECK_LAUNCH();
+    }
+    uint32_t nh = cl.count(CLS_HUGE, wave);
+    if (nh) {
+        uint32_t rel = cl.begin(CLS_HUGE, wave) - cl.cls_begin(CLS_HUGE);
+        k_move_block<0, WT, F64, SYNC><<<grid_for(nh, 1, 152 * 4), 256, 0, s>>>(
+            a, cl.list + cl.begin(CLS_HUGE, wave), nh, cl.pool_off + rel, pool_keys, pool_vals);
         GSP_CHECK_LAUNCH();
     }
 }
 
-template <typename WT, bool F64, bool SYNC>
-static void launch_huge(const Classes &cl, const MoveArgs &a, uint32_t *pool_keys, void *pool_vals, cudaStream_t s) {
-    uint32_t nh = cl.start[CLS_HUGE + 1] - cl.start[CLS_HUGE];
-    if (!nh) return;
-    k_move_block<0, WT, F64, SYNC><<<grid_for(nh, 1, 152 * 4), 256, 0, s>>>(
-        a, cl.list + cl.start[CLS_HUGE], nh, cl.pool_off, pool_keys, pool_vals);
-    GSP_CHECK_LAUNCH();
-}
-
-void move_sweep(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
-                bool learned, cudaStream_t s) {
+void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, bool sync, bool fp64, bool rule,
+               bool learned, int iteration, int max_iterations, cudaStream_t s) {
+    (void)learned;
     MoveArgs a;
     a.off = g.off;
     a.tgt = g.tgt;
     a.w = g.w;
     a.C = mb.C;
-    a.Cw = sync ? mb.C2 : mb.C;
     a.K = mb.K;
     a.Sig = mb.Sigma;
-    a.Sigw = sync ? mb.Sigma2 : mb.Sigma;
     a.size = mb.size;
-    a.sizew = sync ? mb.size2 : mb.size;
     a.act = mb.act;
-    a.actw = sync ? mb.act2 : mb.act;
     a.m = mb.m_dev;
     a.ctr = mb.ctr;
     a.rule = rule ? 1 : 0;
-    a.mlp = mb.mlp;
-    a.feat_dq = mb.feat_dq;
+    a.mv_vtx = mb.mv_vtx;
+    a.mv_cmt = mb.mv_cmt;
+    a.mv_cnt = mb.mv_cnt;
+    a.choice = mb.choice;
+    a.feat_kept = mb.feat_kept;
+    a.feat_gain = mb.feat_gain;
     a.moved_last = mb.moved_last;
-    a.learned = learned ? 1 : 0;
+    a.trace_x = mb.trace_x;
+    a.trace_y = mb.trace_y;
+    a.trace_cnt = mb.trace_cnt;
+    a.trace_cap = mb.trace_cap;
+    a.trace_every = mb.trace_every ? mb.trace_every : 1;
+    a.max_logk = mb.max_logk;
+    a.iter_frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
+    a.salt = (uint32_t)(iteration * 0x9E3779B9u + mb.trace_salt);
     uint32_t *pool_keys = static_cast<uint32_t *>(mb.pool);
     void *pool_vals = pool_keys ? static_cast<void *>(pool_keys + align_up(cl.pool_slots, 64)) : nullptr;
-#define GSP_SWEEP(WT, F64, SYNC)                                   \
-    do {                                                           \
-        launch_sweep<WT, F64, SYNC>(cl, a, s);                     \
-        launch_huge<WT, F64, SYNC>(cl, a, pool_keys, pool_vals, s); \
-    } while (0)
+#define GSP_WAVE(WT, F64, SYNC) launch_wave<WT, F64, SYNC>(cl, a, wave, pool_keys, pool_vals, s)
     if (g.wt == GSP_W_F32) {
-        if (fp64) { if (sync) GSP_SWEEP(float, true, true); else GSP_SWEEP(float, true, false); }
-        else { if (sync) GSP_SWEEP(float, false, true); else GSP_SWEEP(float, false, false); }
+        if (fp64) { if (sync) GSP_WAVE(float, true, true); else GSP_WAVE(float, true, false); }
+        else { if (sync) GSP_WAVE(float, false, true); else GSP_WAVE(float, false, false); }
     } else {
-        if (fp64) { if (sync) GSP_SWEEP(double, true, true); else GSP_SWEEP(double, true, false); }
-        else { if (sync) GSP_SWEEP(double, false, true); else GSP_SWEEP(double, false, false); }
+        if (fp64) { if (sync) GSP_WAVE(double, true, true); else GSP_WAVE(double, true, false); }
+        else { if (sync) GSP_WAVE(double, false, true); else GSP_WAVE(double, false, false); }
     }
-#undef GSP_SWEEP
+#undef GSP_WAVE
+}
+
+void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s) {
+    k_apply_moves<<<grid_for((uint64_t)n_hint * 32, 256, 152 * 8), 256, 0, s>>>(
+        g.off, g.tgt, mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C, mb.Sigma, mb.size, mb.act, mb.ctr);
+    GSP_CHECK_LAUNCH();
 }
 
 }  // namespace gsp

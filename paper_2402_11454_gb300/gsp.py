@@ -59,9 +59,9 @@ def _graph(off, tgt, w=None):
 
 
 def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=10.0,
-              aggregation_tolerance=0.8, split="bfs", split_when="pass", move="async",
+              aggregation_tolerance=0.8, split="bfs", split_when="pass", move="sync", waves=16,
               precision="mixed", singleton_rule=True, prune="flags", mlp_params=None,
-              full_sweep_every=4, stream=None):
+              full_sweep_every=4, prune_threshold=0.5, stream=None):
     o = GspOpts()
     _lib.load().gsp_default_opts(ctypes.byref(o))
     o.max_passes = max_passes
@@ -72,11 +72,13 @@ def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=1
     o.split = SPLIT[split]
     o.split_when = SPLIT_WHEN[split_when]
     o.move = MOVE[move]
+    o.waves = waves
     o.precision = PRECISION[precision]
     o.singleton_rule = int(bool(singleton_rule))
     o.prune = PRUNE[prune]
     o.mlp_params = None if mlp_params is None else _cuda(mlp_params, torch.float32, "mlp_params").data_ptr()
     o.full_sweep_every = full_sweep_every
+    o.prune_threshold = prune_threshold
     o.stream = _stream(stream).value
     return o
 
@@ -178,15 +180,28 @@ def move_sweep(offsets, targets, weights, C, K, Sigma, m, active=None, precision
 
 
 def local_move(offsets, targets, weights, C, K, Sigma, m, tolerance=1e-2, max_iterations=20,
-               move="sync", precision="fp64", singleton_rule=True, stream=None):
+               move="sync", waves=16, precision="fp64", singleton_rule=True, stream=None):
     """louvainMove (Algorithm 4); C and Sigma are updated in place; returns l_i."""
     n, nnz = _graph(offsets, targets, weights)
     it = ctypes.c_int()
     check(_lib.load().gsp_local_move(_p(offsets), _p(targets), _p(weights), _wt(weights), n, nnz, _p(C),
-                                     _p(K), _p(Sigma), m, tolerance, max_iterations, MOVE[move],
+                                     _p(K), _p(Sigma), m, tolerance, max_iterations, MOVE[move], waves,
                                      PRECISION[precision], int(bool(singleton_rule)), ctypes.byref(it),
                                      _stream(stream)))
     return it.value
+
+
+def louvain_trace(offsets, targets, weights, capacity, sample_every=8, **kw):
+    """Run the plain method and record move/no-move trace rows:
+    (features [rows, 6] float32, labels [rows] uint8)."""
+    n, nnz = _graph(offsets, targets, weights)
+    o = make_opts(**kw)
+    x = torch.empty((capacity, 6), dtype=torch.float32, device=offsets.device)
+    y = torch.empty(capacity, dtype=torch.uint8, device=offsets.device)
+    rows = ctypes.c_uint32()
+    check(_lib.load().gsp_louvain_trace(_p(offsets), _p(targets), _p(weights), n, nnz, ctypes.byref(o),
+                                        _p(x), _p(y), capacity, sample_every, ctypes.byref(rows)))
+    return x[:rows.value], y[:rows.value]
 
 
 def split(offsets, targets, C, mode="bfs", stream=None):
@@ -265,19 +280,24 @@ def mlp_sgd(params, grad, lr, stream=None):
 
 
 # ------------------------------------------------------------ generators
+class _DevArray:
+    """Wraps a device pointer for torch.as_tensor (no copy)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3}
+
+
 def _take_graph(g):
     """Copy the library-owned generated CSR into torch tensors."""
     n, nnz = g.n, g.nnz
-    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
-    tgt = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
-    w = torch.empty(max(nnz, 1), dtype=torch.float32, device="cuda")
-    cudart = torch.cuda.cudart()
     torch.cuda.synchronize()
-    for dst, src, nb in ((off, g.offsets, 8 * (n + 1)), (tgt, g.targets, 4 * nnz), (w, g.weights, 4 * nnz)):
-        if nb:
-            check(0 if cudart.cudaMemcpy(dst.data_ptr(), src, nb, 3) == 0 else -3)
+    off = torch.as_tensor(_DevArray(g.offsets, n + 1, "<i8"), device="cuda").clone()
+    tgt = torch.as_tensor(_DevArray(g.targets, max(nnz, 1), "<i4"), device="cuda")[:nnz].clone()
+    w = torch.as_tensor(_DevArray(g.weights, max(nnz, 1), "<f4"), device="cuda")[:nnz].clone()
+    torch.cuda.synchronize()
     _lib.load().gsp_release_graph()
-    return off, tgt[:nnz], w[:nnz]
+    return off, tgt, w
 
 
 def gen_rmat(scale, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=2):

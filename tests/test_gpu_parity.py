@@ -27,8 +27,9 @@ def gsp():
 def dev(off, tgt, w=None):
     d_off = torch.from_numpy(np.asarray(off).astype(np.int64)).cuda()
     d_tgt = torch.from_numpy(np.asarray(tgt).astype(np.int32)).cuda()
-    d_w = None if w is None else torch.from_numpy(np.asarray(w)).cuda()
-    return d_off, d_tgt, d_w
+    if w is None:
+        return d_off, d_tgt
+    return d_off, d_tgt, torch.from_numpy(np.asarray(w)).cuda()
 
 
 def host(t):
@@ -166,18 +167,20 @@ def test_sync_sweep_mixed_precision_close(gsp, name):
     assert len(diff) <= max(5, 0.001 * n)
 
 
-@pytest.mark.parametrize("name", ["planted", "grid"])
-def test_sync_local_move_fp64_matches_oracle(gsp, name):
+@pytest.mark.parametrize("name", ["planted", "grid", "rmat14"])
+@pytest.mark.parametrize("waves", [1, 16])
+def test_sync_local_move_fp64_matches_oracle(gsp, name, waves):
     off, tgt, w = GRAPHS[name]
     n = len(off) - 1
     g = og(name)
     K, m = oracle.vertex_weights(g)
     C0 = np.arange(n, dtype=np.uint32)
-    Co, So, li_o, _ = oracle.move(g, C0, K, K.copy(), m, tau=1e-2, max_iterations=20, sync=True)
+    Co, So, li_o, _ = oracle.move(g, C0, K, K.copy(), m, tau=1e-2, max_iterations=20, sync=True,
+                                  waves=waves)
     dC = torch.from_numpy(C0.astype(np.int32)).cuda()
     dS = torch.from_numpy(K.copy()).cuda()
     li = gsp.local_move(*dev(off, tgt, w), dC, torch.from_numpy(K).cuda(), dS, m, tolerance=1e-2,
-                        max_iterations=20, move="sync", precision="fp64")
+                        max_iterations=20, move="sync", waves=waves, precision="fp64")
     assert li == li_o
     assert np.array_equal(host(dC).astype(np.uint32), Co)
     assert np.array_equal(host(dS), So)
@@ -256,16 +259,18 @@ def test_aggregate_of_aggregate_f64_weights(gsp):
 
 # ------------------------------------------------------------- full runs
 @pytest.mark.parametrize("split", ["bfs", "lp", "lpp"])
-def test_louvain_planted_against_oracle(gsp, split):
+@pytest.mark.parametrize("move", ["sync", "async"])
+def test_louvain_planted_against_oracle(gsp, split, move):
     off, tgt, w = GRAPHS["planted"]
     g = og("planted")
-    C, q, st = gsp.louvain(*dev(off, tgt, w), split=split)
+    C, q, st = gsp.louvain(*dev(off, tgt, w), split=split, move=move)
     C = host(C).astype(np.uint32)
     q_re = oracle.modularity(g, C)
     assert q == pytest.approx(q_re, rel=1e-9)
     assert oracle.disconnected(g, C)[0] == 0
     _, ost = oracle.louvain(g, oracle.LouvainOptions(split=split, sync=False))
-    assert q >= ost["modularity"] - 0.002
+    if move == "sync":  # the paper's in-place loop on a GPU is timing-dependent
+        assert q >= ost["modularity"] - 0.002
     first = np.unique(C, return_index=True)[1]
     assert np.all(np.diff(first) > 0) and C.max() + 1 == st["final_communities"]
 
@@ -287,7 +292,8 @@ def test_louvain_sync_fp64_equals_oracle(gsp, name):
 def test_louvain_invariants(gsp, name):
     off, tgt, w = GRAPHS[name]
     g = og(name)
-    for kw in ({}, {"split_when": "last"}, {"precision": "fp64"}, {"split": "none"}):
+    for kw in ({}, {"split_when": "last"}, {"precision": "fp64"}, {"split": "none"}, {"move": "async"},
+               {"waves": 1}, {"split": "lp"}):
         C, q, st = gsp.louvain(*dev(off, tgt, w), **kw)
         C = host(C).astype(np.uint32)
         assert -0.5 <= q <= 1.0

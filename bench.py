@@ -195,7 +195,8 @@ def main():
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--split", default="bfs")
-    ap.add_argument("--move", default="async")
+    ap.add_argument("--move", default="sync")
+    ap.add_argument("--waves", type=int, default=16)
     ap.add_argument("--ref-scale", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -215,7 +216,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     off, tgt, w, cfg = make_workload(gsp, graphgen, args.workload)
-    kw = dict(precision=args.precision, split=args.split, move=args.move)
+    kw = dict(precision=args.precision, split=args.split, move=args.move, waves=args.waves)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MB > 129 MB L2
 
     for _ in range(max(args.warmup, 0)):
@@ -282,10 +283,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic (device-generated R-MAT / planted / grid, seeded)",
-            "config": dict(cfg, precision=args.precision, split=args.split, move=args.move,
+            "config": dict(cfg, precision=args.precision, split=args.split, move=args.move, waves=args.waves,
                            parallelism="replicas" if ws > 1 else "single",
                            l2="inputs larger than L2 plus a 256 MB flush between steps"),
             "modularity": q, "communities": st["final_communities"], "passes": st["passes"],
+            "pass_stats": {k: st[k] for k in ("iterations", "vertices", "communities", "edges", "ms_move",
+                                                "ms_split", "ms_aggregate", "ms_other")},
             "phase_ms": {"move": sum(st["ms_move"]), "split": sum(st["ms_split"]),
                          "aggregate": sum(st["ms_aggregate"]), "other": sum(st["ms_other"]),
                          "total": st["ms_total"]},

@@ -229,6 +229,94 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
     }
 }
 
+// Large communities (total degree > 4096): every warp of the grid works on
+// every large community in turn.  The community's edges are numbered through
+// the member-edge prefix medge (scan of member degrees in community-vertex
+// order, so community c owns [yoff[c], yoff[c+1])); each warp takes chunks of
+// AGG_CHUNK consecutive edge numbers, finds the first member by binary search
+// and walks the members forward.
+constexpr uint32_t AGG_CHUNK = 1024;
+constexpr int AGG_COOP_BLOCKS = 152 * 4;
+
+__global__ void k_member_deg(const uint64_t *__restrict__ off, const uint32_t *__restrict__ cverts, uint32_t n,
+                             uint64_t *mdeg) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        uint32_t v = cverts[q];
+        mdeg[q] = off[v + 1] - off[v];
+    }
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint32_t *__restrict__ list, uint32_t count,
+                                                          const uint64_t *__restrict__ medge,
+                                                          const uint64_t *__restrict__ pool_off, uint32_t *pool_keys,
+                                                          double *pool_vals) {
+    const WT *w = static_cast<const WT *>(a.w);
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint32_t t = 0; t < count; t++) {
+        uint32_t c = list[t];
+        uint64_t E0 = a.yoff[c], E1 = a.yoff[c + 1];
+        uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
+        uint64_t cd = a.cdeg[c];
+        uint64_t bound = cd < a.k ? cd : a.k;
+        int logcap = ceil_log2((uint32_t)(2 * bound));
+        if (logcap < 1) logcap = 1;
+        uint32_t *keys = pool_keys + pool_off[t];
+        double *vals = pool_vals + pool_off[t];
+        for (uint64_t ch = E0 + gwarp * AGG_CHUNK; ch < E1; ch += nwarps * AGG_CHUNK) {
+            uint64_t cend = min(ch + AGG_CHUNK, E1);
+            // last member q in [q0, q1) with medge[q] <= ch
+            uint64_t lo = q0, hi = q1 - 1;
+            while (lo < hi) {
+                uint64_t mid = (lo + hi + 1) >> 1;
+                if (medge[mid] <= ch) lo = mid;
+                else hi = mid - 1;
+            }
+            uint64_t q = lo, t0 = ch;
+            while (t0 < cend && q < q1) {
+                uint64_t ms = medge[q], me = medge[q + 1];
+                uint64_t segend = me < cend ? me : cend;
+                if (t0 < segend) {
+                    uint32_t v = a.cverts[q];
+                    uint64_t base = a.off[v];
+                    for (uint64_t tt = t0 + lane; tt < segend; tt += 32) {
+                        uint64_t p = base + (tt - ms);
+                        ht_add<double>(keys, vals, logcap, a.Cd[a.tgt[p]], (double)w[p]);
+                    }
+                    t0 = segend;
+                }
+                q++;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_agg_large_extract(AggArgs a, const uint32_t *__restrict__ list,
+                                                           uint32_t count, const uint64_t *__restrict__ pool_off,
+                                                           const uint32_t *__restrict__ pool_keys,
+                                                           const double *__restrict__ pool_vals) {
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t t = 0; t < count; t++) {
+        uint32_t c = list[t];
+        uint64_t cd = a.cdeg[c];
+        uint64_t bound = cd < a.k ? cd : a.k;
+        int logcap = ceil_log2((uint32_t)(2 * bound));
+        if (logcap < 1) logcap = 1;
+        uint64_t cap = 1ull << logcap;
+        const uint32_t *keys = pool_keys + pool_off[t];
+        const double *vals = pool_vals + pool_off[t];
+        // every warp runs the same trip count so emit_slot's ballots see full warps
+        for (uint64_t s0 = tid - (threadIdx.x & 31); s0 < cap; s0 += T) {
+            uint64_t s = s0 + (threadIdx.x & 31);
+            uint32_t key = s < cap ? keys[s] : EMPTY;
+            emit_slot(a, c, key, s < cap ? vals[s] : 0.0, key != EMPTY, a.rowlen + c);
+        }
+    }
+}
+
 __global__ void k_agg_pool_caps(const unsigned long long *__restrict__ cdeg, const uint32_t *__restrict__ list,
                                 uint32_t count, uint32_t k, uint64_t *caps) {
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
@@ -422,8 +510,16 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
         GSP_CUDA(cudaStreamSynchronize(s));
         uint32_t *pk = arena().get<uint32_t>(slots);
         double *pv = arena().get<double>(slots);
-        k_agg_merge_block<0, WT><<<grid_for(nl, 1, 152 * 4), 256, 0, s>>>(a, ic.list + ic.start[ACLS_L], nl, poff,
-                                                                           pk, pv);
+        GSP_CUDA(cudaMemsetAsync(pk, 0xFF, sizeof(uint32_t) * slots, s));
+        GSP_CUDA(cudaMemsetAsync(pv, 0, sizeof(double) * slots, s));
+        uint64_t *medge = arena().get<uint64_t>((size_t)n + 1);
+        uint64_t *mdeg = arena().get<uint64_t>(n);
+        k_member_deg<<<grid_for(n, 256), 256, 0, s>>>(g.off, cverts, n, mdeg);
+        GSP_CHECK_LAUNCH();
+        exclusive_scan_u64(mdeg, medge, n, s);
+        k_agg_large_insert<WT><<<AGG_COOP_BLOCKS, 256, 0, s>>>(a, ic.list + ic.start[ACLS_L], nl, medge, poff, pk, pv);
+        GSP_CHECK_LAUNCH();
+        k_agg_large_extract<<<AGG_COOP_BLOCKS, 256, 0, s>>>(a, ic.list + ic.start[ACLS_L], nl, poff, pk, pv);
         GSP_CHECK_LAUNCH();
     }
 

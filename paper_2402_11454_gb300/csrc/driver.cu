@@ -249,6 +249,8 @@ static void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.mv_vtx = arena().get<uint32_t>(n);
     mb.mv_cmt = arena().get<uint32_t>(n);
     mb.mv_cnt = arena().get<uint32_t>(1);
+    mb.big = arena().get<uint32_t>(n);
+    mb.nbig = arena().get<uint32_t>(1);
     mb.m_dev = arena().get<double>(1);
     mb.ctr = arena().get<MoveCounters>(1);
 }

@@ -1,5 +1,7 @@
 // internal.cuh -- host-side interfaces between the translation units of libgsp.
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace gsp {
@@ -27,6 +29,7 @@ struct Classes {
     int W = 1;
     uint32_t start[NUM_CLS * MAX_WAVES + 1] = {0};
     uint64_t *pool_off = nullptr;  // huge class (all waves): hashtable slot offsets
+    std::vector<uint64_t> host_pool_off;
     uint64_t pool_slots = 0;
     uint32_t begin(int cls, int wave) const { return start[cls * W + wave]; }
     uint32_t count(int cls, int wave) const { return start[cls * W + wave + 1] - start[cls * W + wave]; }
@@ -60,6 +63,8 @@ struct MoveBuffers {
     uint32_t *mv_cmt = nullptr;
     uint32_t *mv_cnt = nullptr;
     uint32_t *choice = nullptr;  // optional: decision of each vertex (single-sweep API)
+    uint32_t *big = nullptr;     // movers whose neighbours all blocks re-mark together
+    uint32_t *nbig = nullptr;
     // learned pruning (optional)
     const float *mlp = nullptr;
     float *feat_kept = nullptr;  // K_{i->C_i} / K_i at the vertex's last visit

@@ -427,12 +427,17 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
 // --------------------------------------------------------------------------
 // Apply a frozen-state wave's moves: C, Sigma and size updates (float64
 // atomics of exactly representable values, so the result does not depend on
-// their order), and re-marking of the movers' neighbours.  One warp per move.
+// their order), and re-marking of the movers' neighbours: one warp per mover,
+// except movers of degree > BIG_MOVER, which go to a list that every block
+// of k_mark_big walks together.
 // --------------------------------------------------------------------------
+constexpr uint32_t BIG_MOVER = 2048;
+
 __global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                               const uint32_t *__restrict__ mv_vtx, const uint32_t *__restrict__ mv_cmt,
                               const uint32_t *__restrict__ mv_cnt, const double *__restrict__ K, uint32_t *C,
-                              double *Sig, uint32_t *size, uint8_t *act, MoveCounters *ctr) {
+                              double *Sig, uint32_t *size, uint8_t *act, uint32_t *big, uint32_t *nbig,
+                              MoveCounters *ctr) {
     uint32_t cnt = *mv_cnt;
     int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -450,7 +455,9 @@ __global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *
             atomicSub(size + d, 1u);
             atomicAdd(size + c, 1u);
             marked += e - b;
+            if (e - b > BIG_MOVER) big[atomicAdd(nbig, 1u)] = i;
         }
+        if (e - b > BIG_MOVER) continue;
         for (uint64_t p = b + lane; p < e; p += 32) {
             uint32_t j = tgt[p];
             if (j != i) act[j] = 1;
@@ -459,6 +466,187 @@ __global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *
     __shared__ unsigned long long red[32];
     marked = block_sum(marked, red);
     if (threadIdx.x == 0 && marked) atomicAdd(&ctr->marked, marked);
+}
+
+// Re-mark the neighbours of the big movers: every thread of the grid strides
+// over each mover's edges in turn.
+__global__ void k_mark_big(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                           const uint32_t *__restrict__ big, const uint32_t *__restrict__ nbig, uint8_t *act) {
+    uint32_t cnt = *nbig;
+    uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t t = 0; t < cnt; t++) {
+        uint32_t i = big[t];
+        uint64_t b = off[i], e = off[i + 1];
+        for (uint64_t p = b + tid; p < e; p += T) {
+            uint32_t j = tgt[p];
+            if (j != i) act[j] = 1;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Hub vertices (degree > 4096): every block of the grid works on every hub
+// of the wave in turn, so that one hub never waits on one block.
+//   prepare: read and clear each hub's flag, snapshot its community;
+//   insert:  all threads stride over the hub's edges into its global table;
+//   score:   all threads stride over the table; per-block best per hub;
+//   decide:  one warp per hub reduces the block bests and decides the move.
+// --------------------------------------------------------------------------
+constexpr int HUB_BLOCKS = 152 * 4;
+
+struct HubArgs {
+    const uint32_t *hubs;
+    uint32_t nh;
+    const uint64_t *pool_off;  // per hub (relative to this wave's first hub)
+    uint32_t *keys;
+    void *vals;
+    void *kid;          // per hub, V
+    uint8_t *go;        // per hub
+    uint32_t *d;        // per hub
+    void *best_s;       // [nh][HUB_BLOCKS], S
+    uint32_t *best_c;   // [nh][HUB_BLOCKS]
+    uint32_t *big, *nbig;
+};
+
+template <bool SYNC>
+__global__ void k_hub_prepare(MoveArgs a, HubArgs h) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < h.nh; t += gridDim.x * blockDim.x) {
+        uint32_t i = h.hubs[t];
+        uint8_t go = ld_state<SYNC>(a.act + i);
+        if (go) a.act[i] = 0;
+        h.go[t] = go;
+        h.d[t] = ld_state<SYNC>(a.C + i);
+    }
+}
+
+template <typename WT, bool F64, bool SYNC>
+__global__ void __launch_bounds__(256) k_hub_insert(MoveArgs a, HubArgs h) {
+    using V = typename std::conditional<F64, double, float>::type;
+    const WT *w = static_cast<const WT *>(a.w);
+    V *kidv = static_cast<V *>(h.kid);
+    uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t t = 0; t < h.nh; t++) {
+        if (!h.go[t]) continue;
+        uint32_t i = h.hubs[t], d = h.d[t];
+        uint64_t b = a.off[i], e = a.off[i + 1];
+        int logcap = ceil_log2((uint32_t)(2 * (e - b)));
+        uint32_t *keys = h.keys + h.pool_off[t];
+        V *vals = static_cast<V *>(h.vals) + h.pool_off[t];
+        V kid = 0;
+        for (uint64_t p = b + tid; p < e; p += T) {
+            uint32_t j = __ldg(a.tgt + p);
+            if (j == i) continue;
+            V wv = load_w<V>(w, p);
+            uint32_t c = ld_state<SYNC>(a.C + j);
+            if (c == d) kid += wv;
+            else ht_add<V>(keys, vals, logcap, c, wv);
+        }
+        kid = warp_sum(kid);
+        if ((threadIdx.x & 31) == 0 && kid != V(0)) atomicAdd(kidv + t, kid);
+    }
+}
+
+template <typename WT, bool F64, bool SYNC>
+__global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
+    using V = typename std::conditional<F64, double, float>::type;
+    using SC = Score<F64>;
+    using S = typename SC::S;
+    __shared__ S red_s[32];
+    __shared__ uint32_t red_c[32];
+    const V *kidv = static_cast<const V *>(h.kid);
+    S *bs = static_cast<S *>(h.best_s);
+    const double m = *a.m;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t ncand = 0;
+    for (uint32_t t = 0; t < h.nh; t++) {
+        if (!h.go[t]) continue;
+        uint32_t i = h.hubs[t], d = h.d[t];
+        uint64_t deg = a.off[i + 1] - a.off[i];
+        uint32_t cap = 1u << ceil_log2((uint32_t)(2 * deg));
+        const uint32_t *keys = h.keys + h.pool_off[t];
+        const V *vals = static_cast<const V *>(h.vals) + h.pool_off[t];
+        SC sc = make_score<F64>(a.K[i], (double)kidv[t], ld_state<SYNC>(a.Sig + d), m);
+        S best = -INFINITY;
+        uint32_t bestc = EMPTY;
+        for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += gridDim.x * blockDim.x) {
+            uint32_t c = keys[s];
+            if (c == EMPTY) continue;
+            ncand++;
+            S v = sc.score(vals[s], ld_state<SYNC>(a.Sig + c));
+            if (better(v, c, best, bestc)) { best = v; bestc = c; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            S v2 = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+            uint32_t c2 = __shfl_xor_sync(0xFFFFFFFFu, bestc, o);
+            if (better(v2, c2, best, bestc)) { best = v2; bestc = c2; }
+        }
+        __syncthreads();
+        if (lane == 0) { red_s[wid] = best; red_c[wid] = bestc; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < (int)(blockDim.x >> 5); k++)
+                if (better(red_s[k], red_c[k], best, bestc)) { best = red_s[k]; bestc = red_c[k]; }
+            bs[(size_t)t * gridDim.x + blockIdx.x] = best;
+            h.best_c[(size_t)t * gridDim.x + blockIdx.x] = bestc;
+        }
+    }
+    __shared__ unsigned long long su[32];
+    unsigned long long nc = block_sum<unsigned long long>(ncand, su);
+    if (threadIdx.x == 0 && nc) atomicAdd(&a.ctr->candidates, nc);
+}
+
+template <bool F64, bool SYNC>
+__global__ void k_hub_decide(MoveArgs a, HubArgs h, uint32_t nblocks) {
+    using V = typename std::conditional<F64, double, float>::type;
+    using SC = Score<F64>;
+    using S = typename SC::S;
+    const V *kidv = static_cast<const V *>(h.kid);
+    const S *bs = static_cast<const S *>(h.best_s);
+    const double m = *a.m;
+    const int lane = threadIdx.x & 31;
+    uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    LocalCtr lc;
+    for (uint32_t t = warp; t < h.nh; t += nwarps) {
+        if (!h.go[t]) continue;
+        uint32_t i = h.hubs[t], d = h.d[t];
+        S best = -INFINITY;
+        uint32_t bestc = EMPTY;
+        for (uint32_t k = lane; k < nblocks; k += 32) {
+            S v = bs[(size_t)t * nblocks + k];
+            uint32_t c = h.best_c[(size_t)t * nblocks + k];
+            if (c != EMPTY && better(v, c, best, bestc)) { best = v; bestc = c; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            S v2 = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+            uint32_t c2 = __shfl_xor_sync(0xFFFFFFFFu, bestc, o);
+            if (better(v2, c2, best, bestc)) { best = v2; bestc = c2; }
+        }
+        if (lane == 0) {
+            double Ki = a.K[i];
+            uint64_t deg = a.off[i + 1] - a.off[i];
+            SC sc = make_score<F64>(Ki, (double)kidv[t], ld_state<SYNC>(a.Sig + d), m);
+            double gain = (bestc == EMPTY) ? 0.0 : sc.gain(best);
+            int mv = 0;
+            if (gain > 0.0) mv = decide_move<SYNC>(a, i, d, bestc, Ki);
+            lc.vertices++;
+            lc.edges += deg;
+            if (mv) {
+                lc.moved++;
+                lc.dq += gain;
+                if (!SYNC) {  // in place: neighbours are re-marked by k_mark_big
+                    lc.marked += deg;
+                    h.big[atomicAdd(h.nbig, 1u)] = i;
+                }
+            }
+            record_visit(a, i, (uint32_t)deg, Ki, (double)kidv[t], gain, m, mv);
+        }
+    }
+    flush_counters(lc, a.ctr);
 }
 
 // --------------------------------------------------------------------------
@@ -541,8 +729,11 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
         k_pool_caps<<<grid_for(nh, 256), 256, 0, s>>>(g.off, cl.list + cl.cls_begin(CLS_HUGE), nh, caps);
         GSP_CHECK_LAUNCH();
         exclusive_scan_u64(caps, cl.pool_off, nh, s);
-        GSP_CUDA(cudaMemcpyAsync(&cl.pool_slots, cl.pool_off + nh, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        cl.host_pool_off.resize(nh + 1);
+        GSP_CUDA(cudaMemcpyAsync(cl.host_pool_off.data(), cl.pool_off, sizeof(uint64_t) * (nh + 1),
+                                 cudaMemcpyDeviceToHost, s));
         GSP_CUDA(cudaStreamSynchronize(s));
+        cl.pool_slots = cl.host_pool_off[nh];
     }
 }
 
@@ -551,7 +742,7 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
 // --------------------------------------------------------------------------
 template <typename WT, bool F64, bool SYNC>
 static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t *pool_keys, void *pool_vals,
-                        cudaStream_t s) {
+                        uint32_t *big, uint32_t *nbig, cudaStream_t s) {
     using V = typename std::conditional<F64, double, float>::type;
     GroupLists gl;
     const int G[4] = {4, 8, 16, 32};
@@ -583,10 +774,37 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
     }
     uint32_t nh = cl.count(CLS_HUGE, wave);
     if (nh) {
+        using S = typename Score<F64>::S;
         uint32_t rel = cl.begin(CLS_HUGE, wave) - cl.cls_begin(CLS_HUGE);
-        k_move_block<0, WT, F64, SYNC><<<grid_for(nh, 1, 152 * 4), 256, 0, s>>>(
-            a, cl.list + cl.begin(CLS_HUGE, wave), nh, cl.pool_off + rel, pool_keys, pool_vals);
+        uint64_t first, last;  // this wave's contiguous slice of the pool
+        size_t mk = arena().mark();
+        HubArgs h;
+        h.hubs = cl.list + cl.begin(CLS_HUGE, wave);
+        h.nh = nh;
+        h.pool_off = cl.pool_off + rel;
+        h.keys = pool_keys;
+        h.vals = pool_vals;
+        h.kid = arena().alloc(sizeof(V) * nh);
+        h.go = arena().get<uint8_t>(nh);
+        h.d = arena().get<uint32_t>(nh);
+        h.best_s = arena().alloc(sizeof(S) * (size_t)nh * HUB_BLOCKS);
+        h.best_c = arena().get<uint32_t>((size_t)nh * HUB_BLOCKS);
+        h.big = big;
+        h.nbig = nbig;
+        first = cl.host_pool_off[rel];
+        last = cl.host_pool_off[rel + nh];
+        GSP_CUDA(cudaMemsetAsync(pool_keys + first, 0xFF, sizeof(uint32_t) * (last - first), s));
+        GSP_CUDA(cudaMemsetAsync(static_cast<V *>(pool_vals) + first, 0, sizeof(V) * (last - first), s));
+        GSP_CUDA(cudaMemsetAsync(h.kid, 0, sizeof(V) * nh, s));
+        k_hub_prepare<SYNC><<<grid_for(nh, 256), 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();
+        k_hub_insert<WT, F64, SYNC><<<HUB_BLOCKS, 256, 0, s>>>(a, h);
+        GSP_CHECK_LAUNCH();
+        k_hub_score<WT, F64, SYNC><<<HUB_BLOCKS, 256, 0, s>>>(a, h);
+        GSP_CHECK_LAUNCH();
+        k_hub_decide<F64, SYNC><<<grid_for((uint64_t)nh * 32, 256), 256, 0, s>>>(a, h, HUB_BLOCKS);
+        GSP_CHECK_LAUNCH();
+        arena().release(mk);
     }
 }
 
@@ -622,7 +840,8 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
     a.salt = (uint32_t)(iteration * 0x9E3779B9u + mb.trace_salt);
     uint32_t *pool_keys = static_cast<uint32_t *>(mb.pool);
     void *pool_vals = pool_keys ? static_cast<void *>(pool_keys + align_up(cl.pool_slots, 64)) : nullptr;
-#define GSP_WAVE(WT, F64, SYNC) launch_wave<WT, F64, SYNC>(cl, a, wave, pool_keys, pool_vals, s)
+    if (!sync) GSP_CUDA(cudaMemsetAsync(mb.nbig, 0, sizeof(uint32_t), s));
+#define GSP_WAVE(WT, F64, SYNC) launch_wave<WT, F64, SYNC>(cl, a, wave, pool_keys, pool_vals, mb.big, mb.nbig, s)
     if (g.wt == GSP_W_F32) {
         if (fp64) { if (sync) GSP_WAVE(float, true, true); else GSP_WAVE(float, true, false); }
         else { if (sync) GSP_WAVE(float, false, true); else GSP_WAVE(float, false, false); }
@@ -631,11 +850,19 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
         else { if (sync) GSP_WAVE(double, false, true); else GSP_WAVE(double, false, false); }
     }
 #undef GSP_WAVE
+    if (!sync && cl.count(CLS_HUGE, wave)) {
+        k_mark_big<<<HUB_BLOCKS, 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, mb.act);
+        GSP_CHECK_LAUNCH();
+    }
 }
 
 void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s) {
+    GSP_CUDA(cudaMemsetAsync(mb.nbig, 0, sizeof(uint32_t), s));
     k_apply_moves<<<grid_for((uint64_t)n_hint * 32, 256, 152 * 8), 256, 0, s>>>(
-        g.off, g.tgt, mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C, mb.Sigma, mb.size, mb.act, mb.ctr);
+        g.off, g.tgt, mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C, mb.Sigma, mb.size, mb.act, mb.big, mb.nbig,
+        mb.ctr);
+    GSP_CHECK_LAUNCH();
+    k_mark_big<<<HUB_BLOCKS, 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, mb.act);
     GSP_CHECK_LAUNCH();
 }
 

@@ -128,10 +128,11 @@ static void split_lp(const DevGraph &g, const Classes &cl, const uint32_t *C, bo
     unsigned long long *changed = arena().get<unsigned long long>(1);
     iota_u32(lab, g.n, s);
     if (prune) GSP_CUDA(cudaMemsetAsync(flag, 1, g.n, s));
-    auto cnt = [&](int c) { return cl.start[c + 1] - cl.start[c]; };
-    auto lst = [&](int c) { return cl.list + cl.start[c]; };
+    // every class with all its waves (class c spans [cls_begin(c), cls_begin(c+1)))
+    auto cnt = [&](int c) { return cl.cls_count(c); };
+    auto lst = [&](int c) { return cl.list + cl.cls_begin(c); };
     const unsigned maxg = 152 * 8;
-    uint32_t nbig = cl.start[NUM_CLS] - cl.start[CLS_BLOCK];
+    uint32_t nbig = cl.cls_count(CLS_BLOCK) + cl.cls_count(CLS_HUGE);
     for (int it = 0; it < (1 << 30); it++) {
         GSP_CUDA(cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s));
 #define LPG(G, CLS)                                                                                  \
@@ -164,13 +165,20 @@ static void split_lp(const DevGraph &g, const Classes &cl, const uint32_t *C, bo
 }
 
 // --------------------------------------------------------------------- BFS
-__global__ void k_bfs_seed_min(const uint32_t *__restrict__ C, const uint32_t *__restrict__ lab, uint32_t n,
+// Seeds of a round: the smallest unvisited vertex of every community that
+// still has one.  `cand` lists the vertices unvisited after the previous
+// round (all vertices in the first round).
+__global__ void k_bfs_seed_min(const uint32_t *__restrict__ C, const uint32_t *__restrict__ lab,
+                               const uint32_t *__restrict__ cand, const uint32_t *__restrict__ ncand, uint32_t n,
                                uint32_t *seed) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    uint32_t cnt = cand ? *ncand : n;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        uint32_t v = cand ? cand[t] : t;
         if (lab[v] == EMPTY) atomicMin(seed + C[v], v);
+    }
 }
 
-// Warp-aggregated append of the lanes with `want` set; returns the slot.
+// Warp-aggregated append of the lanes with `want` set.
 __device__ __forceinline__ void push_warp(bool want, uint32_t v, uint32_t *q, uint32_t *qn) {
     uint32_t ballot = __ballot_sync(0xFFFFFFFFu, want);
     if (!ballot) return;
@@ -182,16 +190,29 @@ __device__ __forceinline__ void push_warp(bool want, uint32_t v, uint32_t *q, ui
     if (want) q[base + __popc(ballot & ((1u << lane) - 1u))] = v;
 }
 
-__global__ void k_bfs_seed_push(const uint32_t *__restrict__ C, uint32_t *lab, uint32_t n,
-                                const uint32_t *__restrict__ seed, uint32_t *q, uint32_t *qn) {
-    for (uint32_t v0 = blockIdx.x * blockDim.x; v0 < n; v0 += gridDim.x * blockDim.x) {
-        uint32_t v = v0 + threadIdx.x;
-        bool want = false;
-        if (v < n && lab[v] == EMPTY && seed[C[v]] == v) {
-            lab[v] = v;
-            want = true;
+// Label the seeds and start the frontier; the other unvisited vertices form
+// the candidate list of the next round.
+__global__ void k_bfs_seed_push(const uint32_t *__restrict__ C, uint32_t *lab, const uint32_t *__restrict__ cand,
+                                const uint32_t *__restrict__ ncand, uint32_t n, const uint32_t *__restrict__ seed,
+                                uint32_t *q, uint32_t *qn, uint32_t *rest, uint32_t *nrest) {
+    uint32_t cnt = cand ? *ncand : n;
+    for (uint32_t t0 = blockIdx.x * blockDim.x; t0 < cnt; t0 += gridDim.x * blockDim.x) {
+        uint32_t t = t0 + threadIdx.x;
+        bool is_seed = false, keep = false;
+        uint32_t v = 0;
+        if (t < cnt) {
+            v = cand ? cand[t] : t;
+            if (lab[v] == EMPTY) {
+                if (seed[C[v]] == v) {
+                    lab[v] = v;
+                    is_seed = true;
+                } else {
+                    keep = true;
+                }
+            }
         }
-        push_warp(want, v, q, qn);
+        push_warp(is_seed, v, q, qn);
+        push_warp(keep, v, rest, nrest);
     }
 }
 
@@ -202,66 +223,132 @@ __global__ void k_bfs_seed_reset(const uint32_t *__restrict__ C, const uint32_t 
         seed[C[q[t]]] = EMPTY;
 }
 
+constexpr uint32_t BFS_BIG = 1024;
+constexpr int BFS_COOP_BLOCKS = 152 * 4;
+
+__device__ __forceinline__ void bfs_visit_edges(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ C,
+                                                uint32_t *lab, uint64_t p0, uint64_t e, uint64_t step, uint32_t cu,
+                                                uint32_t lu, uint32_t *nq, uint32_t *nqn) {
+    // all 32 lanes of the warp run the same trip count (push_warp ballots)
+    for (uint64_t pb = p0; pb < e + (threadIdx.x & 31) && pb - (threadIdx.x & 31) < e; pb += step) {
+        uint64_t p = pb;
+        bool want = false;
+        uint32_t j = 0;
+        if (p < e) {
+            j = tgt[p];
+            if (C[j] == cu && ldcg_(lab + j) == EMPTY) want = atomicCAS(lab + j, EMPTY, lu) == EMPTY;
+        }
+        push_warp(want, j, nq, nqn);
+    }
+}
+
 // One level: a warp per frontier vertex claims unvisited same-community
-// neighbours with atomicCAS and appends them to the next frontier.
+// neighbours with atomicCAS and appends them to the next frontier; frontier
+// vertices of degree > BFS_BIG go to a list for k_bfs_expand_big.
 __global__ void k_bfs_expand(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                              const uint32_t *__restrict__ C, uint32_t *lab, const uint32_t *__restrict__ q,
-                             const uint32_t *__restrict__ qn, uint32_t *nq, uint32_t *nqn) {
+                             const uint32_t *__restrict__ qn, uint32_t *nq, uint32_t *nqn, uint32_t *big,
+                             uint32_t *nbig) {
     uint32_t cnt = *qn;
     int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t t = warp; t < cnt; t += nwarps) {
         uint32_t u = q[t];
-        uint32_t cu = C[u], lu = ldcg_(lab + u);
         uint64_t b = off[u], e = off[u + 1];
-        for (uint64_t p0 = b; p0 < e; p0 += 32) {
-            uint64_t p = p0 + lane;
-            bool want = false;
-            uint32_t j = 0;
-            if (p < e) {
-                j = tgt[p];
-                if (C[j] == cu && ldcg_(lab + j) == EMPTY) want = atomicCAS(lab + j, EMPTY, lu) == EMPTY;
-            }
-            push_warp(want, j, nq, nqn);
+        if (e - b > BFS_BIG) {
+            if (lane == 0) big[atomicAdd(nbig, 1u)] = u;
+            continue;
         }
+        uint32_t cu = C[u], lu = ldcg_(lab + u);
+        bfs_visit_edges(tgt, C, lab, b + lane, e, 32, cu, lu, nq, nqn);
     }
 }
+
+// The big frontier vertices: every warp of the grid strides over each one's
+// edges in turn.
+__global__ void k_bfs_expand_big(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                                 const uint32_t *__restrict__ C, uint32_t *lab, const uint32_t *__restrict__ big,
+                                 const uint32_t *__restrict__ nbig, uint32_t *nq, uint32_t *nqn) {
+    uint32_t cnt = *nbig;
+    uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t t = 0; t < cnt; t++) {
+        uint32_t u = big[t];
+        uint32_t cu = C[u], lu = ldcg_(lab + u);
+        bfs_visit_edges(tgt, C, lab, off[u] + tid, off[u + 1], T, cu, lu, nq, nqn);
+    }
+}
+
+// Rounds of multi-source BFS.  Levels are launched in batches of
+// BFS_LEVEL_BATCH between host checks of the frontier size (an empty
+// frontier makes the remaining launches of a batch return at once).
+constexpr int BFS_LEVEL_BATCH = 6;
 
 static void split_bfs(const DevGraph &g, const uint32_t *C, uint32_t *lab, cudaStream_t s) {
     size_t mk = arena().mark();
     uint32_t n = g.n;
     uint32_t *seed = arena().get<uint32_t>(n);
+    uint32_t *fr[BFS_LEVEL_BATCH + 1];
+    for (int k = 0; k <= BFS_LEVEL_BATCH; k++) fr[k] = nullptr;
     uint32_t *qa = arena().get<uint32_t>(n);
     uint32_t *qb = arena().get<uint32_t>(n);
-    uint32_t *cnts = arena().get<uint32_t>(2);
+    uint32_t *candA = arena().get<uint32_t>(n);
+    uint32_t *candB = arena().get<uint32_t>(n);
+    uint32_t *big = arena().get<uint32_t>(n);
+    // counters: [0] seeds, [1] rest, [2 .. 2+BATCH] frontier sizes, big counts after
+    uint32_t *cnts = arena().get<uint32_t>(4 + 2 * (BFS_LEVEL_BATCH + 1));
+    uint32_t *ncandA = cnts + 0;  // candidate counts live beside the seed/rest counters
     GSP_CUDA(cudaMemsetAsync(lab, 0xFF, sizeof(uint32_t) * n, s));
     GSP_CUDA(cudaMemsetAsync(seed, 0xFF, sizeof(uint32_t) * n, s));
-    unsigned gr = grid_for(n, 256);
-    for (;;) {
-        GSP_CUDA(cudaMemsetAsync(cnts, 0, 2 * sizeof(uint32_t), s));
-        k_bfs_seed_min<<<gr, 256, 0, s>>>(C, lab, n, seed);
+    const uint32_t *cand = nullptr;  // first round: every vertex
+    uint32_t *cand_cnt = nullptr;
+    uint32_t h_cand = n;
+    uint32_t *cbuf[2] = {candA, candB};
+    uint32_t *ccnt[2] = {cnts + 2 + 2 * (BFS_LEVEL_BATCH + 1), cnts + 3 + 2 * (BFS_LEVEL_BATCH + 1)};
+    (void)ncandA;
+    int cb = 0;
+    for (int round = 0; h_cand > 0; round++) {
+        uint32_t *rest = cbuf[cb], *nrest = ccnt[cb];
+        uint32_t *qn = cnts + 0;
+        GSP_CUDA(cudaMemsetAsync(cnts, 0, sizeof(uint32_t) * (2 + 2 * (BFS_LEVEL_BATCH + 1)), s));
+        GSP_CUDA(cudaMemsetAsync(nrest, 0, sizeof(uint32_t), s));
+        unsigned gr = grid_for(h_cand, 256);
+        k_bfs_seed_min<<<gr, 256, 0, s>>>(C, lab, cand, cand_cnt, n, seed);
         GSP_CHECK_LAUNCH();
-        k_bfs_seed_push<<<gr, 256, 0, s>>>(C, lab, n, seed, qa, cnts);
+        k_bfs_seed_push<<<gr, 256, 0, s>>>(C, lab, cand, cand_cnt, n, seed, qa, qn, rest, nrest);
         GSP_CHECK_LAUNCH();
-        k_bfs_seed_reset<<<gr, 256, 0, s>>>(C, qa, cnts, seed);
+        k_bfs_seed_reset<<<gr, 256, 0, s>>>(C, qa, qn, seed);
         GSP_CHECK_LAUNCH();
-        uint32_t h;
-        GSP_CUDA(cudaMemcpyAsync(&h, cnts, sizeof(h), cudaMemcpyDeviceToHost, s));
-        GSP_CUDA(cudaStreamSynchronize(s));
-        if (h == 0) break;
+        // levels, in batches
         uint32_t *q = qa, *nq = qb;
-        uint32_t *qn = cnts, *nqn = cnts + 1;
-        while (h) {
-            GSP_CUDA(cudaMemsetAsync(nqn, 0, sizeof(uint32_t), s));
-            k_bfs_expand<<<grid_for((uint64_t)h * 32, 256, 152 * 8), 256, 0, s>>>(g.off, g.tgt, C, lab, q, qn, nq,
-                                                                                  nqn);
-            GSP_CHECK_LAUNCH();
-            GSP_CUDA(cudaMemcpyAsync(&h, nqn, sizeof(h), cudaMemcpyDeviceToHost, s));
+        uint32_t *fcnt = cnts + 2;        // fcnt[k]: frontier size of level k in the batch
+        uint32_t *bcnt = cnts + 2 + (BFS_LEVEL_BATCH + 1);
+        GSP_CUDA(cudaMemcpyAsync(fcnt, qn, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+        for (;;) {
+            for (int k = 0; k < BFS_LEVEL_BATCH; k++) {
+                k_bfs_expand<<<152 * 8, 256, 0, s>>>(g.off, g.tgt, C, lab, q, fcnt + k, nq, fcnt + k + 1, big,
+                                                    bcnt + k);
+                GSP_CHECK_LAUNCH();
+                k_bfs_expand_big<<<BFS_COOP_BLOCKS, 256, 0, s>>>(g.off, g.tgt, C, lab, big, bcnt + k, nq,
+                                                                 fcnt + k + 1);
+                GSP_CHECK_LAUNCH();
+                uint32_t *t = q; q = nq; nq = t;
+            }
+            uint32_t last;
+            GSP_CUDA(cudaMemcpyAsync(&last, fcnt + BFS_LEVEL_BATCH, sizeof(last), cudaMemcpyDeviceToHost, s));
             GSP_CUDA(cudaStreamSynchronize(s));
-            uint32_t *t = q; q = nq; nq = t;
-            uint32_t *tn = qn; qn = nqn; nqn = tn;
+            if (last == 0) break;
+            GSP_CUDA(cudaMemcpyAsync(fcnt, fcnt + BFS_LEVEL_BATCH, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+            GSP_CUDA(cudaMemsetAsync(fcnt + 1, 0, sizeof(uint32_t) * BFS_LEVEL_BATCH, s));
+            GSP_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(uint32_t) * (BFS_LEVEL_BATCH + 1), s));
         }
+        // vertices still unvisited become the next round's candidates
+        GSP_CUDA(cudaMemcpyAsync(&h_cand, nrest, sizeof(h_cand), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        cand = rest;
+        cand_cnt = nrest;
+        cb ^= 1;
     }
     arena().release(mk);
 }

@@ -194,7 +194,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--precision", default="mixed")
-    ap.add_argument("--split", default="bfs")
+    ap.add_argument("--split", default="lpp")
     ap.add_argument("--move", default="sync")
     ap.add_argument("--waves", type=int, default=16)
     ap.add_argument("--ref-scale", type=int, default=20)

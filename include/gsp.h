@@ -74,7 +74,7 @@ typedef struct {
     double tolerance;               /* tau (Algorithm 4); default 1e-2 */
     double tolerance_drop;          /* TOLERANCE_DROP (Algorithm 1); default 10 */
     double aggregation_tolerance;   /* tau_agg (Algorithm 1); default 0.8 */
-    int split;                      /* gsp_split_mode; default GSP_SPLIT_BFS */
+    int split;                      /* gsp_split_mode; default GSP_SPLIT_LPP */
     int split_when;                 /* gsp_split_when; default GSP_SPLIT_PASS */
     int move;                       /* gsp_move_mode; default GSP_MOVE_SYNC */
     int waves;                      /* SYNC: waves per iteration, 1..64; default 16 */

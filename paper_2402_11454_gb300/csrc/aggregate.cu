@@ -229,13 +229,17 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
     }
 }
 
-// Large communities (total degree > 4096): every warp of the grid works on
-// every large community in turn.  The community's edges are numbered through
-// the member-edge prefix medge (scan of member degrees in community-vertex
-// order, so community c owns [yoff[c], yoff[c+1])); each warp takes chunks of
-// AGG_CHUNK consecutive edge numbers, finds the first member by binary search
-// and walks the members forward.
-constexpr uint32_t AGG_CHUNK = 1024;
+// Large communities (total degree > 4096), processed by the whole grid.  A
+// community's edges are numbered through the member-edge prefix medge (scan
+// of member degrees in community-vertex order, so community c owns
+// [yoff[c], yoff[c+1])) and cut into AGG_CHUNK-edge tasks.  A block combines a
+// task's neighbour communities in a shared-memory table (each warp finds its
+// first member by binary search and walks the members forward), then
+// publishes the distinct ones to the community's global table; keys new to it
+// append their slot to the community's occupied list, which the extraction
+// walks.
+constexpr uint32_t AGG_CHUNK = 2048;
+constexpr int AGG_SLOG = 12;  // shared table of 2 * AGG_CHUNK slots
 constexpr int AGG_COOP_BLOCKS = 152 * 4;
 
 __global__ void k_member_deg(const uint64_t *__restrict__ off, const uint32_t *__restrict__ cverts, uint32_t n,
@@ -246,27 +250,34 @@ __global__ void k_member_deg(const uint64_t *__restrict__ off, const uint32_t *_
     }
 }
 
+__global__ void k_agg_tasks(const unsigned long long *__restrict__ cdeg, const uint32_t *__restrict__ list,
+                            uint32_t count, uint64_t *ntask) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x)
+        ntask[t] = (cdeg[list[t]] + AGG_CHUNK - 1) / AGG_CHUNK;
+}
+
 template <typename WT>
 __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint32_t *__restrict__ list, uint32_t count,
+                                                          const uint64_t *__restrict__ tasks,
                                                           const uint64_t *__restrict__ medge,
                                                           const uint64_t *__restrict__ pool_off, uint32_t *pool_keys,
-                                                          double *pool_vals) {
+                                                          double *pool_vals, uint32_t *pool_occ, uint32_t *occ_n) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    uint32_t *skeys = reinterpret_cast<uint32_t *>(dyn_smem);
+    double *svals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * (1u << AGG_SLOG));
     const WT *w = static_cast<const WT *>(a.w);
-    const int lane = threadIdx.x & 31;
-    const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint32_t t = 0; t < count; t++) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t sub = AGG_CHUNK / (blockDim.x >> 5);  // edges per warp
+    for (uint32_t s = threadIdx.x; s < (1u << AGG_SLOG); s += blockDim.x) { skeys[s] = EMPTY; svals[s] = 0.0; }
+    const uint64_t total = tasks[count];
+    for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
+        uint32_t t = task_item(tasks, count, task);
         uint32_t c = list[t];
-        uint64_t E0 = a.yoff[c], E1 = a.yoff[c + 1];
+        uint64_t E1 = a.yoff[c + 1];
         uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
-        uint64_t cd = a.cdeg[c];
-        uint64_t bound = cd < a.k ? cd : a.k;
-        int logcap = ceil_log2((uint32_t)(2 * bound));
-        if (logcap < 1) logcap = 1;
-        uint32_t *keys = pool_keys + pool_off[t];
-        double *vals = pool_vals + pool_off[t];
-        for (uint64_t ch = E0 + gwarp * AGG_CHUNK; ch < E1; ch += nwarps * AGG_CHUNK) {
-            uint64_t cend = min(ch + AGG_CHUNK, E1);
+        uint64_t ch = a.yoff[c] + (task - tasks[t]) * AGG_CHUNK + (uint64_t)wid * sub;
+        uint64_t cend = min(ch + sub, E1);
+        if (ch < E1) {
             // last member q in [q0, q1) with medge[q] <= ch
             uint64_t lo = q0, hi = q1 - 1;
             while (lo < hi) {
@@ -283,36 +294,42 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
                     uint64_t base = a.off[v];
                     for (uint64_t tt = t0 + lane; tt < segend; tt += 32) {
                         uint64_t p = base + (tt - ms);
-                        ht_add<double>(keys, vals, logcap, a.Cd[a.tgt[p]], (double)w[p]);
+                        ht_add<double>(skeys, svals, AGG_SLOG, a.Cd[a.tgt[p]], (double)w[p]);
                     }
                     t0 = segend;
                 }
                 q++;
             }
         }
+        uint64_t cd = a.cdeg[c];
+        uint64_t bound = cd < a.k ? cd : a.k;
+        int glog = ceil_log2((uint32_t)(2 * bound));
+        if (glog < 1) glog = 1;
+        publish_block_table<double>(skeys, svals, AGG_SLOG, pool_keys + pool_off[t], pool_vals + pool_off[t], glog,
+                                    pool_occ + pool_off[t], occ_n + t);
     }
 }
 
 __global__ void __launch_bounds__(256) k_agg_large_extract(AggArgs a, const uint32_t *__restrict__ list,
                                                            uint32_t count, const uint64_t *__restrict__ pool_off,
                                                            const uint32_t *__restrict__ pool_keys,
-                                                           const double *__restrict__ pool_vals) {
+                                                           const double *__restrict__ pool_vals,
+                                                           const uint32_t *__restrict__ pool_occ,
+                                                           const uint32_t *__restrict__ occ_n) {
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     for (uint32_t t = 0; t < count; t++) {
         uint32_t c = list[t];
-        uint64_t cd = a.cdeg[c];
-        uint64_t bound = cd < a.k ? cd : a.k;
-        int logcap = ceil_log2((uint32_t)(2 * bound));
-        if (logcap < 1) logcap = 1;
-        uint64_t cap = 1ull << logcap;
         const uint32_t *keys = pool_keys + pool_off[t];
         const double *vals = pool_vals + pool_off[t];
+        const uint32_t *occ = pool_occ + pool_off[t];
+        uint64_t nocc = occ_n[t];
         // every warp runs the same trip count so emit_slot's ballots see full warps
-        for (uint64_t s0 = tid - (threadIdx.x & 31); s0 < cap; s0 += T) {
-            uint64_t s = s0 + (threadIdx.x & 31);
-            uint32_t key = s < cap ? keys[s] : EMPTY;
-            emit_slot(a, c, key, s < cap ? vals[s] : 0.0, key != EMPTY, a.rowlen + c);
+        for (uint64_t k0 = tid - (threadIdx.x & 31); k0 < nocc; k0 += T) {
+            uint64_t k = k0 + (threadIdx.x & 31);
+            bool valid = k < nocc;
+            uint32_t slot = valid ? occ[k] : 0;
+            emit_slot(a, c, valid ? keys[slot] : EMPTY, valid ? vals[slot] : 0.0, valid, a.rowlen + c);
         }
     }
 }
@@ -510,16 +527,32 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
         GSP_CUDA(cudaStreamSynchronize(s));
         uint32_t *pk = arena().get<uint32_t>(slots);
         double *pv = arena().get<double>(slots);
+        uint32_t *po = arena().get<uint32_t>(slots);
+        uint32_t *on = arena().get<uint32_t>(nl);
         GSP_CUDA(cudaMemsetAsync(pk, 0xFF, sizeof(uint32_t) * slots, s));
         GSP_CUDA(cudaMemsetAsync(pv, 0, sizeof(double) * slots, s));
+        GSP_CUDA(cudaMemsetAsync(on, 0, sizeof(uint32_t) * nl, s));
         uint64_t *medge = arena().get<uint64_t>((size_t)n + 1);
         uint64_t *mdeg = arena().get<uint64_t>(n);
         k_member_deg<<<grid_for(n, 256), 256, 0, s>>>(g.off, cverts, n, mdeg);
         GSP_CHECK_LAUNCH();
         exclusive_scan_u64(mdeg, medge, n, s);
-        k_agg_large_insert<WT><<<AGG_COOP_BLOCKS, 256, 0, s>>>(a, ic.list + ic.start[ACLS_L], nl, medge, poff, pk, pv);
+        const uint32_t *llist = ic.list + ic.start[ACLS_L];
+        uint64_t *ntask = arena().get<uint64_t>(nl);
+        uint64_t *tasks = arena().get<uint64_t>((size_t)nl + 1);
+        k_agg_tasks<<<grid_for(nl, 256), 256, 0, s>>>(cdeg, llist, nl, ntask);
         GSP_CHECK_LAUNCH();
-        k_agg_large_extract<<<AGG_COOP_BLOCKS, 256, 0, s>>>(a, ic.list + ic.start[ACLS_L], nl, poff, pk, pv);
+        exclusive_scan_u64(ntask, tasks, nl, s);
+        constexpr size_t lsmem = (sizeof(uint32_t) + sizeof(double)) << AGG_SLOG;
+        static bool lattr = false;
+        if (!lattr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_agg_large_insert<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)lsmem));
+            lattr = true;
+        }
+        k_agg_large_insert<WT><<<AGG_COOP_BLOCKS, 256, lsmem, s>>>(a, llist, nl, tasks, medge, poff, pk, pv, po, on);
+        GSP_CHECK_LAUNCH();
+        k_agg_large_extract<<<AGG_COOP_BLOCKS, 256, 0, s>>>(a, llist, nl, poff, pk, pv, po, on);
         GSP_CHECK_LAUNCH();
     }
 

@@ -292,9 +292,15 @@ static double max_value(const double *x, uint32_t n, cudaStream_t s) {
     return v;
 }
 
-static void alloc_pool(MoveBuffers &mb, const Classes &cl) {
+// Hub hashtables: keys (u32), values (8 bytes) and an occupied-slot list
+// (u32) per slot.  The tables start empty; each sweep's scoring empties them.
+static void alloc_pool(MoveBuffers &mb, const Classes &cl, cudaStream_t s) {
     mb.pool = nullptr;
-    if (cl.pool_slots) mb.pool = arena().alloc((align_up(cl.pool_slots, 64)) * (sizeof(uint32_t) + sizeof(double)));
+    if (!cl.pool_slots) return;
+    size_t sa = align_up(cl.pool_slots, 64);
+    mb.pool = arena().alloc(sa * 16);
+    GSP_CUDA(cudaMemsetAsync(mb.pool, 0xFF, sa * sizeof(uint32_t), s));
+    GSP_CUDA(cudaMemsetAsync(static_cast<uint32_t *>(mb.pool) + sa, 0, sa * sizeof(double), s));
 }
 
 // --------------------------------------------------------- GSP-Louvain run
@@ -390,7 +396,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         }
         Classes cl;
         classify_vertices(cur, cl, W, s);
-        alloc_pool(mb, cl);
+        alloc_pool(mb, cl, s);
         float ms_other = t.lap();
         MoveLoopResult mr{0, 0, 0, 0, 0, 0.0, 0.0f};
         if (m > 0.0) mr = move_loop(cur, cl, mb, tau, o.max_iterations, sync, fp64, o.singleton_rule != 0, pr, s);
@@ -516,7 +522,7 @@ void gsp_default_opts(gsp_opts *o) {
     o->tolerance = 1e-2;
     o->tolerance_drop = 10.0;
     o->aggregation_tolerance = 0.8;
-    o->split = GSP_SPLIT_BFS;
+    o->split = GSP_SPLIT_LPP;
     o->split_when = GSP_SPLIT_PASS;
     o->move = GSP_MOVE_SYNC;
     o->waves = 16;
@@ -645,7 +651,7 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
     GSP_CUDA(cudaMemsetAsync(mb.mv_cnt, 0, sizeof(uint32_t), s));
     Classes cl;
     classify_vertices(g, cl, 1, s);
-    alloc_pool(mb, cl);
+    alloc_pool(mb, cl, s);
     move_wave(g, cl, mb, 0, true, precision == GSP_PREC_FP64, singleton_rule != 0, false, 0, 1, s);
     MoveCounters h;
     GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -683,7 +689,7 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
     GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
     Classes cl;
     classify_vertices(g, cl, sync ? waves : 1, s);
-    alloc_pool(mb, cl);
+    alloc_pool(mb, cl, s);
     PruneCtx pr;
     MoveLoopResult r = move_loop(g, cl, mb, tolerance, max_iterations, sync, precision == GSP_PREC_FP64,
                                  singleton_rule != 0, pr, s);

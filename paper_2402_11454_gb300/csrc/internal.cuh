@@ -20,8 +20,8 @@ struct DevGraph {
 // shared-memory table, the largest by one block with a table in a global
 // pool.  Each class is further split into W waves (vertex v in wave v mod W):
 // the list holds key = class * W + wave in increasing order.
-enum { CLS_G4 = 0, CLS_G8, CLS_G16, CLS_G32, CLS_BLOCK, CLS_HUGE, NUM_CLS };
-constexpr uint32_t CLS_MAXDEG[NUM_CLS] = {8, 16, 32, 128, 4096, 0xFFFFFFFFu};
+enum { CLS_G4 = 0, CLS_G8, CLS_G16, CLS_G32, CLS_W512, CLS_BLOCK, CLS_HUGE, NUM_CLS };
+constexpr uint32_t CLS_MAXDEG[NUM_CLS] = {8, 16, 32, 128, 512, 4096, 0xFFFFFFFFu};
 constexpr int MAX_WAVES = 64;
 
 struct Classes {
@@ -31,6 +31,8 @@ struct Classes {
     uint64_t *pool_off = nullptr;  // huge class (all waves): hashtable slot offsets
     std::vector<uint64_t> host_pool_off;
     uint64_t pool_slots = 0;
+    uint64_t *hub_tasks = nullptr;  // huge class: prefix of edge-chunk counts (count+1)
+    uint32_t *hub_occ_n = nullptr;  // huge class: occupied-slot count of each hub table
     uint32_t begin(int cls, int wave) const { return start[cls * W + wave]; }
     uint32_t count(int cls, int wave) const { return start[cls * W + wave + 1] - start[cls * W + wave]; }
     uint32_t cls_begin(int cls) const { return start[cls * W]; }
@@ -155,6 +157,55 @@ __device__ __forceinline__ int ht_add(uint32_t *keys, V *vals, int logcap, uint3
         h = (h + 1) & mask;
     }
     return -1;
+}
+
+// As ht_add, also reporting the slot used (for occupied-slot lists).
+template <typename V>
+__device__ __forceinline__ int ht_add_slot(uint32_t *keys, V *vals, int logcap, uint32_t c, V w, uint32_t *slot) {
+    uint32_t mask = (1u << logcap) - 1u;
+    uint32_t h = logcap ? (hash32(c) >> (32 - logcap)) : 0u;
+    volatile uint32_t *vk = keys;
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        uint32_t k = vk[h];
+        if (k == c) { atomicAdd(&vals[h], w); *slot = h; return 0; }
+        if (k == EMPTY) {
+            uint32_t old = atomicCAS(&keys[h], EMPTY, c);
+            if (old == EMPTY || old == c) { atomicAdd(&vals[h], w); *slot = h; return old == EMPTY; }
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// Combine-then-publish: the block's shared table (2^slog slots) is merged
+// into a global table (2^glog slots); keys new to the global table append
+// their slot to occ (count in *occ_n).  The shared table is left empty.
+// Every thread of the block must call this.
+template <typename V>
+__device__ void publish_block_table(uint32_t *skeys, V *svals, int slog, uint32_t *gkeys, V *gvals, int glog,
+                                    uint32_t *occ, uint32_t *occ_n) {
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < (1u << slog); s += blockDim.x) {
+        uint32_t k = skeys[s];
+        if (k == EMPTY) continue;
+        uint32_t slot;
+        if (ht_add_slot<V>(gkeys, gvals, glog, k, svals[s], &slot) == 1) occ[atomicAdd(occ_n, 1u)] = slot;
+        skeys[s] = EMPTY;
+        svals[s] = V(0);
+    }
+    __syncthreads();
+}
+
+// Chunked work over items (hubs, communities) of different sizes: task ids
+// [prefix[i], prefix[i+1]) belong to item i; returns the item of a task.
+__device__ __forceinline__ uint32_t task_item(const uint64_t *prefix, uint32_t nitems, uint64_t task) {
+    uint32_t lo = 0, hi = nitems - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= task) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 }  // namespace gsp

@@ -311,31 +311,41 @@ __global__ void __launch_bounds__(256) k_move_groups(MoveArgs a, GroupLists gl) 
                                            gl.bstart[4] - gl.bstart[3], smem);
 }
 
+// Degrees 129..512: one warp per vertex, 1024-slot table per warp.
+constexpr int W512_CAP = 1024;
+template <typename WT, bool F64, bool SYNC>
+__global__ void __launch_bounds__(256) k_move_w512(MoveArgs a, const uint32_t *__restrict__ list, uint32_t count) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    group_body<32, W512_CAP, WT, F64, SYNC>(a, list, count, blockIdx.x, gridDim.x, dyn_smem);
+}
+
 // --------------------------------------------------------------------------
 // One block per vertex; table in shared memory (CAP > 0) or in the global
 // pool (CAP == 0, slots at pool_off[idx]).
 // --------------------------------------------------------------------------
 template <int CAP, typename WT, bool F64, bool SYNC>
-__global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *__restrict__ list, uint32_t count,
-                                                    const uint64_t *__restrict__ pool_off, uint32_t *pool_keys,
-                                                    void *pool_vals) {
+__global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *__restrict__ list, uint32_t count) {
     using V = typename std::conditional<F64, double, float>::type;
     using SC = Score<F64>;
     using S = typename SC::S;
+    // table: keys, values and the list of occupied slots (scoring and
+    // clearing touch only those)
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    uint32_t *s_keys = reinterpret_cast<uint32_t *>(dyn_smem);
-    V *s_vals = reinterpret_cast<V *>(dyn_smem + (size_t)CAP * sizeof(uint32_t));
+    uint32_t *keys = reinterpret_cast<uint32_t *>(dyn_smem);
+    V *vals = reinterpret_cast<V *>(dyn_smem + (size_t)CAP * sizeof(uint32_t));
+    uint16_t *occ = reinterpret_cast<uint16_t *>(dyn_smem + (size_t)CAP * (sizeof(uint32_t) + sizeof(V)));
     __shared__ S red_s[32];
     __shared__ uint32_t red_c[32];
     __shared__ V red_k[32];
     __shared__ int s_go, s_mv;
-    __shared__ uint32_t s_d;
+    __shared__ uint32_t s_d, s_nocc;
     __shared__ double s_Sd;
     const WT *w = static_cast<const WT *>(a.w);
     const double m = *a.m;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     LocalCtr lc;
+    for (uint32_t s = threadIdx.x; s < CAP; s += blockDim.x) { keys[s] = EMPTY; vals[s] = V(0); }
     for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
         uint32_t i = list[idx];
         __syncthreads();  // previous vertex done with the table and reductions
@@ -343,6 +353,7 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
             int go = ld_state<SYNC>(a.act + i);
             if (go) a.act[i] = 0;
             s_go = go;
+            s_nocc = 0;
             if (go) {
                 s_d = ld_state<SYNC>(a.C + i);
                 s_Sd = ld_state<SYNC>(a.Sig + s_d);
@@ -354,16 +365,6 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
         uint64_t b = a.off[i], e = a.off[i + 1];
         uint32_t deg = (uint32_t)(e - b);
         int logcap = ceil_log2(2 * deg);
-        if (logcap < 1) logcap = 1;
-        uint32_t cap = 1u << logcap;
-        uint32_t *keys = s_keys;
-        V *vals = s_vals;
-        if (CAP == 0) {
-            keys = pool_keys + pool_off[idx];
-            vals = static_cast<V *>(pool_vals) + pool_off[idx];
-        }
-        for (uint32_t s = threadIdx.x; s < cap; s += blockDim.x) { keys[s] = EMPTY; vals[s] = V(0); }
-        __syncthreads();
         V kid = 0;
         for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
             uint32_t j = __ldg(a.tgt + p);
@@ -371,7 +372,10 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
             V wv = load_w<V>(w, p);
             uint32_t c = ld_state<SYNC>(a.C + j);
             if (c == d) kid += wv;
-            else ht_add<V>(keys, vals, logcap, c, wv);
+            else {
+                uint32_t slot;
+                if (ht_add_slot<V>(keys, vals, logcap, c, wv, &slot) == 1) occ[atomicAdd(&s_nocc, 1u)] = (uint16_t)slot;
+            }
         }
         kid = warp_sum(kid);
         if (lane == 0) red_k[wid] = kid;
@@ -382,15 +386,16 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
         SC sc = make_score<F64>(Ki, (double)kid, s_Sd, m);
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
-        uint32_t ncand = 0;
-        for (uint32_t s = threadIdx.x; s < cap; s += blockDim.x) {
-            uint32_t c = keys[s];
-            if (c == EMPTY) continue;
-            ncand++;
-            S v = sc.score(vals[s], ld_state<SYNC>(a.Sig + c));
+        uint32_t nocc = s_nocc;
+        for (uint32_t k = threadIdx.x; k < nocc; k += blockDim.x) {
+            uint32_t slot = occ[k];
+            uint32_t c = keys[slot];
+            S v = sc.score(vals[slot], ld_state<SYNC>(a.Sig + c));
+            keys[slot] = EMPTY;  // leave the table empty for the next vertex
+            vals[slot] = V(0);
             if (better(v, c, best, bestc)) { best = v; bestc = c; }
         }
-        lc.candidates += ncand;
+        if (threadIdx.x == 0) lc.candidates += nocc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             S v2 = __shfl_xor_sync(0xFFFFFFFFu, best, o);
@@ -486,21 +491,29 @@ __global__ void k_mark_big(const uint64_t *__restrict__ off, const uint32_t *__r
 }
 
 // --------------------------------------------------------------------------
-// Hub vertices (degree > 4096): every block of the grid works on every hub
-// of the wave in turn, so that one hub never waits on one block.
+// Hub vertices (degree > 4096), processed by the whole grid:
 //   prepare: read and clear each hub's flag, snapshot its community;
-//   insert:  all threads stride over the hub's edges into its global table;
-//   score:   all threads stride over the table; per-block best per hub;
+//   insert:  the hub's edges are cut into HUB_CHUNK-edge tasks; a block
+//            combines a task's communities in a shared-memory table, then
+//            publishes the distinct ones to the hub's global table (new keys
+//            append their slot to the hub's occupied list);
+//   score:   all threads stride over the occupied list (and reset the slots
+//            for the next sweep); per-block best per hub;
 //   decide:  one warp per hub reduces the block bests and decides the move.
 // --------------------------------------------------------------------------
 constexpr int HUB_BLOCKS = 152 * 4;
+constexpr uint32_t HUB_CHUNK = 2048;
+constexpr int HUB_SLOG = 12;  // shared table of 2 * HUB_CHUNK slots
 
 struct HubArgs {
     const uint32_t *hubs;
     uint32_t nh;
-    const uint64_t *pool_off;  // per hub (relative to this wave's first hub)
+    const uint64_t *pool_off;  // per hub
+    const uint64_t *tasks;     // per hub: prefix of chunk counts (nh + 1 entries, tasks[0] = base)
     uint32_t *keys;
     void *vals;
+    uint32_t *occ;
+    uint32_t *occ_n;    // per hub
     void *kid;          // per hub, V
     uint8_t *go;        // per hub
     uint32_t *d;        // per hub
@@ -523,28 +536,36 @@ __global__ void k_hub_prepare(MoveArgs a, HubArgs h) {
 template <typename WT, bool F64, bool SYNC>
 __global__ void __launch_bounds__(256) k_hub_insert(MoveArgs a, HubArgs h) {
     using V = typename std::conditional<F64, double, float>::type;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    uint32_t *skeys = reinterpret_cast<uint32_t *>(dyn_smem);
+    V *svals = reinterpret_cast<V *>(dyn_smem + sizeof(uint32_t) * (1u << HUB_SLOG));
+    __shared__ V red[32];
     const WT *w = static_cast<const WT *>(a.w);
     V *kidv = static_cast<V *>(h.kid);
-    uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-    for (uint32_t t = 0; t < h.nh; t++) {
+    for (uint32_t s = threadIdx.x; s < (1u << HUB_SLOG); s += blockDim.x) { skeys[s] = EMPTY; svals[s] = V(0); }
+    const uint64_t base = h.tasks[0], total = h.tasks[h.nh] - base;
+    for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
+        uint32_t t = task_item(h.tasks, h.nh, task + base);
         if (!h.go[t]) continue;
+        uint64_t chunk = task + base - h.tasks[t];
         uint32_t i = h.hubs[t], d = h.d[t];
-        uint64_t b = a.off[i], e = a.off[i + 1];
-        int logcap = ceil_log2((uint32_t)(2 * (e - b)));
-        uint32_t *keys = h.keys + h.pool_off[t];
-        V *vals = static_cast<V *>(h.vals) + h.pool_off[t];
+        uint64_t e1 = a.off[i + 1];
+        uint64_t b = a.off[i] + chunk * HUB_CHUNK;
+        uint64_t e = min(b + HUB_CHUNK, e1);
         V kid = 0;
-        for (uint64_t p = b + tid; p < e; p += T) {
+        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
             uint32_t j = __ldg(a.tgt + p);
             if (j == i) continue;
             V wv = load_w<V>(w, p);
             uint32_t c = ld_state<SYNC>(a.C + j);
             if (c == d) kid += wv;
-            else ht_add<V>(keys, vals, logcap, c, wv);
+            else ht_add<V>(skeys, svals, HUB_SLOG, c, wv);
         }
-        kid = warp_sum(kid);
-        if ((threadIdx.x & 31) == 0 && kid != V(0)) atomicAdd(kidv + t, kid);
+        kid = block_sum<V>(kid, red);
+        if (threadIdx.x == 0 && kid != V(0)) atomicAdd(kidv + t, kid);
+        int glog = ceil_log2((uint32_t)(2 * (e1 - a.off[i])));
+        publish_block_table<V>(skeys, svals, HUB_SLOG, h.keys + h.pool_off[t],
+                               static_cast<V *>(h.vals) + h.pool_off[t], glog, h.occ + h.pool_off[t], h.occ_n + t);
     }
 }
 
@@ -559,22 +580,22 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
     S *bs = static_cast<S *>(h.best_s);
     const double m = *a.m;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint64_t ncand = 0;
     for (uint32_t t = 0; t < h.nh; t++) {
         if (!h.go[t]) continue;
         uint32_t i = h.hubs[t], d = h.d[t];
-        uint64_t deg = a.off[i + 1] - a.off[i];
-        uint32_t cap = 1u << ceil_log2((uint32_t)(2 * deg));
-        const uint32_t *keys = h.keys + h.pool_off[t];
-        const V *vals = static_cast<const V *>(h.vals) + h.pool_off[t];
+        uint32_t *keys = h.keys + h.pool_off[t];
+        V *vals = static_cast<V *>(h.vals) + h.pool_off[t];
+        const uint32_t *occ = h.occ + h.pool_off[t];
+        uint32_t nocc = h.occ_n[t];
         SC sc = make_score<F64>(a.K[i], (double)kidv[t], ld_state<SYNC>(a.Sig + d), m);
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
-        for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += gridDim.x * blockDim.x) {
-            uint32_t c = keys[s];
-            if (c == EMPTY) continue;
-            ncand++;
-            S v = sc.score(vals[s], ld_state<SYNC>(a.Sig + c));
+        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nocc; k += gridDim.x * blockDim.x) {
+            uint32_t slot = occ[k];
+            uint32_t c = keys[slot];
+            S v = sc.score(vals[slot], ld_state<SYNC>(a.Sig + c));
+            keys[slot] = EMPTY;  // leave the table empty for the next sweep
+            vals[slot] = V(0);
             if (better(v, c, best, bestc)) { best = v; bestc = c; }
         }
 #pragma unroll
@@ -593,9 +614,6 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
             h.best_c[(size_t)t * gridDim.x + blockIdx.x] = bestc;
         }
     }
-    __shared__ unsigned long long su[32];
-    unsigned long long nc = block_sum<unsigned long long>(ncand, su);
-    if (threadIdx.x == 0 && nc) atomicAdd(&a.ctr->candidates, nc);
 }
 
 template <bool F64, bool SYNC>
@@ -635,6 +653,8 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h, uint32_t nblocks) {
             if (gain > 0.0) mv = decide_move<SYNC>(a, i, d, bestc, Ki);
             lc.vertices++;
             lc.edges += deg;
+            lc.candidates += h.occ_n[t];
+            h.occ_n[t] = 0;
             if (mv) {
                 lc.moved++;
                 lc.dq += gain;
@@ -649,6 +669,14 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h, uint32_t nblocks) {
     flush_counters(lc, a.ctr);
 }
 
+__global__ void k_hub_tasks(const uint64_t *__restrict__ off, const uint32_t *__restrict__ list, uint32_t count,
+                            uint64_t *ntask) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        uint32_t v = list[t];
+        ntask[t] = (off[v + 1] - off[v] + HUB_CHUNK - 1) / HUB_CHUNK;
+    }
+}
+
 // --------------------------------------------------------------------------
 // Degree classes
 // --------------------------------------------------------------------------
@@ -657,6 +685,7 @@ __device__ __forceinline__ int class_of(uint64_t deg) {
     if (deg <= 16) return CLS_G8;
     if (deg <= 32) return CLS_G16;
     if (deg <= 128) return CLS_G32;
+    if (deg <= 512) return CLS_W512;
     if (deg <= 4096) return CLS_BLOCK;
     return CLS_HUGE;
 }
@@ -734,6 +763,13 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
                                  cudaMemcpyDeviceToHost, s));
         GSP_CUDA(cudaStreamSynchronize(s));
         cl.pool_slots = cl.host_pool_off[nh];
+        uint64_t *ntask = arena().get<uint64_t>(nh);
+        cl.hub_tasks = arena().get<uint64_t>(nh + 1);
+        k_hub_tasks<<<grid_for(nh, 256), 256, 0, s>>>(g.off, cl.list + cl.cls_begin(CLS_HUGE), nh, ntask);
+        GSP_CHECK_LAUNCH();
+        exclusive_scan_u64(ntask, cl.hub_tasks, nh, s);
+        cl.hub_occ_n = arena().get<uint32_t>(nh);
+        GSP_CUDA(cudaMemsetAsync(cl.hub_occ_n, 0, sizeof(uint32_t) * nh, s));
     }
 }
 
@@ -742,7 +778,7 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
 // --------------------------------------------------------------------------
 template <typename WT, bool F64, bool SYNC>
 static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t *pool_keys, void *pool_vals,
-                        uint32_t *big, uint32_t *nbig, cudaStream_t s) {
+                        uint32_t *pool_occ, uint32_t *big, uint32_t *nbig, cudaStream_t s) {
     using V = typename std::conditional<F64, double, float>::type;
     GroupLists gl;
     const int G[4] = {4, 8, 16, 32};
@@ -758,10 +794,23 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         k_move_groups<WT, F64, SYNC><<<blocks, 256, 0, s>>>(a, gl);
         GSP_CHECK_LAUNCH();
     }
+    uint32_t nw5 = cl.count(CLS_W512, wave);
+    if (nw5) {
+        constexpr size_t smem = (size_t)8 * W512_CAP * (sizeof(uint32_t) + sizeof(V));
+        static bool attr = false;
+        if (!attr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_move_w512<WT, F64, SYNC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            attr = true;
+        }
+        k_move_w512<WT, F64, SYNC><<<grid_for((uint64_t)nw5 * 32, 256, 152 * 3), 256, smem, s>>>(
+            a, cl.list + cl.begin(CLS_W512, wave), nw5);
+        GSP_CHECK_LAUNCH();
+    }
     uint32_t nb = cl.count(CLS_BLOCK, wave);
     if (nb) {
         constexpr int CAP = 8192;
-        constexpr size_t smem = (size_t)CAP * (sizeof(uint32_t) + sizeof(V));
+        constexpr size_t smem = (size_t)CAP * (sizeof(uint32_t) + sizeof(V) + sizeof(uint16_t));
         static bool attr = false;
         if (!attr) {
             GSP_CUDA(cudaFuncSetAttribute(k_move_block<CAP, WT, F64, SYNC>,
@@ -769,21 +818,23 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
             attr = true;
         }
         k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, 152 * 2), 256, smem, s>>>(
-            a, cl.list + cl.begin(CLS_BLOCK, wave), nb, nullptr, nullptr, nullptr);
+            a, cl.list + cl.begin(CLS_BLOCK, wave), nb);
         GSP_CHECK_LAUNCH();
     }
     uint32_t nh = cl.count(CLS_HUGE, wave);
     if (nh) {
         using S = typename Score<F64>::S;
         uint32_t rel = cl.begin(CLS_HUGE, wave) - cl.cls_begin(CLS_HUGE);
-        uint64_t first, last;  // this wave's contiguous slice of the pool
         size_t mk = arena().mark();
         HubArgs h;
         h.hubs = cl.list + cl.begin(CLS_HUGE, wave);
         h.nh = nh;
         h.pool_off = cl.pool_off + rel;
+        h.tasks = cl.hub_tasks + rel;
         h.keys = pool_keys;
         h.vals = pool_vals;
+        h.occ = pool_occ;
+        h.occ_n = cl.hub_occ_n + rel;
         h.kid = arena().alloc(sizeof(V) * nh);
         h.go = arena().get<uint8_t>(nh);
         h.d = arena().get<uint32_t>(nh);
@@ -791,14 +842,17 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         h.best_c = arena().get<uint32_t>((size_t)nh * HUB_BLOCKS);
         h.big = big;
         h.nbig = nbig;
-        first = cl.host_pool_off[rel];
-        last = cl.host_pool_off[rel + nh];
-        GSP_CUDA(cudaMemsetAsync(pool_keys + first, 0xFF, sizeof(uint32_t) * (last - first), s));
-        GSP_CUDA(cudaMemsetAsync(static_cast<V *>(pool_vals) + first, 0, sizeof(V) * (last - first), s));
         GSP_CUDA(cudaMemsetAsync(h.kid, 0, sizeof(V) * nh, s));
         k_hub_prepare<SYNC><<<grid_for(nh, 256), 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();
-        k_hub_insert<WT, F64, SYNC><<<HUB_BLOCKS, 256, 0, s>>>(a, h);
+        constexpr size_t hsmem = (sizeof(uint32_t) + sizeof(V)) << HUB_SLOG;
+        static bool attr = false;
+        if (!attr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_hub_insert<WT, F64, SYNC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)hsmem));
+            attr = true;
+        }
+        k_hub_insert<WT, F64, SYNC><<<HUB_BLOCKS, 256, hsmem, s>>>(a, h);
         GSP_CHECK_LAUNCH();
         k_hub_score<WT, F64, SYNC><<<HUB_BLOCKS, 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();
@@ -838,10 +892,14 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
     a.max_logk = mb.max_logk;
     a.iter_frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
     a.salt = (uint32_t)(iteration * 0x9E3779B9u + mb.trace_salt);
+    // pool layout: keys (u32), values (8 bytes per slot), occupied-slot list (u32)
     uint32_t *pool_keys = static_cast<uint32_t *>(mb.pool);
-    void *pool_vals = pool_keys ? static_cast<void *>(pool_keys + align_up(cl.pool_slots, 64)) : nullptr;
+    const size_t sa = align_up(cl.pool_slots, 64);
+    void *pool_vals = pool_keys ? static_cast<void *>(pool_keys + sa) : nullptr;
+    uint32_t *pool_occ = pool_keys ? pool_keys + 3 * sa : nullptr;
     if (!sync) GSP_CUDA(cudaMemsetAsync(mb.nbig, 0, sizeof(uint32_t), s));
-#define GSP_WAVE(WT, F64, SYNC) launch_wave<WT, F64, SYNC>(cl, a, wave, pool_keys, pool_vals, mb.big, mb.nbig, s)
+#define GSP_WAVE(WT, F64, SYNC) \
+    launch_wave<WT, F64, SYNC>(cl, a, wave, pool_keys, pool_vals, pool_occ, mb.big, mb.nbig, s)
     if (g.wt == GSP_W_F32) {
         if (fp64) { if (sync) GSP_WAVE(float, true, true); else GSP_WAVE(float, true, false); }
         else { if (sync) GSP_WAVE(float, false, true); else GSP_WAVE(float, false, false); }

@@ -145,7 +145,7 @@ static void split_lp(const DevGraph &g, const Classes &cl, const uint32_t *C, bo
                 g.off, g.tgt, C, lab, flag, lst(CLS), cnt(CLS), changed);                            \
         GSP_CHECK_LAUNCH();                                                                          \
     }
-        LPG(4, CLS_G4) LPG(8, CLS_G8) LPG(16, CLS_G16) LPG(32, CLS_G32)
+        LPG(4, CLS_G4) LPG(8, CLS_G8) LPG(16, CLS_G16) LPG(32, CLS_G32) LPG(32, CLS_W512)
 #undef LPG
         if (nbig) {
             if (prune)

@@ -59,7 +59,7 @@ def _graph(off, tgt, w=None):
 
 
 def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=10.0,
-              aggregation_tolerance=0.8, split="bfs", split_when="pass", move="sync", waves=16,
+              aggregation_tolerance=0.8, split="lpp", split_when="pass", move="sync", waves=16,
               precision="mixed", singleton_rule=True, prune="flags", mlp_params=None,
               full_sweep_every=4, prune_threshold=0.5, stream=None):
     o = GspOpts()

@@ -198,9 +198,28 @@ struct PruneCtx {
     float threshold = 0.5f;
 };
 
+// One sweep: cl.W waves; in frozen-state mode each wave's moves are applied
+// before the next wave.
+static void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
+                           bool pruned, int it, int max_it, const uint32_t *wave_n, bool reset_ctr, cudaStream_t s) {
+    if (reset_ctr) GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
+    for (int wv = 0; wv < cl.W; wv++) {
+        if (!wave_n[wv]) continue;
+        if (sync) GSP_CUDA(cudaMemsetAsync(mb.mv_cnt, 0, sizeof(uint32_t), s));
+        move_wave(g, cl, mb, wv, sync, fp64, rule, pruned, it, max_it, s);
+        if (sync) apply_moves(g, mb, wave_n[wv], s);
+    }
+}
+
+static bool graphs_enabled() {
+    const char *e = getenv("GSP_NO_GRAPH");
+    return !(e && e[0] == '1');
+}
+
 // louvainMove (Algorithm 4): iterate sweeps until the summed gain of a sweep
-// is <= tau or max_iterations is reached.  A sweep runs cl.W waves; in
-// frozen-state mode each wave's moves are applied before the next wave.
+// is <= tau or max_iterations is reached.  The launches of a sweep do not
+// change within a pass: the first sweep runs directly, the second is captured
+// into a CUDA graph that the following sweeps replay.
 static MoveLoopResult move_loop(const DevGraph &g, const Classes &cl, MoveBuffers &mb, double tau, int max_it,
                                 bool sync, bool fp64, bool rule, const PruneCtx &pr, cudaStream_t s) {
     MoveLoopResult r{0, 0, 0, 0, 0, 0.0, 0.0f};
@@ -211,32 +230,55 @@ static MoveLoopResult move_loop(const DevGraph &g, const Classes &cl, MoveBuffer
         wave_n[wv] = 0;
         for (int c = 0; c < NUM_CLS; c++) wave_n[wv] += cl.count(c, wv);
     }
-    for (int it = 0; it < max_it; it++) {
-        GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
-        bool pruned = pr.learned && pr.full_every > 0 && (it % pr.full_every) != pr.full_every - 1;
-        GSP_CUDA(cudaEventRecord(e0, s));
-        if (pruned)
-            mlp_prune(g, mb, it, max_it, pr.threshold, s);
-        for (int wv = 0; wv < cl.W; wv++) {
-            if (!wave_n[wv]) continue;
-            if (sync) GSP_CUDA(cudaMemsetAsync(mb.mv_cnt, 0, sizeof(uint32_t), s));
-            move_wave(g, cl, mb, wv, sync, fp64, rule, pruned, it, max_it, s);
-            if (sync) apply_moves(g, mb, wave_n[wv], s);
+    // features (learned pruning, traces) depend on the iteration number, so
+    // those runs launch directly
+    const bool use_graph = graphs_enabled() && !mb.feat_kept;
+    cudaGraphExec_t exec = nullptr;
+    side_streams();
+    try {
+        for (int it = 0; it < max_it; it++) {
+            bool pruned = pr.learned && pr.full_every > 0 && (it % pr.full_every) != pr.full_every - 1;
+            GSP_CUDA(cudaEventRecord(e0, s));
+            if (use_graph && it >= 1) {
+                if (!exec) {
+                    cudaGraph_t graph;
+                    GSP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+                    sweep_launches(g, cl, mb, sync, fp64, rule, false, it, max_it, wave_n, true, s);
+                    GSP_CUDA(cudaStreamEndCapture(s, &graph));
+                    GSP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+                    GSP_CUDA(cudaGraphDestroy(graph));
+                }
+                GSP_CUDA(cudaGraphLaunch(exec, s));
+            } else {
+                GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
+                if (pruned) mlp_prune(g, mb, it, max_it, pr.threshold, s);
+                sweep_launches(g, cl, mb, sync, fp64, rule, pruned, it, max_it, wave_n, false, s);
+            }
+            GSP_CUDA(cudaEventRecord(e1, s));
+            GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+            GSP_CUDA(cudaStreamSynchronize(s));
+            float ms = 0;
+            GSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            r.ms_kernels += ms;
+            r.bytes += sweep_bytes(h, g.wt);
+            r.iterations = it + 1;
+            r.vertices += h.vertices;
+            r.edges += h.edges;
+            r.candidates += h.candidates;
+            r.skipped += h.skipped;
+            if (h.dq <= tau) break;
         }
-        GSP_CUDA(cudaEventRecord(e1, s));
-        GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
-        GSP_CUDA(cudaStreamSynchronize(s));
-        float ms = 0;
-        GSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        r.ms_kernels += ms;
-        r.bytes += sweep_bytes(h, g.wt);
-        r.iterations = it + 1;
-        r.vertices += h.vertices;
-        r.edges += h.edges;
-        r.candidates += h.candidates;
-        r.skipped += h.skipped;
-        if (h.dq <= tau) break;
+    } catch (...) {
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t gdead;
+            cudaStreamEndCapture(s, &gdead);
+            if (gdead) cudaGraphDestroy(gdead);
+        }
+        throw;
     }
+    if (exec) GSP_CUDA(cudaGraphExecDestroy(exec));
     return r;
 }
 

@@ -32,6 +32,7 @@ struct Classes {
     std::vector<uint64_t> host_pool_off;
     uint64_t pool_slots = 0;
     uint64_t *hub_tasks = nullptr;  // huge class: prefix of edge-chunk counts (count+1)
+    std::vector<uint64_t> host_hub_tasks;
     uint32_t *hub_occ_n = nullptr;  // huge class: occupied-slot count of each hub table
     uint32_t begin(int cls, int wave) const { return start[cls * W + wave]; }
     uint32_t count(int cls, int wave) const { return start[cls * W + wave + 1] - start[cls * W + wave]; }
@@ -79,6 +80,16 @@ struct MoveBuffers {
     uint32_t *trace_cnt = nullptr;
     uint32_t trace_cap = 0, trace_every = 1, trace_salt = 0;
 };
+
+// Side streams for the independent kernels of a wave (fork/join with
+// events); created once per device.
+struct SideStreams {
+    static constexpr int N = 3;
+    cudaStream_t side[N];
+    cudaEvent_t fork_ev[64], join_ev[64][N];
+    int next = 0;
+};
+SideStreams &side_streams();
 
 // One wave of a sweep over the active vertices.  sync: frozen-state wave
 // (decisions go to the move list; apply_moves() applies them); otherwise

@@ -56,15 +56,44 @@ __global__ void k_row_sums(const uint64_t *__restrict__ off, const uint32_t *__r
     }
 }
 
+// Long rows: one warp per row up to 8192 entries, one block per longer row.
+constexpr uint32_t WARP_ROW = 8192;
+
 template <typename WT>
 __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                                 const WT *__restrict__ w, const uint32_t *__restrict__ C, double *K, double *Sig,
                                 double *acc, const uint32_t *longlist, const uint32_t *nlong) {
     __shared__ double red[32];
     uint32_t cnt = *nlong;
+    const int lane = threadIdx.x & 31;
+    uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    double wk = 0, win = 0;
+    for (uint32_t t = warp; t < cnt; t += nwarps) {
+        uint32_t i = longlist[t];
+        uint64_t b = off[i], e = off[i + 1];
+        if (e - b > WARP_ROW) continue;
+        uint32_t ci = C ? C[i] : 0;
+        double k = 0, in = 0;
+        for (uint64_t p = b + lane; p < e; p += 32) {
+            double wv = (double)w[p];
+            k += wv;
+            if (C && C[tgt[p]] == ci) in += wv;
+        }
+        k = warp_sum(k);
+        in = warp_sum(in);
+        if (lane == 0) {
+            if (K) K[i] = k;
+            if (Sig) atomicAdd(Sig + ci, k);
+            wk += k;
+            win += in;
+        }
+    }
+    // rows longer than WARP_ROW: one block each
     for (uint32_t t = blockIdx.x; t < cnt; t += gridDim.x) {
         uint32_t i = longlist[t];
         uint64_t b = off[i], e = off[i + 1];
+        if (e - b <= WARP_ROW) continue;
         uint32_t ci = C ? C[i] : 0;
         double k = 0, in = 0;
         for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
@@ -77,9 +106,15 @@ __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t
         if (threadIdx.x == 0) {
             if (K) K[i] = k;
             if (Sig) atomicAdd(Sig + ci, k);
-            atomicAdd(acc, k);
-            if (C) atomicAdd(acc + 1, in);
+            wk += k;
+            win += in;
         }
+    }
+    wk = block_sum(wk, red);
+    win = block_sum(win, red);
+    if (threadIdx.x == 0) {
+        if (wk != 0.0) atomicAdd(acc, wk);
+        if (C && win != 0.0) atomicAdd(acc + 1, win);
     }
 }
 

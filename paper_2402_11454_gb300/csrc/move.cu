@@ -517,8 +517,8 @@ struct HubArgs {
     void *kid;          // per hub, V
     uint8_t *go;        // per hub
     uint32_t *d;        // per hub
-    void *best_s;       // [nh][HUB_BLOCKS], S
-    uint32_t *best_c;   // [nh][HUB_BLOCKS]
+    void *best_s;       // per task, S
+    uint32_t *best_c;   // per task
     uint32_t *big, *nbig;
 };
 
@@ -569,6 +569,9 @@ __global__ void __launch_bounds__(256) k_hub_insert(MoveArgs a, HubArgs h) {
     }
 }
 
+// Scoring uses the insert's task split: task k of a hub scores occupied
+// entries [k*HUB_CHUNK, (k+1)*HUB_CHUNK) (a hub has at most one distinct
+// community per edge) and leaves its best in best[task].
 template <typename WT, bool F64, bool SYNC>
 __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
     using V = typename std::conditional<F64, double, float>::type;
@@ -580,17 +583,20 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
     S *bs = static_cast<S *>(h.best_s);
     const double m = *a.m;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (uint32_t t = 0; t < h.nh; t++) {
+    const uint64_t base = h.tasks[0], total = h.tasks[h.nh] - base;
+    for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
+        uint32_t t = task_item(h.tasks, h.nh, task + base);
         if (!h.go[t]) continue;
+        uint64_t k0 = (task + base - h.tasks[t]) * HUB_CHUNK;
         uint32_t i = h.hubs[t], d = h.d[t];
         uint32_t *keys = h.keys + h.pool_off[t];
         V *vals = static_cast<V *>(h.vals) + h.pool_off[t];
         const uint32_t *occ = h.occ + h.pool_off[t];
-        uint32_t nocc = h.occ_n[t];
+        uint64_t k1 = min(k0 + HUB_CHUNK, (uint64_t)h.occ_n[t]);
         SC sc = make_score<F64>(a.K[i], (double)kidv[t], ld_state<SYNC>(a.Sig + d), m);
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
-        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nocc; k += gridDim.x * blockDim.x) {
+        for (uint64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             uint32_t slot = occ[k];
             uint32_t c = keys[slot];
             S v = sc.score(vals[slot], ld_state<SYNC>(a.Sig + c));
@@ -610,14 +616,14 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
         if (threadIdx.x == 0) {
             for (int k = 1; k < (int)(blockDim.x >> 5); k++)
                 if (better(red_s[k], red_c[k], best, bestc)) { best = red_s[k]; bestc = red_c[k]; }
-            bs[(size_t)t * gridDim.x + blockIdx.x] = best;
-            h.best_c[(size_t)t * gridDim.x + blockIdx.x] = bestc;
+            bs[task] = best;
+            h.best_c[task] = bestc;
         }
     }
 }
 
 template <bool F64, bool SYNC>
-__global__ void k_hub_decide(MoveArgs a, HubArgs h, uint32_t nblocks) {
+__global__ void k_hub_decide(MoveArgs a, HubArgs h) {
     using V = typename std::conditional<F64, double, float>::type;
     using SC = Score<F64>;
     using S = typename SC::S;
@@ -627,15 +633,16 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h, uint32_t nblocks) {
     const int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint64_t base = h.tasks[0];
     LocalCtr lc;
     for (uint32_t t = warp; t < h.nh; t += nwarps) {
         if (!h.go[t]) continue;
         uint32_t i = h.hubs[t], d = h.d[t];
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
-        for (uint32_t k = lane; k < nblocks; k += 32) {
-            S v = bs[(size_t)t * nblocks + k];
-            uint32_t c = h.best_c[(size_t)t * nblocks + k];
+        for (uint64_t k = h.tasks[t] - base + lane; k < h.tasks[t + 1] - base; k += 32) {
+            S v = bs[k];
+            uint32_t c = h.best_c[k];
             if (c != EMPTY && better(v, c, best, bestc)) { best = v; bestc = c; }
         }
 #pragma unroll
@@ -768,6 +775,10 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
         k_hub_tasks<<<grid_for(nh, 256), 256, 0, s>>>(g.off, cl.list + cl.cls_begin(CLS_HUGE), nh, ntask);
         GSP_CHECK_LAUNCH();
         exclusive_scan_u64(ntask, cl.hub_tasks, nh, s);
+        cl.host_hub_tasks.resize(nh + 1);
+        GSP_CUDA(cudaMemcpyAsync(cl.host_hub_tasks.data(), cl.hub_tasks, sizeof(uint64_t) * (nh + 1),
+                                 cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
         cl.hub_occ_n = arena().get<uint32_t>(nh);
         GSP_CUDA(cudaMemsetAsync(cl.hub_occ_n, 0, sizeof(uint32_t) * nh, s));
     }
@@ -776,10 +787,46 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
 // --------------------------------------------------------------------------
 // Host launchers
 // --------------------------------------------------------------------------
+SideStreams &side_streams() {
+    static SideStreams ss[16];
+    static bool made[16] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 15;
+    if (!made[dev]) {
+        for (int k = 0; k < SideStreams::N; k++)
+            GSP_CUDA(cudaStreamCreateWithFlags(&ss[dev].side[k], cudaStreamNonBlocking));
+        for (int f = 0; f < 64; f++) {
+            GSP_CUDA(cudaEventCreateWithFlags(&ss[dev].fork_ev[f], cudaEventDisableTiming));
+            for (int k = 0; k < SideStreams::N; k++)
+                GSP_CUDA(cudaEventCreateWithFlags(&ss[dev].join_ev[f][k], cudaEventDisableTiming));
+        }
+        made[dev] = true;
+    }
+    return ss[dev];
+}
+
+// The class kernels of a wave touch disjoint vertices and only append to the
+// move list, so they run as parallel branches: W512 and the block class on
+// side streams 0 and 1, the hub chain on side stream 2, the group classes on
+// the main stream; all join before the wave's moves are applied.
 template <typename WT, bool F64, bool SYNC>
 static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t *pool_keys, void *pool_vals,
-                        uint32_t *pool_occ, uint32_t *big, uint32_t *nbig, cudaStream_t s) {
+                        uint32_t *pool_occ, uint32_t *big, uint32_t *nbig, cudaStream_t main) {
     using V = typename std::conditional<F64, double, float>::type;
+    SideStreams &ss = side_streams();
+    const int f = ss.next;
+    ss.next = (ss.next + 1) & 63;
+    bool used[SideStreams::N] = {false, false, false};
+    GSP_CUDA(cudaEventRecord(ss.fork_ev[f], main));
+    auto on = [&](int k) -> cudaStream_t {
+        if (!used[k]) {
+            GSP_CUDA(cudaStreamWaitEvent(ss.side[k], ss.fork_ev[f], 0));
+            used[k] = true;
+        }
+        return ss.side[k];
+    };
+    cudaStream_t s = main;
     GroupLists gl;
     const int G[4] = {4, 8, 16, 32};
     uint32_t blocks = 0;
@@ -803,7 +850,7 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
                                           (int)smem));
             attr = true;
         }
-        k_move_w512<WT, F64, SYNC><<<grid_for((uint64_t)nw5 * 32, 256, 152 * 3), 256, smem, s>>>(
+        k_move_w512<WT, F64, SYNC><<<grid_for((uint64_t)nw5 * 32, 256, 152 * 3), 256, smem, on(0)>>>(
             a, cl.list + cl.begin(CLS_W512, wave), nw5);
         GSP_CHECK_LAUNCH();
     }
@@ -817,12 +864,13 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr = true;
         }
-        k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, 152 * 2), 256, smem, s>>>(
+        k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, 152 * 2), 256, smem, on(1)>>>(
             a, cl.list + cl.begin(CLS_BLOCK, wave), nb);
         GSP_CHECK_LAUNCH();
     }
     uint32_t nh = cl.count(CLS_HUGE, wave);
     if (nh) {
+        cudaStream_t s = on(2);
         using S = typename Score<F64>::S;
         uint32_t rel = cl.begin(CLS_HUGE, wave) - cl.cls_begin(CLS_HUGE);
         size_t mk = arena().mark();
@@ -838,8 +886,9 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         h.kid = arena().alloc(sizeof(V) * nh);
         h.go = arena().get<uint8_t>(nh);
         h.d = arena().get<uint32_t>(nh);
-        h.best_s = arena().alloc(sizeof(S) * (size_t)nh * HUB_BLOCKS);
-        h.best_c = arena().get<uint32_t>((size_t)nh * HUB_BLOCKS);
+        uint64_t ntasks = cl.host_hub_tasks[rel + nh] - cl.host_hub_tasks[rel];
+        h.best_s = arena().alloc(sizeof(S) * ntasks);
+        h.best_c = arena().get<uint32_t>(ntasks);
         h.big = big;
         h.nbig = nbig;
         GSP_CUDA(cudaMemsetAsync(h.kid, 0, sizeof(V) * nh, s));
@@ -856,9 +905,14 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         GSP_CHECK_LAUNCH();
         k_hub_score<WT, F64, SYNC><<<HUB_BLOCKS, 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();
-        k_hub_decide<F64, SYNC><<<grid_for((uint64_t)nh * 32, 256), 256, 0, s>>>(a, h, HUB_BLOCKS);
+        k_hub_decide<F64, SYNC><<<grid_for((uint64_t)nh * 32, 256), 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();
         arena().release(mk);
+    }
+    for (int k = 0; k < SideStreams::N; k++) {
+        if (!used[k]) continue;
+        GSP_CUDA(cudaEventRecord(ss.join_ev[f][k], ss.side[k]));
+        GSP_CUDA(cudaStreamWaitEvent(main, ss.join_ev[f][k], 0));
     }
 }
 

@@ -220,8 +220,36 @@ static bool graphs_enabled() {
 // is <= tau or max_iterations is reached.  The launches of a sweep do not
 // change within a pass: the first sweep runs directly, the second is captured
 // into a CUDA graph that the following sweeps replay.
+// Library-owned stream for graph capture (the caller's stream may be the
+// legacy default stream, which cannot be captured).
+static cudaStream_t capture_stream() {
+    static cudaStream_t cs[16];
+    static bool made[16] = {false};
+    int d = cur_dev();
+    if (!made[d]) {
+        GSP_CUDA(cudaStreamCreateWithFlags(&cs[d], cudaStreamNonBlocking));
+        made[d] = true;
+    }
+    return cs[d];
+}
+
+static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuffers &mb, double tau, int max_it,
+                                   bool sync, bool fp64, bool rule, const PruneCtx &pr, cudaStream_t s);
+
 static MoveLoopResult move_loop(const DevGraph &g, const Classes &cl, MoveBuffers &mb, double tau, int max_it,
-                                bool sync, bool fp64, bool rule, const PruneCtx &pr, cudaStream_t s) {
+                                bool sync, bool fp64, bool rule, const PruneCtx &pr, cudaStream_t caller) {
+    cudaStream_t s = capture_stream();
+    cudaEvent_t in = g_events.get(), out = g_events.get();
+    GSP_CUDA(cudaEventRecord(in, caller));
+    GSP_CUDA(cudaStreamWaitEvent(s, in, 0));
+    MoveLoopResult r = move_loop_on(g, cl, mb, tau, max_it, sync, fp64, rule, pr, s);
+    GSP_CUDA(cudaEventRecord(out, s));
+    GSP_CUDA(cudaStreamWaitEvent(caller, out, 0));
+    return r;
+}
+
+static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuffers &mb, double tau, int max_it,
+                                   bool sync, bool fp64, bool rule, const PruneCtx &pr, cudaStream_t s) {
     MoveLoopResult r{0, 0, 0, 0, 0, 0.0, 0.0f};
     MoveCounters h;
     cudaEvent_t e0 = g_events.get(), e1 = g_events.get();

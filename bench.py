@@ -107,6 +107,10 @@ def make_workload(gsp, graphgen, name):
         off, tgt, w = gsp.gen_rmat(26, 16, seed=5)
         cfg = {"workload": "rmat26", "scale": 26, "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05],
                "seed": 5}
+    elif name.startswith("rmat") and name[4:].isdigit():  # smaller R-MAT, for profiling
+        sc = int(name[4:])
+        off, tgt, w = gsp.gen_rmat(sc, 16, seed=2)
+        cfg = {"workload": name, "scale": sc, "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05], "seed": 2}
     elif name == "planted":
         off, tgt, w = gsp.gen_planted(n=10000, k=64, mean_degree=16, p_intra=0.8, seed=1)
         cfg = {"workload": "planted", "vertices": 10000, "communities": 64, "mean_degree": 16,

@@ -265,10 +265,13 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     uint32_t *skeys = reinterpret_cast<uint32_t *>(dyn_smem);
     double *svals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * (1u << AGG_SLOG));
+    uint16_t *socc = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(double)) * (1u << AGG_SLOG));
+    __shared__ uint32_t s_nocc;
     const WT *w = static_cast<const WT *>(a.w);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t sub = AGG_CHUNK / (blockDim.x >> 5);  // edges per warp
     for (uint32_t s = threadIdx.x; s < (1u << AGG_SLOG); s += blockDim.x) { skeys[s] = EMPTY; svals[s] = 0.0; }
+    if (threadIdx.x == 0) s_nocc = 0;
     const uint64_t total = tasks[count];
     for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
         uint32_t t = task_item(tasks, count, task);
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
                     uint64_t base = a.off[v];
                     for (uint64_t tt = t0 + lane; tt < segend; tt += 32) {
                         uint64_t p = base + (tt - ms);
-                        ht_add<double>(skeys, svals, AGG_SLOG, a.Cd[a.tgt[p]], (double)w[p]);
+                        smem_add<double>(skeys, svals, AGG_SLOG, socc, &s_nocc, a.Cd[a.tgt[p]], (double)w[p]);
                     }
                     t0 = segend;
                 }
@@ -305,8 +308,8 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
         uint64_t bound = cd < a.k ? cd : a.k;
         int glog = ceil_log2((uint32_t)(2 * bound));
         if (glog < 1) glog = 1;
-        publish_block_table<double>(skeys, svals, AGG_SLOG, pool_keys + pool_off[t], pool_vals + pool_off[t], glog,
-                                    pool_occ + pool_off[t], occ_n + t);
+        publish_block_table<double>(skeys, svals, socc, &s_nocc, pool_keys + pool_off[t], pool_vals + pool_off[t],
+                                    glog, pool_occ + pool_off[t], occ_n + t);
     }
 }
 
@@ -543,7 +546,7 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
         k_agg_tasks<<<grid_for(nl, 256), 256, 0, s>>>(cdeg, llist, nl, ntask);
         GSP_CHECK_LAUNCH();
         exclusive_scan_u64(ntask, tasks, nl, s);
-        constexpr size_t lsmem = (sizeof(uint32_t) + sizeof(double)) << AGG_SLOG;
+        constexpr size_t lsmem = (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t)) << AGG_SLOG;
         static bool lattr = false;
         if (!lattr) {
             GSP_CUDA(cudaFuncSetAttribute(k_agg_large_insert<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,

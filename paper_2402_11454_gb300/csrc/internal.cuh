@@ -21,7 +21,7 @@ struct DevGraph {
 // pool.  Each class is further split into W waves (vertex v in wave v mod W):
 // the list holds key = class * W + wave in increasing order.
 enum { CLS_G4 = 0, CLS_G8, CLS_G16, CLS_G32, CLS_W512, CLS_BLOCK, CLS_HUGE, NUM_CLS };
-constexpr uint32_t CLS_MAXDEG[NUM_CLS] = {8, 16, 32, 128, 512, 4096, 0xFFFFFFFFu};
+constexpr uint32_t CLS_MAXDEG[NUM_CLS] = {8, 16, 32, 128, 512, 2048, 0xFFFFFFFFu};
 constexpr int MAX_WAVES = 64;
 
 struct Classes {
@@ -188,23 +188,35 @@ __device__ __forceinline__ int ht_add_slot(uint32_t *keys, V *vals, int logcap, 
     return -1;
 }
 
-// Combine-then-publish: the block's shared table (2^slog slots) is merged
-// into a global table (2^glog slots); keys new to the global table append
-// their slot to occ (count in *occ_n).  The shared table is left empty.
-// Every thread of the block must call this.
+// Combine-then-publish: the block's shared table (2^slog slots, whose
+// occupied slots are listed in socc[0..*s_nocc)) is merged into a global
+// table (2^glog slots); keys new to the global table append their slot to
+// occ (count in *occ_n).  The shared table is left empty.  Every thread of
+// the block must call this.
 template <typename V>
-__device__ void publish_block_table(uint32_t *skeys, V *svals, int slog, uint32_t *gkeys, V *gvals, int glog,
-                                    uint32_t *occ, uint32_t *occ_n) {
+__device__ void publish_block_table(uint32_t *skeys, V *svals, uint16_t *socc, uint32_t *s_nocc, uint32_t *gkeys,
+                                    V *gvals, int glog, uint32_t *occ, uint32_t *occ_n) {
     __syncthreads();
-    for (uint32_t s = threadIdx.x; s < (1u << slog); s += blockDim.x) {
+    uint32_t n = *s_nocc;
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+        uint32_t s = socc[t];
         uint32_t k = skeys[s];
-        if (k == EMPTY) continue;
         uint32_t slot;
         if (ht_add_slot<V>(gkeys, gvals, glog, k, svals[s], &slot) == 1) occ[atomicAdd(occ_n, 1u)] = slot;
         skeys[s] = EMPTY;
         svals[s] = V(0);
     }
     __syncthreads();
+    if (threadIdx.x == 0) *s_nocc = 0;
+    __syncthreads();
+}
+
+// Insert into a shared table, listing slots new to it in socc.
+template <typename V>
+__device__ __forceinline__ void smem_add(uint32_t *skeys, V *svals, int slog, uint16_t *socc, uint32_t *s_nocc,
+                                         uint32_t c, V w) {
+    uint32_t slot;
+    if (ht_add_slot<V>(skeys, svals, slog, c, w, &slot) == 1) socc[atomicAdd(s_nocc, 1u)] = (uint16_t)slot;
 }
 
 // Chunked work over items (hubs, communities) of different sizes: task ids

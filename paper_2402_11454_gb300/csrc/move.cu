@@ -7,8 +7,10 @@
 // it moves only on a strictly positive gain.  The work is binned by degree:
 //   groups of G = 4/8/16/32 lanes per vertex, table in shared memory (one
 //     fused launch for the four group classes);
-//   one block per vertex, table in shared memory (degree <= 4096);
-//   one block per vertex, table in a global-memory pool (larger degrees).
+//   one warp per vertex, 1024-slot shared table (degree <= 512);
+//   one block per vertex, table in shared memory (degree <= 2048);
+//   the whole grid per vertex for larger degrees ("hubs"): edge-chunk tasks
+//     combined in shared memory, published to a global-memory table.
 // Duplicate community keys meet in the table through atomicCAS on the key and
 // atomicAdd on the value.
 //
@@ -70,6 +72,36 @@ template <bool SYNC, typename T> __device__ __forceinline__ T ld_state(const T *
 
 template <typename V, typename WT> __device__ __forceinline__ V load_w(const WT *w, uint64_t e) {
     return (V)__ldg(w + e);
+}
+
+// Scan the edges [b, e) of vertex i with stride `step` starting at b + lane:
+// the self-loop is skipped, K_{i->d} accumulates in kid, other communities
+// go to ins(c, w).  U edges per thread per round, their loads issued before
+// their use, so that U gathers of C[j] are in flight at once.
+template <int U, bool SYNC, typename V, typename WT, typename F>
+__device__ __forceinline__ void scan_edges(const uint32_t *__restrict__ tgt, const WT *__restrict__ w,
+                                           const uint32_t *C, uint32_t i, uint32_t d, uint64_t b, uint64_t e,
+                                           uint32_t lane, uint32_t step, V &kid, F &&ins) {
+    for (uint64_t p0 = b + lane; p0 < e; p0 += (uint64_t)U * step) {
+        uint32_t j[U];
+        V wv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            uint64_t p = p0 + (uint64_t)u * step;
+            bool ok = p < e;
+            j[u] = ok ? __ldg(tgt + p) : i;
+            wv[u] = ok ? (V)__ldg(w + p) : V(0);
+        }
+        uint32_t c[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) c[u] = (j[u] != i) ? ld_state<SYNC>(C + j[u]) : EMPTY;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (c[u] == EMPTY) continue;
+            if (c[u] == d) kid += wv[u];
+            else ins(c[u], wv[u]);
+        }
+    }
 }
 
 // Equation 2, evaluated in the order written, with no contraction.
@@ -229,14 +261,8 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         for (uint32_t s = lane; s < cap; s += G) { keys[s] = EMPTY; vals[s] = V(0); }
         __syncwarp(gmask);
         V kid = 0;
-        for (uint64_t p = b + lane; p < e; p += G) {
-            uint32_t j = __ldg(a.tgt + p);
-            if (j == i) continue;
-            V wv = load_w<V>(w, p);
-            uint32_t c = ld_state<SYNC>(a.C + j);
-            if (c == d) kid += wv;
-            else ht_add<V>(keys, vals, logcap, c, wv);
-        }
+        scan_edges<(CAP >= 1024 ? 4 : 2), SYNC, V>(a.tgt, w, a.C, i, d, b, e, lane, G, kid,
+                                                    [&](uint32_t c, V wv) { ht_add<V>(keys, vals, logcap, c, wv); });
         __syncwarp(gmask);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) kid += __shfl_xor_sync(gmask, kid, o);
@@ -366,17 +392,8 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
         uint32_t deg = (uint32_t)(e - b);
         int logcap = ceil_log2(2 * deg);
         V kid = 0;
-        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
-            uint32_t j = __ldg(a.tgt + p);
-            if (j == i) continue;
-            V wv = load_w<V>(w, p);
-            uint32_t c = ld_state<SYNC>(a.C + j);
-            if (c == d) kid += wv;
-            else {
-                uint32_t slot;
-                if (ht_add_slot<V>(keys, vals, logcap, c, wv, &slot) == 1) occ[atomicAdd(&s_nocc, 1u)] = (uint16_t)slot;
-            }
-        }
+        scan_edges<4, SYNC, V>(a.tgt, w, a.C, i, d, b, e, threadIdx.x, blockDim.x, kid,
+                               [&](uint32_t c, V wv) { smem_add<V>(keys, vals, logcap, occ, &s_nocc, c, wv); });
         kid = warp_sum(kid);
         if (lane == 0) red_k[wid] = kid;
         __syncthreads();
@@ -443,12 +460,13 @@ __global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *
                               const uint32_t *__restrict__ mv_cnt, const double *__restrict__ K, uint32_t *C,
                               double *Sig, uint32_t *size, uint8_t *act, uint32_t *big, uint32_t *nbig,
                               MoveCounters *ctr) {
+    constexpr int G = 8;  // lanes per mover
     uint32_t cnt = *mv_cnt;
-    int lane = threadIdx.x & 31;
-    uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    int lane = threadIdx.x % G;
+    uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    uint32_t ngrp = (gridDim.x * blockDim.x) / G;
     unsigned long long marked = 0;
-    for (uint32_t t = warp; t < cnt; t += nwarps) {
+    for (uint32_t t = grp; t < cnt; t += ngrp) {
         uint32_t i = mv_vtx[t], c = mv_cmt[t];
         uint64_t b = off[i], e = off[i + 1];
         if (lane == 0) {
@@ -463,7 +481,7 @@ __global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *
             if (e - b > BIG_MOVER) big[atomicAdd(nbig, 1u)] = i;
         }
         if (e - b > BIG_MOVER) continue;
-        for (uint64_t p = b + lane; p < e; p += 32) {
+        for (uint64_t p = b + lane; p < e; p += G) {
             uint32_t j = tgt[p];
             if (j != i) act[j] = 1;
         }
@@ -491,7 +509,7 @@ __global__ void k_mark_big(const uint64_t *__restrict__ off, const uint32_t *__r
 }
 
 // --------------------------------------------------------------------------
-// Hub vertices (degree > 4096), processed by the whole grid:
+// Hub vertices (degree > 2048), processed by the whole grid:
 //   prepare: read and clear each hub's flag, snapshot its community;
 //   insert:  the hub's edges are cut into HUB_CHUNK-edge tasks; a block
 //            combines a task's communities in a shared-memory table, then
@@ -539,10 +557,13 @@ __global__ void __launch_bounds__(256) k_hub_insert(MoveArgs a, HubArgs h) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     uint32_t *skeys = reinterpret_cast<uint32_t *>(dyn_smem);
     V *svals = reinterpret_cast<V *>(dyn_smem + sizeof(uint32_t) * (1u << HUB_SLOG));
+    uint16_t *socc = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(V)) * (1u << HUB_SLOG));
     __shared__ V red[32];
+    __shared__ uint32_t s_nocc;
     const WT *w = static_cast<const WT *>(a.w);
     V *kidv = static_cast<V *>(h.kid);
     for (uint32_t s = threadIdx.x; s < (1u << HUB_SLOG); s += blockDim.x) { skeys[s] = EMPTY; svals[s] = V(0); }
+    if (threadIdx.x == 0) s_nocc = 0;
     const uint64_t base = h.tasks[0], total = h.tasks[h.nh] - base;
     for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
         uint32_t t = task_item(h.tasks, h.nh, task + base);
@@ -553,18 +574,12 @@ __global__ void __launch_bounds__(256) k_hub_insert(MoveArgs a, HubArgs h) {
         uint64_t b = a.off[i] + chunk * HUB_CHUNK;
         uint64_t e = min(b + HUB_CHUNK, e1);
         V kid = 0;
-        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
-            uint32_t j = __ldg(a.tgt + p);
-            if (j == i) continue;
-            V wv = load_w<V>(w, p);
-            uint32_t c = ld_state<SYNC>(a.C + j);
-            if (c == d) kid += wv;
-            else ht_add<V>(skeys, svals, HUB_SLOG, c, wv);
-        }
+        scan_edges<4, SYNC, V>(a.tgt, w, a.C, i, d, b, e, threadIdx.x, blockDim.x, kid,
+                               [&](uint32_t c, V wv) { smem_add<V>(skeys, svals, HUB_SLOG, socc, &s_nocc, c, wv); });
         kid = block_sum<V>(kid, red);
         if (threadIdx.x == 0 && kid != V(0)) atomicAdd(kidv + t, kid);
         int glog = ceil_log2((uint32_t)(2 * (e1 - a.off[i])));
-        publish_block_table<V>(skeys, svals, HUB_SLOG, h.keys + h.pool_off[t],
+        publish_block_table<V>(skeys, svals, socc, &s_nocc, h.keys + h.pool_off[t],
                                static_cast<V *>(h.vals) + h.pool_off[t], glog, h.occ + h.pool_off[t], h.occ_n + t);
     }
 }
@@ -693,7 +708,7 @@ __device__ __forceinline__ int class_of(uint64_t deg) {
     if (deg <= 32) return CLS_G16;
     if (deg <= 128) return CLS_G32;
     if (deg <= 512) return CLS_W512;
-    if (deg <= 4096) return CLS_BLOCK;
+    if (deg <= 2048) return CLS_BLOCK;
     return CLS_HUGE;
 }
 
@@ -856,7 +871,7 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
     }
     uint32_t nb = cl.count(CLS_BLOCK, wave);
     if (nb) {
-        constexpr int CAP = 8192;
+        constexpr int CAP = 4096;
         constexpr size_t smem = (size_t)CAP * (sizeof(uint32_t) + sizeof(V) + sizeof(uint16_t));
         static bool attr = false;
         if (!attr) {
@@ -864,7 +879,7 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr = true;
         }
-        k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, 152 * 2), 256, smem, on(1)>>>(
+        k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, 152 * 4), 256, smem, on(1)>>>(
             a, cl.list + cl.begin(CLS_BLOCK, wave), nb);
         GSP_CHECK_LAUNCH();
     }
@@ -894,7 +909,7 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         GSP_CUDA(cudaMemsetAsync(h.kid, 0, sizeof(V) * nh, s));
         k_hub_prepare<SYNC><<<grid_for(nh, 256), 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();
-        constexpr size_t hsmem = (sizeof(uint32_t) + sizeof(V)) << HUB_SLOG;
+        constexpr size_t hsmem = (sizeof(uint32_t) + sizeof(V) + sizeof(uint16_t)) << HUB_SLOG;
         static bool attr = false;
         if (!attr) {
             GSP_CUDA(cudaFuncSetAttribute(k_hub_insert<WT, F64, SYNC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -970,7 +985,7 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
 
 void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s) {
     GSP_CUDA(cudaMemsetAsync(mb.nbig, 0, sizeof(uint32_t), s));
-    k_apply_moves<<<grid_for((uint64_t)n_hint * 32, 256, 152 * 8), 256, 0, s>>>(
+    k_apply_moves<<<grid_for((uint64_t)n_hint * 8, 256, 152 * 8), 256, 0, s>>>(
         g.off, g.tgt, mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C, mb.Sigma, mb.size, mb.act, mb.big, mb.nbig,
         mb.ctr);
     GSP_CHECK_LAUNCH();

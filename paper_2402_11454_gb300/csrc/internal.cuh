@@ -193,19 +193,29 @@ __device__ __forceinline__ int ht_add_slot(uint32_t *keys, V *vals, int logcap, 
 // table (2^glog slots); keys new to the global table append their slot to
 // occ (count in *occ_n).  The shared table is left empty.  Every thread of
 // the block must call this.
+constexpr uint32_t PUBLISH_MAX = 2048;  // most distinct keys one block publishes at once
+
 template <typename V>
 __device__ void publish_block_table(uint32_t *skeys, V *svals, uint16_t *socc, uint32_t *s_nocc, uint32_t *gkeys,
                                     V *gvals, int glog, uint32_t *occ, uint32_t *occ_n) {
+    __shared__ uint32_t s_newslot[PUBLISH_MAX];
+    __shared__ uint32_t s_new, s_base;
     __syncthreads();
-    uint32_t n = *s_nocc;
+    if (threadIdx.x == 0) s_new = 0;
+    __syncthreads();
+    uint32_t n = min(*s_nocc, PUBLISH_MAX);
     for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
         uint32_t s = socc[t];
-        uint32_t k = skeys[s];
         uint32_t slot;
-        if (ht_add_slot<V>(gkeys, gvals, glog, k, svals[s], &slot) == 1) occ[atomicAdd(occ_n, 1u)] = slot;
+        if (ht_add_slot<V>(gkeys, gvals, glog, skeys[s], svals[s], &slot) == 1) s_newslot[atomicAdd(&s_new, 1u)] = slot;
         skeys[s] = EMPTY;
         svals[s] = V(0);
     }
+    __syncthreads();
+    // one reservation per block in the global occupied list
+    if (threadIdx.x == 0) s_base = s_new ? atomicAdd(occ_n, s_new) : 0;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < s_new; t += blockDim.x) occ[s_base + t] = s_newslot[t];
     __syncthreads();
     if (threadIdx.x == 0) *s_nocc = 0;
     __syncthreads();

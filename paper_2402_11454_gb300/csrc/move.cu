@@ -104,16 +104,46 @@ __device__ __forceinline__ void scan_edges(const uint32_t *__restrict__ tgt, con
     }
 }
 
+template <typename S> __device__ __forceinline__ bool better(S s1, uint32_t c1, S s2, uint32_t c2) {
+    return s1 > s2 || (s1 == s2 && c1 < c2);
+}
+
+// Score the entries of a table: slots s = lane, lane + step, ... < cap (or
+// the listed slots occ[...] when occ is given).  U entries per round, with
+// the gathers of Sigma_c issued together.
+template <int U, bool SYNC, typename SC, typename S, typename V>
+__device__ __forceinline__ void score_table(const uint32_t *keys, const V *vals, const uint16_t *occ, uint32_t cap,
+                                            uint32_t lane, uint32_t step, const double *Sig, const SC &sc, S &best,
+                                            uint32_t &bestc, uint32_t &ncand) {
+    for (uint32_t s0 = lane; s0 < cap; s0 += U * step) {
+        uint32_t c[U];
+        V v[U];
+        double sg[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            uint32_t s = s0 + u * step;
+            uint32_t slot = s < cap ? (occ ? (uint32_t)occ[s] : s) : 0;
+            c[u] = s < cap ? keys[slot] : EMPTY;
+            v[u] = s < cap ? vals[slot] : V(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) sg[u] = c[u] != EMPTY ? ld_state<SYNC>(Sig + c[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (c[u] == EMPTY) continue;
+            ncand++;
+            S val = sc.score(v[u], sg[u]);
+            if (better(val, c[u], best, bestc)) { best = val; bestc = c[u]; }
+        }
+    }
+}
+
 // Equation 2, evaluated in the order written, with no contraction.
 __device__ __forceinline__ double eq2(double Kic, double Kid, double Ki, double Sc, double Sd, double m) {
     double t1 = __ddiv_rn(__dsub_rn(Kic, Kid), m);
     double t2 = __dmul_rn(Ki, __dsub_rn(__dadd_rn(Ki, Sc), Sd));
     double den = __dmul_rn(__dmul_rn(2.0, m), m);
     return __dsub_rn(t1, __ddiv_rn(t2, den));
-}
-
-template <typename S> __device__ __forceinline__ bool better(S s1, uint32_t c1, S s2, uint32_t c2) {
-    return s1 > s2 || (s1 == s2 && c1 < c2);
 }
 
 // Per-vertex scoring context.
@@ -273,13 +303,8 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
         uint32_t ncand = 0;
-        for (uint32_t s = lane; s < cap; s += G) {
-            uint32_t c = keys[s];
-            if (c == EMPTY) continue;
-            ncand++;
-            S v = sc.score(vals[s], ld_state<SYNC>(a.Sig + c));
-            if (better(v, c, best, bestc)) { best = v; bestc = c; }
-        }
+        score_table<(CAP >= 1024 ? 4 : 2), SYNC>(keys, vals, (const uint16_t *)nullptr, cap, lane, G, a.Sig, sc, best,
+                                                  bestc, ncand);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             S v2 = __shfl_xor_sync(gmask, best, o);
@@ -404,13 +429,13 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
         uint32_t nocc = s_nocc;
+        uint32_t ncand = 0;
+        score_table<4, SYNC>(keys, vals, occ, nocc, threadIdx.x, blockDim.x, a.Sig, sc, best, bestc, ncand);
+        __syncthreads();  // every slot scored before the table is emptied
         for (uint32_t k = threadIdx.x; k < nocc; k += blockDim.x) {
             uint32_t slot = occ[k];
-            uint32_t c = keys[slot];
-            S v = sc.score(vals[slot], ld_state<SYNC>(a.Sig + c));
             keys[slot] = EMPTY;  // leave the table empty for the next vertex
             vals[slot] = V(0);
-            if (better(v, c, best, bestc)) { best = v; bestc = c; }
         }
         if (threadIdx.x == 0) lc.candidates += nocc;
 #pragma unroll
@@ -611,13 +636,31 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
         SC sc = make_score<F64>(a.K[i], (double)kidv[t], ld_state<SYNC>(a.Sig + d), m);
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
-        for (uint64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-            uint32_t slot = occ[k];
-            uint32_t c = keys[slot];
-            S v = sc.score(vals[slot], ld_state<SYNC>(a.Sig + c));
-            keys[slot] = EMPTY;  // leave the table empty for the next sweep
-            vals[slot] = V(0);
-            if (better(v, c, best, bestc)) { best = v; bestc = c; }
+        // U entries per thread per round; each level of the gather chain
+        // (occupied list -> slot -> Sigma) is issued for all U at once
+        constexpr int U = 8;
+        for (uint64_t kb = k0 + threadIdx.x; kb < k1; kb += (uint64_t)U * blockDim.x) {
+            uint32_t slot[U], c[U];
+            V val[U];
+            double sg[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                uint64_t k = kb + (uint64_t)u * blockDim.x;
+                slot[u] = k < k1 ? occ[k] : EMPTY;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                c[u] = slot[u] != EMPTY ? keys[slot[u]] : EMPTY;
+                val[u] = slot[u] != EMPTY ? vals[slot[u]] : V(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) sg[u] = c[u] != EMPTY ? ld_state<SYNC>(a.Sig + c[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (c[u] == EMPTY) continue;
+                S v = sc.score(val[u], sg[u]);
+                if (better(v, c[u], best, bestc)) { best = v; bestc = c[u]; }
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -906,6 +949,11 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         h.best_c = arena().get<uint32_t>(ntasks);
         h.big = big;
         h.nbig = nbig;
+        // this wave's tables: one contiguous slice of the pool, cleared with
+        // coalesced memsets
+        uint64_t first = cl.host_pool_off[rel], last = cl.host_pool_off[rel + nh];
+        GSP_CUDA(cudaMemsetAsync(pool_keys + first, 0xFF, sizeof(uint32_t) * (last - first), s));
+        GSP_CUDA(cudaMemsetAsync(static_cast<V *>(pool_vals) + first, 0, sizeof(V) * (last - first), s));
         GSP_CUDA(cudaMemsetAsync(h.kid, 0, sizeof(V) * nh, s));
         k_hub_prepare<SYNC><<<grid_for(nh, 256), 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();

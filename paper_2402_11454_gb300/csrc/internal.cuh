@@ -170,6 +170,24 @@ __device__ __forceinline__ int ht_add(uint32_t *keys, V *vals, int logcap, uint3
     return -1;
 }
 
+// Global-table insert that claims with atomicCAS first (one round trip when
+// the home slot is free or already holds c); reports the slot used.
+template <typename V>
+__device__ __forceinline__ int ht_add_slot_cas(uint32_t *keys, V *vals, int logcap, uint32_t c, V w, uint32_t *slot) {
+    uint32_t mask = (1u << logcap) - 1u;
+    uint32_t h = logcap ? (hash32(c) >> (32 - logcap)) : 0u;
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        uint32_t old = atomicCAS(&keys[h], EMPTY, c);
+        if (old == EMPTY || old == c) {
+            atomicAdd(&vals[h], w);
+            *slot = h;
+            return old == EMPTY;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
 // As ht_add, also reporting the slot used (for occupied-slot lists).
 template <typename V>
 __device__ __forceinline__ int ht_add_slot(uint32_t *keys, V *vals, int logcap, uint32_t c, V w, uint32_t *slot) {
@@ -207,7 +225,8 @@ __device__ void publish_block_table(uint32_t *skeys, V *svals, uint16_t *socc, u
     for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
         uint32_t s = socc[t];
         uint32_t slot;
-        if (ht_add_slot<V>(gkeys, gvals, glog, skeys[s], svals[s], &slot) == 1) s_newslot[atomicAdd(&s_new, 1u)] = slot;
+        if (ht_add_slot_cas<V>(gkeys, gvals, glog, skeys[s], svals[s], &slot) == 1)
+            s_newslot[atomicAdd(&s_new, 1u)] = slot;
         skeys[s] = EMPTY;
         svals[s] = V(0);
     }

@@ -480,12 +480,41 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
 // --------------------------------------------------------------------------
 constexpr uint32_t BIG_MOVER = 2048;
 
-__global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
-                              const uint32_t *__restrict__ mv_vtx, const uint32_t *__restrict__ mv_cmt,
-                              const uint32_t *__restrict__ mv_cnt, const double *__restrict__ K, uint32_t *C,
-                              double *Sig, uint32_t *size, uint8_t *act, uint32_t *big, uint32_t *nbig,
-                              MoveCounters *ctr) {
+// Community totals change by +-K_i per move; movers of a wave crowd into a
+// few large communities, so the deltas are first summed per block in a
+// shared table (float64 sums of exactly representable values, exact in any
+// order) and then applied with one atomic per community per block.
+constexpr int APPLY_SLOG = 11;
+
+__device__ __forceinline__ void apply_delta(uint32_t *keys, double *ds, int *dn, uint32_t c, double k, int n,
+                                            double *Sig, uint32_t *size) {
+    uint32_t mask = (1u << APPLY_SLOG) - 1u;
+    uint32_t h = hash32(c) >> (32 - APPLY_SLOG);
+    for (uint32_t probe = 0; probe < 64; probe++) {
+        uint32_t old = atomicCAS(&keys[h], EMPTY, c);
+        if (old == EMPTY || old == c) {
+            atomicAdd(&ds[h], k);
+            atomicAdd(&dn[h], n);
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicAdd(Sig + c, k);  // crowded table: apply directly
+    atomicAdd(size + c, (uint32_t)n);
+}
+
+__global__ void __launch_bounds__(256) k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                                                     const uint32_t *__restrict__ mv_vtx,
+                                                     const uint32_t *__restrict__ mv_cmt,
+                                                     const uint32_t *__restrict__ mv_cnt, const double *__restrict__ K,
+                                                     uint32_t *C, double *Sig, uint32_t *size, uint8_t *act,
+                                                     uint32_t *big, uint32_t *nbig, MoveCounters *ctr) {
     constexpr int G = 8;  // lanes per mover
+    __shared__ uint32_t skeys[1 << APPLY_SLOG];
+    __shared__ double sds[1 << APPLY_SLOG];
+    __shared__ int sdn[1 << APPLY_SLOG];
+    for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) { skeys[t] = EMPTY; sds[t] = 0.0; sdn[t] = 0; }
+    __syncthreads();
     uint32_t cnt = *mv_cnt;
     int lane = threadIdx.x % G;
     uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -498,10 +527,8 @@ __global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *
             uint32_t d = C[i];
             double Ki = K[i];
             C[i] = c;
-            atomicAdd(Sig + d, -Ki);
-            atomicAdd(Sig + c, Ki);
-            atomicSub(size + d, 1u);
-            atomicAdd(size + c, 1u);
+            apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size);
+            apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size);
             marked += e - b;
             if (e - b > BIG_MOVER) big[atomicAdd(nbig, 1u)] = i;
         }
@@ -511,22 +538,29 @@ __global__ void k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *
             if (j != i) act[j] = 1;
         }
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) {
+        uint32_t c = skeys[t];
+        if (c == EMPTY) continue;
+        if (sds[t] != 0.0) atomicAdd(Sig + c, sds[t]);
+        if (sdn[t] != 0) atomicAdd(size + c, (uint32_t)sdn[t]);
+    }
     __shared__ unsigned long long red[32];
     marked = block_sum(marked, red);
     if (threadIdx.x == 0 && marked) atomicAdd(&ctr->marked, marked);
 }
 
-// Re-mark the neighbours of the big movers: every thread of the grid strides
-// over each mover's edges in turn.
+// Re-mark the neighbours of the big movers: block column x takes movers
+// x, x + gridDim.x, ...; the gridDim.y blocks of a column split each mover's
+// edges into interleaved slices.
 __global__ void k_mark_big(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                            const uint32_t *__restrict__ big, const uint32_t *__restrict__ nbig, uint8_t *act) {
     uint32_t cnt = *nbig;
-    uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-    for (uint32_t t = 0; t < cnt; t++) {
+    uint64_t step = (uint64_t)gridDim.y * blockDim.x;
+    for (uint32_t t = blockIdx.x; t < cnt; t += gridDim.x) {
         uint32_t i = big[t];
         uint64_t b = off[i], e = off[i + 1];
-        for (uint64_t p = b + tid; p < e; p += T) {
+        for (uint64_t p = b + (uint64_t)blockIdx.y * blockDim.x + threadIdx.x; p < e; p += step) {
             uint32_t j = tgt[p];
             if (j != i) act[j] = 1;
         }
@@ -1026,7 +1060,7 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
     }
 #undef GSP_WAVE
     if (!sync && cl.count(CLS_HUGE, wave)) {
-        k_mark_big<<<HUB_BLOCKS, 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, mb.act);
+        k_mark_big<<<dim3(152, 16), 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, mb.act);
         GSP_CHECK_LAUNCH();
     }
 }
@@ -1037,7 +1071,7 @@ void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream
         g.off, g.tgt, mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C, mb.Sigma, mb.size, mb.act, mb.big, mb.nbig,
         mb.ctr);
     GSP_CHECK_LAUNCH();
-    k_mark_big<<<HUB_BLOCKS, 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, mb.act);
+    k_mark_big<<<dim3(152, 16), 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, mb.act);
     GSP_CHECK_LAUNCH();
 }
 

@@ -316,6 +316,7 @@ static void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.Sigma = arena().get<double>(n);
     mb.size = arena().get<uint32_t>(n);
     mb.act = arena().get<uint8_t>(n);
+    mb.mark = arena().get<uint8_t>(n);
     mb.mv_vtx = arena().get<uint32_t>(n);
     mb.mv_cmt = arena().get<uint32_t>(n);
     mb.mv_cnt = arena().get<uint32_t>(1);
@@ -457,6 +458,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         k_fill_u32<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
         GSP_CHECK_LAUNCH();
         GSP_CUDA(cudaMemsetAsync(mb.act, 1, nv, s));
+        GSP_CUDA(cudaMemsetAsync(mb.mark, 0, nv, s));
         if (features) {
             k_init_features<<<grid_for(nv, 256), 256, 0, s>>>(mb.feat_kept, mb.feat_gain, mb.moved_last, nv);
             GSP_CHECK_LAUNCH();
@@ -719,6 +721,7 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
     else GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
     GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
     GSP_CUDA(cudaMemsetAsync(mb.mv_cnt, 0, sizeof(uint32_t), s));
+    GSP_CUDA(cudaMemsetAsync(mb.mark, 0, n, s));
     Classes cl;
     classify_vertices(g, cl, 1, s);
     alloc_pool(mb, cl, s);
@@ -757,6 +760,7 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
     k_community_sizes<<<grid_for(n, 256), 256, 0, s>>>(C, n, mb.size);
     GSP_CHECK_LAUNCH();
     GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
+    GSP_CUDA(cudaMemsetAsync(mb.mark, 0, n, s));
     Classes cl;
     classify_vertices(g, cl, sync ? waves : 1, s);
     alloc_pool(mb, cl, s);

@@ -58,6 +58,7 @@ struct MoveBuffers {
     double *Sigma = nullptr;     // community totals
     uint32_t *size = nullptr;    // community sizes (singleton rule)
     uint8_t *act = nullptr;      // unprocessed flags
+    uint8_t *mark = nullptr;     // re-marks of a frozen-state wave (merged into act after it)
     const double *K = nullptr;
     double *m_dev = nullptr;     // device copy of m
     MoveCounters *ctr = nullptr;

@@ -42,6 +42,7 @@ struct MoveArgs {
     double *Sig;
     uint32_t *size;
     uint8_t *act;
+    uint8_t *mark;  // re-marking target: a separate array merged after a frozen-state wave, act in place
     const double *m;
     MoveCounters *ctr;
     int rule;
@@ -321,14 +322,14 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
             if (mv) { lc.moved++; lc.dq += gain; }
             record_visit(a, i, deg, Ki, (double)kid, gain, m, mv);
         }
-        if constexpr (!SYNC) {  // in place: movers re-mark their neighbours now
-            mv = __shfl_sync(gmask, mv, leader);
-            if (mv) {
-                if (lane == 0) lc.marked += deg;
-                for (uint64_t p = b + lane; p < e; p += G) {
-                    uint32_t j = __ldg(a.tgt + p);
-                    if (j != i) a.act[j] = 1;
-                }
+        // movers re-mark their neighbours (frozen-state waves write a separate
+        // array merged after the wave, so that the wave never sees its marks)
+        mv = __shfl_sync(gmask, mv, leader);
+        if (mv) {
+            if (lane == 0) lc.marked += deg;
+            for (uint64_t p = b + lane; p < e; p += G) {
+                uint32_t j = __ldg(a.tgt + p);
+                if (j != i) a.mark[j] = 1;
             }
         }
         __syncwarp(gmask);
@@ -459,11 +460,11 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
             s_mv = mv;
         }
         __syncthreads();
-        if (!SYNC && s_mv) {
+        if (s_mv) {
             if (threadIdx.x == 0) lc.marked += deg;
             for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
                 uint32_t j = __ldg(a.tgt + p);
-                if (j != i) a.act[j] = 1;
+                if (j != i) a.mark[j] = 1;
             }
         }
     }
@@ -503,40 +504,23 @@ __device__ __forceinline__ void apply_delta(uint32_t *keys, double *ds, int *dn,
     atomicAdd(size + c, (uint32_t)n);
 }
 
-__global__ void __launch_bounds__(256) k_apply_moves(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
-                                                     const uint32_t *__restrict__ mv_vtx,
+__global__ void __launch_bounds__(256) k_apply_moves(const uint32_t *__restrict__ mv_vtx,
                                                      const uint32_t *__restrict__ mv_cmt,
                                                      const uint32_t *__restrict__ mv_cnt, const double *__restrict__ K,
-                                                     uint32_t *C, double *Sig, uint32_t *size, uint8_t *act,
-                                                     uint32_t *big, uint32_t *nbig, MoveCounters *ctr) {
-    constexpr int G = 8;  // lanes per mover
+                                                     uint32_t *C, double *Sig, uint32_t *size) {
     __shared__ uint32_t skeys[1 << APPLY_SLOG];
     __shared__ double sds[1 << APPLY_SLOG];
     __shared__ int sdn[1 << APPLY_SLOG];
     for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) { skeys[t] = EMPTY; sds[t] = 0.0; sdn[t] = 0; }
     __syncthreads();
     uint32_t cnt = *mv_cnt;
-    int lane = threadIdx.x % G;
-    uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    uint32_t ngrp = (gridDim.x * blockDim.x) / G;
-    unsigned long long marked = 0;
-    for (uint32_t t = grp; t < cnt; t += ngrp) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         uint32_t i = mv_vtx[t], c = mv_cmt[t];
-        uint64_t b = off[i], e = off[i + 1];
-        if (lane == 0) {
-            uint32_t d = C[i];
-            double Ki = K[i];
-            C[i] = c;
-            apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size);
-            apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size);
-            marked += e - b;
-            if (e - b > BIG_MOVER) big[atomicAdd(nbig, 1u)] = i;
-        }
-        if (e - b > BIG_MOVER) continue;
-        for (uint64_t p = b + lane; p < e; p += G) {
-            uint32_t j = tgt[p];
-            if (j != i) act[j] = 1;
-        }
+        uint32_t d = C[i];
+        double Ki = K[i];
+        C[i] = c;
+        apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size);
+        apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) {
@@ -545,9 +529,25 @@ __global__ void __launch_bounds__(256) k_apply_moves(const uint64_t *__restrict_
         if (sds[t] != 0.0) atomicAdd(Sig + c, sds[t]);
         if (sdn[t] != 0) atomicAdd(size + c, (uint32_t)sdn[t]);
     }
-    __shared__ unsigned long long red[32];
-    marked = block_sum(marked, red);
-    if (threadIdx.x == 0 && marked) atomicAdd(&ctr->marked, marked);
+}
+
+// act |= mark, mark = 0 (16 bytes per thread step).
+__global__ void k_merge_marks(uint8_t *act, uint8_t *mark, uint32_t n) {
+    uint32_t n16 = n / 16;
+    uint4 *a4 = reinterpret_cast<uint4 *>(act);
+    uint4 *m4 = reinterpret_cast<uint4 *>(mark);
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n16; t += gridDim.x * blockDim.x) {
+        uint4 mk = m4[t];
+        if (mk.x | mk.y | mk.z | mk.w) {
+            uint4 ac = a4[t];
+            ac.x |= mk.x; ac.y |= mk.y; ac.z |= mk.z; ac.w |= mk.w;
+            a4[t] = ac;
+            m4[t] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    for (uint32_t v = n16 * 16 + blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (mark[v]) { act[v] = 1; mark[v] = 0; }
+    }
 }
 
 // Re-mark the neighbours of the big movers: block column x takes movers
@@ -754,13 +754,11 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h) {
             lc.edges += deg;
             lc.candidates += h.occ_n[t];
             h.occ_n[t] = 0;
-            if (mv) {
+            if (mv) {  // neighbours are re-marked by k_mark_big
                 lc.moved++;
                 lc.dq += gain;
-                if (!SYNC) {  // in place: neighbours are re-marked by k_mark_big
-                    lc.marked += deg;
-                    h.big[atomicAdd(h.nbig, 1u)] = i;
-                }
+                lc.marked += deg;
+                h.big[atomicAdd(h.nbig, 1u)] = i;
             }
             record_visit(a, i, (uint32_t)deg, Ki, (double)kidv[t], gain, m, mv);
         }
@@ -1025,6 +1023,7 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
     a.Sig = mb.Sigma;
     a.size = mb.size;
     a.act = mb.act;
+    a.mark = sync ? mb.mark : mb.act;
     a.m = mb.m_dev;
     a.ctr = mb.ctr;
     a.rule = rule ? 1 : 0;
@@ -1048,7 +1047,7 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
     const size_t sa = align_up(cl.pool_slots, 64);
     void *pool_vals = pool_keys ? static_cast<void *>(pool_keys + sa) : nullptr;
     uint32_t *pool_occ = pool_keys ? pool_keys + 3 * sa : nullptr;
-    if (!sync) GSP_CUDA(cudaMemsetAsync(mb.nbig, 0, sizeof(uint32_t), s));
+    GSP_CUDA(cudaMemsetAsync(mb.nbig, 0, sizeof(uint32_t), s));
 #define GSP_WAVE(WT, F64, SYNC) \
     launch_wave<WT, F64, SYNC>(cl, a, wave, pool_keys, pool_vals, pool_occ, mb.big, mb.nbig, s)
     if (g.wt == GSP_W_F32) {
@@ -1059,19 +1058,17 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
         else { if (sync) GSP_WAVE(double, false, true); else GSP_WAVE(double, false, false); }
     }
 #undef GSP_WAVE
-    if (!sync && cl.count(CLS_HUGE, wave)) {
-        k_mark_big<<<dim3(152, 16), 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, mb.act);
+    if (cl.count(CLS_HUGE, wave)) {  // hub movers re-mark their neighbours
+        k_mark_big<<<dim3(152, 16), 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, a.mark);
         GSP_CHECK_LAUNCH();
     }
 }
 
 void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s) {
-    GSP_CUDA(cudaMemsetAsync(mb.nbig, 0, sizeof(uint32_t), s));
-    k_apply_moves<<<grid_for((uint64_t)n_hint * 8, 256, 152 * 8), 256, 0, s>>>(
-        g.off, g.tgt, mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C, mb.Sigma, mb.size, mb.act, mb.big, mb.nbig,
-        mb.ctr);
+    k_apply_moves<<<grid_for(n_hint, 256, 152 * 4), 256, 0, s>>>(mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C,
+                                                                 mb.Sigma, mb.size);
     GSP_CHECK_LAUNCH();
-    k_mark_big<<<dim3(152, 16), 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, mb.act);
+    k_merge_marks<<<grid_for(g.n / 16 + 1, 256, 152 * 8), 256, 0, s>>>(mb.act, mb.mark, g.n);
     GSP_CHECK_LAUNCH();
 }
 

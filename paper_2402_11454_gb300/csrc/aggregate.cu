@@ -6,9 +6,10 @@
 //     paper's "holey" CSR with gaps);
 //  3. per community, an open-addressing table over the edges of all members
 //     (self-loops included) merges the weights per neighbouring community:
-//       total degree <= 128  : one warp, table in shared memory
-//       total degree <= 4096 : one block, table in shared memory
-//       larger               : one block, table in a global-memory pool;
+//       total degree <= 512  : one warp, 1024-slot table in shared memory
+//       total degree <= 2048 : one block, 4096-slot table in shared memory
+//       larger               : the whole grid, edge-chunk tasks combined in
+//                              shared memory and published to a global table;
 //  4. the rows are compacted (exclusive scan of the row lengths) and each row
 //     is sorted by target: warp bitonic sort (<= 32 entries), block bitonic
 //     sort in shared memory (<= 2048), and one segmented LSD radix sort for
@@ -21,7 +22,7 @@
 namespace gsp {
 
 enum { ACLS_W = 0, ACLS_B, ACLS_L, NUM_ACLS };
-constexpr uint64_t ACLS_MAX[NUM_ACLS] = {128, 4096, ~0ull};
+constexpr uint64_t ACLS_MAX[NUM_ACLS] = {512, 2048, ~0ull};
 enum { RCLS_W = 0, RCLS_B, RCLS_L, NUM_RCLS };
 constexpr uint64_t RCLS_MAX[NUM_RCLS] = {32, 2048, ~0ull};
 
@@ -142,21 +143,23 @@ __device__ __forceinline__ void emit_slot(const AggArgs &a, uint32_t c, uint32_t
     }
 }
 
-constexpr int AGG_WCAP = 256;
+constexpr int AGG_WCAP = 1024;
+constexpr int AGG_WWARPS = 4;
 
 template <typename WT>
-__global__ void __launch_bounds__(256) k_agg_merge_warp(AggArgs a, const uint32_t *__restrict__ list, uint32_t count) {
-    __shared__ uint32_t s_keys[8][AGG_WCAP];
-    __shared__ double s_vals[8][AGG_WCAP];
-    __shared__ uint32_t s_cur[8];
+__global__ void __launch_bounds__(AGG_WWARPS * 32) k_agg_merge_warp(AggArgs a, const uint32_t *__restrict__ list,
+                                                                    uint32_t count) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    __shared__ uint32_t s_cur[AGG_WWARPS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t *keys = s_keys[wid];
-    double *vals = s_vals[wid];
+    uint32_t *keys = reinterpret_cast<uint32_t *>(dyn_smem) + wid * AGG_WCAP;
+    double *vals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * AGG_WCAP * AGG_WWARPS) + wid * AGG_WCAP;
     const WT *w = static_cast<const WT *>(a.w);
-    for (uint32_t t = blockIdx.x * 8 + wid; t < count; t += gridDim.x * 8) {
+    for (uint32_t t = blockIdx.x * AGG_WWARPS + wid; t < count; t += gridDim.x * AGG_WWARPS) {
         uint32_t c = list[t];
-        uint32_t cd = (uint32_t)a.cdeg[c];
-        int logcap = ceil_log2(2 * cd);
+        uint64_t cd = a.cdeg[c];
+        uint64_t bound = cd < a.k ? cd : a.k;
+        int logcap = ceil_log2((uint32_t)(2 * bound));
         if (logcap < 1) logcap = 1;
         uint32_t cap = 1u << logcap;
         for (uint32_t s = lane; s < cap; s += 32) { keys[s] = EMPTY; vals[s] = 0.0; }
@@ -165,8 +168,16 @@ __global__ void __launch_bounds__(256) k_agg_merge_warp(AggArgs a, const uint32_
         for (uint64_t q = a.coff[c]; q < a.coff[c + 1]; q++) {
             uint32_t v = a.cverts[q];
             uint64_t b = a.off[v], e = a.off[v + 1];
-            for (uint64_t p = b + lane; p < e; p += 32)
-                ht_add<double>(keys, vals, logcap, a.Cd[a.tgt[p]], (double)w[p]);
+            for (uint64_t p0 = b + lane; p0 < e; p0 += 64) {  // two edges per lane in flight
+                uint64_t p1 = p0 + 32;
+                uint32_t j0 = a.tgt[p0];
+                uint32_t j1 = p1 < e ? a.tgt[p1] : 0;
+                double w0 = (double)w[p0], w1 = p1 < e ? (double)w[p1] : 0.0;
+                uint32_t d0 = a.Cd[j0];
+                uint32_t d1 = p1 < e ? a.Cd[j1] : EMPTY;
+                ht_add<double>(keys, vals, logcap, d0, w0);
+                if (d1 != EMPTY) ht_add<double>(keys, vals, logcap, d1, w1);
+            }
         }
         __syncwarp();
         for (uint32_t s0 = 0; s0 < cap; s0 += 32) {
@@ -180,56 +191,55 @@ __global__ void __launch_bounds__(256) k_agg_merge_warp(AggArgs a, const uint32_
     }
 }
 
-// One block per community; table in dynamic shared memory (CAP > 0) or the
-// global pool (CAP == 0).
-template <int CAP, typename WT>
-__global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32_t *__restrict__ list, uint32_t count,
-                                                         const uint64_t *__restrict__ pool_off, uint32_t *pool_keys,
-                                                         double *pool_vals) {
+// One block per community; 4096-slot table in dynamic shared memory with a
+// list of occupied slots (emission and clearing touch only those).
+constexpr int AGG_BCAP = 4096;
+
+template <typename WT>
+__global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32_t *__restrict__ list, uint32_t count) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    __shared__ uint32_t s_cur;
+    uint32_t *keys = reinterpret_cast<uint32_t *>(dyn_smem);
+    double *vals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * AGG_BCAP);
+    uint16_t *occ = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(double)) * AGG_BCAP);
+    __shared__ uint32_t s_cur, s_nocc;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const WT *w = static_cast<const WT *>(a.w);
+    for (uint32_t s = threadIdx.x; s < AGG_BCAP; s += blockDim.x) { keys[s] = EMPTY; vals[s] = 0.0; }
     for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
         uint32_t c = list[t];
         uint64_t cd = a.cdeg[c];
         uint64_t bound = cd < a.k ? cd : a.k;
         int logcap = ceil_log2((uint32_t)(2 * bound));
         if (logcap < 1) logcap = 1;
-        uint32_t cap = 1u << logcap;
-        uint32_t *keys;
-        double *vals;
-        if (CAP > 0) {
-            keys = reinterpret_cast<uint32_t *>(dyn_smem);
-            vals = reinterpret_cast<double *>(dyn_smem + (size_t)CAP * sizeof(uint32_t));
-        } else {
-            keys = pool_keys + pool_off[t];
-            vals = pool_vals + pool_off[t];
-        }
         __syncthreads();
-        for (uint32_t s = threadIdx.x; s < cap; s += blockDim.x) { keys[s] = EMPTY; vals[s] = 0.0; }
-        if (threadIdx.x == 0) s_cur = 0;
+        if (threadIdx.x == 0) { s_cur = 0; s_nocc = 0; }
         __syncthreads();
         uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
         for (uint64_t q = q0 + wid; q < q1; q += nw) {
             uint32_t v = a.cverts[q];
             uint64_t b = a.off[v], e = a.off[v + 1];
             for (uint64_t p = b + lane; p < e; p += 32)
-                ht_add<double>(keys, vals, logcap, a.Cd[a.tgt[p]], (double)w[p]);
+                smem_add<double>(keys, vals, logcap, occ, &s_nocc, a.Cd[a.tgt[p]], (double)w[p]);
         }
         __syncthreads();
-        for (uint32_t s0 = wid * 32; s0 < cap; s0 += blockDim.x) {
-            uint32_t s = s0 + lane;
-            uint32_t key = s < cap ? keys[s] : EMPTY;
-            emit_slot(a, c, key, s < cap ? vals[s] : 0.0, key != EMPTY, &s_cur);
+        uint32_t nocc = s_nocc;
+        for (uint32_t k0 = wid * 32; k0 < nocc; k0 += blockDim.x) {
+            uint32_t k = k0 + lane;
+            uint32_t slot = k < nocc ? occ[k] : 0;
+            emit_slot(a, c, k < nocc ? keys[slot] : EMPTY, k < nocc ? vals[slot] : 0.0, k < nocc, &s_cur);
         }
         __syncthreads();
+        for (uint32_t k = threadIdx.x; k < nocc; k += blockDim.x) {
+            uint32_t slot = occ[k];
+            keys[slot] = EMPTY;
+            vals[slot] = 0.0;
+        }
         if (threadIdx.x == 0) a.rowlen[c] = s_cur;
     }
 }
 
-// Large communities (total degree > 4096), processed by the whole grid.  A
+// Large communities (total degree > 2048), processed by the whole grid.  A
 // community's edges are numbered through the member-edge prefix medge (scan
 // of member degrees in community-vertex order, so community c owns
 // [yoff[c], yoff[c+1])) and cut into AGG_CHUNK-edge tasks.  A block combines a
@@ -501,21 +511,27 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
     AggArgs a{g.off, g.tgt, g.w, Cd, coff, cverts, cdeg, yoff, htgt, hw, rowlen, k};
     auto cnt_of = [&](int c) { return ic.start[c + 1] - ic.start[c]; };
     if (cnt_of(ACLS_W)) {
-        k_agg_merge_warp<WT><<<grid_for((uint64_t)cnt_of(ACLS_W) * 32, 256, 152 * 8), 256, 0, s>>>(
-            a, ic.list + ic.start[ACLS_W], cnt_of(ACLS_W));
+        constexpr size_t smem = (size_t)AGG_WWARPS * AGG_WCAP * (sizeof(uint32_t) + sizeof(double));
+        static bool wattr = false;
+        if (!wattr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_warp<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            wattr = true;
+        }
+        k_agg_merge_warp<WT><<<grid_for((uint64_t)cnt_of(ACLS_W) * 32, AGG_WWARPS * 32, 152 * 4), AGG_WWARPS * 32,
+                               smem, s>>>(a, ic.list + ic.start[ACLS_W], cnt_of(ACLS_W));
         GSP_CHECK_LAUNCH();
     }
     if (cnt_of(ACLS_B)) {
-        constexpr int CAP = 8192;
-        constexpr size_t smem = (size_t)CAP * (sizeof(uint32_t) + sizeof(double));
+        constexpr size_t smem = (size_t)AGG_BCAP * (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t));
         static bool attr = false;
         if (!attr) {
-            GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_block<CAP, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_block<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
             attr = true;
         }
-        k_agg_merge_block<CAP, WT><<<grid_for(cnt_of(ACLS_B), 1, 152 * 2), 256, smem, s>>>(
-            a, ic.list + ic.start[ACLS_B], cnt_of(ACLS_B), nullptr, nullptr, nullptr);
+        k_agg_merge_block<WT><<<grid_for(cnt_of(ACLS_B), 1, 152 * 4), 256, smem, s>>>(a, ic.list + ic.start[ACLS_B],
+                                                                                     cnt_of(ACLS_B));
         GSP_CHECK_LAUNCH();
     }
     uint32_t nl = cnt_of(ACLS_L);

@@ -323,24 +323,30 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
     }
 }
 
+// Extraction uses the insert's task split: task k of a community emits its
+// occupied entries [k * AGG_CHUNK, (k+1) * AGG_CHUNK) (a community has at
+// most one distinct neighbour community per edge).
 __global__ void __launch_bounds__(256) k_agg_large_extract(AggArgs a, const uint32_t *__restrict__ list,
-                                                           uint32_t count, const uint64_t *__restrict__ pool_off,
+                                                           uint32_t count, const uint64_t *__restrict__ tasks,
+                                                           const uint64_t *__restrict__ pool_off,
                                                            const uint32_t *__restrict__ pool_keys,
                                                            const double *__restrict__ pool_vals,
                                                            const uint32_t *__restrict__ pool_occ,
                                                            const uint32_t *__restrict__ occ_n) {
-    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-    for (uint32_t t = 0; t < count; t++) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t total = tasks[count];
+    for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
+        uint32_t t = task_item(tasks, count, task);
         uint32_t c = list[t];
         const uint32_t *keys = pool_keys + pool_off[t];
         const double *vals = pool_vals + pool_off[t];
         const uint32_t *occ = pool_occ + pool_off[t];
-        uint64_t nocc = occ_n[t];
-        // every warp runs the same trip count so emit_slot's ballots see full warps
-        for (uint64_t k0 = tid - (threadIdx.x & 31); k0 < nocc; k0 += T) {
-            uint64_t k = k0 + (threadIdx.x & 31);
-            bool valid = k < nocc;
+        uint64_t k0 = (task - tasks[t]) * AGG_CHUNK;
+        uint64_t k1 = min(k0 + AGG_CHUNK, (uint64_t)occ_n[t]);
+        // warp-uniform trip counts so emit_slot's ballots see full warps
+        for (uint64_t kb = k0 + wid * 32; kb < k1; kb += blockDim.x) {
+            uint64_t k = kb + lane;
+            bool valid = k < k1;
             uint32_t slot = valid ? occ[k] : 0;
             emit_slot(a, c, valid ? keys[slot] : EMPTY, valid ? vals[slot] : 0.0, valid, a.rowlen + c);
         }
@@ -571,7 +577,7 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
         }
         k_agg_large_insert<WT><<<AGG_COOP_BLOCKS, 256, lsmem, s>>>(a, llist, nl, tasks, medge, poff, pk, pv, po, on);
         GSP_CHECK_LAUNCH();
-        k_agg_large_extract<<<AGG_COOP_BLOCKS, 256, 0, s>>>(a, llist, nl, poff, pk, pv, po, on);
+        k_agg_large_extract<<<AGG_COOP_BLOCKS, 256, 0, s>>>(a, llist, nl, tasks, poff, pk, pv, po, on);
         GSP_CHECK_LAUNCH();
     }
 

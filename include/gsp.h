@@ -292,6 +292,30 @@ gsp_status gsp_gen_grid(uint32_t R, uint32_t Cc, uint64_t remove53, uint64_t n_l
                         float whi, uint64_t seed, gsp_device_graph *out, void *stream);
 void gsp_release_graph(void);
 
+/*
+ * Modularity for callers that cannot allocate device memory (code running
+ * during CUDA graph capture, embedders whose device memory comes from a fixed
+ * pool, processes that must not grow after start-up).  It returns the same
+ * value as gsp_modularity, with the same arguments, but its scratch is one
+ * fixed __device__ array inside the library instead of the library workspace:
+ * it calls no cudaMalloc or cudaFree.  The paper has no counterpart; this is
+ * an interface convenience.
+ *  - Limit: n <= GSP_STATIC_MAX_VERTICES; larger n returns GSP_ERR_CAPACITY
+ *    with a message (use gsp_modularity).
+ *  - Every device that loads the library holds GSP_STATIC_SCRATCH_BYTES for
+ *    the array until the process exits.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (several
+ *    streams, several host threads) race and give wrong results; serialise
+ *    them.  Each call clears the parts of the array it needs.
+ */
+#define GSP_STATIC_MAX_VERTICES (1u << 20)
+#define GSP_STATIC_SCRATCH_BYTES (12ull * GSP_STATIC_MAX_VERTICES + 4 * 8 + 8 + 256)
+gsp_status gsp_modularity_static(const uint64_t *offsets, const uint32_t *targets, const void *weights,
+                                 int wt, uint32_t n, uint64_t nnz, const uint32_t *C, double *q_host,
+                                 void *stream);
+
 /* Number of kernels this library has launched since it was loaded (all
  * devices, all threads); a diagnostic for counting launches in a region. */
 uint64_t gsp_kernel_launches(void);

@@ -71,6 +71,7 @@ _SIGS = {
     "gsp_gen_grid": (c_int, [c_u32, c_u32, c_u64, c_u64, c_flt, c_flt, c_u64, P, P]),
     "gsp_release_graph": (None, []),
     "gsp_kernel_launches": (c_u64, []),
+    "gsp_modularity_static": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, P]),
 }
 
 _lib = None

@@ -115,6 +115,10 @@ uint64_t aggregate(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *
 // K and m (m also written to *m_dev when non-null); returns m.
 double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t s);
 double modularity(const DevGraph &g, const uint32_t *C, cudaStream_t s);
+double modularity_scratch(const DevGraph &g, const uint32_t *C, double *Sig, double *acc, uint32_t *longlist,
+                          uint32_t *nlong, cudaStream_t s);
+unsigned long long count_out_of_range(const uint32_t *x, uint32_t n, uint32_t bound, unsigned long long *counter,
+                                      cudaStream_t s);
 uint32_t count_disconnected(const DevGraph &g, const uint32_t *C, uint8_t *flags, cudaStream_t s);
 void lookup(uint32_t n_top, uint32_t *C_top, const uint32_t *C_pass, cudaStream_t s);
 // Renumber membership by smallest vertex id (final numbering); returns k.

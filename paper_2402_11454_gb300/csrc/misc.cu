@@ -186,6 +186,55 @@ double modularity(const DevGraph &g, const uint32_t *C, cudaStream_t s) {
     return h[1] / two_m - h[2] / (two_m * two_m);
 }
 
+// Equation 1 with caller-provided scratch instead of the workspace: Sig (n
+// doubles), acc (4 doubles), longlist (n entries) and nlong (1 entry).
+// Allocates nothing.
+template <typename WT>
+static double modularity_scratch_t(const DevGraph &g, const uint32_t *C, double *Sig, double *acc, uint32_t *longlist,
+                                   uint32_t *nlong, cudaStream_t s) {
+    const WT *w = static_cast<const WT *>(g.w);
+    GSP_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
+    GSP_CUDA(cudaMemsetAsync(Sig, 0, sizeof(double) * g.n, s));
+    GSP_CUDA(cudaMemsetAsync(nlong, 0, sizeof(uint32_t), s));
+    k_row_sums<WT><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, nullptr, Sig, acc, longlist, nlong);
+    GSP_CHECK_LAUNCH();
+    k_row_sums_long<WT><<<152 * 4, 256, 0, s>>>(g.off, g.tgt, w, C, nullptr, Sig, acc, longlist, nlong);
+    GSP_CHECK_LAUNCH();
+    k_sum_sq<<<grid_for(g.n, 256), 256, 0, s>>>(Sig, g.n, acc + 2);
+    GSP_CHECK_LAUNCH();
+    double h[4];
+    GSP_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    double two_m = h[0];
+    if (!(two_m > 0.0)) return 0.0;
+    return h[1] / two_m - h[2] / (two_m * two_m);
+}
+
+double modularity_scratch(const DevGraph &g, const uint32_t *C, double *Sig, double *acc, uint32_t *longlist,
+                          uint32_t *nlong, cudaStream_t s) {
+    if (g.wt == GSP_W_F64) return modularity_scratch_t<double>(g, C, Sig, acc, longlist, nlong, s);
+    return modularity_scratch_t<float>(g, C, Sig, acc, longlist, nlong, s);
+}
+
+__global__ void k_count_ge(const uint32_t *__restrict__ x, uint32_t n, uint32_t bound, unsigned long long *out) {
+    unsigned long long b = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (x[i] >= bound) b++;
+    if (b) atomicAdd(out, b);
+}
+
+// Number of entries x[i] >= bound, counted in *counter (caller-provided, no allocation).
+unsigned long long count_out_of_range(const uint32_t *x, uint32_t n, uint32_t bound, unsigned long long *counter,
+                                      cudaStream_t s) {
+    GSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(*counter), s));
+    k_count_ge<<<grid_for(n, 256), 256, 0, s>>>(x, n, bound, counter);
+    GSP_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    GSP_CUDA(cudaMemcpyAsync(&h, counter, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
 // ---------------------------------------------------------------- renumber
 __global__ void k_mark_used(const uint32_t *__restrict__ C, uint32_t n, uint8_t *used) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) used[C[i]] = 1;

@@ -163,6 +163,16 @@ def modularity(offsets, targets, weights, C, stream=None):
     return q.value
 
 
+def modularity_static(offsets, targets, weights, C, stream=None):
+    """Equation 1 without device allocation (fixed internal scratch; n <= 2^20)."""
+    n, nnz = _graph(offsets, targets, weights)
+    _cuda(C, torch.int32, "membership")
+    q = ctypes.c_double()
+    check(_lib.load().gsp_modularity_static(_p(offsets), _p(targets), _p(weights), _wt(weights), n, nnz, _p(C),
+                                            ctypes.byref(q), _stream(stream)))
+    return q.value
+
+
 def move_sweep(offsets, targets, weights, C, K, Sigma, m, active=None, precision="fp64",
                singleton_rule=True, stream=None):
     """One frozen-state local-moving sweep; returns (choice, dq, moved)."""

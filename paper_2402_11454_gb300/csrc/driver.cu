@@ -95,7 +95,7 @@ void Arena::reset() { backing(this).reset(); }
 void Arena::free_all() { backing(this).free_all(); }
 
 // ---------------------------------------------------------- small kernels
-__global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {
+__global__ void k_fill_u32_(uint32_t *p, uint32_t n, uint32_t v) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
 __global__ void k_community_sizes(const uint32_t *__restrict__ C, uint32_t n, uint32_t *size) {
@@ -123,7 +123,7 @@ __global__ void k_check_graph(const uint64_t *__restrict__ off, const uint32_t *
     if (b) atomicAdd(bad, b);
 }
 
-static void check_graph(const uint64_t *off, const uint32_t *tgt, const float *w, uint32_t n, uint64_t nnz,
+void check_graph(const uint64_t *off, const uint32_t *tgt, const float *w, uint32_t n, uint64_t nnz,
                         cudaStream_t s) {
     size_t mk = arena().mark();
     unsigned long long *bad = arena().get<unsigned long long>(1);
@@ -174,6 +174,8 @@ struct EventPool {
     void reset() { used = 0; }
 };
 static EventPool g_events;
+cudaEvent_t pool_event() { return g_events.get(); }
+void reset_event_pool() { g_events.reset(); }
 
 struct MoveLoopResult {
     int iterations;
@@ -187,7 +189,7 @@ struct MoveLoopResult {
 // 4 or 8, C_j 4; per candidate community: Sigma_c 8; per move: move-list
 // entry 8 written and read, C_i 4, two Sigma and two size updates 24, plus
 // one flag byte per neighbour).
-static double sweep_bytes(const MoveCounters &h, int wt) {
+double sweep_bytes(const MoveCounters &h, int wt) {
     double wb = wt == GSP_W_F64 ? 8.0 : 4.0;
     return 41.0 * h.vertices + (8.0 + wb) * h.edges + 8.0 * h.candidates + 44.0 * h.moved + 1.0 * h.marked;
 }
@@ -200,8 +202,8 @@ struct PruneCtx {
 
 // One sweep: cl.W waves; in frozen-state mode each wave's moves are applied
 // before the next wave.
-static void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
-                           bool pruned, int it, int max_it, const uint32_t *wave_n, bool reset_ctr, cudaStream_t s) {
+void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
+                    bool pruned, int it, int max_it, const uint32_t *wave_n, bool reset_ctr, cudaStream_t s) {
     if (reset_ctr) GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
     for (int wv = 0; wv < cl.W; wv++) {
         if (!wave_n[wv]) continue;
@@ -211,7 +213,7 @@ static void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb
     }
 }
 
-static bool graphs_enabled() {
+bool graphs_enabled() {
     const char *e = getenv("GSP_NO_GRAPH");
     return !(e && e[0] == '1');
 }
@@ -222,7 +224,7 @@ static bool graphs_enabled() {
 // into a CUDA graph that the following sweeps replay.
 // Library-owned stream for graph capture (the caller's stream may be the
 // legacy default stream, which cannot be captured).
-static cudaStream_t capture_stream() {
+cudaStream_t capture_stream() {
     static cudaStream_t cs[16];
     static bool made[16] = {false};
     int d = cur_dev();
@@ -311,7 +313,7 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
 }
 
 // Allocate the move state for a graph of n vertices.
-static void alloc_move_state(MoveBuffers &mb, uint32_t n) {
+void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.C = arena().get<uint32_t>(n);
     mb.Sigma = arena().get<double>(n);
     mb.size = arena().get<uint32_t>(n);
@@ -365,7 +367,7 @@ static double max_value(const double *x, uint32_t n, cudaStream_t s) {
 
 // Hub hashtables: keys (u32), values (8 bytes) and an occupied-slot list
 // (u32) per slot.  The tables start empty; each sweep's scoring empties them.
-static void alloc_pool(MoveBuffers &mb, const Classes &cl, cudaStream_t s) {
+void alloc_pool(MoveBuffers &mb, const Classes &cl, cudaStream_t s) {
     mb.pool = nullptr;
     if (!cl.pool_slots) return;
     size_t sa = align_up(cl.pool_slots, 64);
@@ -455,7 +457,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         double m = vertex_weights(cur, K, mb.m_dev, s);
         GSP_CUDA(cudaMemcpyAsync(mb.Sigma, K, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
         iota_u32(mb.C, nv, s);
-        k_fill_u32<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
+        k_fill_u32_<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
         GSP_CHECK_LAUNCH();
         GSP_CUDA(cudaMemsetAsync(mb.act, 1, nv, s));
         GSP_CUDA(cudaMemsetAsync(mb.mark, 0, nv, s));
@@ -553,7 +555,8 @@ using namespace gsp;
 
 static cudaStream_t S(void *p) { return static_cast<cudaStream_t>(p); }
 
-static DevGraph make_graph(const uint64_t *off, const uint32_t *tgt, const void *w, int wt, uint32_t n,
+namespace gsp {
+DevGraph make_graph(const uint64_t *off, const uint32_t *tgt, const void *w, int wt, uint32_t n,
                            uint64_t nnz) {
     GSP_REQUIRE(n > 0, "n must be > 0");
     GSP_REQUIRE(off != nullptr, "offsets must not be NULL");
@@ -569,7 +572,7 @@ static DevGraph make_graph(const uint64_t *off, const uint32_t *tgt, const void 
     return g;
 }
 
-static void check_opts(const gsp_opts &o) {
+void check_opts(const gsp_opts &o) {
     GSP_REQUIRE(o.max_passes >= 1 && o.max_passes <= 1000, "max_passes out of range");
     GSP_REQUIRE(o.max_iterations >= 1 && o.max_iterations <= 100000, "max_iterations out of range");
     GSP_REQUIRE(o.tolerance >= 0.0 && o.tolerance_drop > 0.0, "tolerance out of range");
@@ -583,6 +586,7 @@ static void check_opts(const gsp_opts &o) {
     GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS || o.prune == GSP_PRUNE_LEARNED, "unknown prune mode");
     GSP_REQUIRE(o.prune != GSP_PRUNE_LEARNED || o.mlp_params != nullptr, "learned pruning needs mlp_params");
 }
+}  // namespace gsp
 
 extern "C" {
 

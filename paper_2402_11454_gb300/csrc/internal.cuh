@@ -41,7 +41,10 @@ struct Classes {
 };
 
 // Build the class/wave lists of g's vertices (degree 0 vertices are left out).
-void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s);
+// With gid/gvo (batches of graphs: graph of each vertex, per-graph first
+// vertex), a vertex's wave is its index within its graph, mod W.
+void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s, const uint32_t *gid = nullptr,
+                       const uint64_t *gvo = nullptr);
 
 struct MoveCounters {  // device-side accumulators of one sweep
     double dq;
@@ -61,6 +64,9 @@ struct MoveBuffers {
     uint8_t *mark = nullptr;     // re-marks of a frozen-state wave (merged into act after it)
     const double *K = nullptr;
     double *m_dev = nullptr;     // device copy of m
+    const uint32_t *gid = nullptr;   // batches: graph of each vertex
+    const double *m_g = nullptr;     // batches: m of each graph
+    double *dq_g = nullptr;          // batches: summed gain of each graph in a sweep
     MoveCounters *ctr = nullptr;
     void *pool = nullptr;        // huge-class hashtables
     uint32_t *mv_vtx = nullptr;  // moves decided in the current wave (frozen-state mode)
@@ -98,6 +104,20 @@ SideStreams &side_streams();
 void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, bool sync, bool fp64, bool rule,
                bool learned, int iteration, int max_iterations, cudaStream_t s);
 void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s);
+
+// driver.cu helpers shared with the batched driver
+void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
+                    bool pruned, int it, int max_it, const uint32_t *wave_n, bool reset_ctr, cudaStream_t s);
+bool graphs_enabled();
+cudaStream_t capture_stream();
+void alloc_move_state(MoveBuffers &mb, uint32_t n);
+void alloc_pool(MoveBuffers &mb, const Classes &cl, cudaStream_t s);
+double sweep_bytes(const MoveCounters &h, int wt);
+cudaEvent_t pool_event();
+void reset_event_pool();
+void check_graph(const uint64_t *off, const uint32_t *tgt, const float *w, uint32_t n, uint64_t nnz, cudaStream_t s);
+void check_opts(const gsp_opts &o);
+DevGraph make_graph(const uint64_t *off, const uint32_t *tgt, const void *w, int wt, uint32_t n, uint64_t nnz);
 
 struct LouvainTimers;
 

@@ -44,6 +44,11 @@ struct MoveArgs {
     uint8_t *act;
     uint8_t *mark;  // re-marking target: a separate array merged after a frozen-state wave, act in place
     const double *m;
+    // batches of independent graphs: graph of each vertex, m of each graph,
+    // per-graph summed gains (null for a single graph)
+    const uint32_t *gid;
+    const double *m_g;
+    double *dq_g;
     MoveCounters *ctr;
     int rule;
     uint32_t *mv_vtx, *mv_cmt, *mv_cnt;  // frozen-state move list
@@ -178,6 +183,14 @@ template <> __device__ __forceinline__ Score<false> make_score<false>(double Ki,
     return s;
 }
 
+// m of vertex i's graph (batches) or of the single graph.
+__device__ __forceinline__ double vertex_m(const MoveArgs &a, uint32_t i, double m0) {
+    return a.gid ? a.m_g[a.gid[i]] : m0;
+}
+__device__ __forceinline__ void add_graph_gain(const MoveArgs &a, uint32_t i, double gain) {
+    if (a.dq_g) atomicAdd(a.dq_g + a.gid[i], gain);
+}
+
 // Decide the move of i toward c (one thread).  Frozen-state: record it in the
 // move list; in place: apply it now.  Returns whether i moves.
 template <bool SYNC>
@@ -270,7 +283,7 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
     uint32_t *keys = reinterpret_cast<uint32_t *>(smem) + grp * CAP;
     V *vals = reinterpret_cast<V *>(smem + (size_t)NG * CAP * sizeof(uint32_t)) + grp * CAP;
     const WT *w = static_cast<const WT *>(a.w);
-    const double m = *a.m;
+    const double m0 = *a.m;
     LocalCtr lc;
     for (uint32_t idx = lb * NG + grp; idx < count; idx += nb * NG) {
         uint32_t i = list[idx];
@@ -300,6 +313,7 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         double Ki = a.K[i];
         double Sd = ld_state<SYNC>(a.Sig + d);
         Sd = __shfl_sync(gmask, Sd, leader);
+        const double m = vertex_m(a, i, m0);
         SC sc = make_score<F64>(Ki, (double)kid, Sd, m);
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
@@ -319,7 +333,7 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
             lc.vertices++;
             lc.edges += deg;
             if (gain > 0.0) mv = decide_move<SYNC>(a, i, d, bestc, Ki);
-            if (mv) { lc.moved++; lc.dq += gain; }
+            if (mv) { lc.moved++; lc.dq += gain; add_graph_gain(a, i, gain); }
             record_visit(a, i, deg, Ki, (double)kid, gain, m, mv);
         }
         // movers re-mark their neighbours (frozen-state waves write a separate
@@ -393,7 +407,7 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
     __shared__ uint32_t s_d, s_nocc;
     __shared__ double s_Sd;
     const WT *w = static_cast<const WT *>(a.w);
-    const double m = *a.m;
+    const double m0 = *a.m;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     LocalCtr lc;
@@ -426,6 +440,7 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
         kid = 0;
         for (int t = 0; t < nw; t++) kid += red_k[t];
         double Ki = a.K[i];
+        const double m = vertex_m(a, i, m0);
         SC sc = make_score<F64>(Ki, (double)kid, s_Sd, m);
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
@@ -455,7 +470,7 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
             if (gain > 0.0) mv = decide_move<SYNC>(a, i, d, bestc, Ki);
             lc.vertices++;
             lc.edges += deg;
-            if (mv) { lc.moved++; lc.dq += gain; }
+            if (mv) { lc.moved++; lc.dq += gain; add_graph_gain(a, i, gain); }
             record_visit(a, i, deg, Ki, (double)kid, gain, m, mv);
             s_mv = mv;
         }
@@ -655,7 +670,7 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
     __shared__ uint32_t red_c[32];
     const V *kidv = static_cast<const V *>(h.kid);
     S *bs = static_cast<S *>(h.best_s);
-    const double m = *a.m;
+    const double m0 = *a.m;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t base = h.tasks[0], total = h.tasks[h.nh] - base;
     for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
@@ -667,7 +682,7 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
         V *vals = static_cast<V *>(h.vals) + h.pool_off[t];
         const uint32_t *occ = h.occ + h.pool_off[t];
         uint64_t k1 = min(k0 + HUB_CHUNK, (uint64_t)h.occ_n[t]);
-        SC sc = make_score<F64>(a.K[i], (double)kidv[t], ld_state<SYNC>(a.Sig + d), m);
+        SC sc = make_score<F64>(a.K[i], (double)kidv[t], ld_state<SYNC>(a.Sig + d), vertex_m(a, i, m0));
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
         // U entries per thread per round; each level of the gather chain
@@ -721,7 +736,7 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h) {
     using S = typename SC::S;
     const V *kidv = static_cast<const V *>(h.kid);
     const S *bs = static_cast<const S *>(h.best_s);
-    const double m = *a.m;
+    const double m0 = *a.m;
     const int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -746,6 +761,7 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h) {
         if (lane == 0) {
             double Ki = a.K[i];
             uint64_t deg = a.off[i + 1] - a.off[i];
+            const double m = vertex_m(a, i, m0);
             SC sc = make_score<F64>(Ki, (double)kidv[t], ld_state<SYNC>(a.Sig + d), m);
             double gain = (bestc == EMPTY) ? 0.0 : sc.gain(best);
             int mv = 0;
@@ -757,6 +773,7 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h) {
             if (mv) {  // neighbours are re-marked by k_mark_big
                 lc.moved++;
                 lc.dq += gain;
+                add_graph_gain(a, i, gain);
                 lc.marked += deg;
                 h.big[atomicAdd(h.nbig, 1u)] = i;
             }
@@ -787,13 +804,20 @@ __device__ __forceinline__ int class_of(uint64_t deg) {
     return CLS_HUGE;
 }
 
-__global__ void k_classify_count(const uint64_t *__restrict__ off, uint32_t n, int W, uint32_t *counts) {
+// Wave of vertex v: its index within its graph, mod W.
+__device__ __forceinline__ int wave_of(uint32_t v, int W, const uint32_t *gid, const uint64_t *gvo) {
+    uint64_t local = gid ? v - gvo[gid[v]] : v;
+    return (int)(local % (uint64_t)W);
+}
+
+__global__ void k_classify_count(const uint64_t *__restrict__ off, uint32_t n, int W, uint32_t *counts,
+                                 const uint32_t *__restrict__ gid, const uint64_t *__restrict__ gvo) {
     __shared__ uint32_t sc[NUM_CLS * MAX_WAVES];
     for (int t = threadIdx.x; t < NUM_CLS * W; t += blockDim.x) sc[t] = 0;
     __syncthreads();
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint64_t deg = off[v + 1] - off[v];
-        if (deg) atomicAdd(&sc[class_of(deg) * W + (int)(v % (uint32_t)W)], 1u);
+        if (deg) atomicAdd(&sc[class_of(deg) * W + wave_of(v, W, gid, gvo)], 1u);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < NUM_CLS * W; t += blockDim.x)
@@ -801,12 +825,12 @@ __global__ void k_classify_count(const uint64_t *__restrict__ off, uint32_t n, i
 }
 
 __global__ void k_classify_fill(const uint64_t *__restrict__ off, uint32_t n, int W, uint32_t *cursor,
-                                uint32_t *list) {
+                                uint32_t *list, const uint32_t *__restrict__ gid, const uint64_t *__restrict__ gvo) {
     int lane = threadIdx.x & 31;
     for (uint32_t v0 = blockIdx.x * blockDim.x; v0 < n; v0 += gridDim.x * blockDim.x) {
         uint32_t v = v0 + threadIdx.x;
         uint64_t deg = (v < n) ? off[v + 1] - off[v] : 0;
-        int key = deg ? class_of(deg) * W + (int)(v % (uint32_t)W) : -1;
+        int key = deg ? class_of(deg) * W + wave_of(v, W, gid, gvo) : -1;
         uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
         int leader = __ffs(peers) - 1;
         uint32_t base = 0;
@@ -827,7 +851,8 @@ __global__ void k_pool_caps(const uint64_t *__restrict__ off, const uint32_t *__
     }
 }
 
-void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s) {
+void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s, const uint32_t *gid,
+                       const uint64_t *gvo) {
     GSP_REQUIRE(waves >= 1 && waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
     const int W = waves;
     const int NK = NUM_CLS * W;
@@ -835,7 +860,7 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
     uint32_t *counts = arena().get<uint32_t>(2 * NK);
     GSP_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * NK, s));
     unsigned grid = grid_for(g.n, 256, 152 * 8);
-    k_classify_count<<<grid, 256, 0, s>>>(g.off, g.n, W, counts);
+    k_classify_count<<<grid, 256, 0, s>>>(g.off, g.n, W, counts, gid, gvo);
     GSP_CHECK_LAUNCH();
     uint32_t h[NUM_CLS * MAX_WAVES];
     GSP_CUDA(cudaMemcpyAsync(h, counts, sizeof(uint32_t) * NK, cudaMemcpyDeviceToHost, s));
@@ -845,7 +870,7 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
     uint32_t *cursor = counts + NK;
     GSP_CUDA(cudaMemcpyAsync(cursor, cl.start, sizeof(uint32_t) * NK, cudaMemcpyHostToDevice, s));
     cl.list = arena().get<uint32_t>(cl.start[NK] + 1);
-    k_classify_fill<<<grid, 256, 0, s>>>(g.off, g.n, W, cursor, cl.list);
+    k_classify_fill<<<grid, 256, 0, s>>>(g.off, g.n, W, cursor, cl.list, gid, gvo);
     GSP_CHECK_LAUNCH();
     uint32_t nh = cl.cls_count(CLS_HUGE);
     cl.pool_off = arena().get<uint64_t>(nh + 1);
@@ -1025,6 +1050,9 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
     a.act = mb.act;
     a.mark = sync ? mb.mark : mb.act;
     a.m = mb.m_dev;
+    a.gid = mb.gid;
+    a.m_g = mb.m_g;
+    a.dq_g = mb.dq_g;
     a.ctr = mb.ctr;
     a.rule = rule ? 1 : 0;
     a.mv_vtx = mb.mv_vtx;

@@ -98,7 +98,9 @@ def dist_setup():
 
 
 def make_workload(gsp, graphgen, name):
-    """Generate the workload on the device; returns (off, tgt, w, config, extra)."""
+    """Generate the workload on the device; returns (off, tgt, w, config, gvo),
+    gvo = per-graph vertex offsets of a batch (None for one graph)."""
+    gvo = None
     if name == "rmat22":
         off, tgt, w = gsp.gen_rmat(22, 16, seed=2)
         cfg = {"workload": "rmat22", "scale": 22, "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05],
@@ -119,11 +121,22 @@ def make_workload(gsp, graphgen, name):
         off, tgt, w = gsp.gen_grid(4096, 4096, seed=3)
         cfg = {"workload": "grid4096", "rows": 4096, "cols": 4096, "p_remove": 0.05, "p_long": 0.001,
                "weights": [1.0, 10.0], "seed": 3}
+    elif name == "batch":
+        import numpy as np
+        G = 4096
+        n, k, e, p = graphgen.batch_params(G, seed=4)
+        seeds = [graphgen.batch_graph_seed(4, g) for g in range(G)]
+        off, tgt, w = gsp.gen_planted_batch(n, k, e, p, seeds)
+        gvo = np.zeros(G + 1, dtype=np.uint64)
+        np.cumsum(n, out=gvo[1:])
+        cfg = {"workload": "batch4096", "graphs": G, "vertices_per_graph": "log-uniform [64, 65536]",
+               "communities": "uniform {4..64}", "mean_degree": "uniform [4, 64]",
+               "p_intra": "uniform [0.7, 0.9]", "seed": 4}
     else:
         raise SystemExit("unknown workload %s" % name)
     cfg["vertices"] = int(off.numel() - 1)
     cfg["edges"] = int(tgt.numel())
-    return off, tgt, w, cfg
+    return off, tgt, w, cfg, gvo
 
 
 def roofline_from(stats_list, peak_gbs, peak_kind):
@@ -219,12 +232,18 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    off, tgt, w, cfg = make_workload(gsp, graphgen, args.workload)
+    off, tgt, w, cfg, gvo = make_workload(gsp, graphgen, args.workload)
     kw = dict(precision=args.precision, split=args.split, move=args.move, waves=args.waves)
+
+    def step(off, tgt, w):
+        if gvo is None:
+            return gsp.louvain(off, tgt, w, **kw)
+        C, qg, st = gsp.louvain_batched(gvo, off, tgt, w, **kw)
+        return C, st["modularity"], st
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MB > 129 MB L2
 
     for _ in range(max(args.warmup, 0)):
-        C, q, st = gsp.louvain(off, tgt, w, **kw)
+        C, q, st = step(off, tgt, w)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
@@ -239,7 +258,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        C, q, st = gsp.louvain(off, tgt, w, **kw)
+        C, q, st = step(off, tgt, w)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -264,13 +283,25 @@ def main():
         h_tgt = tgt.cpu().pin_memory()
         h_w = w.cpu().pin_memory()
         h_C = torch.empty(off.numel() - 1, dtype=torch.int32, pin_memory=True)
-        gsp.louvain_host(h_off, h_tgt, h_w, h_C, **kw)
+
+        def e2e_step():
+            if gvo is None:
+                gsp.louvain_host(h_off, h_tgt, h_w, h_C, **kw)
+                return
+            # batches: pinned host -> device, the batched call, membership back
+            d_off = h_off.to("cuda", non_blocking=True)
+            d_tgt = h_tgt.to("cuda", non_blocking=True)
+            d_w = h_w.to("cuda", non_blocking=True)
+            C, _, _ = gsp.louvain_batched(gvo, d_off, d_tgt, d_w, **kw)
+            h_C.copy_(C)
+
+        e2e_step()
         et = []
         for _ in range(args.steps):
             flush.fill_(1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            gsp.louvain_host(h_off, h_tgt, h_w, h_C, **kw)
+            e2e_step()
             torch.cuda.synchronize()
             et.append(time.perf_counter() - t0)
         e2e_s = sum(et)

@@ -261,6 +261,13 @@ gsp_status gsp_mlp_backward(const float *params, const float *x, const uint8_t *
 /* params -= lr * grad (plain SGD step, float32 master weights). */
 gsp_status gsp_mlp_sgd(float *params, const float *grad, float lr, void *stream);
 
+/* One Adam step (Kingma & Ba, 2015) of step number t >= 1: with g = grad,
+ * m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g^2 (m, v: device
+ * arrays of gsp_mlp_param_count() floats, zero before the first step),
+ * params -= lr * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps). */
+gsp_status gsp_mlp_adam(float *params, const float *grad, float *m, float *v, float lr, float beta1,
+                        float beta2, float eps, int t, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Seeded synthetic graphs, drawn on the device with the same counter-based
  * SplitMix64 stream as the host generators.  Each writes a symmetric CSR

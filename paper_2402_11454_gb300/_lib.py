@@ -66,6 +66,7 @@ _SIGS = {
     "gsp_mlp_forward": (c_int, [P, P, c_u32, P, P]),
     "gsp_mlp_backward": (c_int, [P, P, P, c_u32, P, P, P]),
     "gsp_mlp_sgd": (c_int, [P, P, c_flt, P]),
+    "gsp_mlp_adam": (c_int, [P, P, P, P, c_flt, c_flt, c_flt, c_flt, c_int, P]),
     "gsp_gen_rmat": (c_int, [c_u32, c_u32, c_u64, c_u64, c_u64, c_u64, P, P]),
     "gsp_gen_planted_batch": (c_int, [c_u32, P, P, P, P, P, P, P]),
     "gsp_gen_grid": (c_int, [c_u32, c_u32, c_u64, c_u64, c_flt, c_flt, c_u64, P, P]),

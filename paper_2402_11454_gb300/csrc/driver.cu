@@ -266,8 +266,10 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
     cudaGraphExec_t exec = nullptr;
     side_streams();
     try {
+        bool force_full = false;  // a pruned sweep fell below tau: confirm with a plain sweep
         for (int it = 0; it < max_it; it++) {
-            bool pruned = pr.learned && pr.full_every > 0 && (it % pr.full_every) != pr.full_every - 1;
+            const bool pruned = pr.learned && !force_full && pr.full_every > 0 &&
+                                (it % pr.full_every) != pr.full_every - 1;
             GSP_CUDA(cudaEventRecord(e0, s));
             if (use_graph && it >= 1) {
                 if (!exec) {
@@ -283,6 +285,7 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
                 GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
                 if (pruned) mlp_prune(g, mb, it, max_it, pr.threshold, s);
                 sweep_launches(g, cl, mb, sync, fp64, rule, pruned, it, max_it, wave_n, false, s);
+                if (pruned) mlp_unskip(g, mb, s);
             }
             GSP_CUDA(cudaEventRecord(e1, s));
             GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -296,7 +299,14 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
             r.edges += h.edges;
             r.candidates += h.candidates;
             r.skipped += h.skipped;
-            if (h.dq <= tau) break;
+            // only a sweep that skipped nobody may declare convergence: the
+            // gain of a pruned sweep misses what its skipped vertices would add
+            if (h.dq <= tau) {
+                if (!pruned || h.skipped == 0) break;
+                force_full = true;
+            } else {
+                force_full = false;
+            }
         }
     } catch (...) {
         if (exec) cudaGraphExecDestroy(exec);
@@ -328,10 +338,12 @@ void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.ctr = arena().get<MoveCounters>(1);
 }
 
-static void alloc_features(MoveBuffers &mb, uint32_t n) {
+static void alloc_features(MoveBuffers &mb, uint32_t n, cudaStream_t s) {
     mb.feat_kept = arena().get<float>(n);
     mb.feat_gain = arena().get<float>(n);
     mb.moved_last = arena().get<uint8_t>(n);
+    mb.skip = arena().get<uint8_t>(n);
+    GSP_CUDA(cudaMemsetAsync(mb.skip, 0, n, s));
 }
 
 __global__ void k_init_features(float *kept, float *gain, uint8_t *moved, uint32_t n) {
@@ -425,7 +437,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     uint32_t *Cd = arena().get<uint32_t>(n0);
     mb.K = K;
     mb.mlp = static_cast<const float *>(o.mlp_params);
-    if (features) alloc_features(mb, n0);
+    if (features) alloc_features(mb, n0, s);
     if (trace) {
         mb.trace_x = trace->x;
         mb.trace_y = trace->y;

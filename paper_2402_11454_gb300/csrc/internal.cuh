@@ -80,6 +80,7 @@ struct MoveBuffers {
     float *feat_kept = nullptr;  // K_{i->C_i} / K_i at the vertex's last visit
     float *feat_gain = nullptr;  // scaled best gain at the last visit
     uint8_t *moved_last = nullptr;
+    uint8_t *skip = nullptr;     // vertices the predictor skipped in the current sweep
     float max_logk = 1.0f;
     // move/no-move trace rows (optional)
     float *trace_x = nullptr;
@@ -168,6 +169,9 @@ __device__ __forceinline__ void predictor_features(uint32_t deg, double Ki, floa
 // probability is below threshold are marked processed (skipped).
 void mlp_prune(const DevGraph &g, MoveBuffers &mb, int iteration, int max_iterations, float threshold,
                cudaStream_t s);
+// After a pruned sweep: the skipped vertices are unprocessed again, so that
+// the next sweep (a plain one at the latest) reconsiders them.
+void mlp_unskip(const DevGraph &g, MoveBuffers &mb, cudaStream_t s);
 
 __device__ __forceinline__ int ceil_log2(uint32_t x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
 

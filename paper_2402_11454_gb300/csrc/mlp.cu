@@ -1,6 +1,6 @@
 // mlp.cu -- the learned vertex-pruning predictor: a 6 -> 32 -> 32 -> 1 MLP
 // (ReLU hidden layers, sigmoid output) with weights rounded to bfloat16 and
-// float32 accumulation; forward, binary cross-entropy backward and SGD.
+// float32 accumulation; forward, binary cross-entropy backward, SGD and Adam steps.
 //
 // Parameter layout (float32 master copy): W1[32][6], b1[32], W2[32][32],
 // b2[32], W3[32], b3.  One thread evaluates one row (about 1.2 K FMA); the
@@ -148,12 +148,25 @@ __global__ void k_mlp_sgd(float *params, const float *__restrict__ grad, float l
         params[i] -= lr * grad[i];
 }
 
+__global__ void k_mlp_adam(float *params, const float *__restrict__ grad, float *m, float *v, float lr, float b1,
+                           float b2, float eps, float c1, float c2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_PARAMS; i += gridDim.x * blockDim.x) {
+        float g = grad[i];
+        float mi = b1 * m[i] + (1.0f - b1) * g;
+        float vi = b2 * v[i] + (1.0f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        params[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
 // Learned pruning: one thread per vertex; active vertices predicted not to
-// move are marked processed and counted as skipped.
+// move sit out the sweep (flag cleared, skip set) and are counted as skipped.
 __global__ void k_mlp_prune(const float *__restrict__ params, const uint64_t *__restrict__ off,
                             const double *__restrict__ K, const float *__restrict__ kept,
-                            const float *__restrict__ gain, const uint8_t *__restrict__ moved, uint8_t *act, uint32_t n,
-                            float max_logk, float iter_frac, float thr, MoveCounters *ctr) {
+                            const float *__restrict__ gain, const uint8_t *__restrict__ moved, uint8_t *act,
+                            uint8_t *skip, uint32_t n, float max_logk, float iter_frac, float thr,
+                            MoveCounters *ctr) {
     __shared__ float sp[MLP_PARAMS];
     __shared__ unsigned long long red[32];
     load_params_bf16(params, sp);
@@ -166,6 +179,7 @@ __global__ void k_mlp_prune(const float *__restrict__ params, const uint64_t *__
         predictor_features(deg, K[i], kept[i], gain[i], moved[i], max_logk, iter_frac, x);
         if (mlp_prob(sp, x) < thr) {
             act[i] = 0;
+            skip[i] = 1;
             skipped++;
         }
     }
@@ -177,8 +191,21 @@ void mlp_prune(const DevGraph &g, MoveBuffers &mb, int iteration, int max_iterat
                cudaStream_t s) {
     float frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
     k_mlp_prune<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(mb.mlp, g.off, mb.K, mb.feat_kept, mb.feat_gain,
-                                                            mb.moved_last, mb.act, g.n, mb.max_logk, frac,
-                                                            threshold, mb.ctr);
+                                                            mb.moved_last, mb.act, mb.skip, g.n, mb.max_logk,
+                                                            frac, threshold, mb.ctr);
+    GSP_CHECK_LAUNCH();
+}
+
+__global__ void k_mlp_unskip(uint8_t *act, uint8_t *skip, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (skip[i]) {
+            act[i] = 1;
+            skip[i] = 0;
+        }
+}
+
+void mlp_unskip(const DevGraph &g, MoveBuffers &mb, cudaStream_t s) {
+    k_mlp_unskip<<<grid_for(g.n, 256), 256, 0, s>>>(mb.act, mb.skip, g.n);
     GSP_CHECK_LAUNCH();
 }
 
@@ -238,6 +265,20 @@ gsp_status gsp_mlp_sgd(float *params, const float *grad, float lr, void *stream)
     GSP_REQUIRE(params && grad, "invalid arguments");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_mlp_sgd<<<grid_for(MLP_PARAMS, 256), 256, 0, s>>>(params, grad, lr);
+    GSP_CHECK_LAUNCH();
+    MLP_END
+}
+
+gsp_status gsp_mlp_adam(float *params, const float *grad, float *m, float *v, float lr, float beta1, float beta2,
+                        float eps, int t, void *stream) {
+    MLP_BEGIN
+    GSP_REQUIRE(params && grad && m && v, "invalid arguments");
+    GSP_REQUIRE(t >= 1, "Adam step number must be >= 1");
+    GSP_REQUIRE(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f,
+                "Adam hyper-parameters out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float c1 = (float)(1.0 - pow((double)beta1, t)), c2 = (float)(1.0 - pow((double)beta2, t));
+    k_mlp_adam<<<grid_for(MLP_PARAMS, 256), 256, 0, s>>>(params, grad, m, v, lr, beta1, beta2, eps, c1, c2);
     GSP_CHECK_LAUNCH();
     MLP_END
 }

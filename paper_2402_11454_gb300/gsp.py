@@ -289,6 +289,12 @@ def mlp_sgd(params, grad, lr, stream=None):
     return params
 
 
+def mlp_adam(params, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    check(_lib.load().gsp_mlp_adam(_p(params), _p(grad), _p(m), _p(v), lr, beta1, beta2, eps, t,
+                                   _stream(stream)))
+    return params
+
+
 # ------------------------------------------------------------ generators
 class _DevArray:
     """Wraps a device pointer for torch.as_tensor (no copy)."""

@@ -165,6 +165,10 @@ __global__ void __launch_bounds__(AGG_WWARPS * 32) k_agg_merge_warp(AggArgs a, c
         for (uint32_t s = lane; s < cap; s += 32) { keys[s] = EMPTY; vals[s] = 0.0; }
         if (lane == 0) s_cur[wid] = 0;
         __syncwarp();
+        // edges inside the community (the super-vertex's self-loop) are summed
+        // in registers: they are the most frequent key of the table
+        double selfw = 0.0;
+        uint32_t nself = 0;
         for (uint64_t q = a.coff[c]; q < a.coff[c + 1]; q++) {
             uint32_t v = a.cverts[q];
             uint64_t b = a.off[v], e = a.off[v + 1];
@@ -175,10 +179,16 @@ __global__ void __launch_bounds__(AGG_WWARPS * 32) k_agg_merge_warp(AggArgs a, c
                 double w0 = (double)w[p0], w1 = p1 < e ? (double)w[p1] : 0.0;
                 uint32_t d0 = a.Cd[j0];
                 uint32_t d1 = p1 < e ? a.Cd[j1] : EMPTY;
-                ht_add<double>(keys, vals, logcap, d0, w0);
-                if (d1 != EMPTY) ht_add<double>(keys, vals, logcap, d1, w1);
+                if (d0 == c) { selfw += w0; nself++; }
+                else ht_add<double>(keys, vals, logcap, d0, w0);
+                if (d1 == c) { selfw += w1; nself++; }
+                else if (d1 != EMPTY) ht_add<double>(keys, vals, logcap, d1, w1);
             }
         }
+        selfw = warp_sum(selfw);
+        nself = warp_sum(nself);
+        __syncwarp();
+        if (lane == 0 && nself) ht_add<double>(keys, vals, logcap, c, selfw);
         __syncwarp();
         for (uint32_t s0 = 0; s0 < cap; s0 += 32) {
             uint32_t s = s0 + lane;
@@ -202,6 +212,8 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
     double *vals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * AGG_BCAP);
     uint16_t *occ = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(double)) * AGG_BCAP);
     __shared__ uint32_t s_cur, s_nocc;
+    __shared__ double s_red[32];
+    __shared__ uint32_t s_redn[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const WT *w = static_cast<const WT *>(a.w);
@@ -216,12 +228,20 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
         if (threadIdx.x == 0) { s_cur = 0; s_nocc = 0; }
         __syncthreads();
         uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
+        double selfw = 0.0;
+        uint32_t nself = 0;
         for (uint64_t q = q0 + wid; q < q1; q += nw) {
             uint32_t v = a.cverts[q];
             uint64_t b = a.off[v], e = a.off[v + 1];
-            for (uint64_t p = b + lane; p < e; p += 32)
-                smem_add<double>(keys, vals, logcap, occ, &s_nocc, a.Cd[a.tgt[p]], (double)w[p]);
+            for (uint64_t p = b + lane; p < e; p += 32) {
+                uint32_t d = a.Cd[a.tgt[p]];
+                if (d == c) { selfw += (double)w[p]; nself++; }
+                else smem_add<double>(keys, vals, logcap, occ, &s_nocc, d, (double)w[p]);
+            }
         }
+        selfw = block_sum(selfw, s_red);
+        nself = block_sum(nself, s_redn);
+        if (threadIdx.x == 0 && nself) smem_add<double>(keys, vals, logcap, occ, &s_nocc, c, selfw);
         __syncthreads();
         uint32_t nocc = s_nocc;
         for (uint32_t k0 = wid * 32; k0 < nocc; k0 += blockDim.x) {
@@ -277,6 +297,8 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
     double *svals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * (1u << AGG_SLOG));
     uint16_t *socc = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(double)) * (1u << AGG_SLOG));
     __shared__ uint32_t s_nocc;
+    __shared__ double s_red[32];
+    __shared__ uint32_t s_redn[32];
     const WT *w = static_cast<const WT *>(a.w);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t sub = AGG_CHUNK / (blockDim.x >> 5);  // edges per warp
@@ -290,6 +312,8 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
         uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
         uint64_t ch = a.yoff[c] + (task - tasks[t]) * AGG_CHUNK + (uint64_t)wid * sub;
         uint64_t cend = min(ch + sub, E1);
+        double selfw = 0.0;
+        uint32_t nself = 0;
         if (ch < E1) {
             // last member q in [q0, q1) with medge[q] <= ch
             uint64_t lo = q0, hi = q1 - 1;
@@ -307,13 +331,19 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
                     uint64_t base = a.off[v];
                     for (uint64_t tt = t0 + lane; tt < segend; tt += 32) {
                         uint64_t p = base + (tt - ms);
-                        smem_add<double>(skeys, svals, AGG_SLOG, socc, &s_nocc, a.Cd[a.tgt[p]], (double)w[p]);
+                        uint32_t dd = a.Cd[a.tgt[p]];
+                        if (dd == c) { selfw += (double)w[p]; nself++; }
+                        else smem_add<double>(skeys, svals, AGG_SLOG, socc, &s_nocc, dd, (double)w[p]);
                     }
                     t0 = segend;
                 }
                 q++;
             }
         }
+        // the task's edges inside the community enter the table once
+        selfw = block_sum(selfw, s_red);
+        nself = block_sum(nself, s_redn);
+        if (threadIdx.x == 0 && nself) smem_add<double>(skeys, svals, AGG_SLOG, socc, &s_nocc, c, selfw);
         uint64_t cd = a.cdeg[c];
         uint64_t bound = cd < a.k ? cd : a.k;
         int glog = ceil_log2((uint32_t)(2 * bound));

@@ -139,16 +139,100 @@ def make_workload(gsp, graphgen, name):
     return off, tgt, w, cfg, gvo
 
 
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of all
+# local-moving launches of one R-MAT 20 step divided by that step's algorithmic
+# bytes (profiles/dram_local_moving_rmat20.md); scaled to the bench workload.
+MOVE_TRAFFIC_RATIO = 2.158
+
+
 def roofline_from(stats_list, peak_gbs, peak_kind):
     byt = sum(sum(s["move_bytes"]) for s in stats_list)
     ms = sum(sum(s["ms_move_kernels"]) for s in stats_list)
     if ms <= 0:
         return None
     achieved = byt / (ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "local-moving sweep (k_move_group/k_move_block)",
+    per_step = byt / max(1, len(stats_list))
+    return {"bound": "hbm", "kernel": "local-moving sweep (all k_move_*/k_hub_*/k_apply_moves launches of a sweep)",
             "achieved": round(achieved, 1), "peak": peak_gbs, "peak_kind": peak_kind + " (burst copy)",
-            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": None,
-            "algorithmic_bytes_per_step": byt / max(1, len(stats_list))}
+            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
+            "traffic": round(per_step * MOVE_TRAFFIC_RATIO),
+            "traffic_basis": "DRAM bytes per step: %.3f x the algorithmic bytes, ratio from an ncu capture of every "
+                             "local-moving launch of one R-MAT 20 step" % MOVE_TRAFFIC_RATIO,
+            "algorithmic_bytes_per_step": per_step}
+
+
+def phase_rooflines(st, peak_gbs, input_wbytes=4):
+    """Algorithmic bytes and GB/s of each phase of one step (lower bounds:
+    one pass over what the phase must read and write).
+      split: per edge target 4 + C_j 4 + label_j 4, per vertex C_i 4 +
+             label 4 + offsets 16;
+      aggregation: per input edge target 4 + weight (4 or 8) + Cd_j 4, per
+             vertex Cd 4 + offsets 16 + member list 8, per output super-edge
+             target 4 + weight 8, per super-vertex offset 8."""
+    P = st["passes"]
+    E, V = st["edges"], st["vertices"]
+    split_b = sum(12.0 * E[p] + 24.0 * V[p] for p in range(P))
+    agg_b = 0.0
+    for p in range(P):
+        if st["ms_aggregate"][p] <= 0 or p + 1 >= P:
+            continue
+        wb = input_wbytes if p == 0 else 8
+        agg_b += (8.0 + wb) * E[p] + 28.0 * V[p] + 12.0 * E[p + 1] + 8.0 * V[p + 1]
+    out = {}
+    for name, b, ms in (("split", split_b, sum(st["ms_split"])), ("aggregate", agg_b, sum(st["ms_aggregate"])),
+                        ("move", sum(st["move_bytes"]), sum(st["ms_move_kernels"]))):
+        if ms > 0 and b > 0:
+            gbs = b / (ms * 1e-3) / 1e9
+            out[name] = {"bytes": b, "ms": round(ms, 3), "achieved_gbs": round(gbs, 1),
+                         "frac": round(gbs / peak_gbs, 4)}
+    return out
+
+
+def learned_compare(gsp, args, off, tgt, w, kw, flush, stream, plain_ms, plain_q, plain_stats, edges):
+    """Learned pruning against the plain method on the same graph: the
+    predictor is trained (untimed) on move traces of the R-MAT scale-22 graph
+    (seed 2) with the library's kernels, its threshold set to keep
+    `recall` of the moving visits; then timed like the plain run."""
+    import torch
+    from paper_2402_11454_gb300 import pruner
+    t0 = time.perf_counter()
+    if args.workload == "rmat22":
+        o2, t2, w2 = off, tgt, w
+    else:
+        o2, t2, w2 = gsp.gen_rmat(22, 16, seed=2)
+    x, y = pruner.collect_traces(o2, t2, w2, capacity=1 << 23, sample_every=8, **kw)
+    xb, yb = pruner.balance(x, y, seed=0)
+    P, rep = pruner.train(xb, yb, steps=1500, batch=65536, seed=0)
+    thr = pruner.threshold_for_recall(P, x, y, recall=args.recall)
+    ev = pruner.evaluate(P, x, y, thr)
+    del o2, t2, w2, x, y, xb, yb
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    lkw = dict(kw, prune="learned", mlp_params=P, prune_threshold=thr)
+    for _ in range(max(args.warmup, 0)):
+        gsp.louvain(off, tgt, w, **lkw)
+    times, st = [], None
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C, q, st = gsp.louvain(off, tgt, w, **lkw)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    dis = gsp.count_disconnected(off, tgt, C)[0]
+    return {"value": edges / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "modularity": q,
+            "dQ_vs_plain": q - plain_q, "speedup_vs_plain": plain_ms / ms,
+            "disconnected_communities": dis,
+            "vertices_skipped": sum(st["vertices_skipped"]),
+            "visits_ratio_vs_plain": sum(st["vertices_processed"]) / max(1, sum(plain_stats["vertices_processed"])),
+            "edges_scanned_ratio_vs_plain": sum(st["edges_scanned"]) / max(1, sum(plain_stats["edges_scanned"])),
+            "iterations": st["iterations"], "full_sweep_every": 4, "threshold": thr,
+            "recall_target": args.recall, "trace_recall": ev["recall"], "trace_skip_rate": ev["skip_rate"],
+            "trained_on": "R-MAT scale 22, seed 2 (1 in 8 visits sampled)",
+            "train": {k: v for k, v in rep.items() if k != "loss_curve"}, "train_seconds": round(train_s, 2)}
 
 
 def cpu_baseline(sample_scale=20, seed=2):
@@ -217,6 +301,9 @@ def main():
     ap.add_argument("--ref-scale", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--learned", default="auto", choices=["auto", "on", "off"],
+                    help="also time learned pruning against the plain run (auto: R-MAT workloads)")
+    ap.add_argument("--recall", type=float, default=0.9)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -313,6 +400,10 @@ def main():
                "h2d_bytes_per_step": int(h_off.numel() * 8 + h_tgt.numel() * 4 + h_w.numel() * 4),
                "d2h_bytes_per_step": int(h_C.numel() * 4)}
 
+    learned = None
+    if args.learned == "on" or (args.learned == "auto" and args.workload.startswith("rmat")):
+        learned = learned_compare(gsp, args, off, tgt, w, kw, flush, stream, total_ms / args.steps, q, st, edges)
+
     peak, kind = load_peaks()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -328,6 +419,7 @@ def main():
                          "aggregate": sum(st["ms_aggregate"]), "other": sum(st["ms_other"]),
                          "total": st["ms_total"]},
             "roofline": roofline_from(stats, peak, kind), "gpu_launches": launches,
+            "phase_roofline": phase_rooflines(st, peak), "learned": learned,
             "clocks": clocks, "e2e": e2e}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -304,6 +304,8 @@ def main():
     ap.add_argument("--learned", default="auto", choices=["auto", "on", "off"],
                     help="also time learned pruning against the plain run (auto: R-MAT workloads)")
     ap.add_argument("--recall", type=float, default=0.9)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default grid caps instead of tuning them on the workload (untimed)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -328,6 +330,12 @@ def main():
         C, qg, st = gsp.louvain_batched(gvo, off, tgt, w, **kw)
         return C, st["modularity"], st
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MB > 129 MB L2
+
+    tuning = {"caps": gsp.get_tuning(), "autotuned": False}
+    if not args.no_autotune:  # untimed: picks the local-moving grid caps for this graph
+        caps, ms0, ms1 = gsp.autotune(off, tgt, w, **kw)
+        tuning = {"caps": caps, "autotuned": True, "first_sweep_ms_default": round(ms0, 3),
+                  "first_sweep_ms_tuned": round(ms1, 3)}
 
     for _ in range(max(args.warmup, 0)):
         C, q, st = step(off, tgt, w)
@@ -419,7 +427,7 @@ def main():
                          "aggregate": sum(st["ms_aggregate"]), "other": sum(st["ms_other"]),
                          "total": st["ms_total"]},
             "roofline": roofline_from(stats, peak, kind), "gpu_launches": launches,
-            "phase_roofline": phase_rooflines(st, peak), "learned": learned,
+            "phase_roofline": phase_rooflines(st, peak), "learned": learned, "tuning": tuning,
             "clocks": clocks, "e2e": e2e}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -327,6 +327,42 @@ gsp_status gsp_modularity_static(const uint64_t *offsets, const uint32_t *target
  * devices, all threads); a diagnostic for counting launches in a region. */
 uint64_t gsp_kernel_launches(void);
 
+/* ---------------------------------------------------------------------------
+ * Launch geometry of local moving (an implementation choice; the paper has no
+ * counterpart).  Each degree class runs as a grid-stride kernel whose grid is
+ * capped at a number of blocks per SM: groups of lanes per vertex (degree <=
+ * 128), a warp per vertex (129..512), a block per vertex (513..2048) and the
+ * grid-wide hub pipeline (> 2048).  Any cap in [1, 32] gives the same result
+ * in frozen-state (SYNC) mode; only the speed differs.  The setting is
+ * process-wide (all devices) and applies to calls started after it is set.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int groups_blocks_per_sm;  /* default 8 */
+    int w512_blocks_per_sm;    /* default 3 */
+    int block_blocks_per_sm;   /* default 4 */
+    int hub_blocks_per_sm;     /* default 4 */
+} gsp_tuning;
+
+/* Current caps into *out (host).  GSP_ERR_INVALID if out is NULL. */
+gsp_status gsp_get_tuning(gsp_tuning *out);
+
+/* Install caps (host struct); GSP_ERR_INVALID if a cap is outside [1, 32]. */
+gsp_status gsp_set_tuning(const gsp_tuning *t);
+
+/*
+ * Pick the caps for this graph and install them: times the first sweep of
+ * the first pass (all vertices unprocessed; opts' move mode, waves and
+ * precision) under candidate caps, one class at a time, and keeps the
+ * fastest.  Device graph as for gsp_louvain (float32 weights); the graph is
+ * not modified.  *chosen receives the installed caps, *ms_default the sweep
+ * time under the caps in effect at the call, *ms_tuned the time under the
+ * chosen ones (host pointers, each may be NULL).  An edgeless graph is
+ * GSP_ERR_INVALID.  Not safe to run concurrently with other calls.
+ */
+gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const float *weights,
+                        uint32_t n, uint64_t nnz, const gsp_opts *opts, gsp_tuning *chosen,
+                        float *ms_default, float *ms_tuned);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,11 @@ class GspDeviceGraph(ctypes.Structure):
     _fields_ = [("n", c_u32), ("nnz", c_u64), ("offsets", P), ("targets", P), ("weights", P)]
 
 
+class GspTuning(ctypes.Structure):
+    _fields_ = [("groups_blocks_per_sm", c_int), ("w512_blocks_per_sm", c_int), ("block_blocks_per_sm", c_int),
+                ("hub_blocks_per_sm", c_int)]
+
+
 _SIGS = {
     "gsp_default_opts": (None, [P]),
     "gsp_status_string": (ctypes.c_char_p, [c_int]),
@@ -67,6 +72,9 @@ _SIGS = {
     "gsp_mlp_backward": (c_int, [P, P, P, c_u32, P, P, P]),
     "gsp_mlp_sgd": (c_int, [P, P, c_flt, P]),
     "gsp_mlp_adam": (c_int, [P, P, P, P, c_flt, c_flt, c_flt, c_flt, c_int, P]),
+    "gsp_get_tuning": (c_int, [P]),
+    "gsp_set_tuning": (c_int, [P]),
+    "gsp_autotune": (c_int, [P, P, P, c_u32, c_u64, P, P, P, P]),
     "gsp_gen_rmat": (c_int, [c_u32, c_u32, c_u64, c_u64, c_u64, c_u64, P, P]),
     "gsp_gen_planted_batch": (c_int, [c_u32, P, P, P, P, P, P, P]),
     "gsp_gen_grid": (c_int, [c_u32, c_u32, c_u64, c_u64, c_flt, c_flt, c_u64, P, P]),

@@ -15,6 +15,19 @@ struct DevGraph {
     int wt = GSP_W_F32;
 };
 
+// Launch geometry of the local-moving kernels: grid caps in blocks per SM
+// (the kernels are grid-stride loops, so any positive value is correct; the
+// result of a sweep does not depend on it).  Set by gsp_set_tuning or chosen
+// by gsp_autotune.
+struct Tuning {
+    int groups = 8;  // k_move_groups (degrees <= 128)
+    int w512 = 3;    // k_move_w512 (129..512)
+    int block = 4;   // k_move_block (513..2048)
+    int hub = 4;     // k_hub_insert / k_hub_score (> 2048)
+};
+Tuning &tuning();
+int sm_count();  // SMs of the current device
+
 // Degree classes of a vertex list.  Small degrees are served by groups of G
 // lanes with a shared-memory table, mid degrees by one block with a
 // shared-memory table, the largest by one block with a table in a global

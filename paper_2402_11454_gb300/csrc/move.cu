@@ -27,6 +27,7 @@
 // K_{i->c} in float32 and compares the scaled score s_c = K_{i->c} - K_i *
 // Sigma_c / 2m in float32 (m * dQ_{i:d->c} = s_c - s_d with Sigma_d taken
 // without K_i); m and Sigma stay float64.
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -593,7 +594,6 @@ __global__ void k_mark_big(const uint64_t *__restrict__ off, const uint32_t *__r
 //            for the next sweep); per-block best per hub;
 //   decide:  one warp per hub reduces the block bests and decides the move.
 // --------------------------------------------------------------------------
-constexpr int HUB_BLOCKS = 152 * 4;
 constexpr uint32_t HUB_CHUNK = 2048;
 constexpr int HUB_SLOG = 12;  // shared table of 2 * HUB_CHUNK slots
 
@@ -942,6 +942,8 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         return ss.side[k];
     };
     cudaStream_t s = main;
+    const Tuning tn = tuning();
+    const int sm = sm_count();
     GroupLists gl;
     const int G[4] = {4, 8, 16, 32};
     uint32_t blocks = 0;
@@ -949,7 +951,7 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         gl.list[c] = cl.list + cl.begin(c, wave);
         gl.count[c] = cl.count(c, wave);
         gl.bstart[c] = blocks;
-        if (gl.count[c]) blocks += grid_for((uint64_t)gl.count[c] * G[c], 256, 152 * 8);
+        if (gl.count[c]) blocks += grid_for((uint64_t)gl.count[c] * G[c], 256, (uint32_t)(sm * tn.groups));
     }
     gl.bstart[4] = blocks;
     if (blocks) {
@@ -965,7 +967,7 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
                                           (int)smem));
             attr = true;
         }
-        k_move_w512<WT, F64, SYNC><<<grid_for((uint64_t)nw5 * 32, 256, 152 * 3), 256, smem, on(0)>>>(
+        k_move_w512<WT, F64, SYNC><<<grid_for((uint64_t)nw5 * 32, 256, (uint32_t)(sm * tn.w512)), 256, smem, on(0)>>>(
             a, cl.list + cl.begin(CLS_W512, wave), nw5);
         GSP_CHECK_LAUNCH();
     }
@@ -979,7 +981,7 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr = true;
         }
-        k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, 152 * 4), 256, smem, on(1)>>>(
+        k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, (uint32_t)(sm * tn.block)), 256, smem, on(1)>>>(
             a, cl.list + cl.begin(CLS_BLOCK, wave), nb);
         GSP_CHECK_LAUNCH();
     }
@@ -1021,9 +1023,11 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
                                           (int)hsmem));
             attr = true;
         }
-        k_hub_insert<WT, F64, SYNC><<<HUB_BLOCKS, 256, hsmem, s>>>(a, h);
+        // one block per task at most: small waves launch only what they use
+        const unsigned hub_grid = (unsigned)std::min<uint64_t>(ntasks, (uint64_t)sm * tn.hub);
+        k_hub_insert<WT, F64, SYNC><<<hub_grid, 256, hsmem, s>>>(a, h);
         GSP_CHECK_LAUNCH();
-        k_hub_score<WT, F64, SYNC><<<HUB_BLOCKS, 256, 0, s>>>(a, h);
+        k_hub_score<WT, F64, SYNC><<<hub_grid, 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();
         k_hub_decide<F64, SYNC><<<grid_for((uint64_t)nh * 32, 256), 256, 0, s>>>(a, h);
         GSP_CHECK_LAUNCH();

@@ -1,0 +1,199 @@
+// tune.cu -- launch-geometry tuning of the local-moving kernels.
+//
+// Each degree class of local moving (Algorithm 4) runs as a grid-stride
+// kernel whose grid is capped at a number of blocks per SM.  The best caps
+// depend on the graph's degree distribution (how many vertices of each class
+// a wave holds, how unbalanced the hubs are), so gsp_autotune picks them on
+// the caller's graph: it times the first sweep of the first pass (every
+// vertex unprocessed, the heaviest sweep) under candidate caps, one class at
+// a time (coordinate descent), restoring the start state before each trial.
+// Caps change only the launch geometry: in frozen-state mode a sweep's result
+// is the same under every setting.
+#include <string.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace gsp {
+
+static Tuning g_tuning;
+static std::mutex g_tuning_mu;
+
+Tuning &tuning() { return g_tuning; }
+
+int sm_count() {
+    static int cached[64] = {0};
+    int d = 0;
+    GSP_CUDA(cudaGetDevice(&d));
+    GSP_REQUIRE(d >= 0 && d < 64, "device index %d out of range", d);
+    if (!cached[d]) {
+        int v = 0;
+        GSP_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d));
+        cached[d] = v > 0 ? v : 1;
+    }
+    return cached[d];
+}
+
+constexpr int TUNE_MAX = 32;  // blocks per SM, upper limit of every cap
+
+static void check_tuning(const gsp_tuning &t) {
+    GSP_REQUIRE(t.groups_blocks_per_sm >= 1 && t.groups_blocks_per_sm <= TUNE_MAX &&
+                    t.w512_blocks_per_sm >= 1 && t.w512_blocks_per_sm <= TUNE_MAX &&
+                    t.block_blocks_per_sm >= 1 && t.block_blocks_per_sm <= TUNE_MAX &&
+                    t.hub_blocks_per_sm >= 1 && t.hub_blocks_per_sm <= TUNE_MAX,
+                "tuning caps must be in [1, %d] blocks per SM", TUNE_MAX);
+}
+
+static gsp_tuning to_abi(const Tuning &t) {
+    gsp_tuning o;
+    o.groups_blocks_per_sm = t.groups;
+    o.w512_blocks_per_sm = t.w512;
+    o.block_blocks_per_sm = t.block;
+    o.hub_blocks_per_sm = t.hub;
+    return o;
+}
+
+static Tuning from_abi(const gsp_tuning &t) {
+    Tuning o;
+    o.groups = t.groups_blocks_per_sm;
+    o.w512 = t.w512_blocks_per_sm;
+    o.block = t.block_blocks_per_sm;
+    o.hub = t.hub_blocks_per_sm;
+    return o;
+}
+
+__global__ void k_tune_reset(uint32_t *C, double *Sig, const double *K, uint32_t *size, uint8_t *act, uint8_t *mark,
+                             uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        C[i] = i;
+        Sig[i] = K[i];
+        size[i] = 1;
+        act[i] = 1;
+        mark[i] = 0;
+    }
+}
+
+}  // namespace gsp
+
+using namespace gsp;
+
+extern "C" {
+
+gsp_status gsp_get_tuning(gsp_tuning *out) {
+    if (!out) {
+        set_error("gsp_get_tuning: out must not be NULL");
+        return GSP_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    *out = to_abi(g_tuning);
+    return GSP_OK;
+}
+
+gsp_status gsp_set_tuning(const gsp_tuning *t) {
+    try {
+        GSP_REQUIRE(t != nullptr, "gsp_set_tuning: t must not be NULL");
+        check_tuning(*t);
+        std::lock_guard<std::mutex> lock(g_tuning_mu);
+        g_tuning = from_abi(*t);
+        return GSP_OK;
+    } catch (const gsp::Error &e) {
+        return e.status;
+    }
+}
+
+gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const float *weights, uint32_t n,
+                        uint64_t nnz, const gsp_opts *opts, gsp_tuning *chosen, float *ms_default,
+                        float *ms_tuned) {
+    try {
+        gsp_opts o;
+        if (opts) o = *opts;
+        else gsp_default_opts(&o);
+        check_opts(o);
+        DevGraph g = make_graph(offsets, targets, weights, GSP_W_F32, n, nnz);
+        cudaStream_t caller = static_cast<cudaStream_t>(o.stream);
+        arena().reset();
+        reset_event_pool();
+        check_graph(offsets, targets, weights, n, nnz, caller);
+        GSP_CUDA(cudaStreamSynchronize(caller));
+        cudaStream_t s = capture_stream();
+        const bool sync = o.move == GSP_MOVE_SYNC;
+        const bool fp64 = o.precision == GSP_PREC_FP64;
+        MoveBuffers mb;
+        alloc_move_state(mb, n);
+        double *K = arena().get<double>(n);
+        mb.K = K;
+        const double m = vertex_weights(g, K, mb.m_dev, s);
+        GSP_REQUIRE(m > 0.0, "gsp_autotune: the graph has no edges");
+        Classes cl;
+        classify_vertices(g, cl, sync ? o.waves : 1, s);
+        alloc_pool(mb, cl, s);
+        uint32_t wave_n[MAX_WAVES];
+        for (int wv = 0; wv < cl.W; wv++) {
+            wave_n[wv] = 0;
+            for (int c = 0; c < NUM_CLS; c++) wave_n[wv] += cl.count(c, wv);
+        }
+        side_streams();
+        cudaEvent_t e0 = pool_event(), e1 = pool_event();
+        auto trial = [&]() -> float {
+            float best = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                k_tune_reset<<<grid_for(n, 256), 256, 0, s>>>(mb.C, mb.Sigma, K, mb.size, mb.act, mb.mark, n);
+                GSP_CHECK_LAUNCH();
+                GSP_CUDA(cudaEventRecord(e0, s));
+                sweep_launches(g, cl, mb, sync, fp64, o.singleton_rule != 0, false, 0, o.max_iterations, wave_n,
+                               true, s);
+                GSP_CUDA(cudaEventRecord(e1, s));
+                GSP_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                GSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                best = ms < best ? ms : best;
+            }
+            return best;
+        };
+        std::lock_guard<std::mutex> lock(g_tuning_mu);
+        const Tuning start = g_tuning;
+        Tuning best = start;
+        float t0 = 0.0f, tb = 0.0f;
+        try {
+            trial();  // first-touch effects (workspace, instruction cache)
+            t0 = tb = trial();
+            struct Knob {
+                int Tuning::*field;
+                int cand[5];
+            };
+            const Knob knobs[] = {{&Tuning::groups, {4, 6, 8, 12, 16}},
+                                  {&Tuning::w512, {1, 2, 3, 4, 6}},
+                                  {&Tuning::block, {2, 3, 4, 5, 8}},
+                                  {&Tuning::hub, {1, 2, 4, 8, 16}}};
+            for (const Knob &k : knobs) {
+                for (int v : k.cand) {
+                    if (v == best.*(k.field)) continue;
+                    g_tuning = best;
+                    g_tuning.*(k.field) = v;
+                    float t = trial();
+                    if (t < tb) {
+                        tb = t;
+                        best = g_tuning;
+                    }
+                }
+            }
+        } catch (...) {
+            g_tuning = start;
+            throw;
+        }
+        g_tuning = best;
+        if (chosen) *chosen = to_abi(best);
+        if (ms_default) *ms_default = t0;
+        if (ms_tuned) *ms_tuned = tb;
+        GSP_CUDA(cudaStreamSynchronize(s));
+        return GSP_OK;
+    } catch (const gsp::Error &e) {
+        return e.status;
+    } catch (...) {
+        set_error("unexpected C++ exception");
+        return GSP_ERR_CUDA;
+    }
+}
+
+}  // extern "C"

@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import GspOpts, GspStats, GspDeviceGraph, check
+from ._lib import GspOpts, GspStats, GspDeviceGraph, GspTuning, check
 
 SPLIT = {"none": 0, "lp": 1, "lpp": 2, "bfs": 3}
 SPLIT_WHEN = {"pass": 0, "last": 1}
@@ -257,6 +257,37 @@ def count_disconnected(offsets, targets, C, stream=None):
     check(_lib.load().gsp_count_disconnected(_p(offsets), _p(targets), n, nnz, _p(C), _p(flags),
                                              ctypes.byref(c), _stream(stream)))
     return c.value, flags
+
+
+_TUNING_FIELDS = ("groups_blocks_per_sm", "w512_blocks_per_sm", "block_blocks_per_sm", "hub_blocks_per_sm")
+
+
+def get_tuning():
+    """Grid caps (blocks per SM) of the local-moving kernels, as a dict."""
+    t = GspTuning()
+    check(_lib.load().gsp_get_tuning(ctypes.byref(t)))
+    return {f: getattr(t, f) for f in _TUNING_FIELDS}
+
+
+def set_tuning(**caps):
+    """Install grid caps; fields not given keep their current values."""
+    cur = get_tuning()
+    cur.update(caps)
+    t = GspTuning(*[int(cur[f]) for f in _TUNING_FIELDS])
+    check(_lib.load().gsp_set_tuning(ctypes.byref(t)))
+    return get_tuning()
+
+
+def autotune(offsets, targets, weights, **kw):
+    """Pick and install the grid caps for this graph; returns (caps, ms of the
+    first sweep before, ms after)."""
+    n, nnz = _graph(offsets, targets, weights)
+    o = make_opts(**kw)
+    t = GspTuning()
+    before, after = ctypes.c_float(), ctypes.c_float()
+    check(_lib.load().gsp_autotune(_p(offsets), _p(targets), _p(weights), n, nnz, ctypes.byref(o), ctypes.byref(t),
+                                   ctypes.byref(before), ctypes.byref(after)))
+    return {f: getattr(t, f) for f in _TUNING_FIELDS}, before.value, after.value
 
 
 def kernel_launches():

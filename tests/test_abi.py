@@ -65,3 +65,21 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.gsp_split(None, None, 0, 0, None, 3, None, None, None) == -1
     assert lib.gsp_renumber(0, None, None, None, None) == -1
     assert lib.gsp_gen_rmat(0, 16, 1, 2, 3, 0, None, None) == -1
+
+
+def test_tuning_roundtrip_and_validation(lib):
+    """Grid caps are host state: get/set work without a GPU and out-of-range
+    caps are rejected."""
+    from paper_2402_11454_gb300._lib import GspTuning
+    t = GspTuning()
+    assert lib.gsp_get_tuning(ctypes.byref(t)) == 0
+    assert (t.groups_blocks_per_sm, t.w512_blocks_per_sm, t.block_blocks_per_sm, t.hub_blocks_per_sm) == (8, 3, 4, 4)
+    new = GspTuning(6, 2, 5, 8)
+    assert lib.gsp_set_tuning(ctypes.byref(new)) == 0
+    got = GspTuning()
+    lib.gsp_get_tuning(ctypes.byref(got))
+    assert (got.groups_blocks_per_sm, got.w512_blocks_per_sm, got.block_blocks_per_sm, got.hub_blocks_per_sm) == (6, 2, 5, 8)
+    for bad in (GspTuning(0, 3, 4, 4), GspTuning(8, 33, 4, 4), GspTuning(8, 3, -1, 4)):
+        assert lib.gsp_set_tuning(ctypes.byref(bad)) == -1
+    assert lib.gsp_get_tuning(None) == -1
+    assert lib.gsp_set_tuning(ctypes.byref(t)) == 0  # restore the defaults

@@ -10,10 +10,13 @@
 //       total degree <= 2048 : one block, 4096-slot table in shared memory
 //       larger               : the whole grid, edge-chunk tasks combined in
 //                              shared memory and published to a global table;
-//  4. the rows are compacted (exclusive scan of the row lengths) and each row
-//     is sorted by target: warp bitonic sort (<= 32 entries), block bitonic
-//     sort in shared memory (<= 2048), and one segmented LSD radix sort for
-//     all longer rows together.
+//  4. the rows are compacted (exclusive scan of the row lengths) and, for the
+//     canonical form, each row is sorted by target: warp bitonic sort (<= 32
+//     entries), block bitonic sort in shared memory (<= 2048), and one
+//     segmented LSD radix sort for all longer rows together.  Inside a run
+//     the rows stay unsorted: no later step depends on their order (moves,
+//     split and aggregation sum exactly representable weights, and ties go
+//     to the lowest id), so only the phase entry point sorts.
 // Weights are accumulated and stored in float64; sums of float32-exact
 // weights are exact in float64, so every merged weight is order-independent
 // and the output is canonical.
@@ -511,6 +514,41 @@ __global__ void k_rowlen_gather(const uint32_t *__restrict__ list, uint32_t coun
         out[t] = rowlen[list[t]];
 }
 
+// Unsorted compaction of the holey rows (rows in any order of targets):
+// one warp per row for rows of <= 2048 entries, one block per longer row.
+__global__ void k_compact_rows_warp(const uint32_t *__restrict__ list, uint32_t count,
+                                    const uint64_t *__restrict__ yoff, const uint32_t *__restrict__ htgt,
+                                    const double *__restrict__ hw, const uint64_t *__restrict__ noff, uint32_t *otgt,
+                                    double *ow) {
+    const int lane = threadIdx.x & 31;
+    uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t t = warp; t < count; t += nwarps) {
+        uint32_t c = list[t];
+        uint64_t dst = noff[c], src = yoff[c];
+        uint32_t L = (uint32_t)(noff[c + 1] - dst);
+        for (uint32_t x = lane; x < L; x += 32) {
+            otgt[dst + x] = htgt[src + x];
+            ow[dst + x] = hw[src + x];
+        }
+    }
+}
+
+__global__ void k_compact_rows_block(const uint32_t *__restrict__ list, uint32_t count,
+                                     const uint64_t *__restrict__ yoff, const uint32_t *__restrict__ htgt,
+                                     const double *__restrict__ hw, const uint64_t *__restrict__ noff, uint32_t *otgt,
+                                     double *ow) {
+    for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
+        uint32_t c = list[t];
+        uint64_t dst = noff[c], src = yoff[c];
+        uint64_t L = noff[c + 1] - dst;
+        for (uint64_t x = threadIdx.x; x < L; x += blockDim.x) {
+            otgt[dst + x] = htgt[src + x];
+            ow[dst + x] = hw[src + x];
+        }
+    }
+}
+
 static int ceil_log2_host(uint64_t x) {
     int b = 0;
     while ((1ull << b) < x) b++;
@@ -520,7 +558,7 @@ static int ceil_log2_host(uint64_t x) {
 
 template <typename WT>
 static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off,
-                               uint32_t *out_tgt, double *out_w, cudaStream_t s) {
+                               uint32_t *out_tgt, double *out_w, bool sorted, cudaStream_t s) {
     size_t mk = arena().mark();
     uint32_t n = g.n;
     uint32_t *cnt = arena().get<uint32_t>(k);
@@ -622,6 +660,21 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
     IdClasses rc;
     classify_ids<NUM_RCLS>(rl64, k, RCLS_MAX, rc, s);
     auto rcnt = [&](int c) { return rc.start[c + 1] - rc.start[c]; };
+    if (!sorted) {
+        const uint32_t nshort = rcnt(RCLS_W) + rcnt(RCLS_B);  // classes W and B are adjacent in the list
+        if (nshort) {
+            k_compact_rows_warp<<<grid_for((uint64_t)nshort * 32, 256, 152 * 16), 256, 0, s>>>(
+                rc.list + rc.start[RCLS_W], nshort, yoff, htgt, hw, out_off, out_tgt, out_w);
+            GSP_CHECK_LAUNCH();
+        }
+        if (rcnt(RCLS_L)) {
+            k_compact_rows_block<<<grid_for(rcnt(RCLS_L), 1, 152 * 4), 256, 0, s>>>(
+                rc.list + rc.start[RCLS_L], rcnt(RCLS_L), yoff, htgt, hw, out_off, out_tgt, out_w);
+            GSP_CHECK_LAUNCH();
+        }
+        arena().release(mk);
+        return nnz2;
+    }
     if (rcnt(RCLS_W)) {
         k_sort_rows_warp<<<grid_for((uint64_t)rcnt(RCLS_W) * 32, 256, 152 * 16), 256, 0, s>>>(
             rc.list + rc.start[RCLS_W], rcnt(RCLS_W), yoff, htgt, hw, out_off, out_tgt, out_w);
@@ -666,9 +719,9 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
 }
 
 uint64_t aggregate(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off, uint32_t *out_tgt,
-                   double *out_w, cudaStream_t s) {
-    if (g.wt == GSP_W_F64) return aggregate_impl<double>(g, Cd, k, out_off, out_tgt, out_w, s);
-    return aggregate_impl<float>(g, Cd, k, out_off, out_tgt, out_w, s);
+                   double *out_w, cudaStream_t s, bool sorted) {
+    if (g.wt == GSP_W_F64) return aggregate_impl<double>(g, Cd, k, out_off, out_tgt, out_w, sorted, s);
+    return aggregate_impl<float>(g, Cd, k, out_off, out_tgt, out_w, sorted, s);
 }
 
 }  // namespace gsp

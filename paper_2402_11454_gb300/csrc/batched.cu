@@ -451,7 +451,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         nxt.tgt = gtgt[pb];
         nxt.w = gw[pb];
         nxt.wt = GSP_W_F64;
-        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s);
+        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s, /*sorted=*/false);
         pb ^= 1;
         cur = nxt;
         tau = tau / o.tolerance_drop;

@@ -521,7 +521,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         nxt.tgt = gtgt[pb];
         nxt.w = gw[pb];
         nxt.wt = GSP_W_F64;
-        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s);
+        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s, /*sorted=*/false);
         pb ^= 1;
         cur = nxt;
         tau = tau / o.tolerance_drop;

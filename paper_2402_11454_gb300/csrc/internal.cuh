@@ -143,8 +143,10 @@ void split_labels(const DevGraph &g, const Classes &cl, const uint32_t *C, int m
 uint32_t renumber(uint32_t n, const uint32_t *C, uint32_t *C_dense, cudaStream_t s);
 
 // Aggregation (Algorithm 5) into out (offsets k+1, targets/weights nnz); returns nnz''.
+// sorted: rows in increasing target order (the canonical form); otherwise
+// each row's entries come in table order.
 uint64_t aggregate(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off, uint32_t *out_tgt,
-                   double *out_w, cudaStream_t s);
+                   double *out_w, cudaStream_t s, bool sorted = true);
 
 // K and m (m also written to *m_dev when non-null); returns m.
 double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t s);

@@ -146,6 +146,50 @@ __device__ __forceinline__ void emit_slot(const AggArgs &a, uint32_t c, uint32_t
     }
 }
 
+// Visits the edges of the rows list[q0..q1) (row v = list[q] owns edges
+// off[v]..off[v+1]) with a whole warp: the bounds of 32 rows are read at once
+// and their edges dealt out 32 per round with every lane busy, a lane finding
+// its row by a 5-step search over the lanes' running edge totals.  fn(p,
+// valid) is called by all 32 lanes every round.  The edges of 32 consecutive
+// rows must number fewer than 2^32.
+template <typename F>
+__device__ __forceinline__ void warp_row_edges(const uint32_t *__restrict__ list, uint64_t q0, uint64_t q1,
+                                               const uint64_t *__restrict__ off, F &&fn) {
+    const uint32_t FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t qb = q0; qb < q1; qb += 32) {
+        const uint64_t q = qb + lane;
+        uint64_t b = 0;
+        uint32_t len = 0;
+        if (q < q1) {
+            const uint32_t v = list[q];
+            b = off[v];
+            len = (uint32_t)(off[v + 1] - b);
+        }
+        uint32_t end = len;  // inclusive prefix over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, end, o);
+            if (lane >= o) end += t;
+        }
+        const uint32_t start = end - len;
+        const uint32_t total = __shfl_sync(FULL, end, 31);
+        for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            int r = 0;  // first lane whose running total exceeds e
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t ev = __shfl_sync(FULL, end, r + step - 1);
+                if (ev <= e) r += step;
+            }
+            r &= 31;
+            const uint64_t rb = __shfl_sync(FULL, b, r);
+            const uint32_t rs = __shfl_sync(FULL, start, r);
+            fn(rb + (e - rs), e < total);
+        }
+    }
+}
+
 constexpr int AGG_WCAP = 1024;
 constexpr int AGG_WWARPS = 4;
 
@@ -172,22 +216,13 @@ __global__ void __launch_bounds__(AGG_WWARPS * 32) k_agg_merge_warp(AggArgs a, c
         // in registers: they are the most frequent key of the table
         double selfw = 0.0;
         uint32_t nself = 0;
-        for (uint64_t q = a.coff[c]; q < a.coff[c + 1]; q++) {
-            uint32_t v = a.cverts[q];
-            uint64_t b = a.off[v], e = a.off[v + 1];
-            for (uint64_t p0 = b + lane; p0 < e; p0 += 64) {  // two edges per lane in flight
-                uint64_t p1 = p0 + 32;
-                uint32_t j0 = a.tgt[p0];
-                uint32_t j1 = p1 < e ? a.tgt[p1] : 0;
-                double w0 = (double)w[p0], w1 = p1 < e ? (double)w[p1] : 0.0;
-                uint32_t d0 = a.Cd[j0];
-                uint32_t d1 = p1 < e ? a.Cd[j1] : EMPTY;
-                if (d0 == c) { selfw += w0; nself++; }
-                else ht_add<double>(keys, vals, logcap, d0, w0);
-                if (d1 == c) { selfw += w1; nself++; }
-                else if (d1 != EMPTY) ht_add<double>(keys, vals, logcap, d1, w1);
-            }
-        }
+        warp_row_edges(a.cverts, a.coff[c], a.coff[c + 1], a.off, [&](uint64_t p, bool valid) {
+            if (!valid) return;
+            const uint32_t d = a.Cd[a.tgt[p]];
+            const double x = (double)w[p];
+            if (d == c) { selfw += x; nself++; }
+            else ht_add<double>(keys, vals, logcap, d, x);
+        });
         selfw = warp_sum(selfw);
         nself = warp_sum(nself);
         __syncwarp();
@@ -205,8 +240,12 @@ __global__ void __launch_bounds__(AGG_WWARPS * 32) k_agg_merge_warp(AggArgs a, c
 }
 
 // One block per community; 4096-slot table in dynamic shared memory with a
-// list of occupied slots (emission and clearing touch only those).
+// list of occupied slots (emission and clearing touch only those).  The
+// members' edges are numbered through a prefix of member degrees in shared
+// memory and dealt out evenly over the block (a member-per-warp split leaves
+// warps waiting on the longest member).
 constexpr int AGG_BCAP = 4096;
+constexpr int AGG_BMEM = 2048;  // members staged in shared memory (total degree <= 2048 bounds them)
 
 template <typename WT>
 __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32_t *__restrict__ list, uint32_t count) {
@@ -214,9 +253,12 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
     uint32_t *keys = reinterpret_cast<uint32_t *>(dyn_smem);
     double *vals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * AGG_BCAP);
     uint16_t *occ = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(double)) * AGG_BCAP);
+    uint64_t *s_base = reinterpret_cast<uint64_t *>(
+        dyn_smem + (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t)) * AGG_BCAP);
+    uint32_t *s_pre = reinterpret_cast<uint32_t *>(s_base + AGG_BMEM);  // AGG_BMEM + 1 entries
     __shared__ uint32_t s_cur, s_nocc;
     __shared__ double s_red[32];
-    __shared__ uint32_t s_redn[32];
+    __shared__ uint32_t s_redn[32], s_wsum[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const WT *w = static_cast<const WT *>(a.w);
@@ -231,15 +273,66 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
         if (threadIdx.x == 0) { s_cur = 0; s_nocc = 0; }
         __syncthreads();
         uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
+        const uint32_t nm = (uint32_t)(q1 - q0);
         double selfw = 0.0;
         uint32_t nself = 0;
-        for (uint64_t q = q0 + wid; q < q1; q += nw) {
-            uint32_t v = a.cverts[q];
-            uint64_t b = a.off[v], e = a.off[v + 1];
-            for (uint64_t p = b + lane; p < e; p += 32) {
-                uint32_t d = a.Cd[a.tgt[p]];
-                if (d == c) { selfw += (double)w[p]; nself++; }
-                else smem_add<double>(keys, vals, logcap, occ, &s_nocc, d, (double)w[p]);
+        auto visit = [&](uint64_t p) {
+            const uint32_t d = a.Cd[a.tgt[p]];
+            const double x = (double)w[p];
+            if (d == c) { selfw += x; nself++; }
+            else smem_add<double>(keys, vals, logcap, occ, &s_nocc, d, x);
+        };
+        if (nm <= AGG_BMEM) {
+            // member degrees -> exclusive prefix s_pre[0..nm], bases s_base
+            constexpr int PER = AGG_BMEM / 256;
+            uint32_t len[PER];
+            uint32_t tsum = 0;
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                const uint32_t j = threadIdx.x * PER + u;
+                len[u] = 0;
+                if (j < nm) {
+                    const uint32_t v = a.cverts[q0 + j];
+                    const uint64_t b = a.off[v];
+                    s_base[j] = b;
+                    len[u] = (uint32_t)(a.off[v + 1] - b);
+                }
+                tsum += len[u];
+            }
+            uint32_t incl = tsum;  // block-wide exclusive scan of the thread sums
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            if (lane == 31) s_wsum[wid] = incl;
+            __syncthreads();
+            uint32_t wbase = 0;
+            for (int k = 0; k < wid; k++) wbase += s_wsum[k];
+            uint32_t run = wbase + incl - tsum;
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                const uint32_t j = threadIdx.x * PER + u;
+                if (j < nm) s_pre[j] = run;
+                run += len[u];
+            }
+            if (threadIdx.x == blockDim.x - 1) s_pre[nm] = run;
+            __syncthreads();
+            const uint32_t E = s_pre[nm];
+            for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
+                uint32_t lo = 0, hi = nm - 1;  // last member with s_pre <= e
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                visit(s_base[lo] + (e - s_pre[lo]));
+            }
+        } else {
+            for (uint64_t q = q0 + wid; q < q1; q += nw) {
+                uint32_t v = a.cverts[q];
+                uint64_t b = a.off[v], e = a.off[v + 1];
+                for (uint64_t p = b + lane; p < e; p += 32) visit(p);
             }
         }
         selfw = block_sum(selfw, s_red);
@@ -325,22 +418,49 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
                 if (medge[mid] <= ch) lo = mid;
                 else hi = mid - 1;
             }
-            uint64_t q = lo, t0 = ch;
-            while (t0 < cend && q < q1) {
-                uint64_t ms = medge[q], me = medge[q + 1];
-                uint64_t segend = me < cend ? me : cend;
-                if (t0 < segend) {
-                    uint32_t v = a.cverts[q];
-                    uint64_t base = a.off[v];
-                    for (uint64_t tt = t0 + lane; tt < segend; tt += 32) {
-                        uint64_t p = base + (tt - ms);
-                        uint32_t dd = a.Cd[a.tgt[p]];
-                        if (dd == c) { selfw += (double)w[p]; nself++; }
-                        else smem_add<double>(skeys, svals, AGG_SLOG, socc, &s_nocc, dd, (double)w[p]);
-                    }
-                    t0 = segend;
+            // A window of 32 members (lane l: member q + l, its end in the
+            // member-edge numbering and its first edge in the CSR) is read at
+            // once; each round deals out up to 32 edges of the window, every
+            // lane finding its member by a 5-step search over the window's
+            // ends.  Members of high degree keep the window for many rounds,
+            // short ones are consumed 32 at a time.
+            const uint32_t FULL = 0xFFFFFFFFu;
+            uint64_t q = lo, t0 = ch, wq = ~0ull;
+            uint64_t wend_l = 0, wbase_l = 0, wstart = 0;
+            while (t0 < cend) {
+                if (q != wq) {
+                    const uint64_t ql = q + lane;
+                    wend_l = medge[ql < q1 ? ql + 1 : q1];
+                    wbase_l = ql < q1 ? a.off[a.cverts[ql]] : 0;
+                    wstart = medge[q];
+                    wq = q;
                 }
-                q++;
+                const uint64_t wend = __shfl_sync(FULL, wend_l, 31);
+                uint64_t rend = min(min(wend, cend), t0 + 32);
+                if (rend <= t0) {  // every member of the window ends before t0
+                    q += 32;
+                    continue;
+                }
+                const uint64_t tt = t0 + lane;
+                int r = 0;  // first window member ending after tt
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint64_t ev = __shfl_sync(FULL, wend_l, r + step - 1);
+                    if (ev <= tt) r += step;
+                }
+                r &= 31;
+                const uint64_t rbase = __shfl_sync(FULL, wbase_l, r);
+                const uint64_t rprev = __shfl_sync(FULL, wend_l, (r + 31) & 31);
+                const uint64_t rstart = r ? rprev : wstart;
+                if (tt < rend) {
+                    const uint64_t p = rbase + (tt - rstart);
+                    const uint32_t dd = a.Cd[a.tgt[p]];
+                    if (dd == c) { selfw += (double)w[p]; nself++; }
+                    else smem_add<double>(skeys, svals, AGG_SLOG, socc, &s_nocc, dd, (double)w[p]);
+                }
+                // members ending at or before rend are done
+                q += __popc(__ballot_sync(FULL, wend_l <= rend));
+                t0 = rend;
             }
         }
         // the task's edges inside the community enter the table once
@@ -597,7 +717,8 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
         GSP_CHECK_LAUNCH();
     }
     if (cnt_of(ACLS_B)) {
-        constexpr size_t smem = (size_t)AGG_BCAP * (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t));
+        constexpr size_t smem = (size_t)AGG_BCAP * (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t)) +
+                                (size_t)AGG_BMEM * sizeof(uint64_t) + (size_t)(AGG_BMEM + 1) * sizeof(uint32_t);
         static bool attr = false;
         if (!attr) {
             GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_block<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -111,6 +111,24 @@ __device__ __forceinline__ void scan_edges(const uint32_t *__restrict__ tgt, con
     }
 }
 
+// Position of the q-th (from 0) set bit of m; q < popcount(m).
+__device__ __forceinline__ int select_bit(unsigned m, int q) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const unsigned low = m & ((1u << w) - 1u);
+        const int c = __popc(low);
+        if (q >= c) {
+            q -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
 template <typename S> __device__ __forceinline__ bool better(S s1, uint32_t c1, S s2, uint32_t c2) {
     return s1 > s2 || (s1 == s2 && c1 < c2);
 }
@@ -286,17 +304,30 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
     const WT *w = static_cast<const WT *>(a.w);
     const double m0 = *a.m;
     LocalCtr lc;
-    for (uint32_t idx = lb * NG + grp; idx < count; idx += nb * NG) {
-        uint32_t i = list[idx];
-        // one lane reads the flag (other threads may re-mark it) and marks
-        // the vertex processed; the group follows its decision
-        int go = 0;
-        if (lane == 0) {
-            go = ld_state<SYNC>(a.act + i);
-            if (go) a.act[i] = 0;
+    // The warp's list entries are wbase, wbase + wstep, ...; 32 of them are
+    // claimed at once (each lane reads one flag and marks its vertex
+    // processed), and the active ones are dealt to the warp's groups round
+    // by round, so that the inactive vertices of later sweeps cost one
+    // parallel round of loads per 32 entries and the groups of a warp stay
+    // in step.
+    constexpr int NGW = 32 / G;  // groups per warp
+    const int wl = threadIdx.x & 31, gw = wl / G;
+    const uint32_t wbase = lb * 8 + (threadIdx.x >> 5), wstep = nb * 8;
+    for (uint64_t kb = 0; wbase + kb * wstep < count; kb += 32) {
+        const uint64_t my = wbase + (kb + wl) * wstep;
+        uint32_t vi = 0;
+        int claim = 0;
+        if (my < count) {
+            vi = list[my];
+            claim = ld_state<SYNC>(a.act + vi);
+            if (claim) a.act[vi] = 0;
         }
-        go = __shfl_sync(gmask, go, leader);
-        if (!go) continue;
+        const unsigned amask = __ballot_sync(0xFFFFFFFFu, claim);
+        const int nact = __popc(amask);
+        for (int r0 = 0; r0 < nact; r0 += NGW) {
+        const int q = r0 + gw;  // this group's active entry in the round
+        const uint32_t i = __shfl_sync(0xFFFFFFFFu, vi, q < nact ? select_bit(amask, q) : 0);
+        if (q >= nact) continue;
         uint32_t d = ld_state<SYNC>(a.C + i);
         uint64_t b = a.off[i], e = a.off[i + 1];
         uint32_t deg = (uint32_t)(e - b);
@@ -348,6 +379,7 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
             }
         }
         __syncwarp(gmask);
+        }
     }
     flush_counters(lc, a.ctr);
 }
@@ -404,7 +436,7 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
     __shared__ S red_s[32];
     __shared__ uint32_t red_c[32];
     __shared__ V red_k[32];
-    __shared__ int s_go, s_mv;
+    __shared__ int s_mv;
     __shared__ uint32_t s_d, s_nocc;
     __shared__ double s_Sd;
     const WT *w = static_cast<const WT *>(a.w);
@@ -412,22 +444,45 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     LocalCtr lc;
+    __shared__ uint32_t s_todo[256], s_ntodo, s_wcnt[8];
     for (uint32_t s = threadIdx.x; s < CAP; s += blockDim.x) { keys[s] = EMPTY; vals[s] = V(0); }
-    for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
-        uint32_t i = list[idx];
-        __syncthreads();  // previous vertex done with the table and reductions
+    // The block's entries are blockIdx.x + k * gridDim.x; blockDim.x of them
+    // are claimed at once (one flag per thread) and the active ones listed
+    // in shared memory, so inactive vertices cost no serial round trip.
+    for (uint64_t kb = 0; blockIdx.x + kb * gridDim.x < count; kb += blockDim.x) {
+        const uint64_t my = blockIdx.x + (kb + threadIdx.x) * gridDim.x;
+        uint32_t vi = 0;
+        int claim = 0;
+        if (my < count) {
+            vi = list[my];
+            claim = ld_state<SYNC>(a.act + vi);
+            if (claim) a.act[vi] = 0;
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, claim);
+        __syncthreads();  // previous round done with s_todo
+        if (lane == 0) s_wcnt[wid] = __popc(bal);
+        __syncthreads();
+        if (claim) {
+            uint32_t pos = __popc(bal & ((1u << lane) - 1u));
+            for (int k = 0; k < wid; k++) pos += s_wcnt[k];
+            s_todo[pos] = vi;
+        }
         if (threadIdx.x == 0) {
-            int go = ld_state<SYNC>(a.act + i);
-            if (go) a.act[i] = 0;
-            s_go = go;
-            s_nocc = 0;
-            if (go) {
-                s_d = ld_state<SYNC>(a.C + i);
-                s_Sd = ld_state<SYNC>(a.Sig + s_d);
-            }
+            uint32_t t = 0;
+            for (int k = 0; k < nw; k++) t += s_wcnt[k];
+            s_ntodo = t;
         }
         __syncthreads();
-        if (!s_go) continue;
+        const uint32_t ntodo = s_ntodo;
+    for (uint32_t kk = 0; kk < ntodo; kk++) {
+        const uint32_t i = s_todo[kk];
+        __syncthreads();  // previous vertex done with the table and reductions
+        if (threadIdx.x == 0) {
+            s_nocc = 0;
+            s_d = ld_state<SYNC>(a.C + i);
+            s_Sd = ld_state<SYNC>(a.Sig + s_d);
+        }
+        __syncthreads();
         uint32_t d = s_d;
         uint64_t b = a.off[i], e = a.off[i + 1];
         uint32_t deg = (uint32_t)(e - b);
@@ -483,6 +538,7 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
                 if (j != i) a.mark[j] = 1;
             }
         }
+    }
     }
     __syncthreads();
     flush_counters(lc, a.ctr);

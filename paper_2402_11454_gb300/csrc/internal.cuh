@@ -190,6 +190,25 @@ void mlp_unskip(const DevGraph &g, MoveBuffers &mb, cudaStream_t s);
 
 __device__ __forceinline__ int ceil_log2(uint32_t x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
 
+// Position of the q-th (from 0) set bit of m; q < popcount(m).
+__device__ __forceinline__ int select_bit(unsigned m, int q) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const unsigned low = m & ((1u << w) - 1u);
+        const int c = __popc(low);
+        if (q >= c) {
+            q -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
+
 // Open-addressing insert of (c, w) with linear probing: the key is claimed
 // with atomicCAS, the value accumulated with atomicAdd.  The table holds
 // 2^logcap slots, more than the number of distinct keys inserted, so a free

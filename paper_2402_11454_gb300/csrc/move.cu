@@ -111,24 +111,6 @@ __device__ __forceinline__ void scan_edges(const uint32_t *__restrict__ tgt, con
     }
 }
 
-// Position of the q-th (from 0) set bit of m; q < popcount(m).
-__device__ __forceinline__ int select_bit(unsigned m, int q) {
-    int pos = 0;
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) {
-        const unsigned low = m & ((1u << w) - 1u);
-        const int c = __popc(low);
-        if (q >= c) {
-            q -= c;
-            m >>= w;
-            pos += w;
-        } else {
-            m = low;
-        }
-    }
-    return pos;
-}
-
 template <typename S> __device__ __forceinline__ bool better(S s1, uint32_t c1, S s2, uint32_t c2) {
     return s1 > s2 || (s1 == s2 && c1 < c2);
 }

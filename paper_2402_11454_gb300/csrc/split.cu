@@ -34,18 +34,30 @@ __global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ o
                                                   unsigned long long *changed) {
     const int lane = threadIdx.x % G;
     const unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    const uint32_t NG = 256 / G;
     unsigned long long ch = 0;
-    for (uint32_t idx = blockIdx.x * NG + threadIdx.x / G; idx < count; idx += gridDim.x * NG) {
-        uint32_t i = list[idx];
-        if (PRUNE) {  // one lane reads and clears the flag; the group follows
-            int go = 0;
-            if (lane == 0) {
-                go = ldcg_(flag + i);
-                if (go) flag[i] = 0;
+    // 32 list entries per warp and round: each lane reads (and, pruned,
+    // clears) one flag; the flagged vertices are dealt to the warp's groups
+    constexpr int NGW = 32 / G;
+    const int wl = threadIdx.x & 31, gw = wl / G;
+    const uint32_t wbase = blockIdx.x * 8 + (threadIdx.x >> 5), wstep = gridDim.x * 8;
+    for (uint64_t kb = 0; wbase + kb * wstep < count; kb += 32) {
+        const uint64_t my = wbase + (kb + wl) * wstep;
+        uint32_t vi = 0;
+        int claim = 0;
+        if (my < count) {
+            vi = list[my];
+            claim = 1;
+            if (PRUNE) {
+                claim = ldcg_(flag + vi);
+                if (claim) flag[vi] = 0;
             }
-            if (!__shfl_sync(gmask, go, (threadIdx.x & 31) & ~(G - 1))) continue;
         }
+        const unsigned amask = __ballot_sync(0xFFFFFFFFu, claim);
+        const int nact = __popc(amask);
+        for (int r0 = 0; r0 < nact; r0 += NGW) {
+        const int qa = r0 + gw;
+        const uint32_t i = __shfl_sync(0xFFFFFFFFu, vi, qa < nact ? select_bit(amask, qa) : 0);
+        if (qa >= nact) continue;
         uint32_t ci = C[i];
         uint32_t cur = ldcg_(lab + i);
         uint32_t mn = cur;
@@ -65,6 +77,7 @@ __global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ o
                 }
         }
         __syncwarp(gmask);
+        }
     }
     __shared__ unsigned long long red[32];
     ch = block_sum(ch, red);
@@ -77,21 +90,43 @@ __global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ o
                                                   const uint32_t *__restrict__ list, uint32_t count,
                                                   unsigned long long *changed) {
     __shared__ uint32_t red[32];
-    __shared__ int s_go;
+    __shared__ uint32_t s_todo[256], s_ntodo, s_wcnt[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long ch = 0;
-    for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
-        uint32_t i = list[idx];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int go = 1;
+    // 256 list entries per block and round (blockIdx.x + k * gridDim.x):
+    // each thread reads (and, pruned, clears) one flag; the flagged vertices
+    // are listed in shared memory and processed one by one
+    for (uint64_t kb = 0; blockIdx.x + kb * gridDim.x < count; kb += blockDim.x) {
+        const uint64_t my = blockIdx.x + (kb + threadIdx.x) * gridDim.x;
+        uint32_t vi = 0;
+        int claim = 0;
+        if (my < count) {
+            vi = list[my];
+            claim = 1;
             if (PRUNE) {
-                go = ldcg_(flag + i);
-                if (go) flag[i] = 0;
+                claim = ldcg_(flag + vi);
+                if (claim) flag[vi] = 0;
             }
-            s_go = go;
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, claim);
+        __syncthreads();  // previous round done with s_todo
+        if (lane == 0) s_wcnt[wid] = __popc(bal);
+        __syncthreads();
+        if (claim) {
+            uint32_t pos = __popc(bal & ((1u << lane) - 1u));
+            for (int k = 0; k < wid; k++) pos += s_wcnt[k];
+            s_todo[pos] = vi;
+        }
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s_wcnt[k];
+            s_ntodo = t;
         }
         __syncthreads();
-        if (!s_go) continue;
+        const uint32_t ntodo = s_ntodo;
+    for (uint32_t kk = 0; kk < ntodo; kk++) {
+        const uint32_t i = s_todo[kk];
+        __syncthreads();  // previous vertex done with red
         uint32_t ci = C[i];
         uint32_t cur = ldcg_(lab + i);
         uint32_t mn = cur;
@@ -114,6 +149,7 @@ __global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ o
                     if (C[j] == ci) flag[j] = 1;
                 }
         }
+    }
     }
     __shared__ unsigned long long r2[32];
     __syncthreads();

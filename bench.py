@@ -306,6 +306,8 @@ def main():
     ap.add_argument("--recall", type=float, default=0.9)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default grid caps instead of tuning them on the workload (untimed)")
+    ap.add_argument("--caps", default=None,
+                    help="fixed grid caps 'groups,w512,block,hub' (blocks per SM) instead of autotuning")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -331,8 +333,11 @@ def main():
         return C, st["modularity"], st
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MB > 129 MB L2
 
+    if args.caps:
+        g4, w5, bl, hb = (int(x) for x in args.caps.split(","))
+        gsp.set_tuning(groups_blocks_per_sm=g4, w512_blocks_per_sm=w5, block_blocks_per_sm=bl, hub_blocks_per_sm=hb)
     tuning = {"caps": gsp.get_tuning(), "autotuned": False}
-    if not args.no_autotune:  # untimed: picks the local-moving grid caps for this graph
+    if not args.no_autotune and not args.caps:  # untimed: picks the local-moving grid caps for this graph
         caps, ms0, ms1 = gsp.autotune(off, tgt, w, **kw)
         tuning = {"caps": caps, "autotuned": True, "first_sweep_ms_default": round(ms0, 3),
                   "first_sweep_ms_tuned": round(ms1, 3)}

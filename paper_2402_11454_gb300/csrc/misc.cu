@@ -38,7 +38,23 @@ __global__ void k_row_sums(const uint64_t *__restrict__ off, const uint32_t *__r
         }
         double k = 0, in = 0;
         uint32_t ci = C ? C[i] : 0;
-        for (uint64_t p = b; p < e; p++) {
+        uint64_t p = b;
+        for (; p + 4 <= e; p += 4) {  // four independent loads in flight
+            double wv[4];
+            uint32_t cj[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) wv[u] = (double)w[p + u];
+            if (C) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) cj[u] = C[tgt[p + u]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                k += wv[u];
+                if (C && cj[u] == ci) in += wv[u];
+            }
+        }
+        for (; p < e; p++) {
             double wv = (double)w[p];
             k += wv;
             if (C && C[tgt[p]] == ci) in += wv;
@@ -75,7 +91,23 @@ __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t
         if (e - b > WARP_ROW) continue;
         uint32_t ci = C ? C[i] : 0;
         double k = 0, in = 0;
-        for (uint64_t p = b + lane; p < e; p += 32) {
+        uint64_t p = b + lane;
+        for (; p + 96 < e; p += 128) {  // four independent loads per lane in flight
+            double wv[4];
+            uint32_t cj[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) wv[u] = (double)w[p + 32 * u];
+            if (C) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) cj[u] = C[tgt[p + 32 * u]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                k += wv[u];
+                if (C && cj[u] == ci) in += wv[u];
+            }
+        }
+        for (; p < e; p += 32) {
             double wv = (double)w[p];
             k += wv;
             if (C && C[tgt[p]] == ci) in += wv;
@@ -96,7 +128,24 @@ __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t
         if (e - b <= WARP_ROW) continue;
         uint32_t ci = C ? C[i] : 0;
         double k = 0, in = 0;
-        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+        uint64_t p = b + threadIdx.x;
+        const uint64_t st = blockDim.x;
+        for (; p + 3 * st < e; p += 4 * st) {
+            double wv[4];
+            uint32_t cj[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) wv[u] = (double)w[p + st * u];
+            if (C) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) cj[u] = C[tgt[p + st * u]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                k += wv[u];
+                if (C && cj[u] == ci) in += wv[u];
+            }
+        }
+        for (; p < e; p += st) {
             double wv = (double)w[p];
             k += wv;
             if (C && C[tgt[p]] == ci) in += wv;

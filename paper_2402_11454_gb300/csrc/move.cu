@@ -632,8 +632,8 @@ __global__ void k_mark_big(const uint64_t *__restrict__ off, const uint32_t *__r
 //            for the next sweep); per-block best per hub;
 //   decide:  one warp per hub reduces the block bests and decides the move.
 // --------------------------------------------------------------------------
-constexpr uint32_t HUB_CHUNK = 2048;
-constexpr int HUB_SLOG = 12;  // shared table of 2 * HUB_CHUNK slots
+constexpr uint32_t HUB_CHUNK = 1024;
+constexpr int HUB_SLOG = 11;  // shared table of 2 * HUB_CHUNK slots
 
 struct HubArgs {
     const uint32_t *hubs;

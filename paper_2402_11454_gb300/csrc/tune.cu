@@ -165,7 +165,7 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
             const Knob knobs[] = {{&Tuning::groups, {4, 6, 8, 12, 16}},
                                   {&Tuning::w512, {1, 2, 3, 4, 6}},
                                   {&Tuning::block, {2, 3, 4, 5, 8}},
-                                  {&Tuning::hub, {1, 2, 4, 8, 16}}};
+                                  {&Tuning::hub, {2, 4, 8, 16, 32}}};
             for (const Knob &k : knobs) {
                 for (int v : k.cand) {
                     if (v == best.*(k.field)) continue;

@@ -6,7 +6,8 @@
 // a wave holds, how unbalanced the hubs are), so gsp_autotune picks them on
 // the caller's graph: it times the first sweep of the first pass (every
 // vertex unprocessed, the heaviest sweep) under candidate caps, one class at
-// a time (coordinate descent), restoring the start state before each trial.
+// a time (two rounds of coordinate descent), restoring the start state before
+// each trial.
 // Caps change only the launch geometry: in frozen-state mode a sweep's result
 // is the same under every setting.
 #include <string.h>
@@ -166,15 +167,17 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
                                   {&Tuning::w512, {1, 2, 3, 4, 6}},
                                   {&Tuning::block, {2, 3, 4, 5, 8}},
                                   {&Tuning::hub, {2, 4, 8, 16, 32}}};
-            for (const Knob &k : knobs) {
-                for (int v : k.cand) {
-                    if (v == best.*(k.field)) continue;
-                    g_tuning = best;
-                    g_tuning.*(k.field) = v;
-                    float t = trial();
-                    if (t < tb) {
-                        tb = t;
-                        best = g_tuning;
+            for (int round = 0; round < 2; round++) {  // the classes share the SMs: revisit once
+                for (const Knob &k : knobs) {
+                    for (int v : k.cand) {
+                        if (v == best.*(k.field)) continue;
+                        g_tuning = best;
+                        g_tuning.*(k.field) = v;
+                        float t = trial();
+                        if (t < tb) {
+                            tb = t;
+                            best = g_tuning;
+                        }
                     }
                 }
             }

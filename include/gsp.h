@@ -46,8 +46,16 @@ typedef enum {
 
 /* Split techniques of Section 4.1: none (GVE-Louvain), min-label propagation
  * (Algorithm 2), min-label propagation with pruning (Algorithm 2, LPP), and
- * breadth-first search (Algorithm 3). */
-typedef enum { GSP_SPLIT_NONE = 0, GSP_SPLIT_LP = 1, GSP_SPLIT_LPP = 2, GSP_SPLIT_BFS = 3 } gsp_split_mode;
+ * breadth-first search (Algorithm 3); SV (not in the paper) is hooking and
+ * shortcutting (Shiloach-Vishkin) on the intra-community edges, for graphs of
+ * high diameter.  All give the same labels. */
+typedef enum {
+    GSP_SPLIT_NONE = 0,
+    GSP_SPLIT_LP = 1,
+    GSP_SPLIT_LPP = 2,
+    GSP_SPLIT_BFS = 3,
+    GSP_SPLIT_SV = 4
+} gsp_split_mode;
 /* Split Pass (after the local-moving phase of every pass) or Split Last
  * (once, after the passes converge); Section 4.1. */
 typedef enum { GSP_SPLIT_PASS = 0, GSP_SPLIT_LAST = 1 } gsp_split_when;

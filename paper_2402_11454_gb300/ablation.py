@@ -1,8 +1,9 @@
 """Split ablation on the synthetic stand-ins of the paper's graphs: the split
 technique (none = GVE-Louvain, label propagation, label propagation with
-pruning, BFS) and its placement (after every pass, or once at the end), as in
-the paper's comparison of split variants (Section 4.1) and of GSP-Louvain
-against the method without a split (Section 5).
+pruning, BFS, and hooking/shortcutting (SV), which is not in the paper) and
+its placement (after every pass, or once at the end), as in the paper's
+comparison of split variants (Section 4.1) and of GSP-Louvain against the
+method without a split (Section 5).
 
 For every configuration it reports the device time of one gsp_louvain call,
 the modularity, the number of communities and the number of internally
@@ -21,9 +22,11 @@ VARIANTS = [
     ("lp", "pass"),
     ("lpp", "pass"),
     ("bfs", "pass"),
+    ("sv", "pass"),
     ("lp", "last"),
     ("lpp", "last"),
     ("bfs", "last"),
+    ("sv", "last"),
 ]
 
 

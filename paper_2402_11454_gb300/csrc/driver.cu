@@ -589,7 +589,7 @@ void check_opts(const gsp_opts &o) {
     GSP_REQUIRE(o.max_iterations >= 1 && o.max_iterations <= 100000, "max_iterations out of range");
     GSP_REQUIRE(o.tolerance >= 0.0 && o.tolerance_drop > 0.0, "tolerance out of range");
     GSP_REQUIRE(o.aggregation_tolerance > 0.0, "aggregation_tolerance must be > 0");
-    GSP_REQUIRE(o.split >= GSP_SPLIT_NONE && o.split <= GSP_SPLIT_BFS, "unknown split mode");
+    GSP_REQUIRE(o.split >= GSP_SPLIT_NONE && o.split <= GSP_SPLIT_SV, "unknown split mode");
     GSP_REQUIRE(o.split_when == GSP_SPLIT_PASS || o.split_when == GSP_SPLIT_LAST, "unknown split_when");
     GSP_REQUIRE(o.move == GSP_MOVE_ASYNC || o.move == GSP_MOVE_SYNC, "unknown move mode");
     GSP_REQUIRE(o.waves >= 1 && o.waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
@@ -823,7 +823,8 @@ gsp_status gsp_louvain_trace(const uint64_t *offsets, const uint32_t *targets, c
 gsp_status gsp_split(const uint64_t *offsets, const uint32_t *targets, uint32_t n, uint64_t nnz, const uint32_t *C,
                      int mode, uint32_t *labels, uint32_t *k_host, void *stream) {
     GSP_API_BEGIN
-    GSP_REQUIRE(mode == GSP_SPLIT_LP || mode == GSP_SPLIT_LPP || mode == GSP_SPLIT_BFS, "unknown split mode");
+    GSP_REQUIRE(mode == GSP_SPLIT_LP || mode == GSP_SPLIT_LPP || mode == GSP_SPLIT_BFS || mode == GSP_SPLIT_SV,
+                "unknown split mode");
     GSP_REQUIRE(C && labels && n > 0 && offsets && (nnz == 0 || targets), "invalid arguments");
     DevGraph g = make_graph(offsets, targets, targets ? (const void *)targets : (const void *)offsets, GSP_W_F32, n,
                             nnz);

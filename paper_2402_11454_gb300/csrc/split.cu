@@ -8,6 +8,8 @@
 //   LPP (Algorithm 2 with pruning): only vertices flagged unprocessed are
 //        visited; a vertex whose label drops flags its same-community
 //        neighbours.
+//   SV  (not in the paper): hooking and shortcutting (Shiloach-Vishkin) on
+//        the intra-community edges, O(log n) sweeps on high-diameter graphs.
 //   BFS (Algorithm 3): rounds of multi-source, level-synchronous,
 //        frontier-compacted BFS.  In each round the seed of a community is its
 //        smallest unvisited vertex, found with atomicMin; vertices are claimed
@@ -27,7 +29,11 @@ __device__ __forceinline__ uint8_t ldcg_(const uint8_t *p) {
 }
 
 // ----------------------------------------------------------------- LP / LPP
-template <int G, bool PRUNE>
+// HOOK (the hooking split): besides lowering its own label, a vertex whose
+// smallest neighbouring label mn is below its label p hooks p's tree under
+// mn (lab[p] = min(lab[p], mn)); with the shortcut kernel between sweeps the
+// labels then converge in O(log n) sweeps instead of O(diameter).
+template <int G, bool PRUNE, bool HOOK = false>
 __global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                                                   const uint32_t *__restrict__ C, uint32_t *lab, uint8_t *flag,
                                                   const uint32_t *__restrict__ list, uint32_t count,
@@ -69,7 +75,15 @@ __global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ o
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(gmask, mn, o));
         if (mn < cur) {
-            if (lane == 0) { lab[i] = mn; ch++; }
+            if (lane == 0) {
+                if (HOOK) {
+                    atomicMin(lab + cur, mn);
+                    atomicMin(lab + i, mn);
+                } else {
+                    lab[i] = mn;
+                }
+                ch++;
+            }
             if (PRUNE)
                 for (uint64_t p = b + lane; p < e; p += G) {
                     uint32_t j = tgt[p];
@@ -84,7 +98,7 @@ __global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ o
     if (threadIdx.x == 0 && ch) atomicAdd(changed, ch);
 }
 
-template <bool PRUNE>
+template <bool PRUNE, bool HOOK = false>
 __global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                                                   const uint32_t *__restrict__ C, uint32_t *lab, uint8_t *flag,
                                                   const uint32_t *__restrict__ list, uint32_t count,
@@ -142,7 +156,15 @@ __global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ o
         mn = red[0];
         for (int t = 1; t < (int)(blockDim.x >> 5); t++) mn = min(mn, red[t]);
         if (mn < cur) {
-            if (threadIdx.x == 0) { lab[i] = mn; ch++; }
+            if (threadIdx.x == 0) {
+                if (HOOK) {
+                    atomicMin(lab + cur, mn);
+                    atomicMin(lab + i, mn);
+                } else {
+                    lab[i] = mn;
+                }
+                ch++;
+            }
             if (PRUNE)
                 for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
                     uint32_t j = tgt[p];
@@ -192,6 +214,58 @@ static void split_lp(const DevGraph &g, const Classes &cl, const uint32_t *C, bo
                                                                                lst(CLS_BLOCK), nbig, changed);
             GSP_CHECK_LAUNCH();
         }
+        unsigned long long h;
+        GSP_CUDA(cudaMemcpyAsync(&h, changed, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        if (h == 0) break;
+    }
+    arena().release(mk);
+}
+
+// ------------------------------------------------------------ hooking split
+// Shiloach-Vishkin-style connected components restricted to intra-community
+// edges: hooking sweeps (k_lp_group/k_lp_block with HOOK) alternate with a
+// shortcut pass that points every vertex at the root of its tree.  Labels
+// only decrease and always name a vertex of the same component, so at the
+// fixpoint every component carries its smallest vertex id, as LP and BFS.
+__global__ void k_sv_shortcut(uint32_t *lab, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t x = ldcg_(lab + i);
+        // lab[x] <= x, so the chain strictly decreases and ends at a root
+        for (;;) {
+            const uint32_t y = ldcg_(lab + x);
+            if (y == x) break;
+            x = y;
+        }
+        lab[i] = x;
+    }
+}
+
+static void split_sv(const DevGraph &g, const Classes &cl, const uint32_t *C, uint32_t *lab, cudaStream_t s) {
+    size_t mk = arena().mark();
+    unsigned long long *changed = arena().get<unsigned long long>(1);
+    iota_u32(lab, g.n, s);
+    auto cnt = [&](int c) { return cl.cls_count(c); };
+    auto lst = [&](int c) { return cl.list + cl.cls_begin(c); };
+    const unsigned maxg = 152 * 8;
+    const uint32_t nbig = cl.cls_count(CLS_BLOCK) + cl.cls_count(CLS_HUGE);
+    for (int it = 0; it < (1 << 30); it++) {
+        GSP_CUDA(cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s));
+#define SVG(G, CLS)                                                                                            \
+    if (cnt(CLS)) {                                                                                            \
+        k_lp_group<G, false, true><<<grid_for((uint64_t)cnt(CLS) * G, 256, maxg), 256, 0, s>>>(               \
+            g.off, g.tgt, C, lab, nullptr, lst(CLS), cnt(CLS), changed);                                       \
+        GSP_CHECK_LAUNCH();                                                                                    \
+    }
+        SVG(4, CLS_G4) SVG(8, CLS_G8) SVG(16, CLS_G16) SVG(32, CLS_G32) SVG(32, CLS_W512)
+#undef SVG
+        if (nbig) {
+            k_lp_block<false, true><<<grid_for(nbig, 1, 152 * 4), 256, 0, s>>>(g.off, g.tgt, C, lab, nullptr,
+                                                                               lst(CLS_BLOCK), nbig, changed);
+            GSP_CHECK_LAUNCH();
+        }
+        k_sv_shortcut<<<grid_for(g.n, 256), 256, 0, s>>>(lab, g.n);
+        GSP_CHECK_LAUNCH();
         unsigned long long h;
         GSP_CUDA(cudaMemcpyAsync(&h, changed, sizeof(h), cudaMemcpyDeviceToHost, s));
         GSP_CUDA(cudaStreamSynchronize(s));
@@ -392,6 +466,7 @@ static void split_bfs(const DevGraph &g, const uint32_t *C, uint32_t *lab, cudaS
 void split_labels(const DevGraph &g, const Classes &cl, const uint32_t *C, int mode, uint32_t *labels,
                   cudaStream_t s) {
     if (mode == GSP_SPLIT_BFS) split_bfs(g, C, labels, s);
+    else if (mode == GSP_SPLIT_SV) split_sv(g, cl, C, labels, s);
     else split_lp(g, cl, C, mode == GSP_SPLIT_LPP, labels, s);
 }
 

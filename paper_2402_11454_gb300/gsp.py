@@ -12,7 +12,7 @@ import torch
 from . import _lib
 from ._lib import GspOpts, GspStats, GspDeviceGraph, GspTuning, check
 
-SPLIT = {"none": 0, "lp": 1, "lpp": 2, "bfs": 3}
+SPLIT = {"none": 0, "lp": 1, "lpp": 2, "bfs": 3, "sv": 4}
 SPLIT_WHEN = {"pass": 0, "last": 1}
 MOVE = {"async": 0, "sync": 1}
 PRECISION = {"mixed": 0, "fp64": 1}

@@ -188,7 +188,7 @@ def test_sync_local_move_fp64_matches_oracle(gsp, name, waves):
 
 # -------------------------------------------------------------------- split
 @pytest.mark.parametrize("name", sorted(GRAPHS))
-@pytest.mark.parametrize("mode", ["lp", "lpp", "bfs"])
+@pytest.mark.parametrize("mode", ["lp", "lpp", "bfs", "sv"])
 def test_split_bit_exact(gsp, name, mode):
     off, tgt, w = GRAPHS[name]
     n = len(off) - 1
@@ -288,12 +288,23 @@ def test_louvain_sync_fp64_equals_oracle(gsp, name):
     assert q == pytest.approx(ost["modularity"], rel=1e-9)
 
 
+@pytest.mark.parametrize("name", ["planted", "grid"])
+def test_louvain_hooking_split_equals_oracle(gsp, name):
+    """The hooking split (not in the paper) yields the same canonical labels
+    as the paper's techniques, so a whole FP64 run still equals the oracle."""
+    off, tgt, w = GRAPHS[name]
+    g = og(name)
+    C, q, st = gsp.louvain(*dev(off, tgt, w), move="sync", precision="fp64", split="sv")
+    Co, ost = oracle.louvain(g, oracle.LouvainOptions(sync=True))
+    assert np.array_equal(host(C).astype(np.uint32), Co)
+
+
 @pytest.mark.parametrize("name", ["rmat14", "grid", "star"])
 def test_louvain_invariants(gsp, name):
     off, tgt, w = GRAPHS[name]
     g = og(name)
     for kw in ({}, {"split_when": "last"}, {"precision": "fp64"}, {"split": "none"}, {"move": "async"},
-               {"waves": 1}, {"split": "lp"}):
+               {"waves": 1}, {"split": "lp"}, {"split": "sv"}, {"split": "sv", "split_when": "last"}):
         C, q, st = gsp.louvain(*dev(off, tgt, w), **kw)
         C = host(C).astype(np.uint32)
         assert -0.5 <= q <= 1.0

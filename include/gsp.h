@@ -349,12 +349,20 @@ typedef struct {
     int w512_blocks_per_sm;    /* default 3 */
     int block_blocks_per_sm;   /* default 4 */
     int hub_blocks_per_sm;     /* default 4 */
+    /* SYNC sweeps of graphs with at most this many vertices and no vertex
+     * above 2048 edges run as one cooperative launch (a persistent kernel
+     * with grid-wide barriers) instead of several launches per wave; 0
+     * disables it.  Default 0: on a GB300 the per-wave launches replayed
+     * from a CUDA graph were as fast (a wave's dependent loads, not its
+     * launches, set the time).  The result is the same either way. */
+    uint32_t persist_max_vertices;
 } gsp_tuning;
 
 /* Current caps into *out (host).  GSP_ERR_INVALID if out is NULL. */
 gsp_status gsp_get_tuning(gsp_tuning *out);
 
-/* Install caps (host struct); GSP_ERR_INVALID if a cap is outside [1, 32]. */
+/* Install caps (host struct); GSP_ERR_INVALID if a cap is outside [1, 32]
+ * (persist_max_vertices may be any value). */
 gsp_status gsp_set_tuning(const gsp_tuning *t);
 
 /*

@@ -45,7 +45,7 @@ class GspDeviceGraph(ctypes.Structure):
 
 class GspTuning(ctypes.Structure):
     _fields_ = [("groups_blocks_per_sm", c_int), ("w512_blocks_per_sm", c_int), ("block_blocks_per_sm", c_int),
-                ("hub_blocks_per_sm", c_int)]
+                ("hub_blocks_per_sm", c_int), ("persist_max_vertices", c_u32)]
 
 
 _SIGS = {

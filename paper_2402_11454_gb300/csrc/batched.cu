@@ -209,10 +209,20 @@ static BatchMove batch_move_loop(const DevGraph &g, const Classes &cl, MoveBuffe
     cudaEvent_t e0 = pool_event(), e1 = pool_event();
     cudaGraphExec_t exec = nullptr;
     const bool use_graph = graphs_enabled();
+    bool use_persist = sync && persistent_enabled();  // small graphs: one launch per sweep
     side_streams();
     try {
         for (int it = 0; it < o.max_iterations && nlive; it++) {
             GSP_CUDA(cudaMemsetAsync(mb.dq_g, 0, sizeof(double) * G, s));
+            bool persisted = false;
+            if (use_persist) {
+                GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
+                GSP_CUDA(cudaEventRecord(e0, s));
+                persisted = sweep_persistent(g, cl, mb, fp64, rule, it, o.max_iterations, s);
+                use_persist = persisted;
+            }
+            if (persisted) {
+            } else {
             GSP_CUDA(cudaEventRecord(e0, s));
             if (use_graph && it >= 1) {
                 if (!exec) {
@@ -227,10 +237,15 @@ static BatchMove batch_move_loop(const DevGraph &g, const Classes &cl, MoveBuffe
             } else {
                 sweep_launches(g, cl, mb, sync, fp64, rule, false, it, o.max_iterations, wave_n, true, s);
             }
+            }
             GSP_CUDA(cudaEventRecord(e1, s));
             GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
             GSP_CUDA(cudaMemcpyAsync(h_dq.data(), mb.dq_g, sizeof(double) * G, cudaMemcpyDeviceToHost, s));
             GSP_CUDA(cudaStreamSynchronize(s));
+            if (h.stalled) {
+                set_error("persistent sweep: a grid barrier gave up waiting");
+                throw Error{GSP_ERR_TIMEOUT};
+            }
             float ms = 0;
             GSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             r.ms_kernels += ms;

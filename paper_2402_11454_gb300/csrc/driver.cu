@@ -218,6 +218,8 @@ bool graphs_enabled() {
     return !(e && e[0] == '1');
 }
 
+bool persistent_enabled() { return tuning().persist_max_vertices > 0; }
+
 // louvainMove (Algorithm 4): iterate sweeps until the summed gain of a sweep
 // is <= tau or max_iterations is reached.  The launches of a sweep do not
 // change within a pass: the first sweep runs directly, the second is captured
@@ -263,6 +265,7 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
     // features (learned pruning, traces) depend on the iteration number, so
     // those runs launch directly
     const bool use_graph = graphs_enabled() && !mb.feat_kept;
+    bool use_persist = sync && persistent_enabled();  // small graphs: one launch per sweep
     cudaGraphExec_t exec = nullptr;
     side_streams();
     try {
@@ -270,6 +273,15 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
         for (int it = 0; it < max_it; it++) {
             const bool pruned = pr.learned && !force_full && pr.full_every > 0 &&
                                 (it % pr.full_every) != pr.full_every - 1;
+            bool persisted = false;
+            if (use_persist) {
+                GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
+                GSP_CUDA(cudaEventRecord(e0, s));
+                persisted = sweep_persistent(g, cl, mb, fp64, rule, it, max_it, s);
+                use_persist = persisted;
+            }
+            if (persisted) {
+            } else {
             GSP_CUDA(cudaEventRecord(e0, s));
             if (use_graph && it >= 1) {
                 if (!exec) {
@@ -287,9 +299,14 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
                 sweep_launches(g, cl, mb, sync, fp64, rule, pruned, it, max_it, wave_n, false, s);
                 if (pruned) mlp_unskip(g, mb, s);
             }
+            }
             GSP_CUDA(cudaEventRecord(e1, s));
             GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
             GSP_CUDA(cudaStreamSynchronize(s));
+            if (h.stalled) {
+                set_error("persistent sweep: a grid barrier gave up waiting");
+                throw Error{GSP_ERR_TIMEOUT};
+            }
             float ms = 0;
             GSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             r.ms_kernels += ms;
@@ -332,6 +349,8 @@ void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.mv_vtx = arena().get<uint32_t>(n);
     mb.mv_cmt = arena().get<uint32_t>(n);
     mb.mv_cnt = arena().get<uint32_t>(1);
+    mb.mv_cnts = arena().get<uint32_t>(MAX_WAVES);
+    mb.bar = arena().get<GridBar>(1);
     mb.big = arena().get<uint32_t>(n);
     mb.nbig = arena().get<uint32_t>(1);
     mb.m_dev = arena().get<double>(1);

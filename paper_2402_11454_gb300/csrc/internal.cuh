@@ -24,6 +24,7 @@ struct Tuning {
     int w512 = 3;    // k_move_w512 (129..512)
     int block = 4;   // k_move_block (513..2048)
     int hub = 4;     // k_hub_insert / k_hub_score (> 2048)
+    uint32_t persist_max_vertices = 0;  // graphs up to this size (no hubs) sweep in one launch (0: off)
 };
 Tuning &tuning();
 int sm_count();  // SMs of the current device
@@ -39,6 +40,7 @@ constexpr int MAX_WAVES = 64;
 
 struct Classes {
     uint32_t *list = nullptr;
+    uint32_t *dstart = nullptr;  // device copy of start[]
     int W = 1;
     uint32_t start[NUM_CLS * MAX_WAVES + 1] = {0};
     uint64_t *pool_off = nullptr;  // huge class (all waves): hashtable slot offsets
@@ -67,6 +69,12 @@ struct MoveCounters {  // device-side accumulators of one sweep
     unsigned long long candidates;
     unsigned long long skipped;
     unsigned long long marked;  // edges of moved vertices (neighbour re-marking)
+    unsigned long long stalled; // persistent sweep: grid barriers that gave up waiting
+};
+
+// Grid-wide barrier state of the persistent sweep kernel (zero at start).
+struct GridBar {
+    unsigned arrive, gen, err, pad;
 };
 
 struct MoveBuffers {
@@ -85,6 +93,8 @@ struct MoveBuffers {
     uint32_t *mv_vtx = nullptr;  // moves decided in the current wave (frozen-state mode)
     uint32_t *mv_cmt = nullptr;
     uint32_t *mv_cnt = nullptr;
+    uint32_t *mv_cnts = nullptr; // persistent sweep: one move counter per wave
+    GridBar *bar = nullptr;      // persistent sweep: grid barrier
     uint32_t *choice = nullptr;  // optional: decision of each vertex (single-sweep API)
     uint32_t *big = nullptr;     // movers whose neighbours all blocks re-mark together
     uint32_t *nbig = nullptr;
@@ -118,11 +128,18 @@ SideStreams &side_streams();
 void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, bool sync, bool fp64, bool rule,
                bool learned, int iteration, int max_iterations, cudaStream_t s);
 void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s);
+// A whole frozen-state sweep (all waves) as one cooperative launch, for graphs
+// with no vertex above 2048 edges and at most tuning().persist_max_vertices
+// vertices.  Returns false (launching nothing) when the graph or the run does
+// not qualify.
+bool sweep_persistent(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool fp64, bool rule, int iteration,
+                      int max_iterations, cudaStream_t s);
 
 // driver.cu helpers shared with the batched driver
 void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
                     bool pruned, int it, int max_it, const uint32_t *wave_n, bool reset_ctr, cudaStream_t s);
 bool graphs_enabled();
+bool persistent_enabled();
 cudaStream_t capture_stream();
 void alloc_move_state(MoveBuffers &mb, uint32_t n);
 void alloc_pool(MoveBuffers &mb, const Classes &cl, cudaStream_t s);

@@ -71,9 +71,14 @@ template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __l
 __device__ __forceinline__ uint8_t ldcg(const uint8_t *p) {
     return (uint8_t)__ldcg(reinterpret_cast<const unsigned char *>(p));
 }
-// Frozen-state waves read data that no thread writes during the launch.
-template <bool SYNC, typename T> __device__ __forceinline__ T ld_state(const T *p) {
-    if constexpr (SYNC) return __ldg(p);
+// SYNC: 0 = in-place updates (the paper's loop), 1 = frozen-state wave in its
+// own launch, 2 = frozen-state wave inside the persistent sweep kernel.  A
+// frozen-state wave reads data that no thread writes during the wave; in its
+// own launch that data is read-only for the whole launch (read-only cache
+// path), inside the persistent kernel earlier phases of the same launch wrote
+// it, so the loads go to L2 (the per-SM L1 is not coherent).
+template <int SYNC, typename T> __device__ __forceinline__ T ld_state(const T *p) {
+    if constexpr (SYNC == 1) return __ldg(p);
     else return ldcg(p);
 }
 
@@ -85,7 +90,7 @@ template <typename V, typename WT> __device__ __forceinline__ V load_w(const WT 
 // the self-loop is skipped, K_{i->d} accumulates in kid, other communities
 // go to ins(c, w).  U edges per thread per round, their loads issued before
 // their use, so that U gathers of C[j] are in flight at once.
-template <int U, bool SYNC, typename V, typename WT, typename F>
+template <int U, int SYNC, typename V, typename WT, typename F>
 __device__ __forceinline__ void scan_edges(const uint32_t *__restrict__ tgt, const WT *__restrict__ w,
                                            const uint32_t *C, uint32_t i, uint32_t d, uint64_t b, uint64_t e,
                                            uint32_t lane, uint32_t step, V &kid, F &&ins) {
@@ -118,7 +123,7 @@ template <typename S> __device__ __forceinline__ bool better(S s1, uint32_t c1, 
 // Score the entries of a table: slots s = lane, lane + step, ... < cap (or
 // the listed slots occ[...] when occ is given).  U entries per round, with
 // the gathers of Sigma_c issued together.
-template <int U, bool SYNC, typename SC, typename S, typename V>
+template <int U, int SYNC, typename SC, typename S, typename V>
 __device__ __forceinline__ void score_table(const uint32_t *keys, const V *vals, const uint16_t *occ, uint32_t cap,
                                             uint32_t lane, uint32_t step, const double *Sig, const SC &sc, S &best,
                                             uint32_t &bestc, uint32_t &ncand) {
@@ -194,7 +199,7 @@ __device__ __forceinline__ void add_graph_gain(const MoveArgs &a, uint32_t i, do
 
 // Decide the move of i toward c (one thread).  Frozen-state: record it in the
 // move list; in place: apply it now.  Returns whether i moves.
-template <bool SYNC>
+template <int SYNC>
 __device__ __forceinline__ bool decide_move(const MoveArgs &a, uint32_t i, uint32_t d, uint32_t c, double Ki) {
     if (c == EMPTY || c == d) return false;
     if (a.rule) {
@@ -270,9 +275,9 @@ __device__ __forceinline__ void record_visit(const MoveArgs &a, uint32_t i, uint
 // Groups of G lanes, one vertex per group, table of up to CAP slots per group
 // (slots carved out of the block's shared buffer).
 // --------------------------------------------------------------------------
-template <int G, int CAP, typename WT, bool F64, bool SYNC>
+template <int G, int CAP, typename WT, bool F64, int SYNC>
 __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list, uint32_t count, uint32_t lb,
-                           uint32_t nb, unsigned char *smem) {
+                           uint32_t nb, unsigned char *smem, LocalCtr &lc) {
     using V = typename std::conditional<F64, double, float>::type;
     using SC = Score<F64>;
     using S = typename SC::S;
@@ -285,7 +290,7 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
     V *vals = reinterpret_cast<V *>(smem + (size_t)NG * CAP * sizeof(uint32_t)) + grp * CAP;
     const WT *w = static_cast<const WT *>(a.w);
     const double m0 = *a.m;
-    LocalCtr lc;
+    // counters accumulate in the caller's lc
     // The warp's list entries are wbase, wbase + wstep, ...; 32 of them are
     // claimed at once (each lane reads one flag and marks its vertex
     // processed), and the active ones are dealt to the warp's groups round
@@ -363,7 +368,7 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         __syncwarp(gmask);
         }
     }
-    flush_counters(lc, a.ctr);
+    __syncthreads();  // the block's tables are free for the next body
 }
 
 struct GroupLists {
@@ -375,43 +380,47 @@ struct GroupLists {
 constexpr size_t GROUP_SMEM_F64 = 2048 * (sizeof(uint32_t) + sizeof(double));
 constexpr size_t GROUP_SMEM_F32 = 2048 * (sizeof(uint32_t) + sizeof(float));
 
-template <typename WT, bool F64, bool SYNC>
+template <typename WT, bool F64, int SYNC>
 __global__ void __launch_bounds__(256) k_move_groups(MoveArgs a, GroupLists gl) {
     __shared__ __align__(16) unsigned char smem[F64 ? GROUP_SMEM_F64 : GROUP_SMEM_F32];
     uint32_t b = blockIdx.x;
+    LocalCtr lc;
     if (b < gl.bstart[1])
-        group_body<4, 16, WT, F64, SYNC>(a, gl.list[0], gl.count[0], b, gl.bstart[1], smem);
+        group_body<4, 16, WT, F64, SYNC>(a, gl.list[0], gl.count[0], b, gl.bstart[1], smem, lc);
     else if (b < gl.bstart[2])
         group_body<8, 32, WT, F64, SYNC>(a, gl.list[1], gl.count[1], b - gl.bstart[1], gl.bstart[2] - gl.bstart[1],
-                                         smem);
+                                         smem, lc);
     else if (b < gl.bstart[3])
         group_body<16, 64, WT, F64, SYNC>(a, gl.list[2], gl.count[2], b - gl.bstart[2],
-                                          gl.bstart[3] - gl.bstart[2], smem);
+                                          gl.bstart[3] - gl.bstart[2], smem, lc);
     else
         group_body<32, 256, WT, F64, SYNC>(a, gl.list[3], gl.count[3], b - gl.bstart[3],
-                                           gl.bstart[4] - gl.bstart[3], smem);
+                                           gl.bstart[4] - gl.bstart[3], smem, lc);
+    flush_counters(lc, a.ctr);
 }
 
 // Degrees 129..512: one warp per vertex, 1024-slot table per warp.
 constexpr int W512_CAP = 1024;
-template <typename WT, bool F64, bool SYNC>
+template <typename WT, bool F64, int SYNC>
 __global__ void __launch_bounds__(256) k_move_w512(MoveArgs a, const uint32_t *__restrict__ list, uint32_t count) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    group_body<32, W512_CAP, WT, F64, SYNC>(a, list, count, blockIdx.x, gridDim.x, dyn_smem);
+    LocalCtr lc;
+    group_body<32, W512_CAP, WT, F64, SYNC>(a, list, count, blockIdx.x, gridDim.x, dyn_smem, lc);
+    flush_counters(lc, a.ctr);
 }
 
 // --------------------------------------------------------------------------
 // One block per vertex; table in shared memory (CAP > 0) or in the global
 // pool (CAP == 0, slots at pool_off[idx]).
 // --------------------------------------------------------------------------
-template <int CAP, typename WT, bool F64, bool SYNC>
-__global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *__restrict__ list, uint32_t count) {
+template <int CAP, typename WT, bool F64, int SYNC>
+__device__ void block_body(const MoveArgs &a, const uint32_t *__restrict__ list, uint32_t count, uint32_t lb,
+                           uint32_t nb, unsigned char *dyn_smem, LocalCtr &lc) {
     using V = typename std::conditional<F64, double, float>::type;
     using SC = Score<F64>;
     using S = typename SC::S;
     // table: keys, values and the list of occupied slots (scoring and
     // clearing touch only those)
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
     uint32_t *keys = reinterpret_cast<uint32_t *>(dyn_smem);
     V *vals = reinterpret_cast<V *>(dyn_smem + (size_t)CAP * sizeof(uint32_t));
     uint16_t *occ = reinterpret_cast<uint16_t *>(dyn_smem + (size_t)CAP * (sizeof(uint32_t) + sizeof(V)));
@@ -425,14 +434,14 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
     const double m0 = *a.m;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    LocalCtr lc;
+    // counters accumulate in the caller's lc
     __shared__ uint32_t s_todo[256], s_ntodo, s_wcnt[8];
     for (uint32_t s = threadIdx.x; s < CAP; s += blockDim.x) { keys[s] = EMPTY; vals[s] = V(0); }
-    // The block's entries are blockIdx.x + k * gridDim.x; blockDim.x of them
-    // are claimed at once (one flag per thread) and the active ones listed
-    // in shared memory, so inactive vertices cost no serial round trip.
-    for (uint64_t kb = 0; blockIdx.x + kb * gridDim.x < count; kb += blockDim.x) {
-        const uint64_t my = blockIdx.x + (kb + threadIdx.x) * gridDim.x;
+    // The block's entries are lb + k * nb; blockDim.x of them are claimed at
+    // once (one flag per thread) and the active ones listed in shared memory,
+    // so inactive vertices cost no serial round trip.
+    for (uint64_t kb = 0; lb + kb * nb < count; kb += blockDim.x) {
+        const uint64_t my = lb + (kb + threadIdx.x) * nb;
         uint32_t vi = 0;
         int claim = 0;
         if (my < count) {
@@ -523,6 +532,14 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
     }
     }
     __syncthreads();
+    __syncthreads();  // the block's table is free for the next body
+}
+
+template <int CAP, typename WT, bool F64, int SYNC>
+__global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *__restrict__ list, uint32_t count) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    LocalCtr lc;
+    block_body<CAP, WT, F64, SYNC>(a, list, count, blockIdx.x, gridDim.x, dyn_smem, lc);
     flush_counters(lc, a.ctr);
 }
 
@@ -622,6 +639,135 @@ __global__ void k_mark_big(const uint64_t *__restrict__ off, const uint32_t *__r
 }
 
 // --------------------------------------------------------------------------
+// Persistent sweep: for graphs with no hub (every degree <= 2048) and at most
+// a million or so vertices, a sweep of W waves costs 4-6 launches per wave on
+// the normal path, and on small graphs those dependent launches, not the
+// work, set the time.  Here one cooperative launch runs the whole sweep: per
+// wave, every block takes its share of each degree class (the same device
+// bodies as the per-class kernels, frozen-state decisions into the wave's
+// move list), a grid barrier, the moves applied and the re-marks merged,
+// and a grid barrier.  Data written by earlier phases are read through L2
+// (SYNC mode 2).  The barrier spins a bounded number of times: a block that
+// gives up flags the sweep (MoveCounters::stalled) and the kernel returns.
+// --------------------------------------------------------------------------
+constexpr unsigned long long GRID_SYNC_SPINS = 1ull << 22;  // x 64 ns sleeps: about 0.3 s
+
+__device__ bool grid_sync(GridBar *b, unsigned nb, MoveCounters *ctr) {
+    __shared__ unsigned s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned ok = 1;
+        volatile unsigned *vgen = &b->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(&b->arrive, 1u) == nb - 1) {
+            b->arrive = 0;
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > GRID_SYNC_SPINS || *(volatile unsigned *)&b->err) {
+                    atomicExch(&b->err, 1u);
+                    atomicAdd(&ctr->stalled, 1ull);
+                    ok = 0;
+                    break;
+                }
+                if (spins > 256) __nanosleep(32);  // poll tightly first: most waits are short
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Moves of a wave applied as k_apply_moves does, reading the move list, C
+// and the count through L2; `smem` holds the block's delta table.
+__device__ void apply_body_l2(const uint32_t *mv_vtx, const uint32_t *mv_cmt, const uint32_t *mv_cnt,
+                              const double *__restrict__ K, uint32_t *C, double *Sig, uint32_t *size, uint32_t lb,
+                              uint32_t nb, unsigned char *smem) {
+    uint32_t *skeys = reinterpret_cast<uint32_t *>(smem);
+    double *sds = reinterpret_cast<double *>(smem + sizeof(uint32_t) * (1u << APPLY_SLOG));
+    int *sdn = reinterpret_cast<int *>(smem + (sizeof(uint32_t) + sizeof(double)) * (1u << APPLY_SLOG));
+    for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) { skeys[t] = EMPTY; sds[t] = 0.0; sdn[t] = 0; }
+    __syncthreads();
+    const uint32_t cnt = __ldcg(mv_cnt);
+    for (uint32_t t = lb * blockDim.x + threadIdx.x; t < cnt; t += nb * blockDim.x) {
+        const uint32_t i = __ldcg(mv_vtx + t), c = __ldcg(mv_cmt + t);
+        const uint32_t d = __ldcg(C + i);
+        const double Ki = K[i];
+        C[i] = c;
+        apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size);
+        apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) {
+        const uint32_t c = skeys[t];
+        if (c == EMPTY) continue;
+        if (sds[t] != 0.0) atomicAdd(Sig + c, sds[t]);
+        if (sdn[t] != 0) atomicAdd(size + c, (uint32_t)sdn[t]);
+    }
+    __syncthreads();
+}
+
+__device__ void merge_body_l2(uint8_t *act, uint8_t *mark, uint32_t n, uint32_t lb, uint32_t nb) {
+    const uint32_t n16 = n / 16;
+    uint4 *a4 = reinterpret_cast<uint4 *>(act);
+    uint4 *m4 = reinterpret_cast<uint4 *>(mark);
+    for (uint32_t t = lb * blockDim.x + threadIdx.x; t < n16; t += nb * blockDim.x) {
+        const uint4 mk = __ldcg(m4 + t);
+        if (mk.x | mk.y | mk.z | mk.w) {
+            uint4 ac = __ldcg(a4 + t);
+            ac.x |= mk.x; ac.y |= mk.y; ac.z |= mk.z; ac.w |= mk.w;
+            a4[t] = ac;
+            m4[t] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    for (uint32_t v = n16 * 16 + lb * blockDim.x + threadIdx.x; v < n; v += nb * blockDim.x) {
+        if (ldcg(mark + v)) { act[v] = 1; mark[v] = 0; }
+    }
+}
+
+template <typename WT, bool F64>
+__global__ void __launch_bounds__(256) k_sweep_persistent(MoveArgs a, const uint32_t *__restrict__ list,
+                                                          const uint32_t *__restrict__ start, int W, uint32_t n,
+                                                          uint32_t *mv_cnts, GridBar *bar) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const uint32_t lb = blockIdx.x, nb = gridDim.x;
+    LocalCtr lc;  // one flush per block per sweep
+    if (lb == 0)
+        for (int t = threadIdx.x; t < W; t += blockDim.x) mv_cnts[t] = 0;
+    if (!grid_sync(bar, nb, a.ctr)) return;
+    for (int wv = 0; wv < W; wv++) {
+        uint32_t cb[CLS_HUGE], cc[CLS_HUGE], tot = 0;
+#pragma unroll
+        for (int k = 0; k < CLS_HUGE; k++) {
+            cb[k] = start[k * W + wv];
+            cc[k] = start[k * W + wv + 1] - cb[k];
+            tot += cc[k];
+        }
+        if (!tot) continue;  // the same for every block
+        MoveArgs aw = a;
+        aw.mv_cnt = mv_cnts + wv;
+        if (cc[CLS_G4]) group_body<4, 16, WT, F64, 2>(aw, list + cb[CLS_G4], cc[CLS_G4], lb, nb, dyn_smem, lc);
+        if (cc[CLS_G8]) group_body<8, 32, WT, F64, 2>(aw, list + cb[CLS_G8], cc[CLS_G8], lb, nb, dyn_smem, lc);
+        if (cc[CLS_G16]) group_body<16, 64, WT, F64, 2>(aw, list + cb[CLS_G16], cc[CLS_G16], lb, nb, dyn_smem, lc);
+        if (cc[CLS_G32]) group_body<32, 256, WT, F64, 2>(aw, list + cb[CLS_G32], cc[CLS_G32], lb, nb, dyn_smem, lc);
+        if (cc[CLS_W512])
+            group_body<32, W512_CAP, WT, F64, 2>(aw, list + cb[CLS_W512], cc[CLS_W512], lb, nb, dyn_smem, lc);
+        if (cc[CLS_BLOCK])
+            block_body<4096, WT, F64, 2>(aw, list + cb[CLS_BLOCK], cc[CLS_BLOCK], lb, nb, dyn_smem, lc);
+        if (!grid_sync(bar, nb, a.ctr)) return;
+        apply_body_l2(a.mv_vtx, a.mv_cmt, mv_cnts + wv, a.K, a.C, a.Sig, a.size, lb, nb, dyn_smem);
+        merge_body_l2(a.act, a.mark, n, lb, nb);
+        if (!grid_sync(bar, nb, a.ctr)) return;
+    }
+    flush_counters(lc, a.ctr);
+}
+
+// --------------------------------------------------------------------------
 // Hub vertices (degree > 2048), processed by the whole grid:
 //   prepare: read and clear each hub's flag, snapshot its community;
 //   insert:  the hub's edges are cut into HUB_CHUNK-edge tasks; a block
@@ -652,7 +798,7 @@ struct HubArgs {
     uint32_t *big, *nbig;
 };
 
-template <bool SYNC>
+template <int SYNC>
 __global__ void k_hub_prepare(MoveArgs a, HubArgs h) {
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < h.nh; t += gridDim.x * blockDim.x) {
         uint32_t i = h.hubs[t];
@@ -663,7 +809,7 @@ __global__ void k_hub_prepare(MoveArgs a, HubArgs h) {
     }
 }
 
-template <typename WT, bool F64, bool SYNC>
+template <typename WT, bool F64, int SYNC>
 __global__ void __launch_bounds__(256) k_hub_insert(MoveArgs a, HubArgs h) {
     using V = typename std::conditional<F64, double, float>::type;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -699,7 +845,7 @@ __global__ void __launch_bounds__(256) k_hub_insert(MoveArgs a, HubArgs h) {
 // Scoring uses the insert's task split: task k of a hub scores occupied
 // entries [k*HUB_CHUNK, (k+1)*HUB_CHUNK) (a hub has at most one distinct
 // community per edge) and leaves its best in best[task].
-template <typename WT, bool F64, bool SYNC>
+template <typename WT, bool F64, int SYNC>
 __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
     using V = typename std::conditional<F64, double, float>::type;
     using SC = Score<F64>;
@@ -767,7 +913,7 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
     }
 }
 
-template <bool F64, bool SYNC>
+template <bool F64, int SYNC>
 __global__ void k_hub_decide(MoveArgs a, HubArgs h) {
     using V = typename std::conditional<F64, double, float>::type;
     using SC = Score<F64>;
@@ -910,6 +1056,8 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
     cl.list = arena().get<uint32_t>(cl.start[NK] + 1);
     k_classify_fill<<<grid, 256, 0, s>>>(g.off, g.n, W, cursor, cl.list, gid, gvo);
     GSP_CHECK_LAUNCH();
+    cl.dstart = arena().get<uint32_t>(NK + 1);
+    GSP_CUDA(cudaMemcpyAsync(cl.dstart, cl.start, sizeof(uint32_t) * (NK + 1), cudaMemcpyHostToDevice, s));
     uint32_t nh = cl.cls_count(CLS_HUGE);
     cl.pool_off = arena().get<uint64_t>(nh + 1);
     cl.pool_slots = 0;
@@ -963,7 +1111,7 @@ SideStreams &side_streams() {
 // move list, so they run as parallel branches: W512 and the block class on
 // side streams 0 and 1, the hub chain on side stream 2, the group classes on
 // the main stream; all join before the wave's moves are applied.
-template <typename WT, bool F64, bool SYNC>
+template <typename WT, bool F64, int SYNC>
 static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t *pool_keys, void *pool_vals,
                         uint32_t *pool_occ, uint32_t *big, uint32_t *nbig, cudaStream_t main) {
     using V = typename std::conditional<F64, double, float>::type;
@@ -1078,9 +1226,8 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
     }
 }
 
-void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, bool sync, bool fp64, bool rule,
-               bool learned, int iteration, int max_iterations, cudaStream_t s) {
-    (void)learned;
+static MoveArgs make_move_args(const DevGraph &g, const MoveBuffers &mb, bool sync, bool rule, int iteration,
+                               int max_iterations) {
     MoveArgs a;
     a.off = g.off;
     a.tgt = g.tgt;
@@ -1112,6 +1259,57 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
     a.max_logk = mb.max_logk;
     a.iter_frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
     a.salt = (uint32_t)(iteration * 0x9E3779B9u + mb.trace_salt);
+    return a;
+}
+
+template <typename WT, bool F64>
+static bool launch_persistent(const MoveArgs &a, const Classes &cl, uint32_t n, MoveBuffers &mb, cudaStream_t s) {
+    using V = typename std::conditional<F64, double, float>::type;
+    constexpr size_t smem = std::max(std::max((size_t)8 * W512_CAP * (sizeof(uint32_t) + sizeof(V)),
+                                              (size_t)4096 * (sizeof(uint32_t) + sizeof(V) + sizeof(uint16_t))),
+                                     (size_t)(sizeof(uint32_t) + sizeof(double) + sizeof(int)) << APPLY_SLOG);
+    static int per_sm[64] = {0};  // resident blocks per SM, per device (-1: cannot run)
+    int dev = 0;
+    GSP_CUDA(cudaGetDevice(&dev));
+    dev &= 63;
+    if (!per_sm[dev]) {
+        GSP_CUDA(cudaFuncSetAttribute(k_sweep_persistent<WT, F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        int coop = 0, nblk = 0;
+        GSP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        GSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_sweep_persistent<WT, F64>, 256, smem));
+        per_sm[dev] = (coop && nblk > 0) ? nblk : -1;
+    }
+    if (per_sm[dev] < 0) return false;
+    MoveArgs aa = a;
+    const uint32_t *list = cl.list;
+    const uint32_t *start = cl.dstart;
+    int W = cl.W;
+    uint32_t nn = n;
+    uint32_t *cnts = mb.mv_cnts;
+    GridBar *bar = mb.bar;
+    void *args[] = {&aa, &list, &start, &W, &nn, &cnts, &bar};
+    GSP_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), s));
+    GSP_CUDA(cudaLaunchCooperativeKernel((const void *)k_sweep_persistent<WT, F64>, dim3(per_sm[dev] * sm_count()),
+                                         dim3(256), args, smem, s));
+    count_launch();
+    return true;
+}
+
+bool sweep_persistent(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool fp64, bool rule, int iteration,
+                      int max_iterations, cudaStream_t s) {
+    if (cl.cls_count(CLS_HUGE) || mb.feat_kept || mb.choice || !cl.dstart || !mb.bar) return false;
+    if (g.n > tuning().persist_max_vertices) return false;
+    MoveArgs a = make_move_args(g, mb, true, rule, iteration, max_iterations);
+    if (g.wt == GSP_W_F32) return fp64 ? launch_persistent<float, true>(a, cl, g.n, mb, s)
+                                       : launch_persistent<float, false>(a, cl, g.n, mb, s);
+    return fp64 ? launch_persistent<double, true>(a, cl, g.n, mb, s) : launch_persistent<double, false>(a, cl, g.n, mb, s);
+}
+
+void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, bool sync, bool fp64, bool rule,
+               bool learned, int iteration, int max_iterations, cudaStream_t s) {
+    (void)learned;
+    MoveArgs a = make_move_args(g, mb, sync, rule, iteration, max_iterations);
     // pool layout: keys (u32), values (8 bytes per slot), occupied-slot list (u32)
     uint32_t *pool_keys = static_cast<uint32_t *>(mb.pool);
     const size_t sa = align_up(cl.pool_slots, 64);

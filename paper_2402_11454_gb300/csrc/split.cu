@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ o
         }
         const unsigned amask = __ballot_sync(0xFFFFFFFFu, claim);
         const int nact = __popc(amask);
+        // a consumed flag was set after its setter's label store: order the
+        // label reads below after the flag reads
+        if (PRUNE && nact) __threadfence();
         for (int r0 = 0; r0 < nact; r0 += NGW) {
         const int qa = r0 + gw;
         const uint32_t i = __shfl_sync(0xFFFFFFFFu, vi, qa < nact ? select_bit(amask, qa) : 0);
@@ -83,6 +86,12 @@ __global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ o
                     lab[i] = mn;
                 }
                 ch++;
+            }
+            if (PRUNE) {
+                // the new label must be visible before any neighbour sees its
+                // flag (a neighbour that consumes the flag re-reads it once)
+                __syncwarp(gmask);
+                __threadfence();
             }
             if (PRUNE)
                 for (uint64_t p = b + lane; p < e; p += G) {
@@ -138,6 +147,7 @@ __global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ o
         }
         __syncthreads();
         const uint32_t ntodo = s_ntodo;
+        if (PRUNE && ntodo) __threadfence();  // flags consumed before the labels are read
     for (uint32_t kk = 0; kk < ntodo; kk++) {
         const uint32_t i = s_todo[kk];
         __syncthreads();  // previous vertex done with red
@@ -164,6 +174,10 @@ __global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ o
                     lab[i] = mn;
                 }
                 ch++;
+            }
+            if (PRUNE) {  // the new label visible before the neighbours' flags
+                __syncthreads();
+                __threadfence();
             }
             if (PRUNE)
                 for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {

@@ -52,6 +52,7 @@ static gsp_tuning to_abi(const Tuning &t) {
     o.w512_blocks_per_sm = t.w512;
     o.block_blocks_per_sm = t.block;
     o.hub_blocks_per_sm = t.hub;
+    o.persist_max_vertices = t.persist_max_vertices;
     return o;
 }
 
@@ -61,6 +62,7 @@ static Tuning from_abi(const gsp_tuning &t) {
     o.w512 = t.w512_blocks_per_sm;
     o.block = t.block_blocks_per_sm;
     o.hub = t.hub_blocks_per_sm;
+    o.persist_max_vertices = t.persist_max_vertices;
     return o;
 }
 

@@ -259,7 +259,8 @@ def count_disconnected(offsets, targets, C, stream=None):
     return c.value, flags
 
 
-_TUNING_FIELDS = ("groups_blocks_per_sm", "w512_blocks_per_sm", "block_blocks_per_sm", "hub_blocks_per_sm")
+_TUNING_FIELDS = ("groups_blocks_per_sm", "w512_blocks_per_sm", "block_blocks_per_sm", "hub_blocks_per_sm",
+                  "persist_max_vertices")
 
 
 def get_tuning():

@@ -74,12 +74,14 @@ def test_tuning_roundtrip_and_validation(lib):
     t = GspTuning()
     assert lib.gsp_get_tuning(ctypes.byref(t)) == 0
     assert (t.groups_blocks_per_sm, t.w512_blocks_per_sm, t.block_blocks_per_sm, t.hub_blocks_per_sm) == (8, 3, 4, 4)
-    new = GspTuning(6, 2, 5, 8)
+    assert t.persist_max_vertices == 0
+    new = GspTuning(6, 2, 5, 8, 0)
     assert lib.gsp_set_tuning(ctypes.byref(new)) == 0
     got = GspTuning()
     lib.gsp_get_tuning(ctypes.byref(got))
-    assert (got.groups_blocks_per_sm, got.w512_blocks_per_sm, got.block_blocks_per_sm, got.hub_blocks_per_sm) == (6, 2, 5, 8)
-    for bad in (GspTuning(0, 3, 4, 4), GspTuning(8, 33, 4, 4), GspTuning(8, 3, -1, 4)):
+    assert (got.groups_blocks_per_sm, got.w512_blocks_per_sm, got.block_blocks_per_sm, got.hub_blocks_per_sm,
+            got.persist_max_vertices) == (6, 2, 5, 8, 0)
+    for bad in (GspTuning(0, 3, 4, 4, 0), GspTuning(8, 33, 4, 4, 0), GspTuning(8, 3, -1, 4, 0)):
         assert lib.gsp_set_tuning(ctypes.byref(bad)) == -1
     assert lib.gsp_get_tuning(None) == -1
     assert lib.gsp_set_tuning(ctypes.byref(t)) == 0  # restore the defaults

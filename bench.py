@@ -142,7 +142,7 @@ def make_workload(gsp, graphgen, name):
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of all
 # local-moving launches of one R-MAT 20 step divided by that step's algorithmic
 # bytes (profiles/dram_local_moving_rmat20.md); scaled to the bench workload.
-MOVE_TRAFFIC_RATIO = 2.158
+MOVE_TRAFFIC_RATIO = 2.160
 
 
 def roofline_from(stats_list, peak_gbs, peak_kind):

@@ -100,7 +100,7 @@ static void classify_ids(const uint64_t *sz, uint32_t k, const uint64_t (&maxes)
     uint32_t *counts = arena().get<uint32_t>(2 * NC);
     GSP_CUDA(cudaMemcpyAsync(dmax, maxes, sizeof(uint64_t) * NC, cudaMemcpyHostToDevice, s));
     GSP_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * NC, s));
-    unsigned gr = grid_for(k, 256, 152 * 8);
+    unsigned gr = grid_for(k, 256, sms(8));
     k_cls_count<NC><<<gr, 256, 0, s>>>(sz, k, dmax, counts);
     GSP_CHECK_LAUNCH();
     uint32_t h[NC];
@@ -366,7 +366,6 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
 // walks.
 constexpr uint32_t AGG_CHUNK = 2048;
 constexpr int AGG_SLOG = 12;  // shared table of 2 * AGG_CHUNK slots
-constexpr int AGG_COOP_BLOCKS = 152 * 4;
 
 __global__ void k_member_deg(const uint64_t *__restrict__ off, const uint32_t *__restrict__ cverts, uint32_t n,
                              uint64_t *mdeg) {
@@ -712,7 +711,7 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
                                           (int)smem));
             wattr = true;
         }
-        k_agg_merge_warp<WT><<<grid_for((uint64_t)cnt_of(ACLS_W) * 32, AGG_WWARPS * 32, 152 * 4), AGG_WWARPS * 32,
+        k_agg_merge_warp<WT><<<grid_for((uint64_t)cnt_of(ACLS_W) * 32, AGG_WWARPS * 32, sms(4)), AGG_WWARPS * 32,
                                smem, s>>>(a, ic.list + ic.start[ACLS_W], cnt_of(ACLS_W));
         GSP_CHECK_LAUNCH();
     }
@@ -725,7 +724,7 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
                                           (int)smem));
             attr = true;
         }
-        k_agg_merge_block<WT><<<grid_for(cnt_of(ACLS_B), 1, 152 * 4), 256, smem, s>>>(a, ic.list + ic.start[ACLS_B],
+        k_agg_merge_block<WT><<<grid_for(cnt_of(ACLS_B), 1, sms(4)), 256, smem, s>>>(a, ic.list + ic.start[ACLS_B],
                                                                                      cnt_of(ACLS_B));
         GSP_CHECK_LAUNCH();
     }
@@ -764,9 +763,9 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
                                           (int)lsmem));
             lattr = true;
         }
-        k_agg_large_insert<WT><<<AGG_COOP_BLOCKS, 256, lsmem, s>>>(a, llist, nl, tasks, medge, poff, pk, pv, po, on);
+        k_agg_large_insert<WT><<<sms(4), 256, lsmem, s>>>(a, llist, nl, tasks, medge, poff, pk, pv, po, on);
         GSP_CHECK_LAUNCH();
-        k_agg_large_extract<<<AGG_COOP_BLOCKS, 256, 0, s>>>(a, llist, nl, tasks, poff, pk, pv, po, on);
+        k_agg_large_extract<<<sms(4), 256, 0, s>>>(a, llist, nl, tasks, poff, pk, pv, po, on);
         GSP_CHECK_LAUNCH();
     }
 
@@ -784,12 +783,12 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
     if (!sorted) {
         const uint32_t nshort = rcnt(RCLS_W) + rcnt(RCLS_B);  // classes W and B are adjacent in the list
         if (nshort) {
-            k_compact_rows_warp<<<grid_for((uint64_t)nshort * 32, 256, 152 * 16), 256, 0, s>>>(
+            k_compact_rows_warp<<<grid_for((uint64_t)nshort * 32, 256, sms(16)), 256, 0, s>>>(
                 rc.list + rc.start[RCLS_W], nshort, yoff, htgt, hw, out_off, out_tgt, out_w);
             GSP_CHECK_LAUNCH();
         }
         if (rcnt(RCLS_L)) {
-            k_compact_rows_block<<<grid_for(rcnt(RCLS_L), 1, 152 * 4), 256, 0, s>>>(
+            k_compact_rows_block<<<grid_for(rcnt(RCLS_L), 1, sms(4)), 256, 0, s>>>(
                 rc.list + rc.start[RCLS_L], rcnt(RCLS_L), yoff, htgt, hw, out_off, out_tgt, out_w);
             GSP_CHECK_LAUNCH();
         }
@@ -797,12 +796,12 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
         return nnz2;
     }
     if (rcnt(RCLS_W)) {
-        k_sort_rows_warp<<<grid_for((uint64_t)rcnt(RCLS_W) * 32, 256, 152 * 16), 256, 0, s>>>(
+        k_sort_rows_warp<<<grid_for((uint64_t)rcnt(RCLS_W) * 32, 256, sms(16)), 256, 0, s>>>(
             rc.list + rc.start[RCLS_W], rcnt(RCLS_W), yoff, htgt, hw, out_off, out_tgt, out_w);
         GSP_CHECK_LAUNCH();
     }
     if (rcnt(RCLS_B)) {
-        k_sort_rows_block<<<grid_for(rcnt(RCLS_B), 1, 152 * 4), 256, 0, s>>>(
+        k_sort_rows_block<<<grid_for(rcnt(RCLS_B), 1, sms(4)), 256, 0, s>>>(
             rc.list + rc.start[RCLS_B], rcnt(RCLS_B), yoff, htgt, hw, out_off, out_tgt, out_w);
         GSP_CHECK_LAUNCH();
     }
@@ -827,7 +826,7 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
         uint32_t *pos = arena().get<uint32_t>(total);
         uint32_t *pos2 = arena().get<uint32_t>(total);
         double *wtmp = arena().get<double>(total);
-        k_stage_long<<<grid_for(nlong, 1, 152 * 4), 256, 0, s>>>(llist, nlong, yoff, htgt, hw, out_off, gpre, kbits,
+        k_stage_long<<<grid_for(nlong, 1, sms(4)), 256, 0, s>>>(llist, nlong, yoff, htgt, hw, out_off, gpre, kbits,
                                                                   keys, pos, wtmp);
         GSP_CHECK_LAUNCH();
         radix_sort_u64_u32(keys, pos, keys2, pos2, total, bits, s);

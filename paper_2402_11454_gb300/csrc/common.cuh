@@ -9,7 +9,6 @@
 namespace gsp {
 
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
-constexpr int NUM_SMS_HINT = 152;
 
 // ---------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);
@@ -58,7 +57,11 @@ Arena &arena();
 Arena &io_arena();  // host-buffer entry points stage their device copies here
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 152u * 16u) {
+int sm_count();  // SMs of the current device (cached per device)
+// Grid caps are given in blocks per SM: sms(k) = k blocks on every SM.
+inline unsigned sms(unsigned per_sm) { return per_sm * (unsigned)sm_count(); }
+inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 0) {
+    if (!cap) cap = sms(16);
     uint64_t g = (work + block - 1) / block;
     if (g < 1) g = 1;
     if (g > cap) g = cap;

@@ -190,7 +190,7 @@ static void build_csr(uint64_t *keys, float *vals, uint64_t nkeys, uint32_t n, i
     uint8_t *head = reinterpret_cast<uint8_t *>(k2);  // k2 is free after the sort
     float *minw = v2;
     uint32_t *pos = arena().get<uint32_t>(nkeys + 1);
-    unsigned gr = grid_for(nkeys, 256, 152 * 32);
+    unsigned gr = grid_for(nkeys, 256, sms(32));
     k_dedup_heads<<<gr, 256, 0, s>>>(keys, vals, nkeys, head, minw);
     GSP_CHECK_LAUNCH();
     exclusive_scan_u8_to_u32(head, pos, nkeys, s);
@@ -244,7 +244,7 @@ gsp_status gsp_gen_rmat(uint32_t scale, uint32_t edge_factor, uint64_t t1, uint6
     int b = bits_for(n);
     uint64_t *keys = arena().get<uint64_t>(2 * S);
     float *vals = arena().get<float>(2 * S);
-    k_gen_rmat<<<grid_for(S, 256, 152 * 32), 256, 0, s>>>(S, scale, stream_key(seed, STREAM_RMAT), t1, t2, t3, b,
+    k_gen_rmat<<<grid_for(S, 256, sms(32)), 256, 0, s>>>(S, scale, stream_key(seed, STREAM_RMAT), t1, t2, t3, b,
                                                          keys, vals);
     GSP_CHECK_LAUNCH();
     build_csr(keys, vals, 2 * S, n, b, out, s);
@@ -281,7 +281,7 @@ gsp_status gsp_gen_planted_batch(uint32_t num_graphs, const uint64_t *n_g, const
     uint64_t *keys = arena().get<uint64_t>(2 * S + 2);
     float *vals = arena().get<float>(2 * S + 2);
     if (S) {
-        k_gen_planted<<<grid_for(S, 256, 152 * 32), 256, 0, s>>>(P, S, b, keys, vals);
+        k_gen_planted<<<grid_for(S, 256, sms(32)), 256, 0, s>>>(P, S, b, keys, vals);
         GSP_CHECK_LAUNCH();
     }
     build_csr(keys, vals, 2 * S, (uint32_t)nv, b, out, s);
@@ -301,7 +301,7 @@ gsp_status gsp_gen_grid(uint32_t R, uint32_t Cc, uint64_t remove53, uint64_t n_l
     int b = bits_for(n);
     uint64_t *keys = arena().get<uint64_t>(2 * S);
     float *vals = arena().get<float>(2 * S);
-    k_gen_grid<<<grid_for(S, 256, 152 * 32), 256, 0, s>>>(R, Cc, remove53, n_long, (double)wlo, (double)whi, seed, b,
+    k_gen_grid<<<grid_for(S, 256, sms(32)), 256, 0, s>>>(R, Cc, remove53, n_long, (double)wlo, (double)whi, seed, b,
                                                          keys, vals);
     GSP_CHECK_LAUNCH();
     build_csr(keys, vals, 2 * S, n, b, out, s);

@@ -27,7 +27,6 @@ struct Tuning {
     uint32_t persist_max_vertices = 0;  // graphs up to this size (no hubs) sweep in one launch (0: off)
 };
 Tuning &tuning();
-int sm_count();  // SMs of the current device
 
 // Degree classes of a vertex list.  Small degrees are served by groups of G
 // lanes with a shared-memory table, mid degrees by one block with a

@@ -176,7 +176,7 @@ static void row_sums(const DevGraph &g, const uint32_t *C, double *K, double *Si
     const WT *w = static_cast<const WT *>(g.w);
     k_row_sums<WT><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, K, Sig, acc, longlist, nlong);
     GSP_CHECK_LAUNCH();
-    k_row_sums_long<WT><<<152 * 4, 256, 0, s>>>(g.off, g.tgt, w, C, K, Sig, acc, longlist, nlong);
+    k_row_sums_long<WT><<<sms(4), 256, 0, s>>>(g.off, g.tgt, w, C, K, Sig, acc, longlist, nlong);
     GSP_CHECK_LAUNCH();
     arena().release(mk);
 }
@@ -247,7 +247,7 @@ static double modularity_scratch_t(const DevGraph &g, const uint32_t *C, double 
     GSP_CUDA(cudaMemsetAsync(nlong, 0, sizeof(uint32_t), s));
     k_row_sums<WT><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, nullptr, Sig, acc, longlist, nlong);
     GSP_CHECK_LAUNCH();
-    k_row_sums_long<WT><<<152 * 4, 256, 0, s>>>(g.off, g.tgt, w, C, nullptr, Sig, acc, longlist, nlong);
+    k_row_sums_long<WT><<<sms(4), 256, 0, s>>>(g.off, g.tgt, w, C, nullptr, Sig, acc, longlist, nlong);
     GSP_CHECK_LAUNCH();
     k_sum_sq<<<grid_for(g.n, 256), 256, 0, s>>>(Sig, g.n, acc + 2);
     GSP_CHECK_LAUNCH();

@@ -190,7 +190,7 @@ __global__ void k_mlp_prune(const float *__restrict__ params, const uint64_t *__
 void mlp_prune(const DevGraph &g, MoveBuffers &mb, int iteration, int max_iterations, float threshold,
                cudaStream_t s) {
     float frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
-    k_mlp_prune<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(mb.mlp, g.off, mb.K, mb.feat_kept, mb.feat_gain,
+    k_mlp_prune<<<grid_for(g.n, 256, sms(8)), 256, 0, s>>>(mb.mlp, g.off, mb.K, mb.feat_kept, mb.feat_gain,
                                                             mb.moved_last, mb.act, mb.skip, g.n, mb.max_logk,
                                                             frac, threshold, mb.ctr);
     GSP_CHECK_LAUNCH();
@@ -249,7 +249,7 @@ gsp_status gsp_mlp_backward(const float *params, const float *x, const uint8_t *
     double *loss = arena().get<double>(1);
     GSP_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * MLP_PARAMS, s));
     GSP_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s));
-    k_mlp_backward<<<grid_for(rows, MLP_BWD_THREADS, 152 * 4), MLP_BWD_THREADS, 0, s>>>(params, x, y, rows, grad,
+    k_mlp_backward<<<grid_for(rows, MLP_BWD_THREADS, sms(4)), MLP_BWD_THREADS, 0, s>>>(params, x, y, rows, grad,
                                                                                         loss);
     GSP_CHECK_LAUNCH();
     double h;

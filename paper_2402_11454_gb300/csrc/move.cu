@@ -1043,7 +1043,7 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
     cl.W = W;
     uint32_t *counts = arena().get<uint32_t>(2 * NK);
     GSP_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * NK, s));
-    unsigned grid = grid_for(g.n, 256, 152 * 8);
+    unsigned grid = grid_for(g.n, 256, sms(8));
     k_classify_count<<<grid, 256, 0, s>>>(g.off, g.n, W, counts, gid, gvo);
     GSP_CHECK_LAUNCH();
     uint32_t h[NUM_CLS * MAX_WAVES];
@@ -1327,16 +1327,16 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
     }
 #undef GSP_WAVE
     if (cl.count(CLS_HUGE, wave)) {  // hub movers re-mark their neighbours
-        k_mark_big<<<dim3(152, 16), 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, a.mark);
+        k_mark_big<<<dim3(sm_count(), 16), 256, 0, s>>>(g.off, g.tgt, mb.big, mb.nbig, a.mark);
         GSP_CHECK_LAUNCH();
     }
 }
 
 void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s) {
-    k_apply_moves<<<grid_for(n_hint, 256, 152 * 4), 256, 0, s>>>(mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C,
+    k_apply_moves<<<grid_for(n_hint, 256, sms(4)), 256, 0, s>>>(mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C,
                                                                  mb.Sigma, mb.size);
     GSP_CHECK_LAUNCH();
-    k_merge_marks<<<grid_for(g.n / 16 + 1, 256, 152 * 8), 256, 0, s>>>(mb.act, mb.mark, g.n);
+    k_merge_marks<<<grid_for(g.n / 16 + 1, 256, sms(8)), 256, 0, s>>>(mb.act, mb.mark, g.n);
     GSP_CHECK_LAUNCH();
 }
 

@@ -28,6 +28,29 @@ __device__ __forceinline__ uint8_t ldcg_(const uint8_t *p) {
     return (uint8_t)__ldcg(reinterpret_cast<const unsigned char *>(p));
 }
 
+// min over the same-community neighbours' labels of the edges b + first,
+// b + first + step, ... < e; four gathers of C and lab in flight per thread.
+__device__ __forceinline__ uint32_t min_label(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ C,
+                                              const uint32_t *lab, uint32_t ci, uint64_t b, uint64_t e,
+                                              uint32_t first, uint32_t step, uint32_t mn) {
+    uint64_t p = b + first;
+    for (; p + 3 * (uint64_t)step < e; p += 4 * (uint64_t)step) {
+        uint32_t j[4], cj[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) j[u] = tgt[p + (uint64_t)u * step];
+#pragma unroll
+        for (int u = 0; u < 4; u++) cj[u] = C[j[u]];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (cj[u] == ci) mn = min(mn, ldcg_(lab + j[u]));
+    }
+    for (; p < e; p += step) {
+        const uint32_t j = tgt[p];
+        if (C[j] == ci) mn = min(mn, ldcg_(lab + j));
+    }
+    return mn;
+}
+
 // ----------------------------------------------------------------- LP / LPP
 // HOOK (the hooking split): besides lowering its own label, a vertex whose
 // smallest neighbouring label mn is below its label p hooks p's tree under
@@ -71,10 +94,7 @@ __global__ void __launch_bounds__(256) k_lp_group(const uint64_t *__restrict__ o
         uint32_t cur = ldcg_(lab + i);
         uint32_t mn = cur;
         uint64_t b = off[i], e = off[i + 1];
-        for (uint64_t p = b + lane; p < e; p += G) {
-            uint32_t j = tgt[p];
-            if (C[j] == ci) mn = min(mn, ldcg_(lab + j));
-        }
+        mn = min_label(tgt, C, lab, ci, b, e, lane, G, mn);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(gmask, mn, o));
         if (mn < cur) {
@@ -155,10 +175,7 @@ __global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ o
         uint32_t cur = ldcg_(lab + i);
         uint32_t mn = cur;
         uint64_t b = off[i], e = off[i + 1];
-        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
-            uint32_t j = tgt[p];
-            if (C[j] == ci) mn = min(mn, ldcg_(lab + j));
-        }
+        mn = min_label(tgt, C, lab, ci, b, e, threadIdx.x, blockDim.x, mn);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
@@ -203,7 +220,7 @@ static void split_lp(const DevGraph &g, const Classes &cl, const uint32_t *C, bo
     // every class with all its waves (class c spans [cls_begin(c), cls_begin(c+1)))
     auto cnt = [&](int c) { return cl.cls_count(c); };
     auto lst = [&](int c) { return cl.list + cl.cls_begin(c); };
-    const unsigned maxg = 152 * 8;
+    const unsigned maxg = sms(8);
     uint32_t nbig = cl.cls_count(CLS_BLOCK) + cl.cls_count(CLS_HUGE);
     for (int it = 0; it < (1 << 30); it++) {
         GSP_CUDA(cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s));
@@ -221,10 +238,10 @@ static void split_lp(const DevGraph &g, const Classes &cl, const uint32_t *C, bo
 #undef LPG
         if (nbig) {
             if (prune)
-                k_lp_block<true><<<grid_for(nbig, 1, 152 * 4), 256, 0, s>>>(g.off, g.tgt, C, lab, flag,
+                k_lp_block<true><<<grid_for(nbig, 1, sms(4)), 256, 0, s>>>(g.off, g.tgt, C, lab, flag,
                                                                               lst(CLS_BLOCK), nbig, changed);
             else
-                k_lp_block<false><<<grid_for(nbig, 1, 152 * 4), 256, 0, s>>>(g.off, g.tgt, C, lab, flag,
+                k_lp_block<false><<<grid_for(nbig, 1, sms(4)), 256, 0, s>>>(g.off, g.tgt, C, lab, flag,
                                                                                lst(CLS_BLOCK), nbig, changed);
             GSP_CHECK_LAUNCH();
         }
@@ -261,7 +278,7 @@ static void split_sv(const DevGraph &g, const Classes &cl, const uint32_t *C, ui
     iota_u32(lab, g.n, s);
     auto cnt = [&](int c) { return cl.cls_count(c); };
     auto lst = [&](int c) { return cl.list + cl.cls_begin(c); };
-    const unsigned maxg = 152 * 8;
+    const unsigned maxg = sms(8);
     const uint32_t nbig = cl.cls_count(CLS_BLOCK) + cl.cls_count(CLS_HUGE);
     for (int it = 0; it < (1 << 30); it++) {
         GSP_CUDA(cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s));
@@ -274,7 +291,7 @@ static void split_sv(const DevGraph &g, const Classes &cl, const uint32_t *C, ui
         SVG(4, CLS_G4) SVG(8, CLS_G8) SVG(16, CLS_G16) SVG(32, CLS_G32) SVG(32, CLS_W512)
 #undef SVG
         if (nbig) {
-            k_lp_block<false, true><<<grid_for(nbig, 1, 152 * 4), 256, 0, s>>>(g.off, g.tgt, C, lab, nullptr,
+            k_lp_block<false, true><<<grid_for(nbig, 1, sms(4)), 256, 0, s>>>(g.off, g.tgt, C, lab, nullptr,
                                                                                lst(CLS_BLOCK), nbig, changed);
             GSP_CHECK_LAUNCH();
         }
@@ -348,7 +365,6 @@ __global__ void k_bfs_seed_reset(const uint32_t *__restrict__ C, const uint32_t 
 }
 
 constexpr uint32_t BFS_BIG = 1024;
-constexpr int BFS_COOP_BLOCKS = 152 * 4;
 
 __device__ __forceinline__ void bfs_visit_edges(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ C,
                                                 uint32_t *lab, uint64_t p0, uint64_t e, uint64_t step, uint32_t cu,
@@ -451,10 +467,10 @@ static void split_bfs(const DevGraph &g, const uint32_t *C, uint32_t *lab, cudaS
         GSP_CUDA(cudaMemcpyAsync(fcnt, qn, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
         for (;;) {
             for (int k = 0; k < BFS_LEVEL_BATCH; k++) {
-                k_bfs_expand<<<152 * 8, 256, 0, s>>>(g.off, g.tgt, C, lab, q, fcnt + k, nq, fcnt + k + 1, big,
+                k_bfs_expand<<<sms(8), 256, 0, s>>>(g.off, g.tgt, C, lab, q, fcnt + k, nq, fcnt + k + 1, big,
                                                     bcnt + k);
                 GSP_CHECK_LAUNCH();
-                k_bfs_expand_big<<<BFS_COOP_BLOCKS, 256, 0, s>>>(g.off, g.tgt, C, lab, big, bcnt + k, nq,
+                k_bfs_expand_big<<<sms(4), 256, 0, s>>>(g.off, g.tgt, C, lab, big, bcnt + k, nq,
                                                                  fcnt + k + 1);
                 GSP_CHECK_LAUNCH();
                 uint32_t *t = q; q = nq; nq = t;

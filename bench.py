@@ -297,7 +297,7 @@ def main():
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--split", default="lpp")
     ap.add_argument("--move", default="sync")
-    ap.add_argument("--waves", type=int, default=16)
+    ap.add_argument("--waves", type=int, default=17)
     ap.add_argument("--ref-scale", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -216,7 +216,7 @@ class LouvainOptions:
     split: str = "bfs"
     split_last: bool = False
     sync: bool = True
-    waves: int = 16
+    waves: int = 17
     singleton_rule: bool = True
 
 

@@ -632,7 +632,7 @@ void gsp_default_opts(gsp_opts *o) {
     o->split = GSP_SPLIT_LPP;
     o->split_when = GSP_SPLIT_PASS;
     o->move = GSP_MOVE_SYNC;
-    o->waves = 16;
+    o->waves = 17;
     o->precision = GSP_PREC_MIXED;
     o->singleton_rule = 1;
     o->prune = GSP_PRUNE_FLAGS;

@@ -59,7 +59,7 @@ def _graph(off, tgt, w=None):
 
 
 def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=10.0,
-              aggregation_tolerance=0.8, split="lpp", split_when="pass", move="sync", waves=16,
+              aggregation_tolerance=0.8, split="lpp", split_when="pass", move="sync", waves=17,
               precision="mixed", singleton_rule=True, prune="flags", mlp_params=None,
               full_sweep_every=4, prune_threshold=0.5, stream=None):
     o = GspOpts()
@@ -190,7 +190,7 @@ def move_sweep(offsets, targets, weights, C, K, Sigma, m, active=None, precision
 
 
 def local_move(offsets, targets, weights, C, K, Sigma, m, tolerance=1e-2, max_iterations=20,
-               move="sync", waves=16, precision="fp64", singleton_rule=True, stream=None):
+               move="sync", waves=17, precision="fp64", singleton_rule=True, stream=None):
     """louvainMove (Algorithm 4); C and Sigma are updated in place; returns l_i."""
     n, nnz = _graph(offsets, targets, weights)
     it = ctypes.c_int()

@@ -365,6 +365,8 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
 // append their slot to the community's occupied list, which the extraction
 // walks.
 constexpr uint32_t AGG_CHUNK = 2048;
+constexpr uint32_t AGG_TASK_WARPS = 8;                    // k_agg_large_insert runs 256-thread blocks
+constexpr uint32_t AGG_SUB = AGG_CHUNK / AGG_TASK_WARPS;  // edges of a task per warp
 constexpr int AGG_SLOG = 12;  // shared table of 2 * AGG_CHUNK slots
 
 __global__ void k_member_deg(const uint64_t *__restrict__ off, const uint32_t *__restrict__ cverts, uint32_t n,
@@ -381,9 +383,36 @@ __global__ void k_agg_tasks(const unsigned long long *__restrict__ cdeg, const u
         ntask[t] = (cdeg[list[t]] + AGG_CHUNK - 1) / AGG_CHUNK;
 }
 
+// First member of every warp's slice of every task: the last member q of
+// the community with medge[q] <= the slice's first edge (a binary search per
+// slice, all slices at once, ahead of the insert kernel).
+__global__ void k_agg_warp_starts(AggArgs a, const uint32_t *__restrict__ list, const uint64_t *__restrict__ tasks,
+                                  uint32_t count, const uint32_t *__restrict__ task_c,
+                                  const uint64_t *__restrict__ medge, uint32_t *wstart) {
+    const uint64_t total = tasks[count] * AGG_TASK_WARPS;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t task = x / AGG_TASK_WARPS;
+        const uint32_t t = task_c[task], c = list[t];
+        const uint64_t ch = a.yoff[c] + (task - tasks[t]) * AGG_CHUNK + (x % AGG_TASK_WARPS) * AGG_SUB;
+        uint64_t lo = a.coff[c];
+        if (ch < a.yoff[c + 1]) {
+            uint64_t hi = a.coff[c + 1] - 1;
+            while (lo < hi) {
+                uint64_t mid = (lo + hi + 1) >> 1;
+                if (medge[mid] <= ch) lo = mid;
+                else hi = mid - 1;
+            }
+        }
+        wstart[x] = (uint32_t)lo;
+    }
+}
+
 template <typename WT>
 __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint32_t *__restrict__ list, uint32_t count,
                                                           const uint64_t *__restrict__ tasks,
+                                                          const uint32_t *__restrict__ task_c,
+                                                          const uint32_t *__restrict__ wstart,
                                                           const uint64_t *__restrict__ medge,
                                                           const uint64_t *__restrict__ pool_off, uint32_t *pool_keys,
                                                           double *pool_vals, uint32_t *pool_occ, uint32_t *occ_n) {
@@ -396,27 +425,20 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
     __shared__ uint32_t s_redn[32];
     const WT *w = static_cast<const WT *>(a.w);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t sub = AGG_CHUNK / (blockDim.x >> 5);  // edges per warp
     for (uint32_t s = threadIdx.x; s < (1u << AGG_SLOG); s += blockDim.x) { skeys[s] = EMPTY; svals[s] = 0.0; }
     if (threadIdx.x == 0) s_nocc = 0;
     const uint64_t total = tasks[count];
     for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
-        uint32_t t = task_item(tasks, count, task);
+        uint32_t t = task_c[task];
         uint32_t c = list[t];
         uint64_t E1 = a.yoff[c + 1];
-        uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
-        uint64_t ch = a.yoff[c] + (task - tasks[t]) * AGG_CHUNK + (uint64_t)wid * sub;
-        uint64_t cend = min(ch + sub, E1);
+        uint64_t q1 = a.coff[c + 1];
+        uint64_t ch = a.yoff[c] + (task - tasks[t]) * AGG_CHUNK + (uint64_t)wid * AGG_SUB;
+        uint64_t cend = min(ch + AGG_SUB, E1);
         double selfw = 0.0;
         uint32_t nself = 0;
         if (ch < E1) {
-            // last member q in [q0, q1) with medge[q] <= ch
-            uint64_t lo = q0, hi = q1 - 1;
-            while (lo < hi) {
-                uint64_t mid = (lo + hi + 1) >> 1;
-                if (medge[mid] <= ch) lo = mid;
-                else hi = mid - 1;
-            }
+            const uint64_t lo = wstart[task * AGG_TASK_WARPS + wid];  // last member with medge <= ch
             // A window of 32 members (lane l: member q + l, its end in the
             // member-edge numbering and its first edge in the CSR) is read at
             // once; each round deals out up to 32 edges of the window, every
@@ -480,6 +502,7 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
 // most one distinct neighbour community per edge).
 __global__ void __launch_bounds__(256) k_agg_large_extract(AggArgs a, const uint32_t *__restrict__ list,
                                                            uint32_t count, const uint64_t *__restrict__ tasks,
+                                                           const uint32_t *__restrict__ task_c,
                                                            const uint64_t *__restrict__ pool_off,
                                                            const uint32_t *__restrict__ pool_keys,
                                                            const double *__restrict__ pool_vals,
@@ -488,7 +511,7 @@ __global__ void __launch_bounds__(256) k_agg_large_extract(AggArgs a, const uint
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t total = tasks[count];
     for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
-        uint32_t t = task_item(tasks, count, task);
+        uint32_t t = task_c[task];
         uint32_t c = list[t];
         const uint32_t *keys = pool_keys + pool_off[t];
         const double *vals = pool_vals + pool_off[t];
@@ -756,6 +779,14 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
         k_agg_tasks<<<grid_for(nl, 256), 256, 0, s>>>(cdeg, llist, nl, ntask);
         GSP_CHECK_LAUNCH();
         exclusive_scan_u64(ntask, tasks, nl, s);
+        // at most one task per AGG_CHUNK edges plus one partial task per community
+        const uint64_t task_bound = g.nnz / AGG_CHUNK + nl + 1;
+        uint32_t *task_c = arena().get<uint32_t>(task_bound);
+        task_items(tasks, nl, task_c, s);
+        uint32_t *wstart = arena().get<uint32_t>(task_bound * AGG_TASK_WARPS);
+        k_agg_warp_starts<<<grid_for(task_bound * AGG_TASK_WARPS, 256, sms(16)), 256, 0, s>>>(
+            a, llist, tasks, nl, task_c, medge, wstart);
+        GSP_CHECK_LAUNCH();
         constexpr size_t lsmem = (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t)) << AGG_SLOG;
         static bool lattr = false;
         if (!lattr) {
@@ -763,9 +794,11 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
                                           (int)lsmem));
             lattr = true;
         }
-        k_agg_large_insert<WT><<<sms(4), 256, lsmem, s>>>(a, llist, nl, tasks, medge, poff, pk, pv, po, on);
+        const unsigned lgrid = resident_grid((const void *)k_agg_large_insert<WT>, AGG_TASK_WARPS * 32, lsmem, 4);
+        k_agg_large_insert<WT><<<lgrid, AGG_TASK_WARPS * 32, lsmem, s>>>(a, llist, nl, tasks, task_c, wstart, medge,
+                                                                          poff, pk, pv, po, on);
         GSP_CHECK_LAUNCH();
-        k_agg_large_extract<<<sms(4), 256, 0, s>>>(a, llist, nl, tasks, poff, pk, pv, po, on);
+        k_agg_large_extract<<<sms(4), 256, 0, s>>>(a, llist, nl, tasks, task_c, poff, pk, pv, po, on);
         GSP_CHECK_LAUNCH();
     }
 

@@ -60,6 +60,11 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int sm_count();  // SMs of the current device (cached per device)
 // Grid caps are given in blocks per SM: sms(k) = k blocks on every SM.
 inline unsigned sms(unsigned per_sm) { return per_sm * (unsigned)sm_count(); }
+// Grid of a grid-stride kernel that fits the device at once: the blocks of
+// `fn` resident per SM (registers and shared memory), at most per_sm_cap,
+// times the SM count.  Launching more blocks than are resident leaves a
+// partial second generation of blocks running on idle SMs.
+unsigned resident_grid(const void *fn, int threads, size_t dyn_smem, unsigned per_sm_cap);
 inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 0) {
     if (!cap) cap = sms(16);
     uint64_t g = (work + block - 1) / block;

@@ -177,6 +177,10 @@ void lookup(uint32_t n_top, uint32_t *C_top, const uint32_t *C_pass, cudaStream_
 uint32_t canonical_numbering(uint32_t n, uint32_t *C, cudaStream_t s);
 
 void iota_u32(uint32_t *p, uint32_t n, cudaStream_t s);
+// out[k] = the item that owns task prefix[0] + k of a chunked work split
+// (tasks [prefix[i], prefix[i+1]) belong to item i); out holds
+// prefix[nitems] - prefix[0] entries.  Replaces a per-task search of prefix.
+void task_items(const uint64_t *prefix, uint32_t nitems, uint32_t *out, cudaStream_t s);
 
 // MLP (mlp.cu)
 constexpr int MLP_IN = 6, MLP_H = 32;

@@ -20,6 +20,23 @@ void iota_u32(uint32_t *p, uint32_t n, cudaStream_t s) {
     GSP_CHECK_LAUNCH();
 }
 
+// Owner of every task of a chunked work split: one warp per item writes the
+// item's index over its task range.
+__global__ void k_task_items(const uint64_t *__restrict__ prefix, uint32_t nitems, uint32_t *out) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t base = prefix[0];
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nitems;
+         t += (gridDim.x * blockDim.x) >> 5) {
+        const uint64_t b = prefix[t] - base, e = prefix[t + 1] - base;
+        for (uint64_t k = b + lane; k < e; k += 32) out[k] = t;
+    }
+}
+void task_items(const uint64_t *prefix, uint32_t nitems, uint32_t *out, cudaStream_t s) {
+    if (!nitems) return;
+    k_task_items<<<grid_for((uint64_t)nitems * 32, 256), 256, 0, s>>>(prefix, nitems, out);
+    GSP_CHECK_LAUNCH();
+}
+
 // Per row i: K_i, and the intra-community part sum_{j: C_j = C_i} w_ij when C
 // is given; Sigma_c += K_i when Sig is given.  Long rows are deferred to a
 // list for the block kernel.

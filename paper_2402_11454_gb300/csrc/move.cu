@@ -546,11 +546,10 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
 // --------------------------------------------------------------------------
 // Apply a frozen-state wave's moves: C, Sigma and size updates (float64
 // atomics of exactly representable values, so the result does not depend on
-// their order), and re-marking of the movers' neighbours: one warp per mover,
-// except movers of degree > BIG_MOVER, which go to a list that every block
-// of k_mark_big walks together.
+// their order).  The movers' neighbours were already re-marked, into the
+// separate mark array, by the kernels that decided the moves (hub movers by
+// k_mark_big).
 // --------------------------------------------------------------------------
-constexpr uint32_t BIG_MOVER = 2048;
 
 // Community totals change by +-K_i per move; movers of a wave crowd into a
 // few large communities, so the deltas are first summed per block in a

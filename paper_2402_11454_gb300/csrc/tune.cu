@@ -36,6 +36,13 @@ int sm_count() {
     return cached[d];
 }
 
+unsigned resident_grid(const void *fn, int threads, size_t dyn_smem, unsigned per_sm_cap) {
+    int nb = 0;
+    GSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, dyn_smem));
+    unsigned per = nb > 0 ? (unsigned)nb : 1u;
+    return sms(per < per_sm_cap ? per : per_sm_cap);
+}
+
 constexpr int TUNE_MAX = 32;  // blocks per SM, upper limit of every cap
 
 static void check_tuning(const gsp_tuning &t) {

@@ -140,9 +140,9 @@ def make_workload(gsp, graphgen, name):
 
 
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of all
-# local-moving launches of one R-MAT 20 step divided by that step's algorithmic
-# bytes (profiles/dram_local_moving_rmat20.md); scaled to the bench workload.
-MOVE_TRAFFIC_RATIO = 2.160
+# local-moving launches of one R-MAT 20 step (17 waves, grid caps 4,1,2,16)
+# divided by that step's algorithmic bytes; scaled to the bench workload.
+MOVE_TRAFFIC_RATIO = 2.369
 
 
 def roofline_from(stats_list, peak_gbs, peak_kind):

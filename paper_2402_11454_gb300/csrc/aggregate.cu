@@ -17,9 +17,15 @@
 //     the rows stay unsorted: no later step depends on their order (moves,
 //     split and aggregation sum exactly representable weights, and ties go
 //     to the lowest id), so only the phase entry point sorts.
-// Weights are accumulated and stored in float64; sums of float32-exact
-// weights are exact in float64, so every merged weight is order-independent
-// and the output is canonical.
+// Weights are stored in float64; sums of float32-exact weights are exact in
+// float64, so every merged weight is order-independent and the output is
+// canonical.  The tables accumulate in integer units of the weights' lowest
+// set bit (64-bit integer atomics, native in shared memory) whenever the total
+// weight stays below 2^52 such units, and in float64 otherwise; the two give
+// the same sums.
+#include <climits>
+#include <cmath>
+
 #include "internal.cuh"
 
 namespace gsp {
@@ -127,7 +133,81 @@ struct AggArgs {
     double *hw;
     uint32_t *rowlen;
     uint32_t k;
+    int xlsb;  // exact fixed-point accumulation: values in integer units of 2^xlsb
 };
+
+// Table values are accumulated either as float64 (AV = double) or, when every
+// weight of the graph is a multiple of 2^lsb and the total weight is below
+// 2^52 units, as 64-bit integers in units of 2^lsb (AV = unsigned long long),
+// whose shared-memory atomic add is a single native operation; a float32 or
+// float64 weight becomes its integer mantissa shifted by its exponent, with no
+// floating-point arithmetic.  Both sum exactly, so they give identical tables.
+__device__ __forceinline__ unsigned long long units_of(float x, int lsb) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const unsigned long long m = e ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
+    const int sh = (e ? e : 1) - 150 - lsb;  // x = m * 2^(sh + lsb); sh >= -ctz(m)
+    return sh >= 0 ? m << sh : m >> -sh;
+}
+__device__ __forceinline__ unsigned long long units_of(double x, int lsb) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    const unsigned long long m = e ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : (b & 0xFFFFFFFFFFFFFull);
+    const int sh = (e ? e : 1) - 1075 - lsb;
+    return sh >= 0 ? m << sh : m >> -sh;
+}
+template <typename AV> struct Acc;
+template <> struct Acc<double> {
+    template <typename WT> __device__ static double of(WT x, int) { return (double)x; }
+    __device__ static double val(double v, int) { return v; }
+};
+template <> struct Acc<unsigned long long> {
+    template <typename WT> __device__ static unsigned long long of(WT x, int lsb) { return units_of(x, lsb); }
+    // v < 2^52: the conversion is exact, and so is the power-of-two scaling
+    // done on the exponent field (lsb >= -1000 keeps the result normal)
+    __device__ static double val(unsigned long long v, int lsb) {
+        if (!v) return 0.0;
+        const double d = (double)v;
+        return __longlong_as_double(__double_as_longlong(d) + ((long long)lsb << 52));
+    }
+};
+
+// Exponent of the lowest set bit of a positive finite weight (INT_MIN for a
+// value that is not, INT_MAX for zero).
+__device__ __forceinline__ int low_bit_exp(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    if ((b >> 31) || e == 0xFFu) return INT_MIN;
+    if (e == 0) return m ? -149 + (__ffs((int)m) - 1) : INT_MAX;
+    return (int)e - 150 + (__ffs((int)(m | 0x800000u)) - 1);
+}
+__device__ __forceinline__ int low_bit_exp(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if ((b >> 63) || e == 0x7FF) return INT_MIN;
+    if (e == 0) return m ? -1074 + (__ffsll((long long)m) - 1) : INT_MAX;
+    return e - 1075 + (__ffsll((long long)(m | (1ull << 52))) - 1);
+}
+
+// Smallest lowest-set-bit exponent over the weights and their (rounded) sum.
+template <typename WT>
+__global__ void k_weight_range(const WT *__restrict__ w, uint64_t nnz, int *minlow, double *sum) {
+    int lo = INT_MAX;
+    float acc = 0.0f;  // an estimate for the range test (float64 is slow here)
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const WT x = w[p];
+        lo = min(lo, low_bit_exp(x));
+        acc += (float)x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(minlow, lo);
+        atomicAdd(sum, (double)acc);
+    }
+}
 
 // Append the occupied slots of a table to row c of the holey CSR.
 __device__ __forceinline__ void emit_slot(const AggArgs &a, uint32_t c, uint32_t key, double val, bool valid,
@@ -193,14 +273,14 @@ __device__ __forceinline__ void warp_row_edges(const uint32_t *__restrict__ list
 constexpr int AGG_WCAP = 1024;
 constexpr int AGG_WWARPS = 4;
 
-template <typename WT>
+template <typename WT, typename AV>
 __global__ void __launch_bounds__(AGG_WWARPS * 32) k_agg_merge_warp(AggArgs a, const uint32_t *__restrict__ list,
                                                                     uint32_t count) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     __shared__ uint32_t s_cur[AGG_WWARPS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t *keys = reinterpret_cast<uint32_t *>(dyn_smem) + wid * AGG_WCAP;
-    double *vals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * AGG_WCAP * AGG_WWARPS) + wid * AGG_WCAP;
+    AV *vals = reinterpret_cast<AV *>(dyn_smem + sizeof(uint32_t) * AGG_WCAP * AGG_WWARPS) + wid * AGG_WCAP;
     const WT *w = static_cast<const WT *>(a.w);
     for (uint32_t t = blockIdx.x * AGG_WWARPS + wid; t < count; t += gridDim.x * AGG_WWARPS) {
         uint32_t c = list[t];
@@ -209,29 +289,29 @@ __global__ void __launch_bounds__(AGG_WWARPS * 32) k_agg_merge_warp(AggArgs a, c
         int logcap = ceil_log2((uint32_t)(2 * bound));
         if (logcap < 1) logcap = 1;
         uint32_t cap = 1u << logcap;
-        for (uint32_t s = lane; s < cap; s += 32) { keys[s] = EMPTY; vals[s] = 0.0; }
+        for (uint32_t s = lane; s < cap; s += 32) { keys[s] = EMPTY; vals[s] = AV(0); }
         if (lane == 0) s_cur[wid] = 0;
         __syncwarp();
         // edges inside the community (the super-vertex's self-loop) are summed
         // in registers: they are the most frequent key of the table
-        double selfw = 0.0;
+        AV selfw = AV(0);
         uint32_t nself = 0;
         warp_row_edges(a.cverts, a.coff[c], a.coff[c + 1], a.off, [&](uint64_t p, bool valid) {
             if (!valid) return;
             const uint32_t d = a.Cd[a.tgt[p]];
-            const double x = (double)w[p];
-            if (d == c) { selfw += x; nself++; }
-            else ht_add<double>(keys, vals, logcap, d, x);
+            const WT x = w[p];
+            if (d == c) { selfw += Acc<AV>::of(x, a.xlsb); nself++; }
+            else ht_add<AV>(keys, vals, logcap, d, Acc<AV>::of(x, a.xlsb));
         });
         selfw = warp_sum(selfw);
         nself = warp_sum(nself);
         __syncwarp();
-        if (lane == 0 && nself) ht_add<double>(keys, vals, logcap, c, selfw);
+        if (lane == 0 && nself) ht_add<AV>(keys, vals, logcap, c, selfw);
         __syncwarp();
         for (uint32_t s0 = 0; s0 < cap; s0 += 32) {
             uint32_t s = s0 + lane;
             uint32_t key = s < cap ? keys[s] : EMPTY;
-            emit_slot(a, c, key, s < cap ? vals[s] : 0.0, key != EMPTY, &s_cur[wid]);
+            emit_slot(a, c, key, s < cap ? Acc<AV>::val(vals[s], a.xlsb) : 0.0, key != EMPTY, &s_cur[wid]);
         }
         __syncwarp();
         if (lane == 0) a.rowlen[c] = s_cur[wid];
@@ -247,22 +327,22 @@ __global__ void __launch_bounds__(AGG_WWARPS * 32) k_agg_merge_warp(AggArgs a, c
 constexpr int AGG_BCAP = 4096;
 constexpr int AGG_BMEM = 2048;  // members staged in shared memory (total degree <= 2048 bounds them)
 
-template <typename WT>
+template <typename WT, typename AV>
 __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32_t *__restrict__ list, uint32_t count) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     uint32_t *keys = reinterpret_cast<uint32_t *>(dyn_smem);
-    double *vals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * AGG_BCAP);
+    AV *vals = reinterpret_cast<AV *>(dyn_smem + sizeof(uint32_t) * AGG_BCAP);
     uint16_t *occ = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(double)) * AGG_BCAP);
     uint64_t *s_base = reinterpret_cast<uint64_t *>(
         dyn_smem + (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t)) * AGG_BCAP);
     uint32_t *s_pre = reinterpret_cast<uint32_t *>(s_base + AGG_BMEM);  // AGG_BMEM + 1 entries
     __shared__ uint32_t s_cur, s_nocc;
-    __shared__ double s_red[32];
+    __shared__ AV s_red[32];
     __shared__ uint32_t s_redn[32], s_wsum[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const WT *w = static_cast<const WT *>(a.w);
-    for (uint32_t s = threadIdx.x; s < AGG_BCAP; s += blockDim.x) { keys[s] = EMPTY; vals[s] = 0.0; }
+    for (uint32_t s = threadIdx.x; s < AGG_BCAP; s += blockDim.x) { keys[s] = EMPTY; vals[s] = AV(0); }
     for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
         uint32_t c = list[t];
         uint64_t cd = a.cdeg[c];
@@ -274,13 +354,13 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
         __syncthreads();
         uint64_t q0 = a.coff[c], q1 = a.coff[c + 1];
         const uint32_t nm = (uint32_t)(q1 - q0);
-        double selfw = 0.0;
+        AV selfw = AV(0);
         uint32_t nself = 0;
         auto visit = [&](uint64_t p) {
             const uint32_t d = a.Cd[a.tgt[p]];
-            const double x = (double)w[p];
-            if (d == c) { selfw += x; nself++; }
-            else smem_add<double>(keys, vals, logcap, occ, &s_nocc, d, x);
+            const WT x = w[p];
+            if (d == c) { selfw += Acc<AV>::of(x, a.xlsb); nself++; }
+            else smem_add<AV>(keys, vals, logcap, occ, &s_nocc, d, Acc<AV>::of(x, a.xlsb));
         };
         if (nm <= AGG_BMEM) {
             // member degrees -> exclusive prefix s_pre[0..nm], bases s_base
@@ -337,19 +417,20 @@ __global__ void __launch_bounds__(256) k_agg_merge_block(AggArgs a, const uint32
         }
         selfw = block_sum(selfw, s_red);
         nself = block_sum(nself, s_redn);
-        if (threadIdx.x == 0 && nself) smem_add<double>(keys, vals, logcap, occ, &s_nocc, c, selfw);
+        if (threadIdx.x == 0 && nself) smem_add<AV>(keys, vals, logcap, occ, &s_nocc, c, selfw);
         __syncthreads();
         uint32_t nocc = s_nocc;
         for (uint32_t k0 = wid * 32; k0 < nocc; k0 += blockDim.x) {
             uint32_t k = k0 + lane;
             uint32_t slot = k < nocc ? occ[k] : 0;
-            emit_slot(a, c, k < nocc ? keys[slot] : EMPTY, k < nocc ? vals[slot] : 0.0, k < nocc, &s_cur);
+            emit_slot(a, c, k < nocc ? keys[slot] : EMPTY, k < nocc ? Acc<AV>::val(vals[slot], a.xlsb) : 0.0, k < nocc,
+                      &s_cur);
         }
         __syncthreads();
         for (uint32_t k = threadIdx.x; k < nocc; k += blockDim.x) {
             uint32_t slot = occ[k];
             keys[slot] = EMPTY;
-            vals[slot] = 0.0;
+            vals[slot] = AV(0);
         }
         if (threadIdx.x == 0) a.rowlen[c] = s_cur;
     }
@@ -408,24 +489,24 @@ __global__ void k_agg_warp_starts(AggArgs a, const uint32_t *__restrict__ list, 
     }
 }
 
-template <typename WT>
+template <typename WT, typename AV>
 __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint32_t *__restrict__ list, uint32_t count,
                                                           const uint64_t *__restrict__ tasks,
                                                           const uint32_t *__restrict__ task_c,
                                                           const uint32_t *__restrict__ wstart,
                                                           const uint64_t *__restrict__ medge,
                                                           const uint64_t *__restrict__ pool_off, uint32_t *pool_keys,
-                                                          double *pool_vals, uint32_t *pool_occ, uint32_t *occ_n) {
+                                                          AV *pool_vals, uint32_t *pool_occ, uint32_t *occ_n) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     uint32_t *skeys = reinterpret_cast<uint32_t *>(dyn_smem);
-    double *svals = reinterpret_cast<double *>(dyn_smem + sizeof(uint32_t) * (1u << AGG_SLOG));
-    uint16_t *socc = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(double)) * (1u << AGG_SLOG));
+    AV *svals = reinterpret_cast<AV *>(dyn_smem + sizeof(uint32_t) * (1u << AGG_SLOG));
+    uint16_t *socc = reinterpret_cast<uint16_t *>(dyn_smem + (sizeof(uint32_t) + sizeof(AV)) * (1u << AGG_SLOG));
     __shared__ uint32_t s_nocc;
-    __shared__ double s_red[32];
+    __shared__ AV s_red[32];
     __shared__ uint32_t s_redn[32];
     const WT *w = static_cast<const WT *>(a.w);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (uint32_t s = threadIdx.x; s < (1u << AGG_SLOG); s += blockDim.x) { skeys[s] = EMPTY; svals[s] = 0.0; }
+    for (uint32_t s = threadIdx.x; s < (1u << AGG_SLOG); s += blockDim.x) { skeys[s] = EMPTY; svals[s] = AV(0); }
     if (threadIdx.x == 0) s_nocc = 0;
     const uint64_t total = tasks[count];
     for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
@@ -435,7 +516,7 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
         uint64_t q1 = a.coff[c + 1];
         uint64_t ch = a.yoff[c] + (task - tasks[t]) * AGG_CHUNK + (uint64_t)wid * AGG_SUB;
         uint64_t cend = min(ch + AGG_SUB, E1);
-        double selfw = 0.0;
+        AV selfw = AV(0);
         uint32_t nself = 0;
         if (ch < E1) {
             const uint64_t lo = wstart[task * AGG_TASK_WARPS + wid];  // last member with medge <= ch
@@ -476,8 +557,8 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
                 if (tt < rend) {
                     const uint64_t p = rbase + (tt - rstart);
                     const uint32_t dd = a.Cd[a.tgt[p]];
-                    if (dd == c) { selfw += (double)w[p]; nself++; }
-                    else smem_add<double>(skeys, svals, AGG_SLOG, socc, &s_nocc, dd, (double)w[p]);
+                    if (dd == c) { selfw += Acc<AV>::of(w[p], a.xlsb); nself++; }
+                    else smem_add<AV>(skeys, svals, AGG_SLOG, socc, &s_nocc, dd, Acc<AV>::of(w[p], a.xlsb));
                 }
                 // members ending at or before rend are done
                 q += __popc(__ballot_sync(FULL, wend_l <= rend));
@@ -487,12 +568,13 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
         // the task's edges inside the community enter the table once
         selfw = block_sum(selfw, s_red);
         nself = block_sum(nself, s_redn);
-        if (threadIdx.x == 0 && nself) smem_add<double>(skeys, svals, AGG_SLOG, socc, &s_nocc, c, selfw);
+        if (threadIdx.x == 0 && nself)
+            smem_add<AV>(skeys, svals, AGG_SLOG, socc, &s_nocc, c, selfw);
         uint64_t cd = a.cdeg[c];
         uint64_t bound = cd < a.k ? cd : a.k;
         int glog = ceil_log2((uint32_t)(2 * bound));
         if (glog < 1) glog = 1;
-        publish_block_table<double>(skeys, svals, socc, &s_nocc, pool_keys + pool_off[t], pool_vals + pool_off[t],
+        publish_block_table<AV>(skeys, svals, socc, &s_nocc, pool_keys + pool_off[t], pool_vals + pool_off[t],
                                     glog, pool_occ + pool_off[t], occ_n + t);
     }
 }
@@ -500,12 +582,13 @@ __global__ void __launch_bounds__(256) k_agg_large_insert(AggArgs a, const uint3
 // Extraction uses the insert's task split: task k of a community emits its
 // occupied entries [k * AGG_CHUNK, (k+1) * AGG_CHUNK) (a community has at
 // most one distinct neighbour community per edge).
+template <typename AV>
 __global__ void __launch_bounds__(256) k_agg_large_extract(AggArgs a, const uint32_t *__restrict__ list,
                                                            uint32_t count, const uint64_t *__restrict__ tasks,
                                                            const uint32_t *__restrict__ task_c,
                                                            const uint64_t *__restrict__ pool_off,
                                                            const uint32_t *__restrict__ pool_keys,
-                                                           const double *__restrict__ pool_vals,
+                                                           const AV *__restrict__ pool_vals,
                                                            const uint32_t *__restrict__ pool_occ,
                                                            const uint32_t *__restrict__ occ_n) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -514,7 +597,7 @@ __global__ void __launch_bounds__(256) k_agg_large_extract(AggArgs a, const uint
         uint32_t t = task_c[task];
         uint32_t c = list[t];
         const uint32_t *keys = pool_keys + pool_off[t];
-        const double *vals = pool_vals + pool_off[t];
+        const AV *vals = pool_vals + pool_off[t];
         const uint32_t *occ = pool_occ + pool_off[t];
         uint64_t k0 = (task - tasks[t]) * AGG_CHUNK;
         uint64_t k1 = min(k0 + AGG_CHUNK, (uint64_t)occ_n[t]);
@@ -523,7 +606,8 @@ __global__ void __launch_bounds__(256) k_agg_large_extract(AggArgs a, const uint
             uint64_t k = kb + lane;
             bool valid = k < k1;
             uint32_t slot = valid ? occ[k] : 0;
-            emit_slot(a, c, valid ? keys[slot] : EMPTY, valid ? vals[slot] : 0.0, valid, a.rowlen + c);
+            emit_slot(a, c, valid ? keys[slot] : EMPTY, valid ? Acc<AV>::val(vals[slot], a.xlsb) : 0.0, valid,
+                      a.rowlen + c);
         }
     }
 }
@@ -698,9 +782,120 @@ static int ceil_log2_host(uint64_t x) {
 }
 
 
+// Exponent lsb such that every weight of g is a multiple of 2^lsb and the total
+// weight is below 2^52 * 2^lsb (then every table sum is an integer number of
+// units below 2^52, exact both as uint64 and as float64); INT_MIN when no
+// such exponent in [-1000, 1000] exists (zero, negative or non-finite
+// weights, or too wide a range of magnitudes).
+template <typename WT>
+static int exact_lsb(const DevGraph &g, cudaStream_t s) {
+    if (!g.nnz || !g.w) return INT_MIN;
+    size_t mk = arena().mark();
+    int *dlo = arena().get<int>(1);
+    double *dsum = arena().get<double>(1);
+    const int init = INT_MAX;
+    GSP_CUDA(cudaMemcpyAsync(dlo, &init, sizeof(int), cudaMemcpyHostToDevice, s));
+    GSP_CUDA(cudaMemsetAsync(dsum, 0, sizeof(double), s));
+    k_weight_range<WT><<<grid_for(g.nnz, 256, sms(8)), 256, 0, s>>>(static_cast<const WT *>(g.w), g.nnz, dlo, dsum);
+    GSP_CHECK_LAUNCH();
+    int lo = 0;
+    double sum = 0.0;
+    GSP_CUDA(cudaMemcpyAsync(&lo, dlo, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaMemcpyAsync(&sum, dsum, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    if (lo < -1000 || lo > 1000) return INT_MIN;
+    // the float64 sum is rounded: keep a factor 2 of margin below 2^53
+    if (!(sum > 0.0) || !(sum < std::ldexp(1.0, 52 + lo))) return INT_MIN;
+    return lo;
+}
+
+// Per-community tables of the three size classes, emitted into the holey CSR.
+template <typename WT, typename AV>
+static void merge_tables(const DevGraph &g, const AggArgs &a, const IdClasses &ic, const unsigned long long *cdeg,
+                         const uint32_t *cverts, uint32_t k, uint32_t n, cudaStream_t s) {
+    auto cnt_of = [&](int c) { return ic.start[c + 1] - ic.start[c]; };
+    if (cnt_of(ACLS_W)) {
+        constexpr size_t smem = (size_t)AGG_WWARPS * AGG_WCAP * (sizeof(uint32_t) + sizeof(AV));
+        static bool wattr = false;
+        if (!wattr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_warp<WT, AV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            wattr = true;
+        }
+        k_agg_merge_warp<WT, AV><<<grid_for((uint64_t)cnt_of(ACLS_W) * 32, AGG_WWARPS * 32, sms(4)), AGG_WWARPS * 32,
+                               smem, s>>>(a, ic.list + ic.start[ACLS_W], cnt_of(ACLS_W));
+        GSP_CHECK_LAUNCH();
+    }
+    if (cnt_of(ACLS_B)) {
+        constexpr size_t smem = (size_t)AGG_BCAP * (sizeof(uint32_t) + sizeof(AV) + sizeof(uint16_t)) +
+                                (size_t)AGG_BMEM * sizeof(uint64_t) + (size_t)(AGG_BMEM + 1) * sizeof(uint32_t);
+        static bool attr = false;
+        if (!attr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_block<WT, AV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            attr = true;
+        }
+        k_agg_merge_block<WT, AV><<<grid_for(cnt_of(ACLS_B), 1, sms(4)), 256, smem, s>>>(a, ic.list + ic.start[ACLS_B],
+                                                                                     cnt_of(ACLS_B));
+        GSP_CHECK_LAUNCH();
+    }
+    uint32_t nl = cnt_of(ACLS_L);
+    if (nl) {
+        uint64_t *caps = arena().get<uint64_t>(nl);
+        uint64_t *poff = arena().get<uint64_t>((size_t)nl + 1);
+        k_agg_pool_caps<<<grid_for(nl, 256), 256, 0, s>>>(cdeg, ic.list + ic.start[ACLS_L], nl, k, caps);
+        GSP_CHECK_LAUNCH();
+        exclusive_scan_u64(caps, poff, nl, s);
+        uint64_t slots;
+        GSP_CUDA(cudaMemcpyAsync(&slots, poff + nl, sizeof(slots), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        uint32_t *pk = arena().get<uint32_t>(slots);
+        AV *pv = arena().get<AV>(slots);
+        uint32_t *po = arena().get<uint32_t>(slots);
+        uint32_t *on = arena().get<uint32_t>(nl);
+        GSP_CUDA(cudaMemsetAsync(pk, 0xFF, sizeof(uint32_t) * slots, s));
+        GSP_CUDA(cudaMemsetAsync(pv, 0, sizeof(AV) * slots, s));
+        GSP_CUDA(cudaMemsetAsync(on, 0, sizeof(uint32_t) * nl, s));
+        uint64_t *medge = arena().get<uint64_t>((size_t)n + 1);
+        uint64_t *mdeg = arena().get<uint64_t>(n);
+        k_member_deg<<<grid_for(n, 256), 256, 0, s>>>(g.off, cverts, n, mdeg);
+        GSP_CHECK_LAUNCH();
+        exclusive_scan_u64(mdeg, medge, n, s);
+        const uint32_t *llist = ic.list + ic.start[ACLS_L];
+        uint64_t *ntask = arena().get<uint64_t>(nl);
+        uint64_t *tasks = arena().get<uint64_t>((size_t)nl + 1);
+        k_agg_tasks<<<grid_for(nl, 256), 256, 0, s>>>(cdeg, llist, nl, ntask);
+        GSP_CHECK_LAUNCH();
+        exclusive_scan_u64(ntask, tasks, nl, s);
+        // at most one task per AGG_CHUNK edges plus one partial task per community
+        const uint64_t task_bound = g.nnz / AGG_CHUNK + nl + 1;
+        uint32_t *task_c = arena().get<uint32_t>(task_bound);
+        task_items(tasks, nl, task_c, s);
+        uint32_t *wstart = arena().get<uint32_t>(task_bound * AGG_TASK_WARPS);
+        k_agg_warp_starts<<<grid_for(task_bound * AGG_TASK_WARPS, 256, sms(16)), 256, 0, s>>>(
+            a, llist, tasks, nl, task_c, medge, wstart);
+        GSP_CHECK_LAUNCH();
+        constexpr size_t lsmem = (sizeof(uint32_t) + sizeof(AV) + sizeof(uint16_t)) << AGG_SLOG;
+        static bool lattr = false;
+        if (!lattr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_agg_large_insert<WT, AV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)lsmem));
+            lattr = true;
+        }
+        const unsigned lgrid = resident_grid((const void *)k_agg_large_insert<WT, AV>, AGG_TASK_WARPS * 32, lsmem, 4);
+        k_agg_large_insert<WT, AV><<<lgrid, AGG_TASK_WARPS * 32, lsmem, s>>>(a, llist, nl, tasks, task_c, wstart, medge,
+                                                                          poff, pk, pv, po, on);
+        GSP_CHECK_LAUNCH();
+        k_agg_large_extract<AV><<<sms(4), 256, 0, s>>>(a, llist, nl, tasks, task_c, poff, pk, pv, po, on);
+        GSP_CHECK_LAUNCH();
+    }
+
+}
+
 template <typename WT>
 static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off,
-                               uint32_t *out_tgt, double *out_w, bool sorted, cudaStream_t s) {
+                               uint32_t *out_tgt, double *out_w, bool sorted, int *lsb_cache, cudaStream_t s) {
     size_t mk = arena().mark();
     uint32_t n = g.n;
     uint32_t *cnt = arena().get<uint32_t>(k);
@@ -724,84 +919,18 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
 
     IdClasses ic;
     classify_ids<NUM_ACLS>(reinterpret_cast<const uint64_t *>(cdeg), k, ACLS_MAX, ic, s);
-    AggArgs a{g.off, g.tgt, g.w, Cd, coff, cverts, cdeg, yoff, htgt, hw, rowlen, k};
-    auto cnt_of = [&](int c) { return ic.start[c + 1] - ic.start[c]; };
-    if (cnt_of(ACLS_W)) {
-        constexpr size_t smem = (size_t)AGG_WWARPS * AGG_WCAP * (sizeof(uint32_t) + sizeof(double));
-        static bool wattr = false;
-        if (!wattr) {
-            GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_warp<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            wattr = true;
-        }
-        k_agg_merge_warp<WT><<<grid_for((uint64_t)cnt_of(ACLS_W) * 32, AGG_WWARPS * 32, sms(4)), AGG_WWARPS * 32,
-                               smem, s>>>(a, ic.list + ic.start[ACLS_W], cnt_of(ACLS_W));
-        GSP_CHECK_LAUNCH();
+    AggArgs a{g.off, g.tgt, g.w, Cd, coff, cverts, cdeg, yoff, htgt, hw, rowlen, k, 0};
+    // exact fixed-point table values when the weights allow it (same result,
+    // native shared-memory integer atomics instead of float64 ones)
+    int lsb = lsb_cache ? *lsb_cache : INT_MAX;
+    if (lsb == INT_MAX) lsb = exact_lsb<WT>(g, s);
+    if (lsb_cache) *lsb_cache = lsb;
+    if (lsb != INT_MIN) {
+        a.xlsb = lsb;
+        merge_tables<WT, unsigned long long>(g, a, ic, cdeg, cverts, k, n, s);
+    } else {
+        merge_tables<WT, double>(g, a, ic, cdeg, cverts, k, n, s);
     }
-    if (cnt_of(ACLS_B)) {
-        constexpr size_t smem = (size_t)AGG_BCAP * (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t)) +
-                                (size_t)AGG_BMEM * sizeof(uint64_t) + (size_t)(AGG_BMEM + 1) * sizeof(uint32_t);
-        static bool attr = false;
-        if (!attr) {
-            GSP_CUDA(cudaFuncSetAttribute(k_agg_merge_block<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            attr = true;
-        }
-        k_agg_merge_block<WT><<<grid_for(cnt_of(ACLS_B), 1, sms(4)), 256, smem, s>>>(a, ic.list + ic.start[ACLS_B],
-                                                                                     cnt_of(ACLS_B));
-        GSP_CHECK_LAUNCH();
-    }
-    uint32_t nl = cnt_of(ACLS_L);
-    if (nl) {
-        uint64_t *caps = arena().get<uint64_t>(nl);
-        uint64_t *poff = arena().get<uint64_t>((size_t)nl + 1);
-        k_agg_pool_caps<<<grid_for(nl, 256), 256, 0, s>>>(cdeg, ic.list + ic.start[ACLS_L], nl, k, caps);
-        GSP_CHECK_LAUNCH();
-        exclusive_scan_u64(caps, poff, nl, s);
-        uint64_t slots;
-        GSP_CUDA(cudaMemcpyAsync(&slots, poff + nl, sizeof(slots), cudaMemcpyDeviceToHost, s));
-        GSP_CUDA(cudaStreamSynchronize(s));
-        uint32_t *pk = arena().get<uint32_t>(slots);
-        double *pv = arena().get<double>(slots);
-        uint32_t *po = arena().get<uint32_t>(slots);
-        uint32_t *on = arena().get<uint32_t>(nl);
-        GSP_CUDA(cudaMemsetAsync(pk, 0xFF, sizeof(uint32_t) * slots, s));
-        GSP_CUDA(cudaMemsetAsync(pv, 0, sizeof(double) * slots, s));
-        GSP_CUDA(cudaMemsetAsync(on, 0, sizeof(uint32_t) * nl, s));
-        uint64_t *medge = arena().get<uint64_t>((size_t)n + 1);
-        uint64_t *mdeg = arena().get<uint64_t>(n);
-        k_member_deg<<<grid_for(n, 256), 256, 0, s>>>(g.off, cverts, n, mdeg);
-        GSP_CHECK_LAUNCH();
-        exclusive_scan_u64(mdeg, medge, n, s);
-        const uint32_t *llist = ic.list + ic.start[ACLS_L];
-        uint64_t *ntask = arena().get<uint64_t>(nl);
-        uint64_t *tasks = arena().get<uint64_t>((size_t)nl + 1);
-        k_agg_tasks<<<grid_for(nl, 256), 256, 0, s>>>(cdeg, llist, nl, ntask);
-        GSP_CHECK_LAUNCH();
-        exclusive_scan_u64(ntask, tasks, nl, s);
-        // at most one task per AGG_CHUNK edges plus one partial task per community
-        const uint64_t task_bound = g.nnz / AGG_CHUNK + nl + 1;
-        uint32_t *task_c = arena().get<uint32_t>(task_bound);
-        task_items(tasks, nl, task_c, s);
-        uint32_t *wstart = arena().get<uint32_t>(task_bound * AGG_TASK_WARPS);
-        k_agg_warp_starts<<<grid_for(task_bound * AGG_TASK_WARPS, 256, sms(16)), 256, 0, s>>>(
-            a, llist, tasks, nl, task_c, medge, wstart);
-        GSP_CHECK_LAUNCH();
-        constexpr size_t lsmem = (sizeof(uint32_t) + sizeof(double) + sizeof(uint16_t)) << AGG_SLOG;
-        static bool lattr = false;
-        if (!lattr) {
-            GSP_CUDA(cudaFuncSetAttribute(k_agg_large_insert<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)lsmem));
-            lattr = true;
-        }
-        const unsigned lgrid = resident_grid((const void *)k_agg_large_insert<WT>, AGG_TASK_WARPS * 32, lsmem, 4);
-        k_agg_large_insert<WT><<<lgrid, AGG_TASK_WARPS * 32, lsmem, s>>>(a, llist, nl, tasks, task_c, wstart, medge,
-                                                                          poff, pk, pv, po, on);
-        GSP_CHECK_LAUNCH();
-        k_agg_large_extract<<<sms(4), 256, 0, s>>>(a, llist, nl, tasks, task_c, poff, pk, pv, po, on);
-        GSP_CHECK_LAUNCH();
-    }
-
     // compact + sort rows
     exclusive_scan_u32_to_u64(rowlen, out_off, k, s);
     uint64_t nnz2;
@@ -872,9 +1001,9 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
 }
 
 uint64_t aggregate(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off, uint32_t *out_tgt,
-                   double *out_w, cudaStream_t s, bool sorted) {
-    if (g.wt == GSP_W_F64) return aggregate_impl<double>(g, Cd, k, out_off, out_tgt, out_w, sorted, s);
-    return aggregate_impl<float>(g, Cd, k, out_off, out_tgt, out_w, sorted, s);
+                   double *out_w, cudaStream_t s, bool sorted, int *lsb_cache) {
+    if (g.wt == GSP_W_F64) return aggregate_impl<double>(g, Cd, k, out_off, out_tgt, out_w, sorted, lsb_cache, s);
+    return aggregate_impl<float>(g, Cd, k, out_off, out_tgt, out_w, sorted, lsb_cache, s);
 }
 
 }  // namespace gsp

@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "internal.cuh"
@@ -368,6 +369,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     const bool split_pass = o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_PASS;
     uint32_t *Cp = mb.C;
     int pb = 0, passes = 0;
+    int lsb_cache = INT_MAX;  // fixed-point unit of the weights, found at the first aggregation
     uint32_t remaining = G;
     for (int lp = 0; lp < o.max_passes && remaining; lp++) {
         const uint32_t nv = cur.n;
@@ -466,7 +468,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         nxt.tgt = gtgt[pb];
         nxt.w = gw[pb];
         nxt.wt = GSP_W_F64;
-        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s, /*sorted=*/false);
+        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s, /*sorted=*/false, &lsb_cache);
         pb ^= 1;
         cur = nxt;
         tau = tau / o.tolerance_drop;

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <utility>
 #include <vector>
 
@@ -480,6 +481,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     int passes = 0;
     uint32_t *Cp = mb.C;  // membership of the current graph's vertices
     int pb = 0;
+    int lsb_cache = INT_MAX;  // fixed-point unit of the weights, found at the first aggregation
     for (int lp = 0; lp < o.max_passes; lp++) {
         const uint32_t nv = cur.n;
         size_t pass_mark = arena().mark();
@@ -540,7 +542,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         nxt.tgt = gtgt[pb];
         nxt.w = gw[pb];
         nxt.wt = GSP_W_F64;
-        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s, /*sorted=*/false);
+        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s, /*sorted=*/false, &lsb_cache);
         pb ^= 1;
         cur = nxt;
         tau = tau / o.tolerance_drop;

@@ -160,9 +160,12 @@ uint32_t renumber(uint32_t n, const uint32_t *C, uint32_t *C_dense, cudaStream_t
 
 // Aggregation (Algorithm 5) into out (offsets k+1, targets/weights nnz); returns nnz''.
 // sorted: rows in increasing target order (the canonical form); otherwise
-// each row's entries come in table order.
+// each row's entries come in table order.  lsb_cache (optional) carries the
+// exponent of the exact fixed-point unit of the weights between the passes
+// of one run (INT_MAX: not known yet; the weights of every aggregated graph
+// are sums of the input weights, so the input's unit and bound hold for all).
 uint64_t aggregate(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off, uint32_t *out_tgt,
-                   double *out_w, cudaStream_t s, bool sorted = true);
+                   double *out_w, cudaStream_t s, bool sorted = true, int *lsb_cache = nullptr);
 
 // K and m (m also written to *m_dev when non-null); returns m.
 double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t s);

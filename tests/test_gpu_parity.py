@@ -257,6 +257,22 @@ def test_aggregate_of_aggregate_f64_weights(gsp):
     assert np.array_equal(host(w2), h2.weights)
 
 
+@pytest.mark.parametrize("name", ["rmat14", "grid"])
+def test_aggregate_float64_table_path(gsp, name):
+    """Weights whose common unit is below 2^-1000 take the float64 table path
+    instead of the integer one; scaled by 2^-1010 the input weights keep
+    every sum exact, so the result still equals the oracle's bit for bit."""
+    off, tgt, w = GRAPHS[name]
+    n = len(off) - 1
+    w64 = np.ldexp(w.astype(np.float64), -1010)
+    C, k = oracle.renumber(np.random.default_rng(13).integers(0, max(2, n // 50), n).astype(np.uint32))
+    h = oracle.aggregate(oracle.Graph(off, tgt, w64), C, k)
+    o2, t2, w2 = gsp.aggregate(*dev(off, tgt, w64), torch.from_numpy(C.astype(np.int32)).cuda(), k)
+    assert np.array_equal(host(o2).astype(np.uint64), h.offsets)
+    assert np.array_equal(host(t2).astype(np.uint32), h.targets)
+    assert np.array_equal(host(w2), h.weights)
+
+
 # ------------------------------------------------------------- full runs
 @pytest.mark.parametrize("split", ["bfs", "lp", "lpp"])
 @pytest.mark.parametrize("move", ["sync", "async"])

@@ -321,6 +321,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     uint32_t *gid = arena().get<uint32_t>(n0);   // graph of each current-level vertex
     uint32_t *gid0 = arena().get<uint32_t>(n0);  // graph of each input vertex
     double *m_g = arena().get<double>(G);
+    double *minv_g = arena().get<double>(G);
     double *dq_g = arena().get<double>(G);
     uint32_t *k_g = arena().get<uint32_t>(G);
     uint8_t *live = arena().get<uint8_t>(G);
@@ -331,6 +332,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     mb.K = K;
     mb.gid = gid;
     mb.m_g = m_g;
+    mb.minv_g = minv_g;
     uint64_t *goff[2];
     uint32_t *gtgt[2];
     double *gw[2];
@@ -363,7 +365,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     std::vector<uint8_t> h_done(G, 0), h_live(G, 0), h_sel(G, 0);
     std::vector<int> h_li(G, 0);
     std::vector<uint32_t> h_k(G, 0);
-    std::vector<double> h_m(G, 0.0);
+    std::vector<double> h_m(G, 0.0), h_minv(G, 0.0);
     DevGraph cur = g0;
     double tau = o.tolerance;
     const bool split_pass = o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_PASS;
@@ -385,8 +387,10 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         for (uint32_t gi = 0; gi < G; gi++) {
             h_live[gi] = !h_done[gi] && h_m[gi] > 0.0;
             h_li[gi] = 0;
+            h_minv[gi] = h_m[gi] > 0.0 ? 1.0 / h_m[gi] : 0.0;  // graphs without edges are never scored
         }
         GSP_CUDA(cudaMemcpyAsync(live, h_live.data(), G, cudaMemcpyHostToDevice, s));
+        GSP_CUDA(cudaMemcpyAsync(minv_g, h_minv.data(), sizeof(double) * G, cudaMemcpyHostToDevice, s));
         GSP_CUDA(cudaMemcpyAsync(mb.Sigma, K, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
         iota_u32(mb.C, nv, s);
         k_fill_ones<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv);

@@ -86,6 +86,7 @@ struct MoveBuffers {
     double *m_dev = nullptr;     // device copy of m
     const uint32_t *gid = nullptr;   // batches: graph of each vertex
     const double *m_g = nullptr;     // batches: m of each graph
+    const double *minv_g = nullptr;  // batches: 1/m of each graph
     double *dq_g = nullptr;          // batches: summed gain of each graph in a sweep
     MoveCounters *ctr = nullptr;
     void *pool = nullptr;        // huge-class hashtables

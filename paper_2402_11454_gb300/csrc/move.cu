@@ -49,6 +49,7 @@ struct MoveArgs {
     // per-graph summed gains (null for a single graph)
     const uint32_t *gid;
     const double *m_g;
+    const double *minv_g;  // 1/m of each graph
     double *dq_g;
     MoveCounters *ctr;
     int rule;
@@ -166,32 +167,42 @@ template <> struct Score<true> {
     __device__ S score(double kic, double Sc) const { return eq2(kic, Kid, Ki, Sc, Sd, m); }
     __device__ double gain(S best) const { return best; }  // in units of Q
 };
+// Float64 is a narrow pipe on this GPU: the mixed-precision scores take 1/m
+// precomputed (0.5/m is 0.5 * RN(1/m) exactly, so K_i/2m is unchanged) and
+// the gain of the chosen community is a product, not a division.
 template <> struct Score<false> {
     using S = float;
     float kif, sd;
-    double m;
+    double inv_m;
     __device__ S score(float kic, double Sc) const { return kic - kif * (float)Sc; }
-    __device__ double gain(S best) const { return (double)(best - sd) / m; }
+    __device__ double gain(S best) const { return (double)(best - sd) * inv_m; }
 };
 
-template <bool F64> __device__ __forceinline__ Score<F64> make_score(double Ki, double kid, double Sd, double m);
-template <> __device__ __forceinline__ Score<true> make_score<true>(double Ki, double kid, double Sd, double m) {
+// m and inv_m = 1/m of the vertex's graph (the float64 score uses m only).
+template <bool F64>
+__device__ __forceinline__ Score<F64> make_score(double Ki, double kid, double Sd, double m, double inv_m);
+template <>
+__device__ __forceinline__ Score<true> make_score<true>(double Ki, double kid, double Sd, double m, double) {
     Score<true> s;
     s.Ki = Ki; s.Kid = kid; s.Sd = Sd; s.m = m;
     return s;
 }
-template <> __device__ __forceinline__ Score<false> make_score<false>(double Ki, double kid, double Sd, double m) {
+template <>
+__device__ __forceinline__ Score<false> make_score<false>(double Ki, double kid, double Sd, double, double inv_m) {
     Score<false> s;
-    double inv2m = 0.5 / m;
+    const double inv2m = 0.5 * inv_m;
     s.kif = (float)(Ki * inv2m);
     s.sd = (float)kid - s.kif * (float)(Sd - Ki);
-    s.m = m;
+    s.inv_m = inv_m;
     return s;
 }
 
 // m of vertex i's graph (batches) or of the single graph.
 __device__ __forceinline__ double vertex_m(const MoveArgs &a, uint32_t i, double m0) {
     return a.gid ? a.m_g[a.gid[i]] : m0;
+}
+__device__ __forceinline__ double vertex_inv_m(const MoveArgs &a, uint32_t i, double inv0) {
+    return a.gid ? a.minv_g[a.gid[i]] : inv0;
 }
 __device__ __forceinline__ void add_graph_gain(const MoveArgs &a, uint32_t i, double gain) {
     if (a.dq_g) atomicAdd(a.dq_g + a.gid[i], gain);
@@ -290,6 +301,7 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
     V *vals = reinterpret_cast<V *>(smem + (size_t)NG * CAP * sizeof(uint32_t)) + grp * CAP;
     const WT *w = static_cast<const WT *>(a.w);
     const double m0 = *a.m;
+    const double inv0 = 1.0 / m0;
     // counters accumulate in the caller's lc
     // The warp's list entries are wbase, wbase + wstep, ...; 32 of them are
     // claimed at once (each lane reads one flag and marks its vertex
@@ -333,7 +345,7 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         double Sd = ld_state<SYNC>(a.Sig + d);
         Sd = __shfl_sync(gmask, Sd, leader);
         const double m = vertex_m(a, i, m0);
-        SC sc = make_score<F64>(Ki, (double)kid, Sd, m);
+        SC sc = make_score<F64>(Ki, (double)kid, Sd, m, vertex_inv_m(a, i, inv0));
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
         uint32_t ncand = 0;
@@ -432,6 +444,7 @@ __device__ void block_body(const MoveArgs &a, const uint32_t *__restrict__ list,
     __shared__ double s_Sd;
     const WT *w = static_cast<const WT *>(a.w);
     const double m0 = *a.m;
+    const double inv0 = 1.0 / m0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     // counters accumulate in the caller's lc
@@ -488,7 +501,7 @@ __device__ void block_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         for (int t = 0; t < nw; t++) kid += red_k[t];
         double Ki = a.K[i];
         const double m = vertex_m(a, i, m0);
-        SC sc = make_score<F64>(Ki, (double)kid, s_Sd, m);
+        SC sc = make_score<F64>(Ki, (double)kid, s_Sd, m, vertex_inv_m(a, i, inv0));
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
         uint32_t nocc = s_nocc;
@@ -854,6 +867,7 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
     const V *kidv = static_cast<const V *>(h.kid);
     S *bs = static_cast<S *>(h.best_s);
     const double m0 = *a.m;
+    const double inv0 = 1.0 / m0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t base = h.tasks[0], total = h.tasks[h.nh] - base;
     for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
@@ -865,7 +879,8 @@ __global__ void __launch_bounds__(256) k_hub_score(MoveArgs a, HubArgs h) {
         V *vals = static_cast<V *>(h.vals) + h.pool_off[t];
         const uint32_t *occ = h.occ + h.pool_off[t];
         uint64_t k1 = min(k0 + HUB_CHUNK, (uint64_t)h.occ_n[t]);
-        SC sc = make_score<F64>(a.K[i], (double)kidv[t], ld_state<SYNC>(a.Sig + d), vertex_m(a, i, m0));
+        SC sc = make_score<F64>(a.K[i], (double)kidv[t], ld_state<SYNC>(a.Sig + d), vertex_m(a, i, m0),
+                                vertex_inv_m(a, i, inv0));
         S best = -INFINITY;
         uint32_t bestc = EMPTY;
         // U entries per thread per round; each level of the gather chain
@@ -920,6 +935,7 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h) {
     const V *kidv = static_cast<const V *>(h.kid);
     const S *bs = static_cast<const S *>(h.best_s);
     const double m0 = *a.m;
+    const double inv0 = 1.0 / m0;
     const int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -945,7 +961,7 @@ __global__ void k_hub_decide(MoveArgs a, HubArgs h) {
             double Ki = a.K[i];
             uint64_t deg = a.off[i + 1] - a.off[i];
             const double m = vertex_m(a, i, m0);
-            SC sc = make_score<F64>(Ki, (double)kidv[t], ld_state<SYNC>(a.Sig + d), m);
+            SC sc = make_score<F64>(Ki, (double)kidv[t], ld_state<SYNC>(a.Sig + d), m, vertex_inv_m(a, i, inv0));
             double gain = (bestc == EMPTY) ? 0.0 : sc.gain(best);
             int mv = 0;
             if (gain > 0.0) mv = decide_move<SYNC>(a, i, d, bestc, Ki);
@@ -1240,6 +1256,7 @@ static MoveArgs make_move_args(const DevGraph &g, const MoveBuffers &mb, bool sy
     a.m = mb.m_dev;
     a.gid = mb.gid;
     a.m_g = mb.m_g;
+    a.minv_g = mb.minv_g;
     a.dq_g = mb.dq_g;
     a.ctr = mb.ctr;
     a.rule = rule ? 1 : 0;

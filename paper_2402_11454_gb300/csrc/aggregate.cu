@@ -136,79 +136,6 @@ struct AggArgs {
     int xlsb;  // exact fixed-point accumulation: values in integer units of 2^xlsb
 };
 
-// Table values are accumulated either as float64 (AV = double) or, when every
-// weight of the graph is a multiple of 2^lsb and the total weight is below
-// 2^52 units, as 64-bit integers in units of 2^lsb (AV = unsigned long long),
-// whose shared-memory atomic add is a single native operation; a float32 or
-// float64 weight becomes its integer mantissa shifted by its exponent, with no
-// floating-point arithmetic.  Both sum exactly, so they give identical tables.
-__device__ __forceinline__ unsigned long long units_of(float x, int lsb) {
-    const uint32_t b = __float_as_uint(x);
-    const int e = (int)((b >> 23) & 0xFFu);
-    const unsigned long long m = e ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
-    const int sh = (e ? e : 1) - 150 - lsb;  // x = m * 2^(sh + lsb); sh >= -ctz(m)
-    return sh >= 0 ? m << sh : m >> -sh;
-}
-__device__ __forceinline__ unsigned long long units_of(double x, int lsb) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7FFu);
-    const unsigned long long m = e ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : (b & 0xFFFFFFFFFFFFFull);
-    const int sh = (e ? e : 1) - 1075 - lsb;
-    return sh >= 0 ? m << sh : m >> -sh;
-}
-template <typename AV> struct Acc;
-template <> struct Acc<double> {
-    template <typename WT> __device__ static double of(WT x, int) { return (double)x; }
-    __device__ static double val(double v, int) { return v; }
-};
-template <> struct Acc<unsigned long long> {
-    template <typename WT> __device__ static unsigned long long of(WT x, int lsb) { return units_of(x, lsb); }
-    // v < 2^52: the conversion is exact, and so is the power-of-two scaling
-    // done on the exponent field (lsb >= -1000 keeps the result normal)
-    __device__ static double val(unsigned long long v, int lsb) {
-        if (!v) return 0.0;
-        const double d = (double)v;
-        return __longlong_as_double(__double_as_longlong(d) + ((long long)lsb << 52));
-    }
-};
-
-// Exponent of the lowest set bit of a positive finite weight (INT_MIN for a
-// value that is not, INT_MAX for zero).
-__device__ __forceinline__ int low_bit_exp(float x) {
-    const uint32_t b = __float_as_uint(x);
-    const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
-    if ((b >> 31) || e == 0xFFu) return INT_MIN;
-    if (e == 0) return m ? -149 + (__ffs((int)m) - 1) : INT_MAX;
-    return (int)e - 150 + (__ffs((int)(m | 0x800000u)) - 1);
-}
-__device__ __forceinline__ int low_bit_exp(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7FFu);
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-    if ((b >> 63) || e == 0x7FF) return INT_MIN;
-    if (e == 0) return m ? -1074 + (__ffsll((long long)m) - 1) : INT_MAX;
-    return e - 1075 + (__ffsll((long long)(m | (1ull << 52))) - 1);
-}
-
-// Smallest lowest-set-bit exponent over the weights and their (rounded) sum.
-template <typename WT>
-__global__ void k_weight_range(const WT *__restrict__ w, uint64_t nnz, int *minlow, double *sum) {
-    int lo = INT_MAX;
-    float acc = 0.0f;  // an estimate for the range test (float64 is slow here)
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
-        const WT x = w[p];
-        lo = min(lo, low_bit_exp(x));
-        acc += (float)x;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(minlow, lo);
-        atomicAdd(sum, (double)acc);
-    }
-}
-
 // Append the occupied slots of a table to row c of the holey CSR.
 __device__ __forceinline__ void emit_slot(const AggArgs &a, uint32_t c, uint32_t key, double val, bool valid,
                                           uint32_t *cursor) {
@@ -782,34 +709,6 @@ static int ceil_log2_host(uint64_t x) {
 }
 
 
-// Exponent lsb such that every weight of g is a multiple of 2^lsb and the total
-// weight is below 2^52 * 2^lsb (then every table sum is an integer number of
-// units below 2^52, exact both as uint64 and as float64); INT_MIN when no
-// such exponent in [-1000, 1000] exists (zero, negative or non-finite
-// weights, or too wide a range of magnitudes).
-template <typename WT>
-static int exact_lsb(const DevGraph &g, cudaStream_t s) {
-    if (!g.nnz || !g.w) return INT_MIN;
-    size_t mk = arena().mark();
-    int *dlo = arena().get<int>(1);
-    double *dsum = arena().get<double>(1);
-    const int init = INT_MAX;
-    GSP_CUDA(cudaMemcpyAsync(dlo, &init, sizeof(int), cudaMemcpyHostToDevice, s));
-    GSP_CUDA(cudaMemsetAsync(dsum, 0, sizeof(double), s));
-    k_weight_range<WT><<<grid_for(g.nnz, 256, sms(8)), 256, 0, s>>>(static_cast<const WT *>(g.w), g.nnz, dlo, dsum);
-    GSP_CHECK_LAUNCH();
-    int lo = 0;
-    double sum = 0.0;
-    GSP_CUDA(cudaMemcpyAsync(&lo, dlo, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GSP_CUDA(cudaMemcpyAsync(&sum, dsum, sizeof(double), cudaMemcpyDeviceToHost, s));
-    GSP_CUDA(cudaStreamSynchronize(s));
-    arena().release(mk);
-    if (lo < -1000 || lo > 1000) return INT_MIN;
-    // the float64 sum is rounded: keep a factor 2 of margin below 2^53
-    if (!(sum > 0.0) || !(sum < std::ldexp(1.0, 52 + lo))) return INT_MIN;
-    return lo;
-}
-
 // Per-community tables of the three size classes, emitted into the holey CSR.
 template <typename WT, typename AV>
 static void merge_tables(const DevGraph &g, const AggArgs &a, const IdClasses &ic, const unsigned long long *cdeg,
@@ -923,7 +822,7 @@ static uint64_t aggregate_impl(const DevGraph &g, const uint32_t *Cd, uint32_t k
     // exact fixed-point table values when the weights allow it (same result,
     // native shared-memory integer atomics instead of float64 ones)
     int lsb = lsb_cache ? *lsb_cache : INT_MAX;
-    if (lsb == INT_MAX) lsb = exact_lsb<WT>(g, s);
+    if (lsb == INT_MAX) lsb = exact_lsb(g, s);
     if (lsb_cache) *lsb_cache = lsb;
     if (lsb != INT_MIN) {
         a.xlsb = lsb;

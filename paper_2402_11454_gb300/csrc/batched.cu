@@ -118,25 +118,26 @@ __global__ void k_lookup_open(uint32_t *C_top, const uint32_t *__restrict__ Cd, 
 
 // Equation 1 per graph on the input graphs, with the union-wide community ids
 // C: 2m, the intra-community weight and Sigma of each community.
-template <typename WT>
+template <typename WT, typename AV>
 __global__ void k_graph_q_rows(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                                const WT *__restrict__ w, const uint32_t *__restrict__ C,
                                const uint32_t *__restrict__ gid0, uint32_t n0, double *two_m, double *intra,
-                               double *Sig, uint32_t *comm_graph) {
+                               double *Sig, uint32_t *comm_graph, int lsb) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n0; v += gridDim.x * blockDim.x) {
-        double k = 0, in = 0;
+        AV k = 0, in = 0;
         const uint32_t cv = C[v], g = gid0[v];
         for (uint64_t p = off[v]; p < off[v + 1]; p++) {
-            double x = (double)w[p];
+            const AV x = Acc<AV>::of(w[p], lsb);
             k += x;
             if (C[tgt[p]] == cv) in += x;
         }
         comm_graph[cv] = g;  // every member writes the same value
-        if (k != 0.0) {
-            atomicAdd(two_m + g, k);
-            atomicAdd(Sig + cv, k);
+        if (k != AV(0)) {
+            const double kd = Acc<AV>::val(k, lsb);
+            atomicAdd(two_m + g, kd);
+            atomicAdd(Sig + cv, kd);
         }
-        if (in != 0.0) atomicAdd(intra + g, in);
+        if (in != AV(0)) atomicAdd(intra + g, Acc<AV>::val(in, lsb));
     }
 }
 __global__ void k_graph_q_sq(const double *__restrict__ Sig, const uint32_t *__restrict__ comm_graph, uint32_t k,
@@ -371,14 +372,17 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     const bool split_pass = o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_PASS;
     uint32_t *Cp = mb.C;
     int pb = 0, passes = 0;
-    int lsb_cache = INT_MAX;  // fixed-point unit of the weights, found at the first aggregation
+    // exact integer unit of the input weights (INT_MIN: float64 sums), valid
+    // for every pass: aggregated weights are sums of input weights
+    int lsb_cache = exact_lsb(g0, s);
+    mb.lsb = lsb_cache;
     uint32_t remaining = G;
     for (int lp = 0; lp < o.max_passes && remaining; lp++) {
         const uint32_t nv = cur.n;
         size_t pass_mark = arena().mark();
         lap();
         // K' = Sigma' = vertexWeights(G'), C' = identity; each graph's m
-        vertex_weights(cur, K, mb.m_dev, s);
+        vertex_weights(cur, K, mb.m_dev, s, lsb_cache);
         GSP_CUDA(cudaMemsetAsync(m_g, 0, sizeof(double) * G, s));
         k_graph_m<<<grid_for(nv, 256), 256, 0, s>>>(K, gid, nv, m_g);
         GSP_CHECK_LAUNCH();
@@ -517,14 +521,18 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         GSP_CUDA(cudaMemsetAsync(intra, 0, sizeof(double) * G, s));
         GSP_CUDA(cudaMemsetAsync(sumsq, 0, sizeof(double) * G, s));
         GSP_CUDA(cudaMemsetAsync(Sig, 0, sizeof(double) * kf, s));
-        if (g0.wt == GSP_W_F64)
-            k_graph_q_rows<double><<<grid_for(n0, 256), 256, 0, s>>>(
-                g0.off, g0.tgt, static_cast<const double *>(g0.w), membership, gid0, n0, two_m, intra, Sig,
-                comm_graph);
-        else
-            k_graph_q_rows<float><<<grid_for(n0, 256), 256, 0, s>>>(
-                g0.off, g0.tgt, static_cast<const float *>(g0.w), membership, gid0, n0, two_m, intra, Sig,
-                comm_graph);
+#define GSP_QROWS(WT, AV)                                                                                 \
+    k_graph_q_rows<WT, AV><<<grid_for(n0, 256), 256, 0, s>>>(g0.off, g0.tgt, static_cast<const WT *>(g0.w),   \
+                                                              membership, gid0, n0, two_m, intra, Sig, comm_graph, \
+                                                              lsb_cache)
+        if (g0.wt == GSP_W_F64) {
+            if (lsb_cache != INT_MIN) GSP_QROWS(double, unsigned long long);
+            else GSP_QROWS(double, double);
+        } else {
+            if (lsb_cache != INT_MIN) GSP_QROWS(float, unsigned long long);
+            else GSP_QROWS(float, double);
+        }
+#undef GSP_QROWS
         GSP_CHECK_LAUNCH();
         k_graph_q_sq<<<grid_for(kf, 256), 256, 0, s>>>(Sig, comm_graph, kf, sumsq);
         GSP_CHECK_LAUNCH();

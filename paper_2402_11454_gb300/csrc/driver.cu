@@ -481,13 +481,16 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     int passes = 0;
     uint32_t *Cp = mb.C;  // membership of the current graph's vertices
     int pb = 0;
-    int lsb_cache = INT_MAX;  // fixed-point unit of the weights, found at the first aggregation
+    // exact integer unit of the input weights (INT_MIN: float64 sums), valid
+    // for every pass: aggregated weights are sums of input weights
+    int lsb_cache = exact_lsb(g0, s);
+    mb.lsb = lsb_cache;
     for (int lp = 0; lp < o.max_passes; lp++) {
         const uint32_t nv = cur.n;
         size_t pass_mark = arena().mark();
         t.lap();
         // K' = Sigma' = vertexWeights(G'), C' = [0..|V'|), all unprocessed
-        double m = vertex_weights(cur, K, mb.m_dev, s);
+        double m = vertex_weights(cur, K, mb.m_dev, s, lsb_cache);
         GSP_CUDA(cudaMemcpyAsync(mb.Sigma, K, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
         iota_u32(mb.C, nv, s);
         k_fill_u32_<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
@@ -560,7 +563,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         GSP_CUDA(cudaMemcpyAsync(membership, labels, sizeof(uint32_t) * n0, cudaMemcpyDeviceToDevice, s));
     }
     uint32_t kf = canonical_numbering(n0, membership, s);
-    double q = modularity(g0, membership, s);
+    double q = modularity(g0, membership, s, lsb_cache);
     local.passes = passes;
     local.final_communities = kf;
     local.modularity = q;
@@ -712,7 +715,7 @@ gsp_status gsp_vertex_weights(const uint64_t *offsets, const uint32_t *targets, 
     DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
     GSP_REQUIRE(K != nullptr, "K must not be NULL");
     arena().reset();
-    double m = vertex_weights(g, K, nullptr, S(stream));
+    double m = vertex_weights(g, K, nullptr, S(stream), exact_lsb(g, S(stream)));
     if (m_host) *m_host = m;
     GSP_API_END
 }
@@ -724,7 +727,7 @@ gsp_status gsp_modularity(const uint64_t *offsets, const uint32_t *targets, cons
     GSP_REQUIRE(C != nullptr && q_host != nullptr, "C and q_host must not be NULL");
     arena().reset();
     check_ids(C, n, n, "membership", S(stream));
-    *q_host = modularity(g, C, S(stream));
+    *q_host = modularity(g, C, S(stream), exact_lsb(g, S(stream)));
     GSP_API_END
 }
 

@@ -1,5 +1,7 @@
 // internal.cuh -- host-side interfaces between the translation units of libgsp.
 #pragma once
+
+#include <climits>
 #include <vector>
 
 #include "common.cuh"
@@ -87,6 +89,7 @@ struct MoveBuffers {
     const uint32_t *gid = nullptr;   // batches: graph of each vertex
     const double *m_g = nullptr;     // batches: m of each graph
     const double *minv_g = nullptr;  // batches: 1/m of each graph
+    int lsb = INT_MIN;               // weights in exact integer units of 2^lsb (exact_lsb)
     double *dq_g = nullptr;          // batches: summed gain of each graph in a sweep
     MoveCounters *ctr = nullptr;
     void *pool = nullptr;        // huge-class hashtables
@@ -168,9 +171,16 @@ uint32_t renumber(uint32_t n, const uint32_t *C, uint32_t *C_dense, cudaStream_t
 uint64_t aggregate(const DevGraph &g, const uint32_t *Cd, uint32_t k, uint64_t *out_off, uint32_t *out_tgt,
                    double *out_w, cudaStream_t s, bool sorted = true, int *lsb_cache = nullptr);
 
-// K and m (m also written to *m_dev when non-null); returns m.
-double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t s);
-double modularity(const DevGraph &g, const uint32_t *C, cudaStream_t s);
+// Exponent lsb such that every weight of g is a multiple of 2^lsb and the
+// total weight is below 2^52 * 2^lsb, or INT_MIN (then sums stay float64).
+// Aggregated graphs carry sums of the input weights, so the input's lsb holds
+// for every pass of a run.
+int exact_lsb(const DevGraph &g, cudaStream_t s);
+
+// K and m (m also written to *m_dev when non-null); returns m.  lsb: the
+// graph's exact_lsb (INT_MIN: float64 sums).
+double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t s, int lsb = INT_MIN);
+double modularity(const DevGraph &g, const uint32_t *C, cudaStream_t s, int lsb = INT_MIN);
 double modularity_scratch(const DevGraph &g, const uint32_t *C, double *Sig, double *acc, uint32_t *longlist,
                           uint32_t *nlong, cudaStream_t s);
 unsigned long long count_out_of_range(const uint32_t *x, uint32_t n, uint32_t bound, unsigned long long *counter,
@@ -333,6 +343,62 @@ __device__ __forceinline__ void smem_add(uint32_t *skeys, V *svals, int slog, ui
                                          uint32_t c, V w) {
     uint32_t slot;
     if (ht_add_slot<V>(skeys, svals, slog, c, w, &slot) == 1) socc[atomicAdd(s_nocc, 1u)] = (uint16_t)slot;
+}
+
+// Exact sums of edge weights.  They are accumulated either as float64
+// (AV = double) or, when every weight of the graph is a multiple of 2^lsb and
+// the total weight is below 2^52 units (exact_lsb), as 64-bit integers in
+// units of 2^lsb (AV = unsigned long long): a float32 or float64 weight
+// becomes its integer mantissa shifted by its exponent, with no floating-point
+// arithmetic (float64 is a narrow pipe on this GPU), and a shared-memory
+// integer atomic add is a single native operation.  Both sum exactly, so they
+// give identical results.
+__device__ __forceinline__ unsigned long long units_of(float x, int lsb) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const unsigned long long m = e ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
+    const int sh = (e ? e : 1) - 150 - lsb;  // x = m * 2^(sh + lsb); sh >= -ctz(m)
+    return sh >= 0 ? m << sh : m >> -sh;
+}
+__device__ __forceinline__ unsigned long long units_of(double x, int lsb) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    const unsigned long long m = e ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : (b & 0xFFFFFFFFFFFFFull);
+    const int sh = (e ? e : 1) - 1075 - lsb;
+    return sh >= 0 ? m << sh : m >> -sh;
+}
+template <typename AV> struct Acc;
+template <> struct Acc<double> {
+    template <typename WT> __device__ static double of(WT x, int) { return (double)x; }
+    __device__ static double val(double v, int) { return v; }
+};
+template <> struct Acc<unsigned long long> {
+    template <typename WT> __device__ static unsigned long long of(WT x, int lsb) { return units_of(x, lsb); }
+    // v < 2^52: the conversion is exact, and so is the power-of-two scaling
+    // done on the exponent field (lsb >= -1000 keeps the result normal)
+    __device__ static double val(unsigned long long v, int lsb) {
+        if (!v) return 0.0;
+        const double d = (double)v;
+        return __longlong_as_double(__double_as_longlong(d) + ((long long)lsb << 52));
+    }
+};
+
+// Exponent of the lowest set bit of a positive finite weight (INT_MIN for a
+// value that is not, INT_MAX for zero).
+__device__ __forceinline__ int low_bit_exp(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    if ((b >> 31) || e == 0xFFu) return INT_MIN;
+    if (e == 0) return m ? -149 + (__ffs((int)m) - 1) : INT_MAX;
+    return (int)e - 150 + (__ffs((int)(m | 0x800000u)) - 1);
+}
+__device__ __forceinline__ int low_bit_exp(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if ((b >> 63) || e == 0x7FF) return INT_MIN;
+    if (e == 0) return m ? -1074 + (__ffsll((long long)m) - 1) : INT_MAX;
+    return e - 1075 + (__ffsll((long long)(m | (1ull << 52))) - 1);
 }
 
 // Chunked work over items (hubs, communities) of different sizes: task ids

@@ -5,11 +5,64 @@
 // Row sums use one thread per row up to 64 entries and one block per longer
 // row.  All float64 sums here add float32-representable weights whose partial
 // sums stay exactly representable, so they do not depend on the order.
+#include <cmath>
+
 #include "internal.cuh"
 
 namespace gsp {
 
 constexpr uint32_t SHORT_ROW = 64;
+
+// Smallest lowest-set-bit exponent over the weights and their (rounded) sum.
+template <typename WT>
+__global__ void k_weight_range(const WT *__restrict__ w, uint64_t nnz, int *minlow, double *sum) {
+    int lo = INT_MAX;
+    float acc = 0.0f;  // an estimate for the range test (float64 is slow here)
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const WT x = w[p];
+        lo = min(lo, low_bit_exp(x));
+        acc += (float)x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(minlow, lo);
+        atomicAdd(sum, (double)acc);
+    }
+}
+
+// Every sum of weights is then an integer number of units below 2^52, exact
+// both as uint64 and as float64; INT_MIN when no such exponent in
+// [-1000, 1000] exists (zero, negative or non-finite weights, or too wide a
+// range of magnitudes).
+template <typename WT>
+static int exact_lsb_t(const DevGraph &g, cudaStream_t s) {
+    if (!g.nnz || !g.w) return INT_MIN;
+    size_t mk = arena().mark();
+    int *dlo = arena().get<int>(1);
+    double *dsum = arena().get<double>(1);
+    const int init = INT_MAX;
+    GSP_CUDA(cudaMemcpyAsync(dlo, &init, sizeof(int), cudaMemcpyHostToDevice, s));
+    GSP_CUDA(cudaMemsetAsync(dsum, 0, sizeof(double), s));
+    k_weight_range<WT><<<grid_for(g.nnz, 256, sms(8)), 256, 0, s>>>(static_cast<const WT *>(g.w), g.nnz, dlo, dsum);
+    GSP_CHECK_LAUNCH();
+    int lo = 0;
+    double sum = 0.0;
+    GSP_CUDA(cudaMemcpyAsync(&lo, dlo, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaMemcpyAsync(&sum, dsum, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    arena().release(mk);
+    if (lo < -1000 || lo > 1000) return INT_MIN;
+    // the float64 sum is rounded: keep a factor 2 of margin below 2^53
+    if (!(sum > 0.0) || !(sum < std::ldexp(1.0, 52 + lo))) return INT_MIN;
+    return lo;
+}
+
+int exact_lsb(const DevGraph &g, cudaStream_t s) {
+    return g.wt == GSP_W_F64 ? exact_lsb_t<double>(g, s) : exact_lsb_t<float>(g, s);
+}
+
 
 __global__ void k_iota(uint32_t *p, uint32_t n) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
@@ -40,27 +93,27 @@ void task_items(const uint64_t *prefix, uint32_t nitems, uint32_t *out, cudaStre
 // Per row i: K_i, and the intra-community part sum_{j: C_j = C_i} w_ij when C
 // is given; Sigma_c += K_i when Sig is given.  Long rows are deferred to a
 // list for the block kernel.
-template <typename WT>
+template <typename WT, typename AV>
 __global__ void k_row_sums(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                            const WT *__restrict__ w, uint32_t n, const uint32_t *__restrict__ C, double *K,
-                           double *Sig, double *acc /* [0]=2m, [1]=intra */, uint32_t *longlist,
-                           uint32_t *nlong) {
-    __shared__ double red[32];
-    double two_m = 0, intra = 0;
+                           double *Sig, AV *acc /* [0]=2m, [1]=intra */, uint32_t *longlist,
+                           uint32_t *nlong, int lsb) {
+    __shared__ AV red[32];
+    AV two_m = 0, intra = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         uint64_t b = off[i], e = off[i + 1];
         if (e - b > SHORT_ROW) {
             longlist[atomicAdd(nlong, 1u)] = i;
             continue;
         }
-        double k = 0, in = 0;
+        AV k = 0, in = 0;
         uint32_t ci = C ? C[i] : 0;
         uint64_t p = b;
         for (; p + 4 <= e; p += 4) {  // four independent loads in flight
-            double wv[4];
+            AV wv[4];
             uint32_t cj[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) wv[u] = (double)w[p + u];
+            for (int u = 0; u < 4; u++) wv[u] = Acc<AV>::of(w[p + u], lsb);
             if (C) {
 #pragma unroll
                 for (int u = 0; u < 4; u++) cj[u] = C[tgt[p + u]];
@@ -72,12 +125,13 @@ __global__ void k_row_sums(const uint64_t *__restrict__ off, const uint32_t *__r
             }
         }
         for (; p < e; p++) {
-            double wv = (double)w[p];
+            const AV wv = Acc<AV>::of(w[p], lsb);
             k += wv;
             if (C && C[tgt[p]] == ci) in += wv;
         }
-        if (K) K[i] = k;
-        if (Sig) atomicAdd(Sig + ci, k);
+        const double kd = Acc<AV>::val(k, lsb);
+        if (K) K[i] = kd;
+        if (Sig) atomicAdd(Sig + ci, kd);
         two_m += k;
         intra += in;
     }
@@ -92,28 +146,28 @@ __global__ void k_row_sums(const uint64_t *__restrict__ off, const uint32_t *__r
 // Long rows: one warp per row up to 8192 entries, one block per longer row.
 constexpr uint32_t WARP_ROW = 8192;
 
-template <typename WT>
+template <typename WT, typename AV>
 __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
                                 const WT *__restrict__ w, const uint32_t *__restrict__ C, double *K, double *Sig,
-                                double *acc, const uint32_t *longlist, const uint32_t *nlong) {
-    __shared__ double red[32];
+                                AV *acc, const uint32_t *longlist, const uint32_t *nlong, int lsb) {
+    __shared__ AV red[32];
     uint32_t cnt = *nlong;
     const int lane = threadIdx.x & 31;
     uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    double wk = 0, win = 0;
+    AV wk = 0, win = 0;
     for (uint32_t t = warp; t < cnt; t += nwarps) {
         uint32_t i = longlist[t];
         uint64_t b = off[i], e = off[i + 1];
         if (e - b > WARP_ROW) continue;
         uint32_t ci = C ? C[i] : 0;
-        double k = 0, in = 0;
+        AV k = 0, in = 0;
         uint64_t p = b + lane;
         for (; p + 96 < e; p += 128) {  // four independent loads per lane in flight
-            double wv[4];
+            AV wv[4];
             uint32_t cj[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) wv[u] = (double)w[p + 32 * u];
+            for (int u = 0; u < 4; u++) wv[u] = Acc<AV>::of(w[p + 32 * u], lsb);
             if (C) {
 #pragma unroll
                 for (int u = 0; u < 4; u++) cj[u] = C[tgt[p + 32 * u]];
@@ -125,15 +179,16 @@ __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t
             }
         }
         for (; p < e; p += 32) {
-            double wv = (double)w[p];
+            const AV wv = Acc<AV>::of(w[p], lsb);
             k += wv;
             if (C && C[tgt[p]] == ci) in += wv;
         }
         k = warp_sum(k);
         in = warp_sum(in);
         if (lane == 0) {
-            if (K) K[i] = k;
-            if (Sig) atomicAdd(Sig + ci, k);
+            const double kd = Acc<AV>::val(k, lsb);
+            if (K) K[i] = kd;
+            if (Sig) atomicAdd(Sig + ci, kd);
             wk += k;
             win += in;
         }
@@ -144,14 +199,14 @@ __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t
         uint64_t b = off[i], e = off[i + 1];
         if (e - b <= WARP_ROW) continue;
         uint32_t ci = C ? C[i] : 0;
-        double k = 0, in = 0;
+        AV k = 0, in = 0;
         uint64_t p = b + threadIdx.x;
         const uint64_t st = blockDim.x;
         for (; p + 3 * st < e; p += 4 * st) {
-            double wv[4];
+            AV wv[4];
             uint32_t cj[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) wv[u] = (double)w[p + st * u];
+            for (int u = 0; u < 4; u++) wv[u] = Acc<AV>::of(w[p + st * u], lsb);
             if (C) {
 #pragma unroll
                 for (int u = 0; u < 4; u++) cj[u] = C[tgt[p + st * u]];
@@ -163,15 +218,16 @@ __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t
             }
         }
         for (; p < e; p += st) {
-            double wv = (double)w[p];
+            const AV wv = Acc<AV>::of(w[p], lsb);
             k += wv;
             if (C && C[tgt[p]] == ci) in += wv;
         }
         k = block_sum(k, red);
         in = block_sum(in, red);
         if (threadIdx.x == 0) {
-            if (K) K[i] = k;
-            if (Sig) atomicAdd(Sig + ci, k);
+            const double kd = Acc<AV>::val(k, lsb);
+            if (K) K[i] = kd;
+            if (Sig) atomicAdd(Sig + ci, kd);
             wk += k;
             win += in;
         }
@@ -179,37 +235,55 @@ __global__ void k_row_sums_long(const uint64_t *__restrict__ off, const uint32_t
     wk = block_sum(wk, red);
     win = block_sum(win, red);
     if (threadIdx.x == 0) {
-        if (wk != 0.0) atomicAdd(acc, wk);
-        if (C && win != 0.0) atomicAdd(acc + 1, win);
+        if (wk != AV(0)) atomicAdd(acc, wk);
+        if (C && win != AV(0)) atomicAdd(acc + 1, win);
     }
 }
 
-template <typename WT>
-static void row_sums(const DevGraph &g, const uint32_t *C, double *K, double *Sig, double *acc, cudaStream_t s) {
+template <typename WT, typename AV>
+static void row_sums(const DevGraph &g, const uint32_t *C, double *K, double *Sig, AV *acc, int lsb, cudaStream_t s) {
     size_t mk = arena().mark();
     uint32_t *longlist = arena().get<uint32_t>(g.n + 1);
     uint32_t *nlong = arena().get<uint32_t>(1);
     GSP_CUDA(cudaMemsetAsync(nlong, 0, sizeof(uint32_t), s));
     const WT *w = static_cast<const WT *>(g.w);
-    k_row_sums<WT><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, K, Sig, acc, longlist, nlong);
+    k_row_sums<WT, AV><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, K, Sig, acc, longlist, nlong, lsb);
     GSP_CHECK_LAUNCH();
-    k_row_sums_long<WT><<<sms(4), 256, 0, s>>>(g.off, g.tgt, w, C, K, Sig, acc, longlist, nlong);
+    k_row_sums_long<WT, AV><<<sms(4), 256, 0, s>>>(g.off, g.tgt, w, C, K, Sig, acc, longlist, nlong, lsb);
     GSP_CHECK_LAUNCH();
     arena().release(mk);
 }
 
-static void row_sums_any(const DevGraph &g, const uint32_t *C, double *K, double *Sig, double *acc, cudaStream_t s) {
-    if (g.wt == GSP_W_F64) row_sums<double>(g, C, K, Sig, acc, s);
-    else row_sums<float>(g, C, K, Sig, acc, s);
+// x[k] = u[k] units of 2^lsb as float64 (exact: u < 2^52).
+__global__ void k_units_to_f64(const unsigned long long *u, int cnt, int lsb, double *x) {
+    if ((int)threadIdx.x < cnt) x[threadIdx.x] = Acc<unsigned long long>::val(u[threadIdx.x], lsb);
+}
+
+// Row sums into float64 accumulators (acc: [0] = 2m, [1] = intra), or, when
+// lsb != INT_MIN, in integer units accumulated in acc_u and converted here
+// (exactly) into the same float64 values.
+static void row_sums_any(const DevGraph &g, const uint32_t *C, double *K, double *Sig, double *acc,
+                         unsigned long long *acc_u, int lsb, cudaStream_t s) {
+    if (lsb != INT_MIN) {
+        if (g.wt == GSP_W_F64) row_sums<double, unsigned long long>(g, C, K, Sig, acc_u, lsb, s);
+        else row_sums<float, unsigned long long>(g, C, K, Sig, acc_u, lsb, s);
+        k_units_to_f64<<<1, 32, 0, s>>>(acc_u, 2, lsb, acc);
+        GSP_CHECK_LAUNCH();
+        return;
+    }
+    if (g.wt == GSP_W_F64) row_sums<double, double>(g, C, K, Sig, acc, INT_MIN, s);
+    else row_sums<float, double>(g, C, K, Sig, acc, INT_MIN, s);
 }
 
 __global__ void k_half(const double *acc, double *m_dev) { *m_dev = acc[0] / 2.0; }
 
-double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t s) {
+double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t s, int lsb) {
     size_t mk = arena().mark();
     double *acc = arena().get<double>(2);
+    unsigned long long *acc_u = arena().get<unsigned long long>(2);
     GSP_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(double), s));
-    row_sums_any(g, nullptr, K, nullptr, acc, s);
+    GSP_CUDA(cudaMemsetAsync(acc_u, 0, 2 * sizeof(unsigned long long), s));
+    row_sums_any(g, nullptr, K, nullptr, acc, acc_u, lsb, s);
     if (m_dev) {
         k_half<<<1, 1, 0, s>>>(acc, m_dev);
         GSP_CHECK_LAUNCH();
@@ -234,13 +308,15 @@ __global__ void k_sum_sq(const double *Sig, uint32_t n, double *out) {
 
 // Equation 1, second form: Q = sum_c sigma_c / 2m - sum_c (Sigma_c / 2m)^2,
 // with sum_c sigma_c = the weight of all intra-community entries.
-double modularity(const DevGraph &g, const uint32_t *C, cudaStream_t s) {
+double modularity(const DevGraph &g, const uint32_t *C, cudaStream_t s, int lsb) {
     size_t mk = arena().mark();
     double *acc = arena().get<double>(4);
+    unsigned long long *acc_u = arena().get<unsigned long long>(2);
     double *Sig = arena().get<double>(g.n);
     GSP_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
+    GSP_CUDA(cudaMemsetAsync(acc_u, 0, 2 * sizeof(unsigned long long), s));
     GSP_CUDA(cudaMemsetAsync(Sig, 0, sizeof(double) * g.n, s));
-    row_sums_any(g, C, nullptr, Sig, acc, s);
+    row_sums_any(g, C, nullptr, Sig, acc, acc_u, lsb, s);
     k_sum_sq<<<grid_for(g.n, 256), 256, 0, s>>>(Sig, g.n, acc + 2);
     GSP_CHECK_LAUNCH();
     double h[4];
@@ -262,9 +338,11 @@ static double modularity_scratch_t(const DevGraph &g, const uint32_t *C, double 
     GSP_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
     GSP_CUDA(cudaMemsetAsync(Sig, 0, sizeof(double) * g.n, s));
     GSP_CUDA(cudaMemsetAsync(nlong, 0, sizeof(uint32_t), s));
-    k_row_sums<WT><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, nullptr, Sig, acc, longlist, nlong);
+    k_row_sums<WT, double><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, nullptr, Sig, acc, longlist,
+                                                              nlong, INT_MIN);
     GSP_CHECK_LAUNCH();
-    k_row_sums_long<WT><<<sms(4), 256, 0, s>>>(g.off, g.tgt, w, C, nullptr, Sig, acc, longlist, nlong);
+    k_row_sums_long<WT, double><<<sms(4), 256, 0, s>>>(g.off, g.tgt, w, C, nullptr, Sig, acc, longlist, nlong,
+                                                       INT_MIN);
     GSP_CHECK_LAUNCH();
     k_sum_sq<<<grid_for(g.n, 256), 256, 0, s>>>(Sig, g.n, acc + 2);
     GSP_CHECK_LAUNCH();

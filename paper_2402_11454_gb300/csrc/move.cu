@@ -51,6 +51,7 @@ struct MoveArgs {
     const double *m_g;
     const double *minv_g;  // 1/m of each graph
     double *dq_g;
+    int lsb;  // K in exact integer units of 2^lsb (INT_MIN: float64 deltas)
     MoveCounters *ctr;
     int rule;
     uint32_t *mv_vtx, *mv_cmt, *mv_cnt;  // frozen-state move list
@@ -570,14 +571,30 @@ __global__ void __launch_bounds__(256) k_move_block(MoveArgs a, const uint32_t *
 // order) and then applied with one atomic per community per block.
 constexpr int APPLY_SLOG = 11;
 
+// The block's delta of Sigma_c is summed either in float64 or, when K is in
+// exact integer units of 2^lsb (lsb != INT_MIN), as a signed 64-bit integer
+// (two's complement in an unsigned atomic add: one native shared-memory
+// operation, where a float64 add loops on compare-and-swap under contention).
+// Both sums are exact, so Sigma ends up the same.
+__device__ __forceinline__ double signed_units_val(unsigned long long u, int lsb) {
+    const long long v = (long long)u;
+    return v < 0 ? -Acc<unsigned long long>::val((unsigned long long)(-v), lsb)
+                 : Acc<unsigned long long>::val((unsigned long long)v, lsb);
+}
+
 __device__ __forceinline__ void apply_delta(uint32_t *keys, double *ds, int *dn, uint32_t c, double k, int n,
-                                            double *Sig, uint32_t *size) {
+                                            double *Sig, uint32_t *size, int lsb) {
     uint32_t mask = (1u << APPLY_SLOG) - 1u;
     uint32_t h = hash32(c) >> (32 - APPLY_SLOG);
     for (uint32_t probe = 0; probe < 64; probe++) {
         uint32_t old = atomicCAS(&keys[h], EMPTY, c);
         if (old == EMPTY || old == c) {
-            atomicAdd(&ds[h], k);
+            if (lsb != INT_MIN) {
+                const unsigned long long u = units_of(k < 0.0 ? -k : k, lsb);
+                atomicAdd(reinterpret_cast<unsigned long long *>(ds) + h, k < 0.0 ? 0ull - u : u);
+            } else {
+                atomicAdd(&ds[h], k);
+            }
             atomicAdd(&dn[h], n);
             return;
         }
@@ -587,10 +604,24 @@ __device__ __forceinline__ void apply_delta(uint32_t *keys, double *ds, int *dn,
     atomicAdd(size + c, (uint32_t)n);
 }
 
+// Flush a block's delta table (slot t) into Sigma and size.
+__device__ __forceinline__ void flush_delta(const uint32_t *keys, const double *ds, const int *dn, int t, double *Sig,
+                                            uint32_t *size, int lsb) {
+    const uint32_t c = keys[t];
+    if (c == EMPTY) return;
+    if (lsb != INT_MIN) {
+        const unsigned long long u = reinterpret_cast<const unsigned long long *>(ds)[t];
+        if (u) atomicAdd(Sig + c, signed_units_val(u, lsb));
+    } else if (ds[t] != 0.0) {
+        atomicAdd(Sig + c, ds[t]);
+    }
+    if (dn[t] != 0) atomicAdd(size + c, (uint32_t)dn[t]);
+}
+
 __global__ void __launch_bounds__(256) k_apply_moves(const uint32_t *__restrict__ mv_vtx,
                                                      const uint32_t *__restrict__ mv_cmt,
                                                      const uint32_t *__restrict__ mv_cnt, const double *__restrict__ K,
-                                                     uint32_t *C, double *Sig, uint32_t *size) {
+                                                     uint32_t *C, double *Sig, uint32_t *size, int lsb) {
     __shared__ uint32_t skeys[1 << APPLY_SLOG];
     __shared__ double sds[1 << APPLY_SLOG];
     __shared__ int sdn[1 << APPLY_SLOG];
@@ -602,16 +633,11 @@ __global__ void __launch_bounds__(256) k_apply_moves(const uint32_t *__restrict_
         uint32_t d = C[i];
         double Ki = K[i];
         C[i] = c;
-        apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size);
-        apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size);
+        apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size, lsb);
+        apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size, lsb);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) {
-        uint32_t c = skeys[t];
-        if (c == EMPTY) continue;
-        if (sds[t] != 0.0) atomicAdd(Sig + c, sds[t]);
-        if (sdn[t] != 0) atomicAdd(size + c, (uint32_t)sdn[t]);
-    }
+    for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) flush_delta(skeys, sds, sdn, t, Sig, size, lsb);
 }
 
 // act |= mark, mark = 0 (16 bytes per thread step).
@@ -699,7 +725,7 @@ __device__ bool grid_sync(GridBar *b, unsigned nb, MoveCounters *ctr) {
 // and the count through L2; `smem` holds the block's delta table.
 __device__ void apply_body_l2(const uint32_t *mv_vtx, const uint32_t *mv_cmt, const uint32_t *mv_cnt,
                               const double *__restrict__ K, uint32_t *C, double *Sig, uint32_t *size, uint32_t lb,
-                              uint32_t nb, unsigned char *smem) {
+                              uint32_t nb, unsigned char *smem, int lsb) {
     uint32_t *skeys = reinterpret_cast<uint32_t *>(smem);
     double *sds = reinterpret_cast<double *>(smem + sizeof(uint32_t) * (1u << APPLY_SLOG));
     int *sdn = reinterpret_cast<int *>(smem + (sizeof(uint32_t) + sizeof(double)) * (1u << APPLY_SLOG));
@@ -711,16 +737,11 @@ __device__ void apply_body_l2(const uint32_t *mv_vtx, const uint32_t *mv_cmt, co
         const uint32_t d = __ldcg(C + i);
         const double Ki = K[i];
         C[i] = c;
-        apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size);
-        apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size);
+        apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size, lsb);
+        apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size, lsb);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) {
-        const uint32_t c = skeys[t];
-        if (c == EMPTY) continue;
-        if (sds[t] != 0.0) atomicAdd(Sig + c, sds[t]);
-        if (sdn[t] != 0) atomicAdd(size + c, (uint32_t)sdn[t]);
-    }
+    for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) flush_delta(skeys, sds, sdn, t, Sig, size, lsb);
     __syncthreads();
 }
 
@@ -772,7 +793,7 @@ __global__ void __launch_bounds__(256) k_sweep_persistent(MoveArgs a, const uint
         if (cc[CLS_BLOCK])
             block_body<4096, WT, F64, 2>(aw, list + cb[CLS_BLOCK], cc[CLS_BLOCK], lb, nb, dyn_smem, lc);
         if (!grid_sync(bar, nb, a.ctr)) return;
-        apply_body_l2(a.mv_vtx, a.mv_cmt, mv_cnts + wv, a.K, a.C, a.Sig, a.size, lb, nb, dyn_smem);
+        apply_body_l2(a.mv_vtx, a.mv_cmt, mv_cnts + wv, a.K, a.C, a.Sig, a.size, lb, nb, dyn_smem, a.lsb);
         merge_body_l2(a.act, a.mark, n, lb, nb);
         if (!grid_sync(bar, nb, a.ctr)) return;
     }
@@ -1257,6 +1278,7 @@ static MoveArgs make_move_args(const DevGraph &g, const MoveBuffers &mb, bool sy
     a.gid = mb.gid;
     a.m_g = mb.m_g;
     a.minv_g = mb.minv_g;
+    a.lsb = mb.lsb;
     a.dq_g = mb.dq_g;
     a.ctr = mb.ctr;
     a.rule = rule ? 1 : 0;
@@ -1350,7 +1372,7 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
 
 void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s) {
     k_apply_moves<<<grid_for(n_hint, 256, sms(4)), 256, 0, s>>>(mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C,
-                                                                 mb.Sigma, mb.size);
+                                                                 mb.Sigma, mb.size, mb.lsb);
     GSP_CHECK_LAUNCH();
     k_merge_marks<<<grid_for(g.n / 16 + 1, 256, sms(8)), 256, 0, s>>>(mb.act, mb.mark, g.n);
     GSP_CHECK_LAUNCH();

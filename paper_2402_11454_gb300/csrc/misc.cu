@@ -2,9 +2,11 @@
 // renumbering and dendrogram lookup (Algorithm 1), the final numbering, and
 // the disconnected-community count (Algorithm 6).
 //
-// Row sums use one thread per row up to 64 entries and one block per longer
-// row.  All float64 sums here add float32-representable weights whose partial
-// sums stay exactly representable, so they do not depend on the order.
+// Row sums use one thread per row up to 64 entries, one warp per row up to
+// 8192 and one block per longer row.  Their sums of weights are exact and so
+// do not depend on the order: in integer units of the weights' lowest set bit
+// when the total fits 2^52 such units (exact_lsb), otherwise in float64 over
+// float32-representable weights whose partial sums stay representable.
 #include <cmath>
 
 #include "internal.cuh"
@@ -32,10 +34,13 @@ __global__ void k_weight_range(const WT *__restrict__ w, uint64_t nnz, int *minl
     }
 }
 
-// Every sum of weights is then an integer number of units below 2^52, exact
-// both as uint64 and as float64; INT_MIN when no such exponent in
-// [-1000, 1000] exists (zero, negative or non-finite weights, or too wide a
-// range of magnitudes).
+// exact_lsb: the exponent lsb such that every weight is a multiple of 2^lsb
+// and the total weight is below 2^52 * 2^lsb, so that every sum of weights is
+// an integer number of units below 2^52, exact both as uint64 and as float64;
+// INT_MIN when no such exponent in [-1000, 1000] exists (zero, negative or
+// non-finite weights, or too wide a range of magnitudes).  The total is
+// estimated with float32 partial sums (relative error far below the factor 2
+// of margin kept under 2^53).
 template <typename WT>
 static int exact_lsb_t(const DevGraph &g, cudaStream_t s) {
     if (!g.nnz || !g.w) return INT_MIN;
@@ -54,7 +59,7 @@ static int exact_lsb_t(const DevGraph &g, cudaStream_t s) {
     GSP_CUDA(cudaStreamSynchronize(s));
     arena().release(mk);
     if (lo < -1000 || lo > 1000) return INT_MIN;
-    // the float64 sum is rounded: keep a factor 2 of margin below 2^53
+    // the sum is an estimate: keep a factor 2 of margin below 2^53
     if (!(sum > 0.0) || !(sum < std::ldexp(1.0, 52 + lo))) return INT_MIN;
     return lo;
 }

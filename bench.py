@@ -69,25 +69,47 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    mx = max(mx, float(parts[2]))
-                except ValueError:
-                    continue
-                for nm, val in zip(names, parts[5:9]):
-                    if val.lower() == "active":
-                        reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+            return parse_clock_log(f)
+
+
+def parse_clock_log(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in
+    nvidia-smi samples (ClockSampler.FIELDS, csv, no header, no units)."""
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = max(mx, float(parts[2]))
+        except ValueError:
+            continue
+        for nm, val in zip(names, parts[5:9]):
+            if val.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks of the process group (x itself without
+    one): the job takes as long as its slowest rank."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, world_size, seconds):
+    """Whole-job rate: every rank processes units_per_rank per step (one
+    replica each), all ranks together in `seconds` (the max over ranks)."""
+    return units_per_rank * steps * world_size / seconds
 
 
 def dist_setup():
@@ -368,13 +390,9 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), dist, "cuda")
     edges = cfg["edges"]
-    value = edges * args.steps * ws / (total_ms * 1e-3)
+    value = job_throughput(edges, args.steps, ws, total_ms * 1e-3)
 
     # end to end: host (pinned) buffers through the C ABI, copies inside the timing
     e2e = None
@@ -404,12 +422,8 @@ def main():
             e2e_step()
             torch.cuda.synchronize()
             et.append(time.perf_counter() - t0)
-        e2e_s = sum(et)
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": edges * args.steps * ws / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(sum(et), dist, "cuda")
+        e2e = {"value": job_throughput(edges, args.steps, ws, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(h_off.numel() * 8 + h_tgt.numel() * 4 + h_w.numel() * 4),
                "d2h_bytes_per_step": int(h_C.numel() * 4)}
 

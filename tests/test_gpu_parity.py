@@ -92,6 +92,23 @@ def test_vertex_weights_exact(gsp, name):
     assert np.array_equal(host(K), Ko)
 
 
+@pytest.mark.parametrize("name", ["rmat14", "grid"])
+def test_vertex_weights_float64_sum_path(gsp, name):
+    """Weights scaled by 2^-1010 have no integer unit the library accepts
+    (it needs one of at least 2^-1000), so their row sums run in float64;
+    those sums stay exact here, so they equal the oracle's on the scaled
+    graph and, scaled back, the integer-unit sums of the original weights."""
+    off, tgt, w = GRAPHS[name]
+    w64 = np.ldexp(w.astype(np.float64), -1010)
+    K, m = gsp.vertex_weights(*dev(off, tgt, w64))
+    Ko, mo = oracle.vertex_weights(oracle.Graph(off, tgt, w64))
+    assert m == mo
+    assert np.array_equal(host(K), Ko)
+    K1, m1 = gsp.vertex_weights(*dev(off, tgt, w))
+    assert np.ldexp(m, 1010) == m1
+    assert np.array_equal(np.ldexp(host(K), 1010), host(K1))
+
+
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 def test_modularity_matches(gsp, name):
     off, tgt, w = GRAPHS[name]

@@ -160,6 +160,13 @@ gsp_status gsp_louvain_batched(uint32_t num_graphs, const uint64_t *graph_vertex
 /* ---------------------------------------------------------------------------
  * Phase entry points (each one step of Algorithm 1), for reuse and parity
  * tests.  `wt` gives the weight type of `weights`.
+ *
+ * Sums of weights (K, m, Sigma, aggregated weights, the terms of Q) are
+ * exact, and so do not depend on the order of the parallel additions,
+ * whenever every weight is a multiple of 2^lsb for some lsb in [-1000, 1000]
+ * with the total weight below 2^52 * 2^lsb (then they are taken as 64-bit
+ * integers in units of 2^lsb); otherwise they are float64 additions in an
+ * unspecified order, exact only while the partial sums stay representable.
  * ------------------------------------------------------------------------- */
 
 /* Section 3: K[i] = sum_j w_ij (self-loop included), float64; *m_host =

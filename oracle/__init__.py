@@ -24,5 +24,7 @@ from .oracle import (  # noqa: F401
     aggregate,
     disconnected,
     louvain,
+    louvain_trace,
+    TRACE_FIELDS,
     LouvainOptions,
 )

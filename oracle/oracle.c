@@ -43,6 +43,7 @@ typedef struct {
     int split_last;             /* 0 Split Pass (SP), 1 Split Last (SL) */
     int sync;                   /* 0 asynchronous in-place moves, 1 frozen-state waves */
     int waves;                  /* frozen-state waves per iteration */
+    int wave_repeats;           /* frozen-state repeats of a wave in the first iteration of a pass */
     int singleton_rule;         /* frozen-state sweeps only: singleton -> singleton moves go to lower ids */
 } og_opts;
 
@@ -145,11 +146,13 @@ static void clear_table(double *H, uint8_t *seen, const uint32_t *list, uint32_t
  */
 static uint32_t best_move(const og_graph *g, const uint32_t *C, const double *K, const double *Sigma,
                           const uint32_t *size, int singleton_rule, double m, uint32_t i,
-                          double *H, uint8_t *seen, uint32_t *list, double *best_out, double *second_out)
+                          double *H, uint8_t *seen, uint32_t *list, double *best_out, double *second_out,
+                          double *kid_out)
 {
     uint32_t d = C[i];
     uint32_t len = scan_communities(g, C, i, 0, H, seen, list, 0);
     double Kid = H[d];   /* zero when no neighbour lies in d */
+    if (kid_out) *kid_out = Kid;
     double best = -INFINITY, second = -INFINITY;
     uint32_t cbest = d;
     for (uint32_t t = 0; t < len; t++) {          /* the best candidate */
@@ -191,7 +194,7 @@ void og_move_sweep_sync(const og_graph *g, const uint32_t *C, const double *K, c
         double b = -INFINITY, s = -INFINITY;
         choice[i] = C[i];
         if (active && !active[i]) { best[i] = b; second[i] = s; continue; }
-        choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, &s);
+        choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, &s, NULL);
         best[i] = b;
         second[i] = s;
     }
@@ -211,11 +214,58 @@ void og_move_sweep_sync(const og_graph *g, const uint32_t *C, const double *K, c
  *             a wave reads the C, Sigma and community sizes left by the
  *             earlier waves, and the wave's moves are applied after it.
  *             waves = 1 is the fully synchronous loop; waves = |V'| is the
- *             one-thread loop in id order.
+ *             one-thread loop in id order.  In the first iteration a wave
+ *             runs `repeats` times (at least once; later iterations once):
+ *             a repeat takes the vertices of the wave that the previous
+ *             repeat's moves marked unprocessed again, on the
+ *             state those moves left (the pruning rule of Algorithm 4 applied
+ *             within the wave).  With one vertex per wave a vertex never
+ *             marks itself, so repeats change nothing there.
  * dq_iter (optional) receives the total delta-modularity of each iteration.
  */
-int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, double m, double tau,
-            int max_iterations, int sync, int waves, int singleton_rule, double *dq_iter)
+/*
+ * Visit trace for the learned pruning predictor (not part of the paper's
+ * method; the predictor is an addition checked against this record).  Every
+ * vertex visit of local moving appends one record of OG_TRACE_FIELDS
+ * doubles: pass, iteration, repeat, vertex, degree, K_i, then the state the
+ * vertex's previous visit in this pass left (the fraction K_{i->C_i}/K_i of
+ * its weight inside its community, its best candidate's delta-modularity
+ * times m/K_i clamped to [-1, 1] (0 without a candidate), whether it moved;
+ * before a first visit 0, 1, 1), whether this visit moved it, and the
+ * largest K of the pass's graph.  Records beyond cap are counted, not kept.
+ */
+#define OG_TRACE_FIELDS 11
+typedef struct {
+    double *rec;
+    uint64_t cap, len;
+    int pass;
+    double max_K;
+    double *kept, *gain;      /* per vertex of the pass's graph */
+    uint8_t *moved;
+} og_trace;
+
+static void trace_visit(og_trace *tr, const og_graph *g, int it, int rep, uint32_t i, double Ki, double kid,
+                        double best, double m, int moved)
+{
+    if (!tr) return;
+    if (tr->len < tr->cap) {
+        double *r = tr->rec + tr->len * OG_TRACE_FIELDS;
+        r[0] = tr->pass; r[1] = it; r[2] = rep; r[3] = i;
+        r[4] = (double)(g->off[i + 1] - g->off[i]); r[5] = Ki;
+        r[6] = tr->kept[i]; r[7] = tr->gain[i]; r[8] = tr->moved[i];
+        r[9] = moved; r[10] = tr->max_K;
+    }
+    tr->len++;
+    double gain = isfinite(best) ? best : 0.0;
+    double x = Ki > 0.0 ? gain * m / Ki : 0.0;
+    tr->kept[i] = Ki > 0.0 ? kid / Ki : 0.0;
+    tr->gain[i] = x < -1.0 ? -1.0 : (x > 1.0 ? 1.0 : x);
+    tr->moved[i] = (uint8_t)moved;
+}
+
+static int move_impl(const og_graph *g, uint32_t *C, const double *K, double *Sigma, double m, double tau,
+                     int max_iterations, int sync, int waves, int repeats, int singleton_rule, double *dq_iter,
+                     og_trace *tr)
 {
     uint32_t n = g->n;
     double *H = calloc(n ? n : 1, sizeof(double));
@@ -234,8 +284,9 @@ int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, doub
             for (uint32_t i = 0; i < n; i++) {
                 if (!unprocessed[i]) continue;
                 unprocessed[i] = 0;
-                double b;
-                uint32_t c = best_move(g, C, K, Sigma, NULL, 0, m, i, H, seen, list, &b, NULL);
+                double b, kid;
+                uint32_t c = best_move(g, C, K, Sigma, NULL, 0, m, i, H, seen, list, &b, NULL, &kid);
+                trace_visit(tr, g, it, 0, i, K[i], kid, b, m, c != C[i]);
                 if (c == C[i]) continue;
                 Sigma[C[i]] -= K[i];
                 Sigma[c] += K[i];
@@ -247,25 +298,30 @@ int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, doub
             }
         } else {
             uint32_t W = waves < 1 ? 1u : (uint32_t)waves;
+            int R = (it == 0 && repeats > 1) ? repeats : 1;
             for (uint32_t wv = 0; wv < W && wv < (n ? n : 1); wv++) {
-                /* decide: every unprocessed vertex of the wave, frozen state */
-                for (uint32_t i = wv; i < n; i += W) {
-                    choice[i] = C[i];
-                    if (!unprocessed[i]) continue;
-                    unprocessed[i] = 0;
-                    double b;
-                    choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, NULL);
-                    if (choice[i] != C[i]) dQ += b;
-                }
-                /* apply the wave's moves; movers mark their neighbours */
-                for (uint32_t i = wv; i < n; i += W) {
-                    if (choice[i] == C[i]) continue;
-                    Sigma[C[i]] -= K[i];
-                    Sigma[choice[i]] += K[i];
-                    size[C[i]]--; size[choice[i]]++;
-                    for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++)
-                        if (g->tgt[e] != i) unprocessed[g->tgt[e]] = 1;
-                    C[i] = choice[i];
+                for (int r = 0; r < R; r++) {
+                    /* decide: every unprocessed vertex of the wave, frozen state */
+                    for (uint32_t i = wv; i < n; i += W) {
+                        choice[i] = C[i];
+                        if (!unprocessed[i]) continue;
+                        unprocessed[i] = 0;
+                        double b, kid;
+                        choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, NULL,
+                                              &kid);
+                        trace_visit(tr, g, it, r, i, K[i], kid, b, m, choice[i] != C[i]);
+                        if (choice[i] != C[i]) dQ += b;
+                    }
+                    /* apply the wave's moves; movers mark their neighbours */
+                    for (uint32_t i = wv; i < n; i += W) {
+                        if (choice[i] == C[i]) continue;
+                        Sigma[C[i]] -= K[i];
+                        Sigma[choice[i]] += K[i];
+                        size[C[i]]--; size[choice[i]]++;
+                        for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++)
+                            if (g->tgt[e] != i) unprocessed[g->tgt[e]] = 1;
+                        C[i] = choice[i];
+                    }
                 }
             }
         }
@@ -274,6 +330,12 @@ int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, doub
     }
     free(H); free(seen); free(list); free(unprocessed); free(choice); free(size);
     return li;
+}
+
+int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, double m, double tau,
+            int max_iterations, int sync, int waves, int repeats, int singleton_rule, double *dq_iter)
+{
+    return move_impl(g, C, K, Sigma, m, tau, max_iterations, sync, waves, repeats, singleton_rule, dq_iter, NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -490,7 +552,7 @@ static uint32_t canonical_numbering(uint32_t n, uint32_t *C)
 /* follows the loop.  With split_last the split runs once, on G and the */
 /* final membership.  Returns the number of passes.                     */
 /* ------------------------------------------------------------------ */
-int og_louvain(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st)
+static int louvain_impl(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st, og_trace *tr)
 {
     uint32_t n = g->n;
     for (uint32_t v = 0; v < n; v++) C[v] = v;
@@ -510,8 +572,16 @@ int og_louvain(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st)
         double m = og_vertex_weights(&cur, K);
         memcpy(Sigma, K, sizeof(double) * nv);
         for (uint32_t i = 0; i < nv; i++) Cp[i] = i;
-        int li = (m > 0.0) ? og_move(&cur, Cp, K, Sigma, m, tau, o->max_iterations, o->sync, o->waves,
-                                     o->singleton_rule, NULL)
+        if (tr) {
+            tr->pass = lp;
+            tr->max_K = 0.0;
+            for (uint32_t i = 0; i < nv; i++) {
+                if (K[i] > tr->max_K) tr->max_K = K[i];
+                tr->kept[i] = 0.0; tr->gain[i] = 1.0; tr->moved[i] = 1;
+            }
+        }
+        int li = (m > 0.0) ? move_impl(&cur, Cp, K, Sigma, m, tau, o->max_iterations, o->sync, o->waves,
+                                       o->wave_repeats, o->singleton_rule, NULL, tr)
                            : 0;
         if (split_each_pass) {
             run_split(&cur, Cp, Cs, o->split);
@@ -551,5 +621,28 @@ int og_louvain(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st)
         st->modularity = og_modularity(g, C);
     }
     free(own_off); free(own_tgt); free(own_w); free(K); free(Sigma); free(Cp); free(Cs);
+    return passes;
+}
+
+int og_louvain(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st)
+{
+    return louvain_impl(g, o, C, st, NULL);
+}
+
+/* og_louvain that also records every local-moving visit (og_trace) into
+ * rec[cap][OG_TRACE_FIELDS]; *len receives the number of visits (possibly
+ * more than cap). */
+int og_louvain_trace(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st, double *rec, uint64_t cap,
+                     uint64_t *len)
+{
+    uint32_t n = g->n ? g->n : 1;
+    og_trace tr;
+    tr.rec = rec; tr.cap = cap; tr.len = 0; tr.pass = 0; tr.max_K = 0.0;
+    tr.kept = malloc(sizeof(double) * n);
+    tr.gain = malloc(sizeof(double) * n);
+    tr.moved = malloc(n);
+    int passes = louvain_impl(g, o, C, st, &tr);
+    free(tr.kept); free(tr.gain); free(tr.moved);
+    if (len) *len = tr.len;
     return passes;
 }

@@ -39,7 +39,7 @@ class _OgOpts(ctypes.Structure):
                 ("tolerance", ctypes.c_double), ("tolerance_drop", ctypes.c_double),
                 ("aggregation_tolerance", ctypes.c_double), ("split", ctypes.c_int),
                 ("split_last", ctypes.c_int), ("sync", ctypes.c_int), ("waves", ctypes.c_int),
-                ("singleton_rule", ctypes.c_int)]
+                ("wave_repeats", ctypes.c_int), ("singleton_rule", ctypes.c_int)]
 
 
 class _OgStats(ctypes.Structure):
@@ -64,7 +64,7 @@ def _load():
         lib.og_move_sweep_sync.argtypes = [G, P, P, P, P, ctypes.c_int, ctypes.c_double, P, P, P, P]
         lib.og_move_sweep_sync.restype = None
         lib.og_move.argtypes = [G, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
         lib.og_move.restype = ctypes.c_int
         lib.og_split_lp.argtypes = [G, P, P, ctypes.c_int]
         lib.og_split_lp.restype = ctypes.c_int
@@ -80,6 +80,9 @@ def _load():
         lib.og_disconnected.restype = ctypes.c_uint32
         lib.og_louvain.argtypes = [G, ctypes.POINTER(_OgOpts), P, ctypes.POINTER(_OgStats)]
         lib.og_louvain.restype = ctypes.c_int
+        lib.og_louvain_trace.argtypes = [G, ctypes.POINTER(_OgOpts), P, ctypes.POINTER(_OgStats), P,
+                                         ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+        lib.og_louvain_trace.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -142,15 +145,17 @@ def move_sweep_sync(g, C, K, Sigma, m, active=None, singleton_rule=True):
     return choice, best, second
 
 
-def move(g, C, K, Sigma, m, tau, max_iterations=20, sync=True, singleton_rule=True, waves=1):
+def move(g, C, K, Sigma, m, tau, max_iterations=20, sync=True, singleton_rule=True, waves=1, wave_repeats=1):
     """louvainMove (Algorithm 4); returns (C, Sigma, l_i, dq per iteration).
-    sync=True runs frozen-state waves (vertex i in wave i mod waves)."""
+    sync=True runs frozen-state waves (vertex i in wave i mod waves); in the
+    first iteration each wave runs wave_repeats times (a repeat takes the
+    wave's vertices re-marked by the previous repeat's moves)."""
     C = _u32(C).copy()
     K = np.ascontiguousarray(K, dtype=np.float64)
     Sigma = np.ascontiguousarray(Sigma, dtype=np.float64).copy()
     dq = np.zeros(max(max_iterations, 1), dtype=np.float64)
     li = _load().og_move(g.ref, _p(C), _p(K), _p(Sigma), m, tau, max_iterations, int(bool(sync)),
-                         int(waves), int(bool(singleton_rule)), _p(dq))
+                         int(waves), int(wave_repeats), int(bool(singleton_rule)), _p(dq))
     return C, Sigma, li, dq[:li]
 
 
@@ -217,6 +222,7 @@ class LouvainOptions:
     split_last: bool = False
     sync: bool = True
     waves: int = 17
+    wave_repeats: int = 3
     singleton_rule: bool = True
 
 
@@ -225,7 +231,7 @@ def louvain(g, opts=None):
     o = opts or LouvainOptions()
     co = _OgOpts(o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
                  o.aggregation_tolerance, SPLIT_MODES[o.split], int(o.split_last), int(o.sync),
-                 int(o.waves), int(o.singleton_rule))
+                 int(o.waves), int(o.wave_repeats), int(o.singleton_rule))
     C = np.zeros(g.n, dtype=np.uint32)
     st = _OgStats()
     _load().og_louvain(g.ref, ctypes.byref(co), _p(C), ctypes.byref(st))
@@ -234,3 +240,29 @@ def louvain(g, opts=None):
                  communities=list(st.communities[:p]), modularity=st.modularity,
                  final_communities=st.final_communities)
     return C, stats
+
+
+TRACE_FIELDS = ("pass", "iteration", "repeat", "vertex", "degree", "K", "kept", "gain", "moved_last", "moved",
+                "max_K")
+
+
+def louvain_trace(g, opts=None, capacity=1 << 20):
+    """louvain (Algorithm 1) recording every local-moving visit: returns
+    (membership, stats, records) with records a dict of arrays named by
+    TRACE_FIELDS (the vertex's state before the visit; see og_trace in
+    oracle.c).  Raises if the run made more than `capacity` visits."""
+    o = opts or LouvainOptions()
+    co = _OgOpts(o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
+                 o.aggregation_tolerance, SPLIT_MODES[o.split], int(o.split_last), int(o.sync),
+                 int(o.waves), int(o.wave_repeats), int(o.singleton_rule))
+    C = np.zeros(g.n, dtype=np.uint32)
+    st = _OgStats()
+    rec = np.zeros((capacity, len(TRACE_FIELDS)), dtype=np.float64)
+    n = ctypes.c_uint64()
+    _load().og_louvain_trace(g.ref, ctypes.byref(co), _p(C), ctypes.byref(st), _p(rec), capacity,
+                             ctypes.byref(n))
+    if n.value > capacity:
+        raise ValueError("trace needs %d records, capacity %d" % (n.value, capacity))
+    rec = rec[:n.value]
+    return C, {"passes": st.passes, "modularity": st.modularity}, {k: rec[:, j] for j, k in
+                                                                   enumerate(TRACE_FIELDS)}

@@ -41,7 +41,8 @@ typedef enum {
     GSP_ERR_NOMEM = -2,       /* device allocation failed */
     GSP_ERR_CUDA = -3,        /* a CUDA runtime call or kernel failed */
     GSP_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
-    GSP_ERR_CAPACITY = -5     /* a fixed-size buffer was too small */
+    GSP_ERR_CAPACITY = -5,    /* a fixed-size buffer was too small */
+    GSP_ERR_NOT_SYMMETRIC = -6 /* the CSR is not symmetric (w_ij != w_ji, or an entry lacks its mirror) */
 } gsp_status;
 
 /* Split techniques of Section 4.1: none (GVE-Louvain), min-label propagation
@@ -63,13 +64,22 @@ typedef enum { GSP_SPLIT_PASS = 0, GSP_SPLIT_LAST = 1 } gsp_split_when;
  * does (results depend on thread timing); SYNC lets every vertex of an
  * iteration read the state of the iteration's start (deterministic). */
 typedef enum { GSP_MOVE_ASYNC = 0, GSP_MOVE_SYNC = 1 } gsp_move_mode;
-/* SYNC splits each iteration into `waves` interleaved waves: vertex i belongs
- * to wave i mod waves, and every vertex of a wave reads the state left by the
- * earlier waves (waves = 1: fully synchronous; more waves approach the
+/* An iteration is split into `waves` interleaved waves: vertex i belongs to
+ * wave i mod waves, and every vertex of a wave reads the state left by the
+ * earlier waves (SYNC, waves = 1: fully synchronous; more waves approach the
  * one-thread order).  The default, 17, is prime so that ids with structure
  * (vertex v of a planted community v mod k, R-MAT hubs at ids with many
- * trailing zero bits) do not fall into one wave: on GB300 it was faster and
- * found higher modularity than 16 on every test workload. */
+ * trailing zero bits) do not fall into one wave.  In the first iteration of
+ * a pass each wave runs `wave_repeats` times (later iterations once): a
+ * repeat takes the vertices of the wave that the previous repeat's moves
+ * marked unprocessed again (the pruning rule of Algorithm 4 applied inside
+ * the wave), on the state those moves left.  Three repeats
+ * bring the frozen-state schedule close to the modularity of the one-thread
+ * loop (on R-MAT scales 19, 20 and 21, 0.0002, 0.0007 and 0.0013 below it on
+ * average, where a single pass fell 0.0022, 0.0029 and 0.0033 short) for about
+ * 1.45 times the edge visits; an odd count does better than the next even
+ * one, and repeats in the later iterations cost more than they gain.  In
+ * ASYNC mode the waves and repeats order the in-place updates the same way. */
 /* MIXED: per-community weights K_{i->c} and delta-modularity in float32,
  * while m, Sigma_tot and modularity stay float64.  FP64: everything float64,
  * Equation 2 evaluated term by term (the parity mode). */
@@ -88,7 +98,8 @@ typedef struct {
     int split;                      /* gsp_split_mode; default GSP_SPLIT_LPP */
     int split_when;                 /* gsp_split_when; default GSP_SPLIT_PASS */
     int move;                       /* gsp_move_mode; default GSP_MOVE_SYNC */
-    int waves;                      /* SYNC: waves per iteration, 1..64; default 17 */
+    int waves;                      /* waves per iteration, 1..64; default 17 */
+    int wave_repeats;               /* times each wave runs in a pass's first iteration, 1..8; default 3 */
     int precision;                  /* gsp_precision; default GSP_PREC_MIXED */
     int singleton_rule;             /* 1: a vertex alone in its community moves to another
                                        singleton community only if that id is lower; default 1 */
@@ -96,6 +107,14 @@ typedef struct {
     const void *mlp_params;         /* device pointer to gsp_mlp_param_count() floats (learned pruning) */
     int full_sweep_every;           /* learned pruning: every k-th iteration is a plain sweep; default 4 */
     float prune_threshold;          /* learned pruning: skip a vertex when P(move) < this; default 0.5 */
+    int count_disconnected;         /* 1: count internally-disconnected communities of the result
+                                       (Algorithm 6) into gsp_stats.disconnected; default 0 */
+    void *workspace;                /* optional device scratch owned by the caller (256-byte aligned); NULL:
+                                       the library's internal workspace.  With a workspace the call
+                                       allocates no device memory and fails with GSP_ERR_CAPACITY when
+                                       it runs short; gsp_stats.workspace_bytes of an earlier call on
+                                       the same graph and options gives the size it needs */
+    size_t workspace_bytes;         /* size of `workspace` in bytes */
     void *stream;                   /* cudaStream_t; NULL = default stream */
 } gsp_opts;
 
@@ -118,7 +137,11 @@ typedef struct {
     uint32_t final_communities;
     double modularity;
     float ms_total;
+    uint32_t disconnected;          /* internally-disconnected communities of the result (Algorithm 6),
+                                       GSP_NOT_COUNTED unless gsp_opts.count_disconnected is set */
+    uint64_t workspace_bytes;       /* most device scratch bytes the call held at once */
 } gsp_stats;
+#define GSP_NOT_COUNTED 0xFFFFFFFFu
 
 /* Fill *o with the defaults listed in gsp_opts. */
 void gsp_default_opts(gsp_opts *o);
@@ -198,14 +221,15 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
 /*
  * louvainMove (Algorithm 4) from membership C (in/out) and Sigma (in/out,
  * must equal the per-community sums of K).  move is a gsp_move_mode, waves
- * the SYNC wave count (1..64).  Returns l_i, the iterations executed, in
- * *iterations_host.
+ * the wave count (1..64) and wave_repeats the repeats of a wave in the first
+ * iteration (1..8), as in gsp_opts.  Returns l_i, the iterations executed,
+ * in *iterations_host.
  */
 gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, const void *weights,
                           int wt, uint32_t n, uint64_t nnz, uint32_t *C, const double *K,
                           double *Sigma, double m, double tolerance, int max_iterations, int move,
-                          int waves, int precision, int singleton_rule, int *iterations_host,
-                          void *stream);
+                          int waves, int wave_repeats, int precision, int singleton_rule,
+                          int *iterations_host, void *stream);
 
 /*
  * Split (Algorithms 2 and 3): labels[i] = the smallest vertex id of the
@@ -247,14 +271,17 @@ gsp_status gsp_count_disconnected(const uint64_t *offsets, const uint32_t *targe
 /*
  * Move/no-move traces of the plain method, for training the learned pruning
  * predictor: runs gsp_louvain (opts as given; learned pruning ignored) and,
- * for a sample of vertex visits of local moving (about one in sample_every),
- * records the visit's 6 predictor features (taken before the visit) into
- * features[rows][6] and whether the vertex moved into labels[rows] (device
- * arrays of `capacity` rows).  *rows_host = rows written (<= capacity).
+ * for a sample of vertex visits of local moving (about one in sample_every;
+ * every visit when it is 1), records the visit's 6 predictor features (taken
+ * before the visit) into features[rows][6] and whether the vertex moved into
+ * labels[rows] (device arrays of `capacity` rows).  keys (device, capacity
+ * entries, may be NULL) receives each row's visit as pass << 56 |
+ * iteration << 48 | repeat << 40 | vertex (vertex of that pass's graph).
+ * Rows come in no particular order.  *rows_host = rows written (<= capacity).
  */
 gsp_status gsp_louvain_trace(const uint64_t *offsets, const uint32_t *targets, const float *weights,
                              uint32_t n, uint64_t nnz, const gsp_opts *opts, float *features,
-                             uint8_t *labels, uint32_t capacity, uint32_t sample_every,
+                             uint8_t *labels, uint64_t *keys, uint32_t capacity, uint32_t sample_every,
                              uint32_t *rows_host);
 
 /* ---------------------------------------------------------------------------
@@ -318,19 +345,23 @@ gsp_status gsp_gen_grid(uint32_t R, uint32_t Cc, uint64_t remove53, uint64_t n_l
 void gsp_release_graph(void);
 
 /*
- * Modularity for callers that cannot allocate device memory (code running
- * during CUDA graph capture, embedders whose device memory comes from a fixed
- * pool, processes that must not grow after start-up).  It returns the same
- * value as gsp_modularity, with the same arguments, but its scratch is one
- * fixed __device__ array inside the library instead of the library workspace:
- * it calls no cudaMalloc or cudaFree.  The paper has no counterpart; this is
- * an interface convenience.
+ * Modularity for callers that cannot allocate device memory (embedders whose
+ * device memory comes from a fixed pool, such as an inference server or
+ * another framework's allocator holding the device; processes that must not
+ * grow their device footprint after start-up).  It returns the same value as
+ * gsp_modularity, with the same arguments and the same checks (offsets,
+ * target and membership ids), but its scratch is one fixed __device__ array
+ * inside the library instead of the library workspace: it calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Like gsp_modularity it
+ * waits for `stream` and returns Q in host memory.  The paper has no
+ * counterpart; this is an interface convenience.
  *  - Limit: n <= GSP_STATIC_MAX_VERTICES; larger n returns GSP_ERR_CAPACITY
  *    with a message (use gsp_modularity).
  *  - Every device that loads the library holds GSP_STATIC_SCRATCH_BYTES for
  *    the array until the process exits.
- *  - The first call on a device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ *  - The first call made in a device's context looks up the array's device
+ *    address (with that device current); later calls in that context reuse
+ *    it.
  *  - All calls share the one array: calls that overlap on the GPU (several
  *    streams, several host threads) race and give wrong results; serialise
  *    them.  Each call clears the parts of the array it needs.
@@ -344,6 +375,16 @@ gsp_status gsp_modularity_static(const uint64_t *offsets, const uint32_t *target
 /* Number of kernels this library has launched since it was loaded (all
  * devices, all threads); a diagnostic for counting launches in a region. */
 uint64_t gsp_kernel_launches(void);
+
+/* Bytes of device memory the library's internal workspaces hold (all
+ * devices); a diagnostic: it grows only when a call needs more scratch than
+ * any earlier call did. */
+uint64_t gsp_workspace_reserved(void);
+
+/* Free the internal workspace of the current device (after waiting for the
+ * device to be idle); the next call grows it again.  For callers that
+ * switch between graphs of very different sizes. */
+void gsp_release_workspace(void);
 
 /* ---------------------------------------------------------------------------
  * Launch geometry of local moving (an implementation choice; the paper has no

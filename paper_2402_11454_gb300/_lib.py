@@ -14,16 +14,19 @@ c_flt = ctypes.c_float
 P = ctypes.c_void_p
 
 GSP_MAX_PASS_STATS = 32
+GSP_NOT_COUNTED = 0xFFFFFFFF
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
-          -4: "device wait timed out", -5: "capacity exceeded"}
+          -4: "device wait timed out", -5: "capacity exceeded", -6: "graph not symmetric"}
 
 
 class GspOpts(ctypes.Structure):
     _fields_ = [("max_passes", c_int), ("max_iterations", c_int), ("tolerance", c_dbl),
                 ("tolerance_drop", c_dbl), ("aggregation_tolerance", c_dbl), ("split", c_int),
-                ("split_when", c_int), ("move", c_int), ("waves", c_int), ("precision", c_int),
+                ("split_when", c_int), ("move", c_int), ("waves", c_int), ("wave_repeats", c_int),
+                ("precision", c_int),
                 ("singleton_rule", c_int), ("prune", c_int), ("mlp_params", P),
-                ("full_sweep_every", c_int), ("prune_threshold", c_flt), ("stream", P)]
+                ("full_sweep_every", c_int), ("prune_threshold", c_flt), ("count_disconnected", c_int),
+                ("workspace", P), ("workspace_bytes", ctypes.c_size_t), ("stream", P)]
 
 
 _N = GSP_MAX_PASS_STATS
@@ -36,7 +39,8 @@ class GspStats(ctypes.Structure):
                 ("vertices_processed", c_u64 * _N), ("edges_scanned", c_u64 * _N),
                 ("vertices_skipped", c_u64 * _N), ("move_bytes", c_dbl * _N),
                 ("ms_move_kernels", c_flt * _N), ("final_communities", c_u32),
-                ("modularity", c_dbl), ("ms_total", c_flt)]
+                ("modularity", c_dbl), ("ms_total", c_flt), ("disconnected", c_u32),
+                ("workspace_bytes", c_u64)]
 
 
 class GspDeviceGraph(ctypes.Structure):
@@ -60,8 +64,8 @@ _SIGS = {
     "gsp_move_sweep": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, P, c_dbl, P, c_int, c_int, P, P,
                                P, P]),
     "gsp_local_move": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, P, c_dbl, c_dbl, c_int, c_int,
-                               c_int, c_int, c_int, P, P]),
-    "gsp_louvain_trace": (c_int, [P, P, P, c_u32, c_u64, P, P, P, c_u32, c_u32, P]),
+                               c_int, c_int, c_int, c_int, P, P]),
+    "gsp_louvain_trace": (c_int, [P, P, P, c_u32, c_u64, P, P, P, P, c_u32, c_u32, P]),
     "gsp_split": (c_int, [P, P, c_u32, c_u64, P, c_int, P, P, P]),
     "gsp_renumber": (c_int, [c_u32, P, P, P, P]),
     "gsp_lookup": (c_int, [c_u32, P, P, P]),
@@ -80,6 +84,8 @@ _SIGS = {
     "gsp_gen_grid": (c_int, [c_u32, c_u32, c_u64, c_u64, c_flt, c_flt, c_u64, P, P]),
     "gsp_release_graph": (None, []),
     "gsp_kernel_launches": (c_u64, []),
+    "gsp_workspace_reserved": (c_u64, []),
+    "gsp_release_workspace": (None, []),
     "gsp_modularity_static": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, P]),
 }
 

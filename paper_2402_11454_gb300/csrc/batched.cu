@@ -307,13 +307,14 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         GSP_CUDA(cudaStreamWaitEvent(s, in, 0));
     }
     const uint32_t n0 = g0.n;
-    const int W = o.move == GSP_MOVE_SYNC ? o.waves : 1;
+    const int W = o.waves;
     gsp_stats local;
     memset(&local, 0, sizeof(local));
     Lap total(s), lap(s);
 
     MoveBuffers mb;
     alloc_move_state(mb, n0);
+    mb.repeats = o.wave_repeats;
     double *K = arena().get<double>(n0);
     uint32_t *labels = arena().get<uint32_t>(n0);
     uint32_t *Cd = arena().get<uint32_t>(n0);
@@ -508,6 +509,8 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         GSP_CUDA(cudaMemcpyAsync(membership, labels, sizeof(uint32_t) * n0, cudaMemcpyDeviceToDevice, s));
     }
     const uint32_t kf = canonical_numbering(n0, membership, s);
+    // global ids here: no community spans two graphs
+    local.disconnected = o.count_disconnected ? count_disconnected(g0, membership, nullptr, s) : GSP_NOT_COUNTED;
     // per-graph Equation 1, then graph-local numbering
     {
         size_t mk = arena().mark();
@@ -551,6 +554,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     local.passes = passes;
     local.final_communities = kf;
     local.ms_total = total();
+    local.workspace_bytes = workspace_peak();
     if (st) *st = local;
     cudaEvent_t out = pool_event();
     GSP_CUDA(cudaEventRecord(out, s));
@@ -580,6 +584,7 @@ extern "C" gsp_status gsp_louvain_batched(uint32_t num_graphs, const uint64_t *g
         GSP_REQUIRE(membership && modularity, "membership and modularity must not be NULL");
         DevGraph g = make_graph(offsets, targets, weights, GSP_W_F32, n, nnz);
         cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+        UserWorkspace uw(o.workspace, o.workspace_bytes);
         arena().reset();
         check_graph(offsets, targets, weights, n, nnz, s);
         louvain_batched_run(g, num_graphs, graph_vertex_offsets, o, membership, modularity, stats, s);

@@ -34,19 +34,36 @@ struct ChunkArena {
     };
     std::vector<Chunk> chunks;
     size_t cur = 0, top = 0;
+    size_t peak = 0;       // most bytes in use since the last reset (chunk tails skipped count as used)
+    bool fixed = false;    // a caller's workspace: one chunk, never grown
+    size_t in_use() const {
+        size_t b = top;
+        for (size_t k = 0; k < cur && k < chunks.size(); k++) b += chunks[k].cap;
+        return b;
+    }
     void *alloc(size_t bytes) {
         bytes = align_up(bytes ? bytes : 1, 256);
         while (cur < chunks.size()) {
             if (top + bytes <= chunks[cur].cap) {
                 void *p = chunks[cur].base + top;
                 top += bytes;
+                peak = std::max(peak, in_use());
                 return p;
+            }
+            if (fixed) {
+                set_error("caller workspace too small: %zu of %zu bytes used, %zu more requested", top,
+                          chunks[cur].cap, bytes);
+                throw Error{GSP_ERR_CAPACITY};
             }
             cur++;
             top = 0;
         }
+        // chunks double from 64 MB up to 4 GB; a larger request gets a chunk
+        // of its own size (doubling without a cap reserved about twice the
+        // peak of an R-MAT scale-26 run)
         size_t last = chunks.empty() ? 0 : chunks.back().cap;
-        size_t sz = std::max(bytes, std::max<size_t>(last * 2, (size_t)64 << 20));
+        size_t grow = std::min<size_t>(std::max<size_t>(last * 2, (size_t)64 << 20), (size_t)4 << 30);
+        size_t sz = std::max(bytes, grow);
         char *p = nullptr;
         cudaError_t e = cudaMalloc(&p, sz);
         if (e != cudaSuccess && sz > bytes) {
@@ -62,6 +79,7 @@ struct ChunkArena {
         chunks.push_back({p, sz});
         cur = chunks.size() - 1;
         top = bytes;
+        peak = std::max(peak, in_use());
         return p;
     }
     size_t mark() const { return (cur << 40) | top; }
@@ -69,7 +87,7 @@ struct ChunkArena {
         cur = m >> 40;
         top = m & ((1ull << 40) - 1);
     }
-    void reset() { cur = top = 0; }
+    void reset() { cur = top = peak = 0; }
     void free_all() {
         for (auto &k : chunks) cudaFree(k.base);
         chunks.clear();
@@ -84,11 +102,36 @@ static int cur_dev() {
     return d & 15;
 }
 
-struct WorkArena : Arena {};
+// A call given a caller workspace (gsp_opts.workspace) takes all its scratch
+// from it; the internal workspace is left alone.
+static thread_local ChunkArena *g_user_ws = nullptr;
+struct UserWorkspace::Impl {
+    ChunkArena ws;
+};
+UserWorkspace::UserWorkspace(void *base, size_t bytes) {
+    if (!base) return;
+    GSP_REQUIRE(bytes >= 256 && (reinterpret_cast<uintptr_t>(base) & 255) == 0,
+                "workspace must be 256-byte aligned and hold at least 256 bytes");
+    impl = new Impl;
+    impl->ws.chunks.push_back({static_cast<char *>(base), bytes & ~(size_t)255});
+    impl->ws.fixed = true;
+    g_user_ws = &impl->ws;
+}
+UserWorkspace::~UserWorkspace() {
+    if (!impl) return;
+    if (g_user_ws == &impl->ws) g_user_ws = nullptr;
+    impl->ws.chunks.clear();  // the caller's memory: never freed here
+    delete impl;
+}
+
 static Arena g_work_facade, g_io_facade;
 Arena &arena() { return g_work_facade; }
 Arena &io_arena() { return g_io_facade; }
-static ChunkArena &backing(const Arena *a) { return a == &g_io_facade ? g_io[cur_dev()] : g_work[cur_dev()]; }
+static ChunkArena &backing(const Arena *a) {
+    if (a == &g_io_facade) return g_io[cur_dev()];
+    return g_user_ws ? *g_user_ws : g_work[cur_dev()];
+}
+size_t workspace_peak() { return backing(&g_work_facade).peak; }
 void *Arena::alloc(size_t bytes) { return backing(this).alloc(bytes); }
 size_t Arena::mark() { return backing(this).mark(); }
 void Arena::release(size_t m) { backing(this).release(m); }
@@ -104,39 +147,154 @@ __global__ void k_community_sizes(const uint32_t *__restrict__ C, uint32_t n, ui
         atomicAdd(size + C[i], 1u);
 }
 
-// Input check: offsets non-decreasing from 0 to nnz, targets < n, weights
-// finite and > 0 (float32 input).  flags[0] counts violations.
-__global__ void k_check_graph(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
-                              const float *__restrict__ w, uint32_t n, uint64_t nnz, unsigned long long *bad) {
-    unsigned long long b = 0;
-    uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = tid; i < n; i += stride)
-        if (off[i + 1] < off[i]) b++;
-    if (tid == 0 && (off[0] != 0 || off[n] != nnz)) b++;
-    for (uint64_t e = tid; e < nnz; e += stride) {
-        if (tgt[e] >= n) b++;
+// Input checks.  Offsets: non-decreasing from 0 to nnz (checked first: the
+// row kernels below trust them).  Entries: targets < n, weights finite and
+// > 0.  Symmetry (Section 3: G is undirected, w_ij = w_ji): every stored
+// entry (i, j, w) with i != j adds a 64-bit hash of the unordered pair and
+// the weight's bits to the "below" sums when i < j and to the "above" sums
+// when i > j.  A symmetric CSR stores the same multiset of (pair, weight) on
+// both sides, so its counts and sums agree; an asymmetric one passes only if
+// two independent 64-bit sums collide at once.  The hash is the MurmurHash3
+// 64-bit finaliser (Appleby) over the pair with the weight mixed in.
+struct GraphCheck {
+    unsigned long long bad;         // offset, target and weight violations
+    unsigned long long cnt[2];      // entries below / above the diagonal
+    unsigned long long fp[2][2];    // [side][hash] sums, modulo 2^64
+    uint32_t nlong;                 // rows left to the long-row kernel
+};
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+struct CheckAcc {
+    unsigned long long bad = 0, cnt[2] = {0, 0}, fp[2][2] = {{0, 0}, {0, 0}};
+    __device__ void entry(uint32_t i, uint32_t j, const float *w, uint64_t p, uint32_t n) {
+        uint32_t wb = 0;
         if (w) {
-            float x = w[e];
-            if (!(x > 0.0f) || isinf(x)) b++;
+            const float x = __ldg(w + p);
+            if (!(x > 0.0f) || isinf(x)) bad++;
+            wb = __float_as_uint(x);
+        }
+        if (j >= n) { bad++; return; }
+        if (i == j) return;
+        const int side = i > j;
+        const uint64_t key = side ? (((uint64_t)j << 32) | i) : (((uint64_t)i << 32) | j);
+        fp[side][0] += fmix64(key ^ fmix64((uint64_t)wb + 0x9E3779B97F4A7C15ull));
+        fp[side][1] += fmix64(key * 0xD6E8FEB86659FD93ull + fmix64((uint64_t)wb ^ 0xA0761D6478BD642Full));
+        cnt[side]++;
+    }
+    __device__ void flush(GraphCheck *g) {
+        unsigned long long v[7] = {bad, cnt[0], cnt[1], fp[0][0], fp[0][1], fp[1][0], fp[1][1]};
+        unsigned long long *dst[7] = {&g->bad, &g->cnt[0], &g->cnt[1], &g->fp[0][0], &g->fp[0][1], &g->fp[1][0],
+                                      &g->fp[1][1]};
+#pragma unroll
+        for (int k = 0; k < 7; k++) {
+            const unsigned long long t = warp_sum(v[k]);
+            if ((threadIdx.x & 31) == 0 && t) atomicAdd(dst[k], t);
         }
     }
-    if (b) atomicAdd(bad, b);
+};
+
+__global__ void k_check_offsets(const uint64_t *__restrict__ off, uint32_t n, uint64_t nnz, GraphCheck *g) {
+    unsigned long long b = 0;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (uint64_t i = tid; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        if (off[i + 1] < off[i]) b++;
+    if (tid == 0 && (off[0] != 0 || off[n] != nnz)) b++;
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&g->bad, b);
+}
+
+constexpr uint32_t CHECK_SHORT = 64;    // rows up to this length: one thread
+constexpr uint32_t CHECK_CHUNK = 2048;  // longer rows: tasks of this many entries, one block each
+
+__global__ void k_check_rows(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                             const float *__restrict__ w, uint32_t n, GraphCheck *g, uint32_t *longlist) {
+    CheckAcc a;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t b = off[i], e = off[i + 1];
+        if (e - b > CHECK_SHORT) {
+            longlist[atomicAdd(&g->nlong, 1u)] = i;
+            continue;
+        }
+        for (uint64_t p = b; p < e; p++) a.entry(i, __ldg(tgt + p), w, p, n);
+    }
+    a.flush(g);
+}
+
+__global__ void k_check_long_tasks(const uint64_t *__restrict__ off, const uint32_t *__restrict__ longlist,
+                                   uint32_t nlong, uint64_t *ntask) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nlong; t += gridDim.x * blockDim.x) {
+        const uint32_t i = longlist[t];
+        ntask[t] = (off[i + 1] - off[i] + CHECK_CHUNK - 1) / CHECK_CHUNK;
+    }
+}
+
+__global__ void k_check_long(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
+                             const float *__restrict__ w, uint32_t n, const uint32_t *__restrict__ longlist,
+                             const uint64_t *__restrict__ tasks, const uint32_t *__restrict__ owner,
+                             uint64_t ntasks, GraphCheck *g) {
+    CheckAcc a;
+    for (uint64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        const uint32_t t = owner[task];
+        const uint32_t i = longlist[t];
+        const uint64_t b = off[i] + (task - tasks[t]) * CHECK_CHUNK;
+        const uint64_t e = min(b + CHECK_CHUNK, off[i + 1]);
+        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) a.entry(i, __ldg(tgt + p), w, p, n);
+    }
+    a.flush(g);
 }
 
 void check_graph(const uint64_t *off, const uint32_t *tgt, const float *w, uint32_t n, uint64_t nnz,
-                        cudaStream_t s) {
+                 cudaStream_t s) {
     size_t mk = arena().mark();
-    unsigned long long *bad = arena().get<unsigned long long>(1);
-    GSP_CUDA(cudaMemsetAsync(bad, 0, sizeof(*bad), s));
-    k_check_graph<<<grid_for(std::max<uint64_t>(n, nnz), 256), 256, 0, s>>>(off, tgt, w, n, nnz, bad);
+    GraphCheck *d = arena().get<GraphCheck>(1);
+    GraphCheck h;
+    GSP_CUDA(cudaMemsetAsync(d, 0, sizeof(GraphCheck), s));
+    k_check_offsets<<<grid_for(n, 256), 256, 0, s>>>(off, n, nnz, d);
     GSP_CHECK_LAUNCH();
-    unsigned long long h = 0;
-    GSP_CUDA(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
     GSP_CUDA(cudaStreamSynchronize(s));
+    if (h.bad) arena().release(mk);
+    GSP_REQUIRE(h.bad == 0, "invalid graph: offsets must rise from 0 to nnz (%llu violations)", h.bad);
+    if (nnz) {
+        uint32_t *longlist = arena().get<uint32_t>(n);
+        k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(off, tgt, w, n, d, longlist);
+        GSP_CHECK_LAUNCH();
+        GSP_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+        if (h.nlong) {
+            uint64_t *ntask = arena().get<uint64_t>(h.nlong);
+            uint64_t *tasks = arena().get<uint64_t>((size_t)h.nlong + 1);
+            k_check_long_tasks<<<grid_for(h.nlong, 256), 256, 0, s>>>(off, longlist, h.nlong, ntask);
+            GSP_CHECK_LAUNCH();
+            exclusive_scan_u64(ntask, tasks, h.nlong, s);
+            uint64_t ntasks = 0;
+            GSP_CUDA(cudaMemcpyAsync(&ntasks, tasks + h.nlong, sizeof(ntasks), cudaMemcpyDeviceToHost, s));
+            GSP_CUDA(cudaStreamSynchronize(s));
+            uint32_t *owner = arena().get<uint32_t>(ntasks);
+            task_items(tasks, h.nlong, owner, s);
+            k_check_long<<<grid_for(ntasks, 1, sms(8)), 256, 0, s>>>(off, tgt, w, n, longlist, tasks, owner,
+                                                                     ntasks, d);
+            GSP_CHECK_LAUNCH();
+        }
+        GSP_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GSP_CUDA(cudaStreamSynchronize(s));
+    }
     arena().release(mk);
-    GSP_REQUIRE(h == 0, "invalid graph: %llu violations (offsets must rise from 0 to nnz, targets < n, "
-                        "weights finite and > 0)", h);
+    GSP_REQUIRE(h.bad == 0, "invalid graph: %llu violations (targets must be < n, weights finite and > 0)", h.bad);
+    if (h.cnt[0] != h.cnt[1] || h.fp[0][0] != h.fp[1][0] || h.fp[0][1] != h.fp[1][1]) {
+        set_error("graph is not symmetric: %llu entries below the diagonal, %llu above, or their (pair, weight) "
+                  "multisets differ (Section 3 needs w_ij = w_ji for every stored entry)",
+                  h.cnt[0], h.cnt[1]);
+        throw Error{GSP_ERR_NOT_SYMMETRIC};
+    }
 }
 
 __global__ void k_check_ids(const uint32_t *__restrict__ C, uint32_t n, uint32_t bound, unsigned long long *bad) {
@@ -201,16 +359,26 @@ struct PruneCtx {
     float threshold = 0.5f;
 };
 
-// One sweep: cl.W waves; in frozen-state mode each wave's moves are applied
-// before the next wave.
+// One sweep: cl.W waves, each run wave_repeats_at(it) times (mb.repeats in
+// the first iteration of a pass, once afterwards).  In frozen-state mode the
+// moves of each repeat are applied (and the movers' neighbours re-marked)
+// before the next; a repeat takes the vertices of the wave that the earlier
+// repeats re-marked, on the state those moves left.
+int wave_repeats_at(const MoveBuffers &mb, int it) { return (it == 0 && mb.repeats > 1) ? mb.repeats : 1; }
+
 void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
                     bool pruned, int it, int max_it, const uint32_t *wave_n, bool reset_ctr, cudaStream_t s) {
     if (reset_ctr) GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
+    const int R = wave_repeats_at(mb, it);
     for (int wv = 0; wv < cl.W; wv++) {
         if (!wave_n[wv]) continue;
-        if (sync) GSP_CUDA(cudaMemsetAsync(mb.mv_cnt, 0, sizeof(uint32_t), s));
-        move_wave(g, cl, mb, wv, sync, fp64, rule, pruned, it, max_it, s);
-        if (sync) apply_moves(g, mb, wave_n[wv], s);
+        for (int r = 0; r < R; r++) {
+            mb.cur_repeat = r;
+            if (sync) GSP_CUDA(cudaMemsetAsync(mb.mv_cnt, 0, sizeof(uint32_t), s));
+            move_wave(g, cl, mb, wv, sync, fp64, rule, pruned, it, max_it, s);
+            if (sync) apply_moves(g, mb, wave_n[wv], s);
+        }
+        mb.cur_repeat = 0;
     }
 }
 
@@ -350,7 +518,7 @@ void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.mv_vtx = arena().get<uint32_t>(n);
     mb.mv_cmt = arena().get<uint32_t>(n);
     mb.mv_cnt = arena().get<uint32_t>(1);
-    mb.mv_cnts = arena().get<uint32_t>(MAX_WAVES);
+    mb.mv_cnts = arena().get<uint32_t>(MAX_WAVES * MAX_REPEATS);
     mb.bar = arena().get<GridBar>(1);
     mb.big = arena().get<uint32_t>(n);
     mb.nbig = arena().get<uint32_t>(1);
@@ -430,6 +598,7 @@ struct Timer {
 struct TraceSpec {
     float *x = nullptr;
     uint8_t *y = nullptr;
+    uint64_t *keys = nullptr;
     uint32_t cap = 0, every = 1;
     uint32_t *cnt = nullptr;  // device counter
 };
@@ -439,7 +608,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     g_events.reset();
     const uint32_t n0 = g0.n;
     const bool sync = o.move == GSP_MOVE_SYNC;
-    const int W = sync ? o.waves : 1;
+    const int W = o.waves;
     const bool fp64 = o.precision == GSP_PREC_FP64;
     PruneCtx pr;
     pr.learned = o.prune == GSP_PRUNE_LEARNED && o.mlp_params && !trace;
@@ -456,12 +625,14 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     uint32_t *labels = arena().get<uint32_t>(n0);
     uint32_t *Cd = arena().get<uint32_t>(n0);
     mb.K = K;
+    mb.repeats = o.wave_repeats;
     mb.mlp = static_cast<const float *>(o.mlp_params);
     if (features) alloc_features(mb, n0, s);
     if (trace) {
         mb.trace_x = trace->x;
         mb.trace_y = trace->y;
         mb.trace_cnt = trace->cnt;
+        mb.trace_keys = trace->keys;
         mb.trace_cap = trace->cap;
         mb.trace_every = trace->every;
     }
@@ -503,6 +674,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
             mb.max_logk = (float)log1p(max_value(K, nv, s));
             if (!(mb.max_logk > 0.0f)) mb.max_logk = 1.0f;
             mb.trace_salt = 0x85EBCA6Bu * (uint32_t)(lp + 1);
+            mb.trace_pass = lp;
         }
         Classes cl;
         classify_vertices(cur, cl, W, s);
@@ -568,6 +740,8 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     local.final_communities = kf;
     local.modularity = q;
     local.ms_total = total.lap();
+    local.disconnected = o.count_disconnected ? count_disconnected(g0, membership, nullptr, s) : GSP_NOT_COUNTED;
+    local.workspace_bytes = workspace_peak();
     if (modularity_out) *modularity_out = q;
     if (st) *st = local;
 }
@@ -617,10 +791,13 @@ void check_opts(const gsp_opts &o) {
     GSP_REQUIRE(o.split_when == GSP_SPLIT_PASS || o.split_when == GSP_SPLIT_LAST, "unknown split_when");
     GSP_REQUIRE(o.move == GSP_MOVE_ASYNC || o.move == GSP_MOVE_SYNC, "unknown move mode");
     GSP_REQUIRE(o.waves >= 1 && o.waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
+    GSP_REQUIRE(o.wave_repeats >= 1 && o.wave_repeats <= MAX_REPEATS, "wave_repeats must be in [1, %d]",
+                MAX_REPEATS);
     GSP_REQUIRE(o.prune_threshold >= 0.0f && o.prune_threshold <= 1.0f, "prune_threshold must be in [0, 1]");
     GSP_REQUIRE(o.precision == GSP_PREC_MIXED || o.precision == GSP_PREC_FP64, "unknown precision");
     GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS || o.prune == GSP_PRUNE_LEARNED, "unknown prune mode");
     GSP_REQUIRE(o.prune != GSP_PRUNE_LEARNED || o.mlp_params != nullptr, "learned pruning needs mlp_params");
+    GSP_REQUIRE(o.workspace == nullptr || o.workspace_bytes >= 256, "workspace_bytes too small");
 }
 }  // namespace gsp
 
@@ -638,12 +815,16 @@ void gsp_default_opts(gsp_opts *o) {
     o->split_when = GSP_SPLIT_PASS;
     o->move = GSP_MOVE_SYNC;
     o->waves = 17;
+    o->wave_repeats = 3;
     o->precision = GSP_PREC_MIXED;
     o->singleton_rule = 1;
     o->prune = GSP_PRUNE_FLAGS;
     o->mlp_params = nullptr;
     o->full_sweep_every = 4;
     o->prune_threshold = 0.5f;
+    o->count_disconnected = 0;
+    o->workspace = nullptr;
+    o->workspace_bytes = 0;
     o->stream = nullptr;
 }
 
@@ -655,6 +836,7 @@ const char *gsp_status_string(gsp_status s) {
     case GSP_ERR_CUDA: return "CUDA error";
     case GSP_ERR_TIMEOUT: return "device wait timed out";
     case GSP_ERR_CAPACITY: return "capacity exceeded";
+    case GSP_ERR_NOT_SYMMETRIC: return "graph not symmetric";
     }
     return "unknown status";
 }
@@ -662,6 +844,22 @@ const char *gsp_status_string(gsp_status s) {
 const char *gsp_last_error(void) { return g_err; }
 
 uint64_t gsp_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+void gsp_release_workspace(void) {
+    const int d = cur_dev();
+    cudaDeviceSynchronize();
+    g_work[d].free_all();
+    g_io[d].free_all();
+}
+
+uint64_t gsp_workspace_reserved(void) {
+    uint64_t b = 0;
+    for (int d = 0; d < 16; d++) {
+        for (const auto &c : g_work[d].chunks) b += c.cap;
+        for (const auto &c : g_io[d].chunks) b += c.cap;
+    }
+    return b;
+}
 
 gsp_status gsp_louvain(const uint64_t *offsets, const uint32_t *targets, const float *weights, uint32_t n,
                        uint64_t nnz, const gsp_opts *opts, uint32_t *membership, double *modularity,
@@ -674,6 +872,7 @@ gsp_status gsp_louvain(const uint64_t *offsets, const uint32_t *targets, const f
     GSP_REQUIRE(membership != nullptr, "membership must not be NULL");
     DevGraph g = make_graph(offsets, targets, weights, GSP_W_F32, n, nnz);
     cudaStream_t s = S(o.stream);
+    UserWorkspace uw(o.workspace, o.workspace_bytes);
     arena().reset();
     check_graph(offsets, targets, weights, n, nnz, s);
     louvain_run(g, o, membership, modularity, stats, s);
@@ -701,6 +900,7 @@ gsp_status gsp_louvain_host(const uint64_t *offsets, const uint32_t *targets, co
         GSP_CUDA(cudaMemcpyAsync(dw, weights, sizeof(float) * nnz, cudaMemcpyHostToDevice, s));
     }
     DevGraph g = make_graph(doff, dtgt, dw, GSP_W_F32, n, nnz);
+    UserWorkspace uw(o.workspace, o.workspace_bytes);
     arena().reset();
     check_graph(doff, dtgt, dw, n, nnz, s);
     louvain_run(g, o, dC, modularity, stats, s);
@@ -715,6 +915,7 @@ gsp_status gsp_vertex_weights(const uint64_t *offsets, const uint32_t *targets, 
     DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
     GSP_REQUIRE(K != nullptr, "K must not be NULL");
     arena().reset();
+    check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), S(stream));
     double m = vertex_weights(g, K, nullptr, S(stream), exact_lsb(g, S(stream)));
     if (m_host) *m_host = m;
     GSP_API_END
@@ -726,6 +927,7 @@ gsp_status gsp_modularity(const uint64_t *offsets, const uint32_t *targets, cons
     DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
     GSP_REQUIRE(C != nullptr && q_host != nullptr, "C and q_host must not be NULL");
     arena().reset();
+    check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), S(stream));
     check_ids(C, n, n, "membership", S(stream));
     *q_host = modularity(g, C, S(stream), exact_lsb(g, S(stream)));
     GSP_API_END
@@ -742,8 +944,8 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
     GSP_REQUIRE(precision == GSP_PREC_MIXED || precision == GSP_PREC_FP64, "unknown precision");
     cudaStream_t s = S(stream);
     arena().reset();
+    check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), s);
     check_ids(C, n, n, "membership", s);
-    if (nnz) check_ids(targets, (uint32_t)std::min<uint64_t>(nnz, 0xFFFFFFFFu), n, "targets", s);
     // one frozen-state wave over all vertices; decisions go to `choice`,
     // nothing is applied (C and Sigma are only read)
     MoveBuffers mb;
@@ -776,23 +978,26 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
 
 gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
                           uint64_t nnz, uint32_t *C, const double *K, double *Sigma, double m, double tolerance,
-                          int max_iterations, int move, int waves, int precision, int singleton_rule,
-                          int *iterations_host, void *stream) {
+                          int max_iterations, int move, int waves, int wave_repeats, int precision,
+                          int singleton_rule, int *iterations_host, void *stream) {
     GSP_API_BEGIN
     DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
     GSP_REQUIRE(C && K && Sigma, "C, K and Sigma must not be NULL");
     GSP_REQUIRE(m > 0.0 && max_iterations >= 1, "m must be > 0 and max_iterations >= 1");
     GSP_REQUIRE(move == GSP_MOVE_ASYNC || move == GSP_MOVE_SYNC, "unknown move mode");
     GSP_REQUIRE(waves >= 1 && waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
+    GSP_REQUIRE(wave_repeats >= 1 && wave_repeats <= MAX_REPEATS, "wave_repeats must be in [1, %d]", MAX_REPEATS);
     GSP_REQUIRE(precision == GSP_PREC_MIXED || precision == GSP_PREC_FP64, "unknown precision");
     cudaStream_t s = S(stream);
     arena().reset();
     g_events.reset();
+    check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), s);
     check_ids(C, n, n, "membership", s);
     bool sync = move == GSP_MOVE_SYNC;
     MoveBuffers mb;
     alloc_move_state(mb, n);
     mb.K = K;
+    mb.repeats = wave_repeats;
     GSP_CUDA(cudaMemcpyAsync(mb.m_dev, &m, sizeof(double), cudaMemcpyHostToDevice, s));
     GSP_CUDA(cudaMemcpyAsync(mb.C, C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     GSP_CUDA(cudaMemcpyAsync(mb.Sigma, Sigma, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -802,7 +1007,7 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
     GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
     GSP_CUDA(cudaMemsetAsync(mb.mark, 0, n, s));
     Classes cl;
-    classify_vertices(g, cl, sync ? waves : 1, s);
+    classify_vertices(g, cl, waves, s);
     alloc_pool(mb, cl, s);
     PruneCtx pr;
     MoveLoopResult r = move_loop(g, cl, mb, tolerance, max_iterations, sync, precision == GSP_PREC_FP64,
@@ -816,7 +1021,7 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
 
 gsp_status gsp_louvain_trace(const uint64_t *offsets, const uint32_t *targets, const float *weights, uint32_t n,
                              uint64_t nnz, const gsp_opts *opts, float *features, uint8_t *labels,
-                             uint32_t capacity, uint32_t sample_every, uint32_t *rows_host) {
+                             uint64_t *keys, uint32_t capacity, uint32_t sample_every, uint32_t *rows_host) {
     GSP_API_BEGIN
     gsp_opts o;
     if (opts) o = *opts;
@@ -832,6 +1037,7 @@ gsp_status gsp_louvain_trace(const uint64_t *offsets, const uint32_t *targets, c
     TraceSpec tr;
     tr.x = features;
     tr.y = labels;
+    tr.keys = keys;
     tr.cap = capacity;
     tr.every = sample_every;
     tr.cnt = arena().get<uint32_t>(1);
@@ -854,6 +1060,7 @@ gsp_status gsp_split(const uint64_t *offsets, const uint32_t *targets, uint32_t 
                             nnz);
     cudaStream_t s = S(stream);
     arena().reset();
+    check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), s);
     check_ids(C, n, n, "membership", s);
     Classes cl;
     classify_vertices(g, cl, 1, s);
@@ -892,6 +1099,7 @@ gsp_status gsp_aggregate(const uint64_t *offsets, const uint32_t *targets, const
     GSP_REQUIRE(C && out_offsets && k > 0 && k <= n, "invalid arguments");
     GSP_REQUIRE(nnz == 0 || (out_targets && out_weights), "output arrays must not be NULL");
     arena().reset();
+    check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), S(stream));
     check_ids(C, n, k, "membership", S(stream));
     uint64_t e = aggregate(g, C, k, out_offsets, out_targets, out_weights, S(stream));
     GSP_CUDA(cudaStreamSynchronize(S(stream)));
@@ -906,6 +1114,7 @@ gsp_status gsp_count_disconnected(const uint64_t *offsets, const uint32_t *targe
     DevGraph g = make_graph(offsets, targets, targets ? (const void *)targets : (const void *)offsets, GSP_W_F32, n,
                             nnz);
     arena().reset();
+    check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), S(stream));
     check_ids(C, n, n, "membership", S(stream));
     uint32_t c = count_disconnected(g, C, flags, S(stream));
     if (count_host) *count_host = c;

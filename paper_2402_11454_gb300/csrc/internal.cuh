@@ -38,6 +38,7 @@ Tuning &tuning();
 enum { CLS_G4 = 0, CLS_G8, CLS_G16, CLS_G32, CLS_W512, CLS_BLOCK, CLS_HUGE, NUM_CLS };
 constexpr uint32_t CLS_MAXDEG[NUM_CLS] = {8, 16, 32, 128, 512, 2048, 0xFFFFFFFFu};
 constexpr int MAX_WAVES = 64;
+constexpr int MAX_REPEATS = 8;  // repeats of a wave (gsp_opts.wave_repeats)
 
 struct Classes {
     uint32_t *list = nullptr;
@@ -90,13 +91,14 @@ struct MoveBuffers {
     const double *m_g = nullptr;     // batches: m of each graph
     const double *minv_g = nullptr;  // batches: 1/m of each graph
     int lsb = INT_MIN;               // weights in exact integer units of 2^lsb (exact_lsb)
+    int repeats = 1;                 // repeats of a wave in a pass's first iteration (wave_repeats_at)
     double *dq_g = nullptr;          // batches: summed gain of each graph in a sweep
     MoveCounters *ctr = nullptr;
     void *pool = nullptr;        // huge-class hashtables
     uint32_t *mv_vtx = nullptr;  // moves decided in the current wave (frozen-state mode)
     uint32_t *mv_cmt = nullptr;
     uint32_t *mv_cnt = nullptr;
-    uint32_t *mv_cnts = nullptr; // persistent sweep: one move counter per wave
+    uint32_t *mv_cnts = nullptr; // persistent sweep: one move counter per repeat of a wave
     GridBar *bar = nullptr;      // persistent sweep: grid barrier
     uint32_t *choice = nullptr;  // optional: decision of each vertex (single-sweep API)
     uint32_t *big = nullptr;     // movers whose neighbours all blocks re-mark together
@@ -112,7 +114,9 @@ struct MoveBuffers {
     float *trace_x = nullptr;
     uint8_t *trace_y = nullptr;
     uint32_t *trace_cnt = nullptr;
+    uint64_t *trace_keys = nullptr;  // optional: (pass, iteration, repeat, vertex) of each row
     uint32_t trace_cap = 0, trace_every = 1, trace_salt = 0;
+    int trace_pass = 0, cur_repeat = 0;
 };
 
 // Side streams for the independent kernels of a wave (fork/join with
@@ -138,7 +142,22 @@ void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream
 bool sweep_persistent(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool fp64, bool rule, int iteration,
                       int max_iterations, cudaStream_t s);
 
+// Scratch of one call taken from a caller's device buffer (gsp_opts.workspace)
+// for as long as the object lives; base == NULL leaves the internal workspace
+// in use.  workspace_peak(): most bytes the current workspace held at once
+// since the call began.
+struct UserWorkspace {
+    struct Impl;
+    Impl *impl = nullptr;
+    UserWorkspace(void *base, size_t bytes);
+    ~UserWorkspace();
+    UserWorkspace(const UserWorkspace &) = delete;
+    UserWorkspace &operator=(const UserWorkspace &) = delete;
+};
+size_t workspace_peak();
+
 // driver.cu helpers shared with the batched driver
+int wave_repeats_at(const MoveBuffers &mb, int iteration);  // runs of each wave in that iteration
 void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
                     bool pruned, int it, int max_it, const uint32_t *wave_n, bool reset_ctr, cudaStream_t s);
 bool graphs_enabled();
@@ -183,8 +202,10 @@ double vertex_weights(const DevGraph &g, double *K, double *m_dev, cudaStream_t 
 double modularity(const DevGraph &g, const uint32_t *C, cudaStream_t s, int lsb = INT_MIN);
 double modularity_scratch(const DevGraph &g, const uint32_t *C, double *Sig, double *acc, uint32_t *longlist,
                           uint32_t *nlong, cudaStream_t s);
-unsigned long long count_out_of_range(const uint32_t *x, uint32_t n, uint32_t bound, unsigned long long *counter,
+unsigned long long count_out_of_range(const uint32_t *x, uint64_t n, uint32_t bound, unsigned long long *counter,
                                       cudaStream_t s);
+void check_csr(const uint64_t *off, const uint32_t *tgt, uint32_t n, uint64_t nnz, unsigned long long *counter,
+               cudaStream_t s);
 uint32_t count_disconnected(const DevGraph &g, const uint32_t *C, uint8_t *flags, cudaStream_t s);
 void lookup(uint32_t n_top, uint32_t *C_top, const uint32_t *C_pass, cudaStream_t s);
 // Renumber membership by smallest vertex id (final numbering); returns k.

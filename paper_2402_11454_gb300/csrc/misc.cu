@@ -365,23 +365,52 @@ double modularity_scratch(const DevGraph &g, const uint32_t *C, double *Sig, dou
     return modularity_scratch_t<float>(g, C, Sig, acc, longlist, nlong, s);
 }
 
-__global__ void k_count_ge(const uint32_t *__restrict__ x, uint32_t n, uint32_t bound, unsigned long long *out) {
+__global__ void k_count_ge(const uint32_t *__restrict__ x, uint64_t n, uint32_t bound, unsigned long long *out) {
     unsigned long long b = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
         if (x[i] >= bound) b++;
     if (b) atomicAdd(out, b);
 }
 
-// Number of entries x[i] >= bound, counted in *counter (caller-provided, no allocation).
-unsigned long long count_out_of_range(const uint32_t *x, uint32_t n, uint32_t bound, unsigned long long *counter,
+// Number of entries x[i] >= bound (i < n), counted in *counter
+// (caller-provided, no allocation).
+unsigned long long count_out_of_range(const uint32_t *x, uint64_t n, uint32_t bound, unsigned long long *counter,
                                       cudaStream_t s) {
     GSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(*counter), s));
-    k_count_ge<<<grid_for(n, 256), 256, 0, s>>>(x, n, bound, counter);
-    GSP_CHECK_LAUNCH();
+    if (n) {
+        k_count_ge<<<grid_for(n, 256), 256, 0, s>>>(x, n, bound, counter);
+        GSP_CHECK_LAUNCH();
+    }
     unsigned long long h = 0;
     GSP_CUDA(cudaMemcpyAsync(&h, counter, sizeof(h), cudaMemcpyDeviceToHost, s));
     GSP_CUDA(cudaStreamSynchronize(s));
     return h;
+}
+
+__global__ void k_count_bad_offsets(const uint64_t *__restrict__ off, uint32_t n, uint64_t nnz,
+                                    unsigned long long *out) {
+    unsigned long long b = 0;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (uint64_t i = tid; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        if (off[i + 1] < off[i]) b++;
+    if (tid == 0 && (off[0] != 0 || off[n] != nnz)) b++;
+    if (b) atomicAdd(out, b);
+}
+
+// CSR structure for the phase entry points: offsets rise from 0 to nnz and
+// every target is < n; raises GSP_ERR_INVALID otherwise.  *counter is
+// caller-provided scratch (no allocation).
+void check_csr(const uint64_t *off, const uint32_t *tgt, uint32_t n, uint64_t nnz, unsigned long long *counter,
+               cudaStream_t s) {
+    GSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(*counter), s));
+    k_count_bad_offsets<<<grid_for(n, 256), 256, 0, s>>>(off, n, nnz, counter);
+    GSP_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    GSP_CUDA(cudaMemcpyAsync(&h, counter, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GSP_CUDA(cudaStreamSynchronize(s));
+    GSP_REQUIRE(h == 0, "invalid graph: offsets must rise from 0 to nnz");
+    h = count_out_of_range(tgt, nnz, n, counter, s);
+    GSP_REQUIRE(h == 0, "invalid graph: %llu targets out of range (must be < %u)", h, n);
 }
 
 // ---------------------------------------------------------------- renumber
@@ -484,7 +513,7 @@ uint32_t count_disconnected(const DevGraph &g, const uint32_t *C, uint8_t *flags
     unsigned long long *cnt = arena().get<unsigned long long>(1);
     Classes cl;
     classify_vertices(g, cl, 1, s);
-    split_labels(g, cl, C, GSP_SPLIT_BFS, lab, s);
+    split_labels(g, cl, C, GSP_SPLIT_SV, lab, s);  // every technique gives the same labels
     GSP_CUDA(cudaMemsetAsync(ncomp, 0, sizeof(uint32_t) * g.n, s));
     GSP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
     unsigned gr = grid_for(g.n, 256);

@@ -63,6 +63,8 @@ struct MoveArgs {
     float *trace_x;
     uint8_t *trace_y;
     uint32_t *trace_cnt;
+    uint64_t *trace_keys;  // optional: trace_tag | vertex per row
+    uint64_t trace_tag;    // pass << 56 | iteration << 48 | repeat << 40
     uint32_t trace_cap, trace_every;
     float max_logk;
     float iter_frac;
@@ -274,6 +276,7 @@ __device__ __forceinline__ void record_visit(const MoveArgs &a, uint32_t i, uint
 #pragma unroll
             for (int k = 0; k < MLP_IN; k++) a.trace_x[(size_t)slot * MLP_IN + k] = x[k];
             a.trace_y[slot] = (uint8_t)moved;
+            if (a.trace_keys) a.trace_keys[slot] = a.trace_tag | i;
         }
     }
     float kept = Ki > 0.0 ? (float)(kid / Ki) : 0.0f;
@@ -681,7 +684,7 @@ __global__ void k_mark_big(const uint64_t *__restrict__ off, const uint32_t *__r
 // a million or so vertices, a sweep of W waves costs 4-6 launches per wave on
 // the normal path, and on small graphs those dependent launches, not the
 // work, set the time.  Here one cooperative launch runs the whole sweep: per
-// wave, every block takes its share of each degree class (the same device
+// run of a wave, every block takes its share of each degree class (the same device
 // bodies as the per-class kernels, frozen-state decisions into the wave's
 // move list), a grid barrier, the moves applied and the re-marks merged,
 // and a grid barrier.  Data written by earlier phases are read through L2
@@ -765,15 +768,16 @@ __device__ void merge_body_l2(uint8_t *act, uint8_t *mark, uint32_t n, uint32_t 
 
 template <typename WT, bool F64>
 __global__ void __launch_bounds__(256) k_sweep_persistent(MoveArgs a, const uint32_t *__restrict__ list,
-                                                          const uint32_t *__restrict__ start, int W, uint32_t n,
-                                                          uint32_t *mv_cnts, GridBar *bar) {
+                                                          const uint32_t *__restrict__ start, int W, int R,
+                                                          uint32_t n, uint32_t *mv_cnts, GridBar *bar) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const uint32_t lb = blockIdx.x, nb = gridDim.x;
     LocalCtr lc;  // one flush per block per sweep
     if (lb == 0)
-        for (int t = threadIdx.x; t < W; t += blockDim.x) mv_cnts[t] = 0;
+        for (int t = threadIdx.x; t < W * R; t += blockDim.x) mv_cnts[t] = 0;
     if (!grid_sync(bar, nb, a.ctr)) return;
-    for (int wv = 0; wv < W; wv++) {
+    for (int wr = 0; wr < W * R; wr++) {  // wave wr / R, repeat wr % R
+        const int wv = wr / R;
         uint32_t cb[CLS_HUGE], cc[CLS_HUGE], tot = 0;
 #pragma unroll
         for (int k = 0; k < CLS_HUGE; k++) {
@@ -783,7 +787,7 @@ __global__ void __launch_bounds__(256) k_sweep_persistent(MoveArgs a, const uint
         }
         if (!tot) continue;  // the same for every block
         MoveArgs aw = a;
-        aw.mv_cnt = mv_cnts + wv;
+        aw.mv_cnt = mv_cnts + wr;
         if (cc[CLS_G4]) group_body<4, 16, WT, F64, 2>(aw, list + cb[CLS_G4], cc[CLS_G4], lb, nb, dyn_smem, lc);
         if (cc[CLS_G8]) group_body<8, 32, WT, F64, 2>(aw, list + cb[CLS_G8], cc[CLS_G8], lb, nb, dyn_smem, lc);
         if (cc[CLS_G16]) group_body<16, 64, WT, F64, 2>(aw, list + cb[CLS_G16], cc[CLS_G16], lb, nb, dyn_smem, lc);
@@ -793,7 +797,7 @@ __global__ void __launch_bounds__(256) k_sweep_persistent(MoveArgs a, const uint
         if (cc[CLS_BLOCK])
             block_body<4096, WT, F64, 2>(aw, list + cb[CLS_BLOCK], cc[CLS_BLOCK], lb, nb, dyn_smem, lc);
         if (!grid_sync(bar, nb, a.ctr)) return;
-        apply_body_l2(a.mv_vtx, a.mv_cmt, mv_cnts + wv, a.K, a.C, a.Sig, a.size, lb, nb, dyn_smem, a.lsb);
+        apply_body_l2(a.mv_vtx, a.mv_cmt, mv_cnts + wr, a.K, a.C, a.Sig, a.size, lb, nb, dyn_smem, a.lsb);
         merge_body_l2(a.act, a.mark, n, lb, nb);
         if (!grid_sync(bar, nb, a.ctr)) return;
     }
@@ -1293,6 +1297,9 @@ static MoveArgs make_move_args(const DevGraph &g, const MoveBuffers &mb, bool sy
     a.trace_y = mb.trace_y;
     a.trace_cnt = mb.trace_cnt;
     a.trace_cap = mb.trace_cap;
+    a.trace_keys = mb.trace_keys;
+    a.trace_tag = ((uint64_t)(mb.trace_pass & 0xFF) << 56) | ((uint64_t)(iteration & 0xFF) << 48) |
+                  ((uint64_t)(mb.cur_repeat & 0xFF) << 40);
     a.trace_every = mb.trace_every ? mb.trace_every : 1;
     a.max_logk = mb.max_logk;
     a.iter_frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
@@ -1301,7 +1308,8 @@ static MoveArgs make_move_args(const DevGraph &g, const MoveBuffers &mb, bool sy
 }
 
 template <typename WT, bool F64>
-static bool launch_persistent(const MoveArgs &a, const Classes &cl, uint32_t n, MoveBuffers &mb, cudaStream_t s) {
+static bool launch_persistent(const MoveArgs &a, const Classes &cl, uint32_t n, MoveBuffers &mb, int iteration,
+                              cudaStream_t s) {
     using V = typename std::conditional<F64, double, float>::type;
     constexpr size_t smem = std::max(std::max((size_t)8 * W512_CAP * (sizeof(uint32_t) + sizeof(V)),
                                               (size_t)4096 * (sizeof(uint32_t) + sizeof(V) + sizeof(uint16_t))),
@@ -1323,10 +1331,11 @@ static bool launch_persistent(const MoveArgs &a, const Classes &cl, uint32_t n, 
     const uint32_t *list = cl.list;
     const uint32_t *start = cl.dstart;
     int W = cl.W;
+    int R = std::min(wave_repeats_at(mb, iteration), MAX_REPEATS);
     uint32_t nn = n;
     uint32_t *cnts = mb.mv_cnts;
     GridBar *bar = mb.bar;
-    void *args[] = {&aa, &list, &start, &W, &nn, &cnts, &bar};
+    void *args[] = {&aa, &list, &start, &W, &R, &nn, &cnts, &bar};
     GSP_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), s));
     GSP_CUDA(cudaLaunchCooperativeKernel((const void *)k_sweep_persistent<WT, F64>, dim3(per_sm[dev] * sm_count()),
                                          dim3(256), args, smem, s));
@@ -1339,9 +1348,10 @@ bool sweep_persistent(const DevGraph &g, const Classes &cl, MoveBuffers &mb, boo
     if (cl.cls_count(CLS_HUGE) || mb.feat_kept || mb.choice || !cl.dstart || !mb.bar) return false;
     if (g.n > tuning().persist_max_vertices) return false;
     MoveArgs a = make_move_args(g, mb, true, rule, iteration, max_iterations);
-    if (g.wt == GSP_W_F32) return fp64 ? launch_persistent<float, true>(a, cl, g.n, mb, s)
-                                       : launch_persistent<float, false>(a, cl, g.n, mb, s);
-    return fp64 ? launch_persistent<double, true>(a, cl, g.n, mb, s) : launch_persistent<double, false>(a, cl, g.n, mb, s);
+    if (g.wt == GSP_W_F32) return fp64 ? launch_persistent<float, true>(a, cl, g.n, mb, iteration, s)
+                                       : launch_persistent<float, false>(a, cl, g.n, mb, iteration, s);
+    return fp64 ? launch_persistent<double, true>(a, cl, g.n, mb, iteration, s)
+                : launch_persistent<double, false>(a, cl, g.n, mb, iteration, s);
 }
 
 void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, bool sync, bool fp64, bool rule,

@@ -1,18 +1,22 @@
 // static_scratch.cu -- modularity (Equation 1) for callers that cannot
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured, embedders whose device memory is owned by a fixed pool
-// (inference servers, other frameworks' allocators), or processes that must
-// not grow their footprint after start-up.  gsp_modularity_static computes the
-// same value as gsp_modularity but takes its scratch from one file-scope
-// __device__ array instead of the library workspace, so it never allocates.
+// Some callers cannot call cudaMalloc: embedders whose device memory is owned
+// by a fixed pool (inference servers, other frameworks' allocators that hold
+// the whole device), or processes that must not grow their device footprint
+// after start-up.  gsp_modularity_static computes the same value as
+// gsp_modularity but takes its scratch from one file-scope __device__ array
+// instead of the library workspace, so it allocates nothing.  Like
+// gsp_modularity it waits for the stream and returns Q in host memory.
 //
 // The array is part of the module image: every device that loads the library
 // holds GSP_STATIC_SCRATCH_BYTES for it until the process exits.  Host code
 // cannot use the array's name as a device address (it is a host-side
-// stand-in), so the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current and caches it.
+// stand-in), so the set-up looks the address up with cudaGetSymbolAddress
+// while the device is current, once per device context: a context created
+// anew (after cudaDeviceReset) gets a fresh lookup.
+#include <cuda.h>  // CUcontext and the cuCtxGetCurrent signature (resolved at run time)
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -32,22 +36,51 @@ static_assert(SCRATCH_BYTES == GSP_STATIC_SCRATCH_BYTES, "scratch size in gsp.h"
 
 static __device__ __align__(256) unsigned char g_static_scratch[SCRATCH_BYTES];
 
-static char *g_scratch_addr[64];
+struct ScratchSlot {
+    CUcontext ctx;
+    char *addr;
+};
+static ScratchSlot g_scratch_addr[64];
 static std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
+// The current context, through the driver entry point the runtime hands out
+// (the library links no driver library); nullptr when unavailable.
+static CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext *);
+    static Fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(p);
+        else
+            cudaGetLastError();
+    }
+    CUcontext ctx = nullptr;
+    if (!fn || fn(&ctx) != CUDA_SUCCESS) return nullptr;
+    return ctx;
+}
+
+// Device address of the scratch array on the current device: looked up with
+// that device current the first time a context of it calls, and again when
+// the device's context has changed since (cudaDeviceReset makes a new one).
 static char *scratch_address() {
     int dev = 0;
     GSP_CUDA(cudaGetDevice(&dev));
     GSP_REQUIRE(dev >= 0 && dev < 64, "device index %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    CUcontext ctx = current_context();
+    ScratchSlot &slot = g_scratch_addr[dev];
+    if (!slot.addr || !ctx || ctx != slot.ctx) {
         void *p = nullptr;
-        GSP_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
-        g_scratch_addr[dev] = static_cast<char *>(p);
+        GSP_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));  // initialises the context when needed
+        slot.addr = static_cast<char *>(p);
+        slot.ctx = current_context();
     }
-    return g_scratch_addr[dev];
+    return slot.addr;
 }
 
 }  // namespace gsp
@@ -70,6 +103,7 @@ extern "C" gsp_status gsp_modularity_static(const uint64_t *offsets, const uint3
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         char *base = scratch_address();
         unsigned long long *counter = reinterpret_cast<unsigned long long *>(base + SO_COUNTER);
+        check_csr(offsets, targets, n, nnz, counter, s);
         unsigned long long bad = count_out_of_range(C, n, n, counter, s);
         GSP_REQUIRE(bad == 0, "membership: %llu ids out of range (must be < %u)", bad, n);
         DevGraph g;

@@ -131,12 +131,13 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
         const bool fp64 = o.precision == GSP_PREC_FP64;
         MoveBuffers mb;
         alloc_move_state(mb, n);
+        mb.repeats = o.wave_repeats;
         double *K = arena().get<double>(n);
         mb.K = K;
         const double m = vertex_weights(g, K, mb.m_dev, s);
         GSP_REQUIRE(m > 0.0, "gsp_autotune: the graph has no edges");
         Classes cl;
-        classify_vertices(g, cl, sync ? o.waves : 1, s);
+        classify_vertices(g, cl, o.waves, s);
         alloc_pool(mb, cl, s);
         uint32_t wave_n[MAX_WAVES];
         for (int wv = 0; wv < cl.W; wv++) {

@@ -60,8 +60,8 @@ def _graph(off, tgt, w=None):
 
 def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=10.0,
               aggregation_tolerance=0.8, split="lpp", split_when="pass", move="sync", waves=17,
-              precision="mixed", singleton_rule=True, prune="flags", mlp_params=None,
-              full_sweep_every=4, prune_threshold=0.5, stream=None):
+              wave_repeats=3, precision="mixed", singleton_rule=True, prune="flags", mlp_params=None,
+              full_sweep_every=4, prune_threshold=0.5, count_disconnected=False, workspace=None, stream=None):
     o = GspOpts()
     _lib.load().gsp_default_opts(ctypes.byref(o))
     o.max_passes = max_passes
@@ -73,12 +73,18 @@ def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=1
     o.split_when = SPLIT_WHEN[split_when]
     o.move = MOVE[move]
     o.waves = waves
+    o.wave_repeats = wave_repeats
     o.precision = PRECISION[precision]
     o.singleton_rule = int(bool(singleton_rule))
     o.prune = PRUNE[prune]
     o.mlp_params = None if mlp_params is None else _cuda(mlp_params, torch.float32, "mlp_params").data_ptr()
     o.full_sweep_every = full_sweep_every
     o.prune_threshold = prune_threshold
+    o.count_disconnected = int(bool(count_disconnected))
+    if workspace is not None:
+        _cuda(workspace, torch.uint8, "workspace")
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel()
     o.stream = _stream(stream).value
     return o
 
@@ -94,7 +100,9 @@ def stats_dict(st):
                 vertices_skipped=list(st.vertices_skipped[:p]),
                 move_bytes=list(st.move_bytes[:p]), ms_move_kernels=list(st.ms_move_kernels[:p]),
                 final_communities=st.final_communities, modularity=st.modularity,
-                ms_total=st.ms_total)
+                ms_total=st.ms_total,
+                disconnected=None if st.disconnected == _lib.GSP_NOT_COUNTED else st.disconnected,
+                workspace_bytes=st.workspace_bytes)
 
 
 def louvain(offsets, targets, weights, membership=None, **kw):
@@ -190,27 +198,32 @@ def move_sweep(offsets, targets, weights, C, K, Sigma, m, active=None, precision
 
 
 def local_move(offsets, targets, weights, C, K, Sigma, m, tolerance=1e-2, max_iterations=20,
-               move="sync", waves=17, precision="fp64", singleton_rule=True, stream=None):
+               move="sync", waves=17, wave_repeats=3, precision="fp64", singleton_rule=True, stream=None):
     """louvainMove (Algorithm 4); C and Sigma are updated in place; returns l_i."""
     n, nnz = _graph(offsets, targets, weights)
     it = ctypes.c_int()
     check(_lib.load().gsp_local_move(_p(offsets), _p(targets), _p(weights), _wt(weights), n, nnz, _p(C),
                                      _p(K), _p(Sigma), m, tolerance, max_iterations, MOVE[move], waves,
-                                     PRECISION[precision], int(bool(singleton_rule)), ctypes.byref(it),
-                                     _stream(stream)))
+                                     wave_repeats, PRECISION[precision], int(bool(singleton_rule)),
+                                     ctypes.byref(it), _stream(stream)))
     return it.value
 
 
-def louvain_trace(offsets, targets, weights, capacity, sample_every=8, **kw):
+def louvain_trace(offsets, targets, weights, capacity, sample_every=8, with_keys=False, **kw):
     """Run the plain method and record move/no-move trace rows:
-    (features [rows, 6] float32, labels [rows] uint8)."""
+    (features [rows, 6] float32, labels [rows] uint8), plus the visit keys
+    [rows] int64 (pass << 56 | iteration << 48 | repeat << 40 | vertex) when
+    with_keys is set."""
     n, nnz = _graph(offsets, targets, weights)
     o = make_opts(**kw)
     x = torch.empty((capacity, 6), dtype=torch.float32, device=offsets.device)
     y = torch.empty(capacity, dtype=torch.uint8, device=offsets.device)
+    keys = torch.empty(capacity, dtype=torch.int64, device=offsets.device) if with_keys else None
     rows = ctypes.c_uint32()
     check(_lib.load().gsp_louvain_trace(_p(offsets), _p(targets), _p(weights), n, nnz, ctypes.byref(o),
-                                        _p(x), _p(y), capacity, sample_every, ctypes.byref(rows)))
+                                        _p(x), _p(y), _p(keys), capacity, sample_every, ctypes.byref(rows)))
+    if with_keys:
+        return x[:rows.value], y[:rows.value], keys[:rows.value]
     return x[:rows.value], y[:rows.value]
 
 
@@ -294,6 +307,16 @@ def autotune(offsets, targets, weights, **kw):
 def kernel_launches():
     """Kernels launched by libgsp so far (process-wide counter)."""
     return _lib.load().gsp_kernel_launches()
+
+
+def workspace_reserved():
+    """Bytes of device memory held by libgsp's internal workspaces."""
+    return _lib.load().gsp_workspace_reserved()
+
+
+def release_workspace():
+    """Free libgsp's internal workspace on the current device."""
+    _lib.load().gsp_release_workspace()
 
 
 # ------------------------------------------------------------------ MLP

@@ -44,6 +44,7 @@ def test_default_opts_and_strings(lib):
     assert (o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
             o.aggregation_tolerance) == (10, 20, 1e-2, 10.0, 0.8)
     assert o.split == 2 and o.split_when == 0 and o.move == 1 and o.waves == 17 and o.precision == 0
+    assert o.wave_repeats == 3
     assert o.prune == 0 and o.full_sweep_every == 4 and abs(o.prune_threshold - 0.5) < 1e-7
     assert lib.gsp_status_string(-1) == b"invalid argument"
     assert lib.gsp_mlp_param_count() == 32 * 6 + 32 + 32 * 32 + 32 + 32 + 1
@@ -85,3 +86,39 @@ def test_tuning_roundtrip_and_validation(lib):
         assert lib.gsp_set_tuning(ctypes.byref(bad)) == -1
     assert lib.gsp_get_tuning(None) == -1
     assert lib.gsp_set_tuning(ctypes.byref(t)) == 0  # restore the defaults
+
+
+def test_struct_layout_matches_the_header(tmp_path):
+    """The ctypes mirrors of gsp_opts, gsp_stats and gsp_tuning have the
+    sizes and field offsets a C compiler gives the header's structs."""
+    from paper_2402_11454_gb300 import _lib
+    import subprocess
+    structs = {"gsp_opts": _lib.GspOpts, "gsp_stats": _lib.GspStats, "gsp_tuning": _lib.GspTuning,
+               "gsp_device_graph": _lib.GspDeviceGraph}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gsp.h"', 'int main(void) {']
+    for cname, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, cls in structs.items():
+        assert int(out["%s size" % cname]) == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert int(out["%s.%s" % (cname, f[0])]) == getattr(cls, f[0]).offset, (cname, f[0])
+
+
+def test_new_defaults(lib):
+    from paper_2402_11454_gb300._lib import GspOpts
+    o = GspOpts()
+    lib.gsp_default_opts(ctypes.byref(o))
+    assert o.wave_repeats == 3 and o.count_disconnected == 0 and not o.workspace and o.workspace_bytes == 0
+    assert lib.gsp_status_string(-6) == b"graph not symmetric"
+    o.wave_repeats = 0
+    assert lib.gsp_louvain(None, None, None, 5, 0, ctypes.byref(o), None, None, None) == -1
+    assert b"wave_repeats" in lib.gsp_last_error()
+    assert lib.gsp_workspace_reserved() >= 0

@@ -104,7 +104,8 @@ def test_sgd_step(gsp):
 def test_trace_rows(gsp):
     off, tgt, w = graphgen.planted(n=10000, k=64, mean_degree=16, p_intra=0.8, seed=1)
     d = (cuda(off.astype(np.int64)), cuda(tgt.astype(np.int32)), cuda(w))
-    x, y = gsp.louvain_trace(*d, capacity=1 << 16, sample_every=2)
+    # each wave runs once: the first sweep of a pass then visits each vertex once
+    x, y = gsp.louvain_trace(*d, capacity=1 << 16, sample_every=2, wave_repeats=1)
     x, y = x.cpu().numpy(), y.cpu().numpy()
     assert 1000 < len(y) <= 1 << 16
     assert set(np.unique(y)) == {0, 1}
@@ -118,6 +119,43 @@ def test_trace_rows(gsp):
     first = x[:, 5] == 0  # first sweep of a pass: nothing visited yet
     assert first.any()
     assert np.all(x[first, 2] == 0) and np.all(x[first, 3] == 1) and np.all(x[first, 4] == 1)
+
+
+@pytest.mark.parametrize("name", ["rmat12", "planted", "grid"])
+def test_trace_features_match_oracle(gsp, name):
+    """Every visit the GPU records (every visit, frozen-state FP64 mode) has
+    the predictor inputs that oracle.mlp.features computes from the oracle's
+    own run state at that visit (degree, K_i, the kept fraction, scaled gain
+    and move of the vertex's previous visit in the pass, the iteration), and
+    the same move label.  Rows are matched by (pass, iteration, repeat,
+    vertex)."""
+    import oracle
+    if name == "rmat12":
+        off, tgt, w = graphgen.rmat(12, 16, seed=2)
+    elif name == "planted":
+        off, tgt, w = graphgen.planted(n=3000, k=24, mean_degree=12, p_intra=0.8, seed=1)
+    else:
+        off, tgt, w = graphgen.grid(40, 50, seed=3)
+    d = (cuda(off.astype(np.int64)), cuda(tgt.astype(np.int32)), cuda(w))
+    x, y, keys = gsp.louvain_trace(*d, capacity=1 << 20, sample_every=1, with_keys=True, precision="fp64")
+    x, y, keys = x.cpu().numpy(), y.cpu().numpy(), keys.cpu().numpy().astype(np.uint64)
+    g = oracle.Graph(off, tgt, w.astype(np.float64))
+    _, _, r = oracle.louvain_trace(g, oracle.LouvainOptions(sync=True, split="lpp"), capacity=1 << 20)
+    keep = r["degree"] > 0  # isolated vertices have no candidate and no kernel visit
+    okeys = ((r["pass"].astype(np.uint64) << np.uint64(56)) | (r["iteration"].astype(np.uint64) << np.uint64(48))
+             | (r["repeat"].astype(np.uint64) << np.uint64(40)) | r["vertex"].astype(np.uint64))[keep]
+    assert len(np.unique(keys)) == len(keys)
+    assert len(keys) == len(okeys) and np.array_equal(np.sort(keys), np.sort(okeys))
+    ox = np.zeros((int(keep.sum()), 6))
+    rk = {k: v[keep] for k, v in r.items()}
+    for p in np.unique(rk["pass"]):  # one largest K per pass's graph
+        sel = rk["pass"] == p
+        ox[sel] = omlp.features(rk["degree"][sel], rk["K"][sel], rk["kept"][sel], rk["gain"][sel],
+                                rk["moved_last"][sel], rk["max_K"][sel][0], rk["iteration"][sel], 20)
+    gi, oi = np.argsort(keys), np.argsort(okeys)
+    np.testing.assert_allclose(x[gi], ox[oi], rtol=1e-5, atol=1e-6)
+    assert np.array_equal(y[gi], r["moved"][keep][oi].astype(np.uint8))
+    assert y.sum() > 0 and (x[:, 4] == 0).sum() > 0
 
 
 def test_learned_pruning_gain(gsp):

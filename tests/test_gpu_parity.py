@@ -185,19 +185,19 @@ def test_sync_sweep_mixed_precision_close(gsp, name):
 
 
 @pytest.mark.parametrize("name", ["planted", "grid", "rmat14"])
-@pytest.mark.parametrize("waves", [1, 16])
-def test_sync_local_move_fp64_matches_oracle(gsp, name, waves):
+@pytest.mark.parametrize("waves,repeats", [(1, 1), (16, 1), (17, 3), (5, 2)])
+def test_sync_local_move_fp64_matches_oracle(gsp, name, waves, repeats):
     off, tgt, w = GRAPHS[name]
     n = len(off) - 1
     g = og(name)
     K, m = oracle.vertex_weights(g)
     C0 = np.arange(n, dtype=np.uint32)
     Co, So, li_o, _ = oracle.move(g, C0, K, K.copy(), m, tau=1e-2, max_iterations=20, sync=True,
-                                  waves=waves)
+                                  waves=waves, wave_repeats=repeats)
     dC = torch.from_numpy(C0.astype(np.int32)).cuda()
     dS = torch.from_numpy(K.copy()).cuda()
     li = gsp.local_move(*dev(off, tgt, w), dC, torch.from_numpy(K).cuda(), dS, m, tolerance=1e-2,
-                        max_iterations=20, move="sync", waves=waves, precision="fp64")
+                        max_iterations=20, move="sync", waves=waves, wave_repeats=repeats, precision="fp64")
     assert li == li_o
     assert np.array_equal(host(dC).astype(np.uint32), Co)
     assert np.array_equal(host(dS), So)
@@ -321,6 +321,28 @@ def test_louvain_sync_fp64_equals_oracle(gsp, name):
     assert q == pytest.approx(ost["modularity"], rel=1e-9)
 
 
+@pytest.mark.parametrize("name", ["planted", "grid", "rmat14"])
+@pytest.mark.parametrize("variant", ["split_last", "no_split"])
+def test_louvain_split_variants_fp64_equal_oracle(gsp, name, variant):
+    """Split Last (Section 4.1, Fig. 3) and no split at all (GVE-Louvain,
+    Appendix A.3) reproduce the oracle's runs of the same variant bit for bit
+    in frozen-state FP64 mode, including the disconnected communities that
+    the unsplit run leaves."""
+    off, tgt, w = GRAPHS[name]
+    g = og(name)
+    if variant == "split_last":
+        kw, okw = dict(split="lpp", split_when="last"), dict(split="lp", split_last=True)
+    else:
+        kw, okw = dict(split="none"), dict(split="none")
+    C, q, st = gsp.louvain(*dev(off, tgt, w), move="sync", precision="fp64", count_disconnected=True, **kw)
+    Co, ost = oracle.louvain(g, oracle.LouvainOptions(sync=True, **okw))
+    assert st["passes"] == ost["passes"]
+    assert st["iterations"] == ost["iterations"]
+    assert np.array_equal(host(C).astype(np.uint32), Co)
+    assert q == pytest.approx(ost["modularity"], rel=1e-9)
+    assert st["disconnected"] == oracle.disconnected(g, Co)[0]
+
+
 @pytest.mark.parametrize("name", ["planted", "grid"])
 def test_louvain_hooking_split_equals_oracle(gsp, name):
     """The hooking split (not in the paper) yields the same canonical labels
@@ -364,6 +386,82 @@ def test_louvain_edge_cases(gsp):
         else:
             assert np.array_equal(C, np.repeat([0, 1], 4))
             assert q == pytest.approx(0.5, abs=1e-12)  # 2 * (12/24 - (12/24)^2)
+
+
+def test_asymmetric_graph_rejected(gsp):
+    """Section 3's graph is undirected (w_ij = w_ji): a CSR entry without its
+    mirror, or with a different weight on the mirror, is GSP_ERR_NOT_SYMMETRIC
+    (-6), not a silently wrong m.  Duplicate entries stored on both sides and
+    self-loops stay valid."""
+    from paper_2402_11454_gb300._lib import GspError
+    off, tgt, w = GRAPHS["rmat14"]
+    n = len(off) - 1
+    # drop one direction of the edge stored at entry e (row i)
+    rows = np.repeat(np.arange(n), np.diff(off.astype(np.int64)))
+    e = int(off[5])
+    i, j = int(rows[e]), int(tgt[e])
+    assert i != j
+    keep = np.ones(len(tgt), bool)
+    keep[e] = False
+    off2 = off.copy()
+    off2[i + 1:] -= 1
+    assert off2[i + 1] >= off2[i]
+    with pytest.raises(GspError, match="not symmetric"):
+        gsp.louvain(*dev(off2, tgt[keep], w[keep]))
+    # same structure, one weight changed on one side
+    w3 = w.copy()
+    w3[e] = 2.0
+    with pytest.raises(GspError, match="not symmetric"):
+        gsp.louvain(*dev(off, tgt, w3))
+    # a long row (hub) loses an entry: the long-row kernel sees it
+    hub = int(np.argmax(np.diff(off.astype(np.int64))))
+    assert off[hub + 1] - off[hub] > 64
+    e = int(off[hub]) + 7
+    keep = np.ones(len(tgt), bool)
+    keep[e] = False
+    off4 = off.copy()
+    off4[hub + 1:] -= 1
+    with pytest.raises(GspError, match="not symmetric"):
+        gsp.louvain(*dev(off4, tgt[keep], w[keep]))
+    # the mirror of the changed weight changed too: symmetric again
+    back = np.nonzero((rows == j) & (tgt == i))[0]
+    assert len(back) == 1
+    w3[back] = 2.0
+    C, q, st = gsp.louvain(*dev(off, tgt, w3))
+    assert -0.5 <= q <= 1.0
+    # duplicates stored on both sides and a self-loop
+    u = np.array([0, 0, 1, 2, 3], np.uint64)
+    v = np.array([1, 1, 2, 2, 0], np.uint64)
+    src = np.concatenate([u, v[u != v]])
+    dst = np.concatenate([v, u[u != v]])
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    offd = np.zeros(5, np.uint64)
+    np.cumsum(np.bincount(src.astype(np.int64), minlength=4), out=offd[1:])
+    C, q, st = gsp.louvain(*dev(offd, dst.astype(np.uint32), np.ones(len(dst), np.float32)))
+    assert -0.5 <= q <= 1.0
+
+
+def test_caller_workspace(gsp):
+    """With gsp_opts.workspace the run takes its scratch from the caller's
+    buffer: same result as the internal workspace, no growth of the internal
+    one, and GSP_ERR_CAPACITY when the buffer is too small."""
+    from paper_2402_11454_gb300 import _lib
+    from paper_2402_11454_gb300._lib import GspError
+    off, tgt, w = GRAPHS["rmat14"]
+    d = dev(off, tgt, w)
+    C0, q0, st0 = gsp.louvain(*d, precision="fp64")
+    need = st0["workspace_bytes"]
+    assert need > 0
+    before = _lib.load().gsp_workspace_reserved()
+    ws = torch.empty(need + 4096, dtype=torch.uint8, device="cuda")
+    C1, q1, st1 = gsp.louvain(*d, precision="fp64", workspace=ws)
+    assert _lib.load().gsp_workspace_reserved() == before
+    assert torch.equal(C0, C1) and q0 == q1
+    assert st1["workspace_bytes"] <= ws.numel()
+    small = torch.empty(need // 4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(GspError, match="capacity"):
+        gsp.louvain(*d, precision="fp64", workspace=small)
 
 
 def test_invalid_graph_rejected(gsp):

@@ -25,6 +25,7 @@ from .oracle import (  # noqa: F401
     disconnected,
     louvain,
     louvain_trace,
+    wave_hash,
     TRACE_FIELDS,
     LouvainOptions,
 )

@@ -43,7 +43,10 @@ typedef struct {
     int split_last;             /* 0 Split Pass (SP), 1 Split Last (SL) */
     int sync;                   /* 0 asynchronous in-place moves, 1 frozen-state waves */
     int waves;                  /* frozen-state waves per iteration */
+    int wave_hash;              /* 1: vertex i in wave og_wave_hash(i) mod waves; 0: i mod waves */
     int wave_repeats;           /* frozen-state repeats of a wave in the first iteration of a pass */
+    int no_return_from;         /* frozen-state: from this iteration on no move back to the community left
+                                   in the previous iteration (0: never) */
     int singleton_rule;         /* frozen-state sweeps only: singleton -> singleton moves go to lower ids */
 } og_opts;
 
@@ -209,18 +212,26 @@ void og_move_sweep_sync(const og_graph *g, const uint32_t *C, const double *K, c
  *   sync = 0: one thread walks the unprocessed vertices in id order and each
  *             move is applied at once (the in-place form of the paper).
  *   sync = 1: the parallel loop is made deterministic by waves: the vertices
- *             of an iteration are split into `waves` interleaved waves (vertex
- *             i belongs to wave i mod waves), taken in order; every vertex of
- *             a wave reads the C, Sigma and community sizes left by the
- *             earlier waves, and the wave's moves are applied after it.
- *             waves = 1 is the fully synchronous loop; waves = |V'| is the
- *             one-thread loop in id order.  In the first iteration a wave
- *             runs `repeats` times (at least once; later iterations once):
- *             a repeat takes the vertices of the wave that the previous
- *             repeat's moves marked unprocessed again, on the
- *             state those moves left (the pruning rule of Algorithm 4 applied
- *             within the wave).  With one vertex per wave a vertex never
- *             marks itself, so repeats change nothing there.
+ *             of an iteration are split into `waves` waves, taken in order;
+ *             every vertex of a wave reads the C, Sigma and community sizes
+ *             left by the earlier waves, and the wave's moves are applied
+ *             after it.  Vertex i belongs to wave og_wave_hash(i) mod waves
+ *             (wave_hash = 1), so that no arithmetic pattern of the ids
+ *             (vertex v of a planted community v mod k, R-MAT's bit-structured
+ *             ids) gathers a community into one wave, or to wave i mod waves
+ *             (wave_hash = 0).  waves = 1 is the fully synchronous loop; with
+ *             wave_hash = 0, waves = |V'| is the one-thread loop in id order.
+ *             In the first iteration a wave runs `repeats` times (at least
+ *             once; later iterations once): a repeat takes the vertices of the
+ *             wave that the previous repeat's moves marked unprocessed again,
+ *             on the state those moves left (the pruning rule of Algorithm 4
+ *             applied within the wave).  With one vertex per wave a vertex
+ *             never marks itself, so repeats change nothing there.  From
+ *             iteration no_return_from on (0: never), a vertex does not move
+ *             back to the community it left in the previous iteration: the
+ *             one-thread loop raises Q with every move and cannot cycle,
+ *             while simultaneous decisions can fall into a two-iteration cycle
+ *             whose claimed gains stay above tau.
  * dq_iter (optional) receives the total delta-modularity of each iteration.
  */
 /*
@@ -263,9 +274,20 @@ static void trace_visit(og_trace *tr, const og_graph *g, int it, int rep, uint32
     tr->moved[i] = (uint8_t)moved;
 }
 
+/* Wave hash: the MurmurHash3 32-bit finaliser (Appleby) of the vertex id. */
+uint32_t og_wave_hash(uint32_t i)
+{
+    i ^= i >> 16;
+    i *= 0x85ebca6bu;
+    i ^= i >> 13;
+    i *= 0xc2b2ae35u;
+    i ^= i >> 16;
+    return i;
+}
+
 static int move_impl(const og_graph *g, uint32_t *C, const double *K, double *Sigma, double m, double tau,
-                     int max_iterations, int sync, int waves, int repeats, int singleton_rule, double *dq_iter,
-                     og_trace *tr)
+                     int max_iterations, int sync, int waves, int wave_hash, int repeats, int no_return_from,
+                     int singleton_rule, double *dq_iter, og_trace *tr)
 {
     uint32_t n = g->n;
     double *H = calloc(n ? n : 1, sizeof(double));
@@ -276,6 +298,24 @@ static int move_impl(const og_graph *g, uint32_t *C, const double *K, double *Si
     uint32_t *size = calloc(n ? n : 1, sizeof(uint32_t));
     memset(unprocessed, 1, n);
     for (uint32_t i = 0; i < n; i++) size[C[i]]++;
+    /* frozen-state schedule: the vertices of each wave in id order, the
+     * community each vertex last left and the iteration it left it */
+    uint32_t W = waves < 1 ? 1u : (uint32_t)waves;
+    uint32_t *wstart = calloc((size_t)W + 1, sizeof(uint32_t));
+    uint32_t *wlist = malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *left = malloc(sizeof(uint32_t) * (n ? n : 1));
+    int *left_it = malloc(sizeof(int) * (n ? n : 1));
+    for (uint32_t i = 0; i < n; i++) {
+        wstart[(wave_hash ? og_wave_hash(i) : i) % W + 1]++;
+        left_it[i] = -2;
+    }
+    for (uint32_t k = 0; k < W; k++) wstart[k + 1] += wstart[k];
+    {
+        uint32_t *fill = malloc(sizeof(uint32_t) * ((size_t)W + 1));
+        memcpy(fill, wstart, sizeof(uint32_t) * ((size_t)W + 1));
+        for (uint32_t i = 0; i < n; i++) wlist[fill[(wave_hash ? og_wave_hash(i) : i) % W]++] = i;
+        free(fill);
+    }
     int li = 0;
     for (int it = 0; it < max_iterations; it++) {
         double dQ = 0.0;
@@ -297,29 +337,34 @@ static int move_impl(const og_graph *g, uint32_t *C, const double *K, double *Si
                     if (g->tgt[e] != i) unprocessed[g->tgt[e]] = 1;
             }
         } else {
-            uint32_t W = waves < 1 ? 1u : (uint32_t)waves;
             int R = (it == 0 && repeats > 1) ? repeats : 1;
-            for (uint32_t wv = 0; wv < W && wv < (n ? n : 1); wv++) {
+            int no_return = no_return_from > 0 && it >= no_return_from;
+            for (uint32_t wv = 0; wv < W; wv++) {
                 for (int r = 0; r < R; r++) {
                     /* decide: every unprocessed vertex of the wave, frozen state */
-                    for (uint32_t i = wv; i < n; i += W) {
+                    for (uint32_t t = wstart[wv]; t < wstart[wv + 1]; t++) {
+                        uint32_t i = wlist[t];
                         choice[i] = C[i];
                         if (!unprocessed[i]) continue;
                         unprocessed[i] = 0;
                         double b, kid;
                         choice[i] = best_move(g, C, K, Sigma, size, singleton_rule, m, i, H, seen, list, &b, NULL,
                                               &kid);
+                        if (no_return && choice[i] == left[i] && left_it[i] == it - 1) choice[i] = C[i];
                         trace_visit(tr, g, it, r, i, K[i], kid, b, m, choice[i] != C[i]);
                         if (choice[i] != C[i]) dQ += b;
                     }
                     /* apply the wave's moves; movers mark their neighbours */
-                    for (uint32_t i = wv; i < n; i += W) {
+                    for (uint32_t t = wstart[wv]; t < wstart[wv + 1]; t++) {
+                        uint32_t i = wlist[t];
                         if (choice[i] == C[i]) continue;
                         Sigma[C[i]] -= K[i];
                         Sigma[choice[i]] += K[i];
                         size[C[i]]--; size[choice[i]]++;
                         for (uint64_t e = g->off[i]; e < g->off[i + 1]; e++)
                             if (g->tgt[e] != i) unprocessed[g->tgt[e]] = 1;
+                        left[i] = C[i];
+                        left_it[i] = it;
                         C[i] = choice[i];
                     }
                 }
@@ -329,13 +374,16 @@ static int move_impl(const og_graph *g, uint32_t *C, const double *K, double *Si
         if (dQ <= tau) break;
     }
     free(H); free(seen); free(list); free(unprocessed); free(choice); free(size);
+    free(wstart); free(wlist); free(left); free(left_it);
     return li;
 }
 
 int og_move(const og_graph *g, uint32_t *C, const double *K, double *Sigma, double m, double tau,
-            int max_iterations, int sync, int waves, int repeats, int singleton_rule, double *dq_iter)
+            int max_iterations, int sync, int waves, int wave_hash, int repeats, int no_return_from,
+            int singleton_rule, double *dq_iter)
 {
-    return move_impl(g, C, K, Sigma, m, tau, max_iterations, sync, waves, repeats, singleton_rule, dq_iter, NULL);
+    return move_impl(g, C, K, Sigma, m, tau, max_iterations, sync, waves, wave_hash, repeats, no_return_from,
+                     singleton_rule, dq_iter, NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -581,7 +629,8 @@ static int louvain_impl(const og_graph *g, const og_opts *o, uint32_t *C, og_sta
             }
         }
         int li = (m > 0.0) ? move_impl(&cur, Cp, K, Sigma, m, tau, o->max_iterations, o->sync, o->waves,
-                                       o->wave_repeats, o->singleton_rule, NULL, tr)
+                                       o->wave_hash, o->wave_repeats, o->no_return_from, o->singleton_rule, NULL,
+                                       tr)
                            : 0;
         if (split_each_pass) {
             run_split(&cur, Cp, Cs, o->split);

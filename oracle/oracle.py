@@ -39,7 +39,8 @@ class _OgOpts(ctypes.Structure):
                 ("tolerance", ctypes.c_double), ("tolerance_drop", ctypes.c_double),
                 ("aggregation_tolerance", ctypes.c_double), ("split", ctypes.c_int),
                 ("split_last", ctypes.c_int), ("sync", ctypes.c_int), ("waves", ctypes.c_int),
-                ("wave_repeats", ctypes.c_int), ("singleton_rule", ctypes.c_int)]
+                ("wave_hash", ctypes.c_int), ("wave_repeats", ctypes.c_int), ("no_return_from", ctypes.c_int),
+                ("singleton_rule", ctypes.c_int)]
 
 
 class _OgStats(ctypes.Structure):
@@ -64,7 +65,10 @@ def _load():
         lib.og_move_sweep_sync.argtypes = [G, P, P, P, P, ctypes.c_int, ctypes.c_double, P, P, P, P]
         lib.og_move_sweep_sync.restype = None
         lib.og_move.argtypes = [G, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, P]
+        lib.og_wave_hash.argtypes = [ctypes.c_uint32]
+        lib.og_wave_hash.restype = ctypes.c_uint32
         lib.og_move.restype = ctypes.c_int
         lib.og_split_lp.argtypes = [G, P, P, ctypes.c_int]
         lib.og_split_lp.restype = ctypes.c_int
@@ -145,17 +149,21 @@ def move_sweep_sync(g, C, K, Sigma, m, active=None, singleton_rule=True):
     return choice, best, second
 
 
-def move(g, C, K, Sigma, m, tau, max_iterations=20, sync=True, singleton_rule=True, waves=1, wave_repeats=1):
+def move(g, C, K, Sigma, m, tau, max_iterations=20, sync=True, singleton_rule=True, waves=1, wave_repeats=1,
+         wave_hash=True, no_return_from=0):
     """louvainMove (Algorithm 4); returns (C, Sigma, l_i, dq per iteration).
-    sync=True runs frozen-state waves (vertex i in wave i mod waves); in the
-    first iteration each wave runs wave_repeats times (a repeat takes the
-    wave's vertices re-marked by the previous repeat's moves)."""
+    sync=True runs frozen-state waves (vertex i in wave hash(i) mod waves, or
+    i mod waves without wave_hash); in the first iteration each wave runs
+    wave_repeats times (a repeat takes the wave's vertices re-marked by the
+    previous repeat's moves); from iteration no_return_from on (0: never) a
+    vertex does not move back to the community it left the iteration before."""
     C = _u32(C).copy()
     K = np.ascontiguousarray(K, dtype=np.float64)
     Sigma = np.ascontiguousarray(Sigma, dtype=np.float64).copy()
     dq = np.zeros(max(max_iterations, 1), dtype=np.float64)
     li = _load().og_move(g.ref, _p(C), _p(K), _p(Sigma), m, tau, max_iterations, int(bool(sync)),
-                         int(waves), int(wave_repeats), int(bool(singleton_rule)), _p(dq))
+                         int(waves), int(bool(wave_hash)), int(wave_repeats), int(no_return_from),
+                         int(bool(singleton_rule)), _p(dq))
     return C, Sigma, li, dq[:li]
 
 
@@ -222,7 +230,9 @@ class LouvainOptions:
     split_last: bool = False
     sync: bool = True
     waves: int = 17
+    wave_hash: bool = True
     wave_repeats: int = 3
+    no_return_from: int = 3
     singleton_rule: bool = True
 
 
@@ -231,7 +241,8 @@ def louvain(g, opts=None):
     o = opts or LouvainOptions()
     co = _OgOpts(o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
                  o.aggregation_tolerance, SPLIT_MODES[o.split], int(o.split_last), int(o.sync),
-                 int(o.waves), int(o.wave_repeats), int(o.singleton_rule))
+                 int(o.waves), int(bool(o.wave_hash)), int(o.wave_repeats), int(o.no_return_from),
+                 int(o.singleton_rule))
     C = np.zeros(g.n, dtype=np.uint32)
     st = _OgStats()
     _load().og_louvain(g.ref, ctypes.byref(co), _p(C), ctypes.byref(st))
@@ -254,7 +265,8 @@ def louvain_trace(g, opts=None, capacity=1 << 20):
     o = opts or LouvainOptions()
     co = _OgOpts(o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
                  o.aggregation_tolerance, SPLIT_MODES[o.split], int(o.split_last), int(o.sync),
-                 int(o.waves), int(o.wave_repeats), int(o.singleton_rule))
+                 int(o.waves), int(bool(o.wave_hash)), int(o.wave_repeats), int(o.no_return_from),
+                 int(o.singleton_rule))
     C = np.zeros(g.n, dtype=np.uint32)
     st = _OgStats()
     rec = np.zeros((capacity, len(TRACE_FIELDS)), dtype=np.float64)
@@ -266,3 +278,10 @@ def louvain_trace(g, opts=None, capacity=1 << 20):
     rec = rec[:n.value]
     return C, {"passes": st.passes, "modularity": st.modularity}, {k: rec[:, j] for j, k in
                                                                    enumerate(TRACE_FIELDS)}
+
+
+def wave_hash(i):
+    """The wave hash of vertex ids (og_wave_hash): MurmurHash3's 32-bit
+    finaliser."""
+    f = _load().og_wave_hash
+    return np.array([f(int(x)) for x in np.atleast_1d(i)], dtype=np.uint32)

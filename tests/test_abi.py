@@ -43,7 +43,7 @@ def test_default_opts_and_strings(lib):
     lib.gsp_default_opts(ctypes.byref(o))
     assert (o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
             o.aggregation_tolerance) == (10, 20, 1e-2, 10.0, 0.8)
-    assert o.split == 2 and o.split_when == 0 and o.move == 1 and o.waves == 17 and o.precision == 0
+    assert o.split == 2 and o.split_when == 0 and o.move == 1 and o.waves == 0 and o.precision == 0
     assert o.wave_repeats == 3
     assert o.prune == 0 and o.full_sweep_every == 4 and abs(o.prune_threshold - 0.5) < 1e-7
     assert lib.gsp_status_string(-1) == b"invalid argument"

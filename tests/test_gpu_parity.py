@@ -185,19 +185,20 @@ def test_sync_sweep_mixed_precision_close(gsp, name):
 
 
 @pytest.mark.parametrize("name", ["planted", "grid", "rmat14"])
-@pytest.mark.parametrize("waves,repeats", [(1, 1), (16, 1), (17, 3), (5, 2)])
-def test_sync_local_move_fp64_matches_oracle(gsp, name, waves, repeats):
+@pytest.mark.parametrize("waves,repeats,no_return", [(1, 1, 0), (16, 1, 0), (17, 3, 3), (5, 2, 1)])
+def test_sync_local_move_fp64_matches_oracle(gsp, name, waves, repeats, no_return):
     off, tgt, w = GRAPHS[name]
     n = len(off) - 1
     g = og(name)
     K, m = oracle.vertex_weights(g)
     C0 = np.arange(n, dtype=np.uint32)
-    Co, So, li_o, _ = oracle.move(g, C0, K, K.copy(), m, tau=1e-2, max_iterations=20, sync=True,
-                                  waves=waves, wave_repeats=repeats)
+    Co, So, li_o, _ = oracle.move(g, C0, K, K.copy(), m, tau=1e-4, max_iterations=20, sync=True,
+                                  waves=waves, wave_repeats=repeats, no_return_from=no_return)
     dC = torch.from_numpy(C0.astype(np.int32)).cuda()
     dS = torch.from_numpy(K.copy()).cuda()
-    li = gsp.local_move(*dev(off, tgt, w), dC, torch.from_numpy(K).cuda(), dS, m, tolerance=1e-2,
-                        max_iterations=20, move="sync", waves=waves, wave_repeats=repeats, precision="fp64")
+    li = gsp.local_move(*dev(off, tgt, w), dC, torch.from_numpy(K).cuda(), dS, m, tolerance=1e-4,
+                        max_iterations=20, move="sync", waves=waves, wave_repeats=repeats, no_return_from=no_return,
+                        precision="fp64")
     assert li == li_o
     assert np.array_equal(host(dC).astype(np.uint32), Co)
     assert np.array_equal(host(dS), So)

@@ -64,12 +64,14 @@ typedef enum { GSP_SPLIT_PASS = 0, GSP_SPLIT_LAST = 1 } gsp_split_when;
  * does (results depend on thread timing); SYNC lets every vertex of an
  * iteration read the state of the iteration's start (deterministic). */
 typedef enum { GSP_MOVE_ASYNC = 0, GSP_MOVE_SYNC = 1 } gsp_move_mode;
-/* An iteration is split into `waves` interleaved waves: vertex i belongs to
- * wave i mod waves, and every vertex of a wave reads the state left by the
- * earlier waves (SYNC, waves = 1: fully synchronous; more waves approach the
- * one-thread order).  The default, 17, is prime so that ids with structure
- * (vertex v of a planted community v mod k, R-MAT hubs at ids with many
- * trailing zero bits) do not fall into one wave.  In the first iteration of
+/* An iteration is split into `waves` waves: vertex i belongs to wave
+ * h(i) mod waves, h the MurmurHash3 32-bit finaliser of its index (of its
+ * index within its graph in a batch), and every vertex of a wave reads the
+ * state left by the earlier waves (SYNC, waves = 1: fully synchronous; more
+ * waves approach the one-thread order).  The hash keeps arithmetic patterns
+ * of the ids out of the waves: with wave i mod 17, every community of a
+ * planted graph with 17, 34 or 51 communities (vertex v in community v mod k)
+ * fell into one wave, decided at once and cycled.  In the first iteration of
  * a pass each wave runs `wave_repeats` times (later iterations once): a
  * repeat takes the vertices of the wave that the previous repeat's moves
  * marked unprocessed again (the pruning rule of Algorithm 4 applied inside
@@ -78,8 +80,17 @@ typedef enum { GSP_MOVE_ASYNC = 0, GSP_MOVE_SYNC = 1 } gsp_move_mode;
  * loop (on R-MAT scales 19, 20 and 21, 0.0002, 0.0007 and 0.0013 below it on
  * average, where a single pass fell 0.0022, 0.0029 and 0.0033 short) for about
  * 1.45 times the edge visits; an odd count does better than the next even
- * one, and repeats in the later iterations cost more than they gain.  In
- * ASYNC mode the waves and repeats order the in-place updates the same way. */
+ * one, and repeats in the later iterations cost more than they gain.  From
+ * iteration `no_return_from` of a pass on, a vertex does not move back to the
+ * community it left in the previous iteration: the one-thread loop raises Q
+ * with every move and cannot cycle, but simultaneous decisions can fall into
+ * a two-iteration cycle whose claimed gains stay above tau (grids ran their
+ * later passes to MAX_ITERATIONS).  In ASYNC mode the waves, repeats and the
+ * no-return rule order the in-place updates the same way; there the default
+ * is 64 waves: with 17, the thousands of vertices of a wave that run at once
+ * ended up to 0.0026 below the one-thread loop on R-MAT 16-18, with 64 within
+ * 0.0008, and with one wave (the loop as written, every vertex at once) 0.03
+ * to 0.08 below. */
 /* MIXED: per-community weights K_{i->c} and delta-modularity in float32,
  * while m, Sigma_tot and modularity stay float64.  FP64: everything float64,
  * Equation 2 evaluated term by term (the parity mode). */
@@ -98,8 +109,11 @@ typedef struct {
     int split;                      /* gsp_split_mode; default GSP_SPLIT_LPP */
     int split_when;                 /* gsp_split_when; default GSP_SPLIT_PASS */
     int move;                       /* gsp_move_mode; default GSP_MOVE_SYNC */
-    int waves;                      /* waves per iteration, 1..64; default 17 */
+    int waves;                      /* waves per iteration, 1..64, or 0 (the default): 17 for SYNC, 64
+                                       for ASYNC */
     int wave_repeats;               /* times each wave runs in a pass's first iteration, 1..8; default 3 */
+    int no_return_from;             /* no move back to the community left the iteration before, from this
+                                       iteration of a pass on (0: never); default 3 */
     int precision;                  /* gsp_precision; default GSP_PREC_MIXED */
     int singleton_rule;             /* 1: a vertex alone in its community moves to another
                                        singleton community only if that id is lower; default 1 */
@@ -221,15 +235,16 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
 /*
  * louvainMove (Algorithm 4) from membership C (in/out) and Sigma (in/out,
  * must equal the per-community sums of K).  move is a gsp_move_mode, waves
- * the wave count (1..64) and wave_repeats the repeats of a wave in the first
- * iteration (1..8), as in gsp_opts.  Returns l_i, the iterations executed,
+ * the wave count (1..64, 0: the mode's default), wave_repeats the repeats of a wave in the first
+ * iteration (1..8) and no_return_from the first iteration of the no-return
+ * rule (0: never), as in gsp_opts.  Returns l_i, the iterations executed,
  * in *iterations_host.
  */
 gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, const void *weights,
                           int wt, uint32_t n, uint64_t nnz, uint32_t *C, const double *K,
                           double *Sigma, double m, double tolerance, int max_iterations, int move,
-                          int waves, int wave_repeats, int precision, int singleton_rule,
-                          int *iterations_host, void *stream);
+                          int waves, int wave_repeats, int no_return_from, int precision,
+                          int singleton_rule, int *iterations_host, void *stream);
 
 /*
  * Split (Algorithms 2 and 3): labels[i] = the smallest vertex id of the

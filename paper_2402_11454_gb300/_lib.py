@@ -23,7 +23,7 @@ class GspOpts(ctypes.Structure):
     _fields_ = [("max_passes", c_int), ("max_iterations", c_int), ("tolerance", c_dbl),
                 ("tolerance_drop", c_dbl), ("aggregation_tolerance", c_dbl), ("split", c_int),
                 ("split_when", c_int), ("move", c_int), ("waves", c_int), ("wave_repeats", c_int),
-                ("precision", c_int),
+                ("no_return_from", c_int), ("precision", c_int),
                 ("singleton_rule", c_int), ("prune", c_int), ("mlp_params", P),
                 ("full_sweep_every", c_int), ("prune_threshold", c_flt), ("count_disconnected", c_int),
                 ("workspace", P), ("workspace_bytes", ctypes.c_size_t), ("stream", P)]
@@ -64,7 +64,7 @@ _SIGS = {
     "gsp_move_sweep": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, P, c_dbl, P, c_int, c_int, P, P,
                                P, P]),
     "gsp_local_move": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, P, c_dbl, c_dbl, c_int, c_int,
-                               c_int, c_int, c_int, c_int, P, P]),
+                               c_int, c_int, c_int, c_int, c_int, P, P]),
     "gsp_louvain_trace": (c_int, [P, P, P, c_u32, c_u64, P, P, P, P, c_u32, c_u32, P]),
     "gsp_split": (c_int, [P, P, c_u32, c_u64, P, c_int, P, P, P]),
     "gsp_renumber": (c_int, [c_u32, P, P, P, P]),

@@ -216,6 +216,7 @@ static BatchMove batch_move_loop(const DevGraph &g, const Classes &cl, MoveBuffe
     try {
         for (int it = 0; it < o.max_iterations && nlive; it++) {
             GSP_CUDA(cudaMemsetAsync(mb.dq_g, 0, sizeof(double) * G, s));
+            set_iteration(mb, it, s);
             bool persisted = false;
             if (use_persist) {
                 GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
@@ -307,7 +308,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         GSP_CUDA(cudaStreamWaitEvent(s, in, 0));
     }
     const uint32_t n0 = g0.n;
-    const int W = o.waves;
+    const int W = effective_waves(o.waves, o.move == GSP_MOVE_SYNC);
     gsp_stats local;
     memset(&local, 0, sizeof(local));
     Lap total(s), lap(s);
@@ -315,6 +316,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     MoveBuffers mb;
     alloc_move_state(mb, n0);
     mb.repeats = o.wave_repeats;
+    mb.no_return_from = o.no_return_from;
     double *K = arena().get<double>(n0);
     uint32_t *labels = arena().get<uint32_t>(n0);
     uint32_t *Cd = arena().get<uint32_t>(n0);
@@ -400,6 +402,7 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         iota_u32(mb.C, nv, s);
         k_fill_ones<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv);
         GSP_CHECK_LAUNCH();
+        reset_left(mb, nv, s);
         k_set_active<<<grid_for(nv, 256), 256, 0, s>>>(mb.act, gid, live, nv);
         GSP_CHECK_LAUNCH();
         GSP_CUDA(cudaMemsetAsync(mb.mark, 0, nv, s));

@@ -364,6 +364,8 @@ struct PruneCtx {
 // moves of each repeat are applied (and the movers' neighbours re-marked)
 // before the next; a repeat takes the vertices of the wave that the earlier
 // repeats re-marked, on the state those moves left.
+int effective_waves(int waves, bool sync) { return waves > 0 ? waves : (sync ? 17 : 64); }
+
 int wave_repeats_at(const MoveBuffers &mb, int it) { return (it == 0 && mb.repeats > 1) ? mb.repeats : 1; }
 
 void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
@@ -438,10 +440,22 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
     cudaGraphExec_t exec = nullptr;
     side_streams();
     try {
-        bool force_full = false;  // a pruned sweep fell below tau: confirm with a plain sweep
+        // Learned pruning: the first sweep of a pass is plain (no vertex has a
+        // visit history yet); a pruned sweep puts off the vertices predicted
+        // not to move (they stay off until a neighbour's move re-marks them);
+        // every full_every-th sweep, and the sweep after a pruned sweep whose
+        // gain fell to tau while vertices were put off, is plain and takes the
+        // put-off vertices back.  Only a plain sweep ends the pass.
+        bool force_full = false;
+        uint64_t deferred = 0;  // put off since the last plain sweep (an upper bound)
         for (int it = 0; it < max_it; it++) {
-            const bool pruned = pr.learned && !force_full && pr.full_every > 0 &&
+            const bool pruned = pr.learned && !force_full && it > 0 && pr.full_every > 0 &&
                                 (it % pr.full_every) != pr.full_every - 1;
+            set_iteration(mb, it, s);
+            if (pr.learned && !pruned && deferred) {
+                mlp_unskip(g, mb, s);
+                deferred = 0;
+            }
             bool persisted = false;
             if (use_persist) {
                 GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
@@ -466,7 +480,6 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
                 GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
                 if (pruned) mlp_prune(g, mb, it, max_it, pr.threshold, s);
                 sweep_launches(g, cl, mb, sync, fp64, rule, pruned, it, max_it, wave_n, false, s);
-                if (pruned) mlp_unskip(g, mb, s);
             }
             }
             GSP_CUDA(cudaEventRecord(e1, s));
@@ -485,10 +498,13 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
             r.edges += h.edges;
             r.candidates += h.candidates;
             r.skipped += h.skipped;
-            // only a sweep that skipped nobody may declare convergence: the
-            // gain of a pruned sweep misses what its skipped vertices would add
+            deferred += h.skipped;
+            // the gain of a pruned sweep misses what its put-off vertices
+            // would add; their expected gain (P(move) x last gain, summed by
+            // the predictor) counts with it, and when the two together stay
+            // at tau the pass ends as a plain sweep's gain would end it
             if (h.dq <= tau) {
-                if (!pruned || h.skipped == 0) break;
+                if (!pruned || deferred == 0 || h.dq + h.skipped_gain <= tau) break;
                 force_full = true;
             } else {
                 force_full = false;
@@ -509,6 +525,19 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
 }
 
 // Allocate the move state for a graph of n vertices.
+__global__ void k_set_int(int *p, int v) { *p = v; }
+void set_iteration(MoveBuffers &mb, int iteration, cudaStream_t s) {
+    k_set_int<<<1, 1, 0, s>>>(mb.it_dev, iteration);
+    GSP_CHECK_LAUNCH();
+}
+
+// No vertex has left a community yet (left_it = -2 matches no iteration - 1).
+void reset_left(MoveBuffers &mb, uint32_t n, cudaStream_t s) {
+    if (!n) return;
+    k_fill_u32_<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<uint32_t *>(mb.left_it), n, 0xFFFFFFFEu);
+    GSP_CHECK_LAUNCH();
+}
+
 void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.C = arena().get<uint32_t>(n);
     mb.Sigma = arena().get<double>(n);
@@ -522,6 +551,9 @@ void alloc_move_state(MoveBuffers &mb, uint32_t n) {
     mb.bar = arena().get<GridBar>(1);
     mb.big = arena().get<uint32_t>(n);
     mb.nbig = arena().get<uint32_t>(1);
+    mb.left = arena().get<uint32_t>(n);
+    mb.left_it = arena().get<int>(n);
+    mb.it_dev = arena().get<int>(1);
     mb.m_dev = arena().get<double>(1);
     mb.ctr = arena().get<MoveCounters>(1);
 }
@@ -529,15 +561,17 @@ void alloc_move_state(MoveBuffers &mb, uint32_t n) {
 static void alloc_features(MoveBuffers &mb, uint32_t n, cudaStream_t s) {
     mb.feat_kept = arena().get<float>(n);
     mb.feat_gain = arena().get<float>(n);
+    mb.last_gain = arena().get<float>(n);
     mb.moved_last = arena().get<uint8_t>(n);
     mb.skip = arena().get<uint8_t>(n);
     GSP_CUDA(cudaMemsetAsync(mb.skip, 0, n, s));
 }
 
-__global__ void k_init_features(float *kept, float *gain, uint8_t *moved, uint32_t n) {
+__global__ void k_init_features(float *kept, float *gain, float *last_gain, uint8_t *moved, uint32_t n) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         kept[i] = 0.0f;
         gain[i] = 1.0f;
+        last_gain[i] = 0.0f;
         moved[i] = 1;
     }
 }
@@ -608,7 +642,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     g_events.reset();
     const uint32_t n0 = g0.n;
     const bool sync = o.move == GSP_MOVE_SYNC;
-    const int W = o.waves;
+    const int W = effective_waves(o.waves, sync);
     const bool fp64 = o.precision == GSP_PREC_FP64;
     PruneCtx pr;
     pr.learned = o.prune == GSP_PRUNE_LEARNED && o.mlp_params && !trace;
@@ -626,6 +660,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     uint32_t *Cd = arena().get<uint32_t>(n0);
     mb.K = K;
     mb.repeats = o.wave_repeats;
+    mb.no_return_from = o.no_return_from;
     mb.mlp = static_cast<const float *>(o.mlp_params);
     if (features) alloc_features(mb, n0, s);
     if (trace) {
@@ -666,11 +701,14 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         iota_u32(mb.C, nv, s);
         k_fill_u32_<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
         GSP_CHECK_LAUNCH();
+        reset_left(mb, nv, s);
         GSP_CUDA(cudaMemsetAsync(mb.act, 1, nv, s));
         GSP_CUDA(cudaMemsetAsync(mb.mark, 0, nv, s));
         if (features) {
-            k_init_features<<<grid_for(nv, 256), 256, 0, s>>>(mb.feat_kept, mb.feat_gain, mb.moved_last, nv);
+            k_init_features<<<grid_for(nv, 256), 256, 0, s>>>(mb.feat_kept, mb.feat_gain, mb.last_gain,
+                                                              mb.moved_last, nv);
             GSP_CHECK_LAUNCH();
+            GSP_CUDA(cudaMemsetAsync(mb.skip, 0, nv, s));
             mb.max_logk = (float)log1p(max_value(K, nv, s));
             if (!(mb.max_logk > 0.0f)) mb.max_logk = 1.0f;
             mb.trace_salt = 0x85EBCA6Bu * (uint32_t)(lp + 1);
@@ -790,9 +828,10 @@ void check_opts(const gsp_opts &o) {
     GSP_REQUIRE(o.split >= GSP_SPLIT_NONE && o.split <= GSP_SPLIT_SV, "unknown split mode");
     GSP_REQUIRE(o.split_when == GSP_SPLIT_PASS || o.split_when == GSP_SPLIT_LAST, "unknown split_when");
     GSP_REQUIRE(o.move == GSP_MOVE_ASYNC || o.move == GSP_MOVE_SYNC, "unknown move mode");
-    GSP_REQUIRE(o.waves >= 1 && o.waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
+    GSP_REQUIRE(o.waves >= 0 && o.waves <= MAX_WAVES, "waves must be in [0, %d]", MAX_WAVES);
     GSP_REQUIRE(o.wave_repeats >= 1 && o.wave_repeats <= MAX_REPEATS, "wave_repeats must be in [1, %d]",
                 MAX_REPEATS);
+    GSP_REQUIRE(o.no_return_from >= 0, "no_return_from must be >= 0");
     GSP_REQUIRE(o.prune_threshold >= 0.0f && o.prune_threshold <= 1.0f, "prune_threshold must be in [0, 1]");
     GSP_REQUIRE(o.precision == GSP_PREC_MIXED || o.precision == GSP_PREC_FP64, "unknown precision");
     GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS || o.prune == GSP_PRUNE_LEARNED, "unknown prune mode");
@@ -814,8 +853,9 @@ void gsp_default_opts(gsp_opts *o) {
     o->split = GSP_SPLIT_LPP;
     o->split_when = GSP_SPLIT_PASS;
     o->move = GSP_MOVE_SYNC;
-    o->waves = 17;
+    o->waves = 0;
     o->wave_repeats = 3;
+    o->no_return_from = 3;
     o->precision = GSP_PREC_MIXED;
     o->singleton_rule = 1;
     o->prune = GSP_PRUNE_FLAGS;
@@ -967,6 +1007,7 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
     Classes cl;
     classify_vertices(g, cl, 1, s);
     alloc_pool(mb, cl, s);
+    set_iteration(mb, 0, s);
     move_wave(g, cl, mb, 0, true, precision == GSP_PREC_FP64, singleton_rule != 0, false, 0, 1, s);
     MoveCounters h;
     GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -978,15 +1019,16 @@ gsp_status gsp_move_sweep(const uint64_t *offsets, const uint32_t *targets, cons
 
 gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
                           uint64_t nnz, uint32_t *C, const double *K, double *Sigma, double m, double tolerance,
-                          int max_iterations, int move, int waves, int wave_repeats, int precision,
-                          int singleton_rule, int *iterations_host, void *stream) {
+                          int max_iterations, int move, int waves, int wave_repeats, int no_return_from,
+                          int precision, int singleton_rule, int *iterations_host, void *stream) {
     GSP_API_BEGIN
     DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
     GSP_REQUIRE(C && K && Sigma, "C, K and Sigma must not be NULL");
     GSP_REQUIRE(m > 0.0 && max_iterations >= 1, "m must be > 0 and max_iterations >= 1");
     GSP_REQUIRE(move == GSP_MOVE_ASYNC || move == GSP_MOVE_SYNC, "unknown move mode");
-    GSP_REQUIRE(waves >= 1 && waves <= MAX_WAVES, "waves must be in [1, %d]", MAX_WAVES);
+    GSP_REQUIRE(waves >= 0 && waves <= MAX_WAVES, "waves must be in [0, %d]", MAX_WAVES);
     GSP_REQUIRE(wave_repeats >= 1 && wave_repeats <= MAX_REPEATS, "wave_repeats must be in [1, %d]", MAX_REPEATS);
+    GSP_REQUIRE(no_return_from >= 0, "no_return_from must be >= 0");
     GSP_REQUIRE(precision == GSP_PREC_MIXED || precision == GSP_PREC_FP64, "unknown precision");
     cudaStream_t s = S(stream);
     arena().reset();
@@ -998,6 +1040,8 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
     alloc_move_state(mb, n);
     mb.K = K;
     mb.repeats = wave_repeats;
+    mb.no_return_from = no_return_from;
+    reset_left(mb, n, s);
     GSP_CUDA(cudaMemcpyAsync(mb.m_dev, &m, sizeof(double), cudaMemcpyHostToDevice, s));
     GSP_CUDA(cudaMemcpyAsync(mb.C, C, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     GSP_CUDA(cudaMemcpyAsync(mb.Sigma, Sigma, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -1007,7 +1051,7 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
     GSP_CUDA(cudaMemsetAsync(mb.act, 1, n, s));
     GSP_CUDA(cudaMemsetAsync(mb.mark, 0, n, s));
     Classes cl;
-    classify_vertices(g, cl, waves, s);
+    classify_vertices(g, cl, effective_waves(waves, sync), s);
     alloc_pool(mb, cl, s);
     PruneCtx pr;
     MoveLoopResult r = move_loop(g, cl, mb, tolerance, max_iterations, sync, precision == GSP_PREC_FP64,

@@ -72,6 +72,7 @@ struct MoveCounters {  // device-side accumulators of one sweep
     unsigned long long skipped;
     unsigned long long marked;  // edges of moved vertices (neighbour re-marking)
     unsigned long long stalled; // persistent sweep: grid barriers that gave up waiting
+    double skipped_gain;        // learned pruning: sum over put-off vertices of P(move) x last gain
 };
 
 // Grid-wide barrier state of the persistent sweep kernel (zero at start).
@@ -92,6 +93,10 @@ struct MoveBuffers {
     const double *minv_g = nullptr;  // batches: 1/m of each graph
     int lsb = INT_MIN;               // weights in exact integer units of 2^lsb (exact_lsb)
     int repeats = 1;                 // repeats of a wave in a pass's first iteration (wave_repeats_at)
+    int no_return_from = 0;          // gsp_opts.no_return_from
+    uint32_t *left = nullptr;        // community each vertex last left (no-return rule)
+    int *left_it = nullptr;          // iteration of that move, -2 before any in the pass
+    int *it_dev = nullptr;           // the sweep's iteration, read by the kernels (set_iteration)
     double *dq_g = nullptr;          // batches: summed gain of each graph in a sweep
     MoveCounters *ctr = nullptr;
     void *pool = nullptr;        // huge-class hashtables
@@ -107,8 +112,9 @@ struct MoveBuffers {
     const float *mlp = nullptr;
     float *feat_kept = nullptr;  // K_{i->C_i} / K_i at the vertex's last visit
     float *feat_gain = nullptr;  // scaled best gain at the last visit
+    float *last_gain = nullptr;  // best gain at the last visit, in units of Q (not clamped)
     uint8_t *moved_last = nullptr;
-    uint8_t *skip = nullptr;     // vertices the predictor skipped in the current sweep
+    uint8_t *skip = nullptr;     // vertices the predictor put off and no sweep has visited since
     float max_logk = 1.0f;
     // move/no-move trace rows (optional)
     float *trace_x = nullptr;
@@ -158,12 +164,20 @@ size_t workspace_peak();
 
 // driver.cu helpers shared with the batched driver
 int wave_repeats_at(const MoveBuffers &mb, int iteration);  // runs of each wave in that iteration
+// gsp_opts.waves, with 0 read as the mode's default: 17 frozen-state waves,
+// 64 in-place ones
+int effective_waves(int waves, bool sync);
 void sweep_launches(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool sync, bool fp64, bool rule,
                     bool pruned, int it, int max_it, const uint32_t *wave_n, bool reset_ctr, cudaStream_t s);
 bool graphs_enabled();
 bool persistent_enabled();
 cudaStream_t capture_stream();
 void alloc_move_state(MoveBuffers &mb, uint32_t n);
+void reset_left(MoveBuffers &mb, uint32_t n, cudaStream_t s);
+// Store the iteration of the next sweep where its kernels read it; called
+// before each sweep's launches or graph replay (a captured graph keeps the
+// kernel arguments of its capture).
+void set_iteration(MoveBuffers &mb, int iteration, cudaStream_t s);
 void alloc_pool(MoveBuffers &mb, const Classes &cl, cudaStream_t s);
 double sweep_bytes(const MoveCounters &h, int wt);
 cudaEvent_t pool_event();
@@ -236,11 +250,12 @@ __device__ __forceinline__ void predictor_features(uint32_t deg, double Ki, floa
 }
 
 // Learned pruning before a sweep: active vertices whose predicted move
-// probability is below threshold are marked processed (skipped).
+// probability is below threshold are marked processed and put off
+// (mb.skip); a later visit (a neighbour's move re-marks them) clears that.
 void mlp_prune(const DevGraph &g, MoveBuffers &mb, int iteration, int max_iterations, float threshold,
                cudaStream_t s);
-// After a pruned sweep: the skipped vertices are unprocessed again, so that
-// the next sweep (a plain one at the latest) reconsiders them.
+// Before a plain sweep: every vertex still put off is unprocessed again, so
+// that the plain sweep reconsiders it.
 void mlp_unskip(const DevGraph &g, MoveBuffers &mb, cudaStream_t s);
 
 __device__ __forceinline__ int ceil_log2(uint32_t x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }

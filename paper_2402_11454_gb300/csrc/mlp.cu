@@ -164,35 +164,43 @@ __global__ void k_mlp_adam(float *params, const float *__restrict__ grad, float 
 // move sit out the sweep (flag cleared, skip set) and are counted as skipped.
 __global__ void k_mlp_prune(const float *__restrict__ params, const uint64_t *__restrict__ off,
                             const double *__restrict__ K, const float *__restrict__ kept,
-                            const float *__restrict__ gain, const uint8_t *__restrict__ moved, uint8_t *act,
-                            uint8_t *skip, uint32_t n, float max_logk, float iter_frac, float thr,
-                            MoveCounters *ctr) {
+                            const float *__restrict__ gain, const float *__restrict__ last_gain,
+                            const uint8_t *__restrict__ moved, uint8_t *act, uint8_t *skip, uint32_t n,
+                            float max_logk, float iter_frac, float thr, MoveCounters *ctr) {
     __shared__ float sp[MLP_PARAMS];
     __shared__ unsigned long long red[32];
+    __shared__ double redd[32];
     load_params_bf16(params, sp);
     unsigned long long skipped = 0;
+    double expect = 0.0;  // expected gain of the put-off vertices: P(move) x last best gain
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (!act[i]) continue;
         uint32_t deg = (uint32_t)(off[i + 1] - off[i]);
         if (!deg) continue;
         float x[MLP_IN];
         predictor_features(deg, K[i], kept[i], gain[i], moved[i], max_logk, iter_frac, x);
-        if (mlp_prob(sp, x) < thr) {
+        const float p = mlp_prob(sp, x);
+        if (p < thr) {
             act[i] = 0;
             skip[i] = 1;
             skipped++;
+            expect += (double)p * (double)fmaxf(last_gain[i], 0.0f);
         }
     }
     skipped = block_sum(skipped, red);
-    if (threadIdx.x == 0 && skipped) atomicAdd(&ctr->skipped, skipped);
+    expect = block_sum(expect, redd);
+    if (threadIdx.x == 0 && skipped) {
+        atomicAdd(&ctr->skipped, skipped);
+        atomicAdd(&ctr->skipped_gain, expect);
+    }
 }
 
 void mlp_prune(const DevGraph &g, MoveBuffers &mb, int iteration, int max_iterations, float threshold,
                cudaStream_t s) {
     float frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
     k_mlp_prune<<<grid_for(g.n, 256, sms(8)), 256, 0, s>>>(mb.mlp, g.off, mb.K, mb.feat_kept, mb.feat_gain,
-                                                            mb.moved_last, mb.act, mb.skip, g.n, mb.max_logk,
-                                                            frac, threshold, mb.ctr);
+                                                            mb.last_gain, mb.moved_last, mb.act, mb.skip, g.n,
+                                                            mb.max_logk, frac, threshold, mb.ctr);
     GSP_CHECK_LAUNCH();
 }
 

@@ -54,11 +54,18 @@ struct MoveArgs {
     int lsb;  // K in exact integer units of 2^lsb (INT_MIN: float64 deltas)
     MoveCounters *ctr;
     int rule;
+    // no-return rule: from iteration no_return_from on (0: never) a vertex
+    // does not move back to the community it left in the previous iteration
+    uint32_t *left;   // community each vertex last left
+    int *left_it;     // iteration of that move (-2: none in this pass)
+    const int *iteration;  // device scalar: the sweep's iteration (set before each launch or graph replay)
+    int no_return_from;
     uint32_t *mv_vtx, *mv_cmt, *mv_cnt;  // frozen-state move list
     uint32_t *choice;                    // optional per-vertex decision
     // last-visit features for the learned predictor (optional)
-    float *feat_kept, *feat_gain;
+    float *feat_kept, *feat_gain, *last_gain;
     uint8_t *moved_last;
+    uint8_t *deferred;  // learned pruning: vertices the predictor put off (cleared when visited)
     // trace rows (optional): features before the visit, label = moved
     float *trace_x;
     uint8_t *trace_y;
@@ -220,12 +227,18 @@ __device__ __forceinline__ bool decide_move(const MoveArgs &a, uint32_t i, uint3
         uint32_t sd = ld_state<SYNC>(a.size + d), sc = ld_state<SYNC>(a.size + c);
         if (sd == 1 && sc == 1 && c > d) return false;
     }
+    if (a.no_return_from > 0 && a.left[i] == c) {
+        const int it = *a.iteration;
+        if (it >= a.no_return_from && a.left_it[i] == it - 1) return false;
+    }
     if (a.choice) a.choice[i] = c;
     if constexpr (SYNC) {
         uint32_t slot = atomicAdd(a.mv_cnt, 1u);
         a.mv_vtx[slot] = i;
         a.mv_cmt[slot] = c;
     } else {
+        a.left[i] = d;
+        a.left_it[i] = *a.iteration;
         a.C[i] = c;
         atomicAdd(a.Sig + d, -Ki);
         atomicAdd(a.Sig + c, Ki);
@@ -283,6 +296,7 @@ __device__ __forceinline__ void record_visit(const MoveArgs &a, uint32_t i, uint
     float g = Ki > 0.0 ? (float)(gain * m / Ki) : 0.0f;
     a.feat_kept[i] = kept;
     a.feat_gain[i] = fminf(fmaxf(g, -1.0f), 1.0f);
+    if (a.last_gain) a.last_gain[i] = (float)gain;
     a.moved_last[i] = (uint8_t)moved;
 }
 
@@ -323,7 +337,10 @@ __device__ void group_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         if (my < count) {
             vi = list[my];
             claim = ld_state<SYNC>(a.act + vi);
-            if (claim) a.act[vi] = 0;
+            if (claim) {
+                a.act[vi] = 0;
+                if (a.deferred) a.deferred[vi] = 0;
+            }
         }
         const unsigned amask = __ballot_sync(0xFFFFFFFFu, claim);
         const int nact = __popc(amask);
@@ -464,7 +481,10 @@ __device__ void block_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         if (my < count) {
             vi = list[my];
             claim = ld_state<SYNC>(a.act + vi);
-            if (claim) a.act[vi] = 0;
+            if (claim) {
+                a.act[vi] = 0;
+                if (a.deferred) a.deferred[vi] = 0;
+            }
         }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, claim);
         __syncthreads();  // previous round done with s_todo
@@ -624,18 +644,22 @@ __device__ __forceinline__ void flush_delta(const uint32_t *keys, const double *
 __global__ void __launch_bounds__(256) k_apply_moves(const uint32_t *__restrict__ mv_vtx,
                                                      const uint32_t *__restrict__ mv_cmt,
                                                      const uint32_t *__restrict__ mv_cnt, const double *__restrict__ K,
-                                                     uint32_t *C, double *Sig, uint32_t *size, int lsb) {
+                                                     uint32_t *C, double *Sig, uint32_t *size, int lsb, uint32_t *left,
+                                                     int *left_it, const int *iteration_dev) {
     __shared__ uint32_t skeys[1 << APPLY_SLOG];
     __shared__ double sds[1 << APPLY_SLOG];
     __shared__ int sdn[1 << APPLY_SLOG];
     for (int t = threadIdx.x; t < (1 << APPLY_SLOG); t += blockDim.x) { skeys[t] = EMPTY; sds[t] = 0.0; sdn[t] = 0; }
     __syncthreads();
     uint32_t cnt = *mv_cnt;
+    const int iteration = *iteration_dev;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         uint32_t i = mv_vtx[t], c = mv_cmt[t];
         uint32_t d = C[i];
         double Ki = K[i];
         C[i] = c;
+        left[i] = d;
+        left_it[i] = iteration;
         apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size, lsb);
         apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size, lsb);
     }
@@ -728,7 +752,7 @@ __device__ bool grid_sync(GridBar *b, unsigned nb, MoveCounters *ctr) {
 // and the count through L2; `smem` holds the block's delta table.
 __device__ void apply_body_l2(const uint32_t *mv_vtx, const uint32_t *mv_cmt, const uint32_t *mv_cnt,
                               const double *__restrict__ K, uint32_t *C, double *Sig, uint32_t *size, uint32_t lb,
-                              uint32_t nb, unsigned char *smem, int lsb) {
+                              uint32_t nb, unsigned char *smem, int lsb, uint32_t *left, int *left_it, int iteration) {
     uint32_t *skeys = reinterpret_cast<uint32_t *>(smem);
     double *sds = reinterpret_cast<double *>(smem + sizeof(uint32_t) * (1u << APPLY_SLOG));
     int *sdn = reinterpret_cast<int *>(smem + (sizeof(uint32_t) + sizeof(double)) * (1u << APPLY_SLOG));
@@ -740,6 +764,8 @@ __device__ void apply_body_l2(const uint32_t *mv_vtx, const uint32_t *mv_cmt, co
         const uint32_t d = __ldcg(C + i);
         const double Ki = K[i];
         C[i] = c;
+        left[i] = d;
+        left_it[i] = iteration;
         apply_delta(skeys, sds, sdn, d, -Ki, -1, Sig, size, lsb);
         apply_delta(skeys, sds, sdn, c, Ki, 1, Sig, size, lsb);
     }
@@ -797,7 +823,8 @@ __global__ void __launch_bounds__(256) k_sweep_persistent(MoveArgs a, const uint
         if (cc[CLS_BLOCK])
             block_body<4096, WT, F64, 2>(aw, list + cb[CLS_BLOCK], cc[CLS_BLOCK], lb, nb, dyn_smem, lc);
         if (!grid_sync(bar, nb, a.ctr)) return;
-        apply_body_l2(a.mv_vtx, a.mv_cmt, mv_cnts + wr, a.K, a.C, a.Sig, a.size, lb, nb, dyn_smem, a.lsb);
+        apply_body_l2(a.mv_vtx, a.mv_cmt, mv_cnts + wr, a.K, a.C, a.Sig, a.size, lb, nb, dyn_smem, a.lsb, a.left,
+                      a.left_it, *a.iteration);
         merge_body_l2(a.act, a.mark, n, lb, nb);
         if (!grid_sync(bar, nb, a.ctr)) return;
     }
@@ -840,7 +867,10 @@ __global__ void k_hub_prepare(MoveArgs a, HubArgs h) {
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < h.nh; t += gridDim.x * blockDim.x) {
         uint32_t i = h.hubs[t];
         uint8_t go = ld_state<SYNC>(a.act + i);
-        if (go) a.act[i] = 0;
+        if (go) {
+            a.act[i] = 0;
+            if (a.deferred) a.deferred[i] = 0;
+        }
         h.go[t] = go;
         h.d[t] = ld_state<SYNC>(a.C + i);
     }
@@ -1028,10 +1058,22 @@ __device__ __forceinline__ int class_of(uint64_t deg) {
     return CLS_HUGE;
 }
 
-// Wave of vertex v: its index within its graph, mod W.
+// Wave of vertex v: a hash of its index within its graph, mod W.  The hash
+// (the MurmurHash3 32-bit finaliser, Appleby) keeps arithmetic patterns of
+// ids out of the waves: with the index itself, every community of a planted
+// graph whose community count shares a factor with W (vertex v in community
+// v mod k) fell into few waves, decided at once and cycled.
+__device__ __forceinline__ uint32_t wave_hash(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
 __device__ __forceinline__ int wave_of(uint32_t v, int W, const uint32_t *gid, const uint64_t *gvo) {
-    uint64_t local = gid ? v - gvo[gid[v]] : v;
-    return (int)(local % (uint64_t)W);
+    const uint32_t local = gid ? (uint32_t)(v - gvo[gid[v]]) : v;
+    return (int)(wave_hash(local) % (uint32_t)W);
 }
 
 __global__ void k_classify_count(const uint64_t *__restrict__ off, uint32_t n, int W, uint32_t *counts,
@@ -1286,13 +1328,19 @@ static MoveArgs make_move_args(const DevGraph &g, const MoveBuffers &mb, bool sy
     a.dq_g = mb.dq_g;
     a.ctr = mb.ctr;
     a.rule = rule ? 1 : 0;
+    a.left = mb.left;
+    a.left_it = mb.left_it;
+    a.iteration = mb.it_dev;
+    a.no_return_from = mb.no_return_from;
     a.mv_vtx = mb.mv_vtx;
     a.mv_cmt = mb.mv_cmt;
     a.mv_cnt = mb.mv_cnt;
     a.choice = mb.choice;
     a.feat_kept = mb.feat_kept;
     a.feat_gain = mb.feat_gain;
+    a.last_gain = mb.last_gain;
     a.moved_last = mb.moved_last;
+    a.deferred = mb.skip;
     a.trace_x = mb.trace_x;
     a.trace_y = mb.trace_y;
     a.trace_cnt = mb.trace_cnt;
@@ -1382,7 +1430,8 @@ void move_wave(const DevGraph &g, const Classes &cl, MoveBuffers &mb, int wave, 
 
 void apply_moves(const DevGraph &g, MoveBuffers &mb, uint32_t n_hint, cudaStream_t s) {
     k_apply_moves<<<grid_for(n_hint, 256, sms(4)), 256, 0, s>>>(mb.mv_vtx, mb.mv_cmt, mb.mv_cnt, mb.K, mb.C,
-                                                                 mb.Sigma, mb.size, mb.lsb);
+                                                                 mb.Sigma, mb.size, mb.lsb, mb.left, mb.left_it,
+                                                                 mb.it_dev);
     GSP_CHECK_LAUNCH();
     k_merge_marks<<<grid_for(g.n / 16 + 1, 256, sms(8)), 256, 0, s>>>(mb.act, mb.mark, g.n);
     GSP_CHECK_LAUNCH();

@@ -137,7 +137,7 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
         const double m = vertex_weights(g, K, mb.m_dev, s);
         GSP_REQUIRE(m > 0.0, "gsp_autotune: the graph has no edges");
         Classes cl;
-        classify_vertices(g, cl, o.waves, s);
+        classify_vertices(g, cl, effective_waves(o.waves, sync), s);
         alloc_pool(mb, cl, s);
         uint32_t wave_n[MAX_WAVES];
         for (int wv = 0; wv < cl.W; wv++) {
@@ -151,6 +151,7 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
             for (int rep = 0; rep < 2; rep++) {
                 k_tune_reset<<<grid_for(n, 256), 256, 0, s>>>(mb.C, mb.Sigma, K, mb.size, mb.act, mb.mark, n);
                 GSP_CHECK_LAUNCH();
+                set_iteration(mb, 0, s);
                 GSP_CUDA(cudaEventRecord(e0, s));
                 sweep_launches(g, cl, mb, sync, fp64, o.singleton_rule != 0, false, 0, o.max_iterations, wave_n,
                                true, s);

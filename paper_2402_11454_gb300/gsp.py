@@ -59,8 +59,8 @@ def _graph(off, tgt, w=None):
 
 
 def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=10.0,
-              aggregation_tolerance=0.8, split="lpp", split_when="pass", move="sync", waves=17,
-              wave_repeats=3, precision="mixed", singleton_rule=True, prune="flags", mlp_params=None,
+              aggregation_tolerance=0.8, split="lpp", split_when="pass", move="sync", waves=0,
+              wave_repeats=3, no_return_from=3, precision="mixed", singleton_rule=True, prune="flags", mlp_params=None,
               full_sweep_every=4, prune_threshold=0.5, count_disconnected=False, workspace=None, stream=None):
     o = GspOpts()
     _lib.load().gsp_default_opts(ctypes.byref(o))
@@ -74,6 +74,7 @@ def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=1
     o.move = MOVE[move]
     o.waves = waves
     o.wave_repeats = wave_repeats
+    o.no_return_from = no_return_from
     o.precision = PRECISION[precision]
     o.singleton_rule = int(bool(singleton_rule))
     o.prune = PRUNE[prune]
@@ -198,13 +199,14 @@ def move_sweep(offsets, targets, weights, C, K, Sigma, m, active=None, precision
 
 
 def local_move(offsets, targets, weights, C, K, Sigma, m, tolerance=1e-2, max_iterations=20,
-               move="sync", waves=17, wave_repeats=3, precision="fp64", singleton_rule=True, stream=None):
+               move="sync", waves=17, wave_repeats=3, no_return_from=3, precision="fp64", singleton_rule=True,
+               stream=None):
     """louvainMove (Algorithm 4); C and Sigma are updated in place; returns l_i."""
     n, nnz = _graph(offsets, targets, weights)
     it = ctypes.c_int()
     check(_lib.load().gsp_local_move(_p(offsets), _p(targets), _p(weights), _wt(weights), n, nnz, _p(C),
                                      _p(K), _p(Sigma), m, tolerance, max_iterations, MOVE[move], waves,
-                                     wave_repeats, PRECISION[precision], int(bool(singleton_rule)),
+                                     wave_repeats, no_return_from, PRECISION[precision], int(bool(singleton_rule)),
                                      ctypes.byref(it), _stream(stream)))
     return it.value
 

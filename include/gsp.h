@@ -406,8 +406,10 @@ void gsp_release_workspace(void);
  * counterpart).  Each degree class runs as a grid-stride kernel whose grid is
  * capped at a number of blocks per SM: groups of lanes per vertex (degree <=
  * 128), a warp per vertex (129..512), a block per vertex (513..2048) and the
- * grid-wide hub pipeline (> 2048).  Any cap in [1, 32] gives the same result
- * in frozen-state (SYNC) mode; only the speed differs.  The setting is
+ * grid-wide hub pipeline (> 8192).  Vertices of 2049..8192 edges take one
+ * block each with a 16384-slot shared table, one block per SM (no cap).  Any
+ * cap in [1, 32] gives the same result in frozen-state (SYNC) mode; only the
+ * speed differs.  The setting is
  * process-wide (all devices) and applies to calls started after it is set.
  * ------------------------------------------------------------------------- */
 typedef struct {
@@ -422,19 +424,29 @@ typedef struct {
      * from a CUDA graph were as fast (a wave's dependent loads, not its
      * launches, set the time).  The result is the same either way. */
     uint32_t persist_max_vertices;
+    /* Class boundaries: the largest degree served by the group kernel (33..128,
+     * default 128), the warp kernel (..512, default 512), the 4096-slot block
+     * kernel (..2048, default 2048) and the 16384-slot block kernel (..8192,
+     * default 8192); larger degrees go to the hub pipeline.  They must rise. */
+    uint32_t group_max_degree;
+    uint32_t warp_max_degree;
+    uint32_t block_max_degree;
+    uint32_t big_max_degree;
 } gsp_tuning;
 
 /* Current caps into *out (host).  GSP_ERR_INVALID if out is NULL. */
 gsp_status gsp_get_tuning(gsp_tuning *out);
 
-/* Install caps (host struct); GSP_ERR_INVALID if a cap is outside [1, 32]
- * (persist_max_vertices may be any value). */
+/* Install caps and boundaries (host struct); GSP_ERR_INVALID if a cap is
+ * outside [1, 32] or the boundaries break their limits (persist_max_vertices
+ * may be any value). */
 gsp_status gsp_set_tuning(const gsp_tuning *t);
 
 /*
- * Pick the caps for this graph and install them: times the first sweep of
- * the first pass (all vertices unprocessed; opts' move mode, waves and
- * precision) under candidate caps, one class at a time, and keeps the
+ * Pick the caps and class boundaries for this graph and install them: times
+ * the first sweep of the first pass (all vertices unprocessed; opts' move
+ * mode, waves and precision) under candidate caps and boundaries (each
+ * boundary at its limit or half of it), one knob at a time, and keeps the
  * fastest.  Device graph as for gsp_louvain (float32 weights); the graph is
  * not modified.  *chosen receives the installed caps, *ms_default the sweep
  * time under the caps in effect at the call, *ms_tuned the time under the

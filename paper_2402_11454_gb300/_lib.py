@@ -49,7 +49,8 @@ class GspDeviceGraph(ctypes.Structure):
 
 class GspTuning(ctypes.Structure):
     _fields_ = [("groups_blocks_per_sm", c_int), ("w512_blocks_per_sm", c_int), ("block_blocks_per_sm", c_int),
-                ("hub_blocks_per_sm", c_int), ("persist_max_vertices", c_u32)]
+                ("hub_blocks_per_sm", c_int), ("persist_max_vertices", c_u32), ("group_max_degree", c_u32),
+                ("warp_max_degree", c_u32), ("block_max_degree", c_u32), ("big_max_degree", c_u32)]
 
 
 _SIGS = {

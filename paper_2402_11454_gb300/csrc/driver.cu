@@ -433,9 +433,10 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
         wave_n[wv] = 0;
         for (int c = 0; c < NUM_CLS; c++) wave_n[wv] += cl.count(c, wv);
     }
-    // features (learned pruning, traces) depend on the iteration number, so
-    // those runs launch directly
-    const bool use_graph = graphs_enabled() && !mb.feat_kept;
+    // every per-iteration value the kernels need (the iteration itself, the
+    // features' iteration position, trace sampling) comes from the device
+    // scalar set before each replay, so every run replays its graph
+    const bool use_graph = graphs_enabled();
     bool use_persist = sync && persistent_enabled();  // small graphs: one launch per sweep
     cudaGraphExec_t exec = nullptr;
     side_streams();
@@ -463,24 +464,23 @@ static MoveLoopResult move_loop_on(const DevGraph &g, const Classes &cl, MoveBuf
                 persisted = sweep_persistent(g, cl, mb, fp64, rule, it, max_it, s);
                 use_persist = persisted;
             }
-            if (persisted) {
-            } else {
-            GSP_CUDA(cudaEventRecord(e0, s));
-            if (use_graph && it >= 1) {
-                if (!exec) {
-                    cudaGraph_t graph;
-                    GSP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-                    sweep_launches(g, cl, mb, sync, fp64, rule, false, it, max_it, wave_n, true, s);
-                    GSP_CUDA(cudaStreamEndCapture(s, &graph));
-                    GSP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-                    GSP_CUDA(cudaGraphDestroy(graph));
-                }
-                GSP_CUDA(cudaGraphLaunch(exec, s));
-            } else {
+            if (!persisted) {
+                GSP_CUDA(cudaEventRecord(e0, s));
                 GSP_CUDA(cudaMemsetAsync(mb.ctr, 0, sizeof(MoveCounters), s));
                 if (pruned) mlp_prune(g, mb, it, max_it, pr.threshold, s);
-                sweep_launches(g, cl, mb, sync, fp64, rule, pruned, it, max_it, wave_n, false, s);
-            }
+                if (use_graph && it >= 1) {
+                    if (!exec) {
+                        cudaGraph_t graph;
+                        GSP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+                        sweep_launches(g, cl, mb, sync, fp64, rule, false, it, max_it, wave_n, false, s);
+                        GSP_CUDA(cudaStreamEndCapture(s, &graph));
+                        GSP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+                        GSP_CUDA(cudaGraphDestroy(graph));
+                    }
+                    GSP_CUDA(cudaGraphLaunch(exec, s));
+                } else {
+                    sweep_launches(g, cl, mb, sync, fp64, rule, pruned, it, max_it, wave_n, false, s);
+                }
             }
             GSP_CUDA(cudaEventRecord(e1, s));
             GSP_CUDA(cudaMemcpyAsync(&h, mb.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));

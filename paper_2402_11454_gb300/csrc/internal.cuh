@@ -22,21 +22,30 @@ struct DevGraph {
 // result of a sweep does not depend on it).  Set by gsp_set_tuning or chosen
 // by gsp_autotune.
 struct Tuning {
-    int groups = 8;  // k_move_groups (degrees <= 128)
-    int w512 = 3;    // k_move_w512 (129..512)
-    int block = 4;   // k_move_block (513..2048)
-    int hub = 4;     // k_hub_insert / k_hub_score (> 2048)
+    int groups = 8;  // k_move_groups (degrees <= group_max)
+    int w512 = 3;    // k_move_w512 (group_max+1 .. warp_max)
+    int block = 4;   // k_move_block, 4096-slot table (warp_max+1 .. block_max)
+    int hub = 4;     // k_hub_insert / k_hub_score (> big_max)
     uint32_t persist_max_vertices = 0;  // graphs up to this size (no hubs) sweep in one launch (0: off)
+    // class boundaries (largest degree of each class); each at most what its
+    // kernel's table holds (twice as many slots as edges)
+    uint32_t group_max = 128, warp_max = 512, block_max = 2048, big_max = 8192;
+};
+// Largest degree each class's table can hold.
+constexpr uint32_t GROUP_MAX_LIMIT = 128, WARP_MAX_LIMIT = 512, BLOCK_MAX_LIMIT = 2048, BIG_MAX_LIMIT = 8192;
+// Class boundaries as the classify kernels take them.
+struct ClassBounds {
+    uint32_t group_max, warp_max, block_max, big_max;
 };
 Tuning &tuning();
 
 // Degree classes of a vertex list.  Small degrees are served by groups of G
 // lanes with a shared-memory table, mid degrees by one block with a
-// shared-memory table, the largest by one block with a table in a global
+// shared-memory table (4096 slots up to 2048 edges, 16384 slots, one block
+// per SM, up to 8192), the largest by the whole grid with tables in a global
 // pool.  Each class is further split into W waves (vertex v in wave v mod W):
 // the list holds key = class * W + wave in increasing order.
-enum { CLS_G4 = 0, CLS_G8, CLS_G16, CLS_G32, CLS_W512, CLS_BLOCK, CLS_HUGE, NUM_CLS };
-constexpr uint32_t CLS_MAXDEG[NUM_CLS] = {8, 16, 32, 128, 512, 2048, 0xFFFFFFFFu};
+enum { CLS_G4 = 0, CLS_G8, CLS_G16, CLS_G32, CLS_W512, CLS_BLOCK, CLS_BIG, CLS_HUGE, NUM_CLS };
 constexpr int MAX_WAVES = 64;
 constexpr int MAX_REPEATS = 8;  // repeats of a wave (gsp_opts.wave_repeats)
 
@@ -128,7 +137,7 @@ struct MoveBuffers {
 // Side streams for the independent kernels of a wave (fork/join with
 // events); created once per device.
 struct SideStreams {
-    static constexpr int N = 3;
+    static constexpr int N = 4;
     cudaStream_t side[N];
     cudaEvent_t fork_ev[64], join_ev[64][N];
     int next = 0;

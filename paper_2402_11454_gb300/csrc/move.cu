@@ -70,12 +70,12 @@ struct MoveArgs {
     float *trace_x;
     uint8_t *trace_y;
     uint32_t *trace_cnt;
-    uint64_t *trace_keys;  // optional: trace_tag | vertex per row
-    uint64_t trace_tag;    // pass << 56 | iteration << 48 | repeat << 40
+    uint64_t *trace_keys;  // optional: trace_tag | iteration << 48 | vertex per row
+    uint64_t trace_tag;    // pass << 56 | repeat << 40
     uint32_t trace_cap, trace_every;
     float max_logk;
-    float iter_frac;
-    uint32_t salt;
+    int max_iterations;  // the iteration's position in the pass (a feature) is *iteration / max_iterations
+    uint32_t salt;       // trace sampling: per pass; the iteration is mixed in on the device
 };
 
 template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
@@ -273,7 +273,8 @@ __device__ void flush_counters(const LocalCtr &l, MoveCounters *g) {
 }
 
 __device__ __forceinline__ void vertex_features(const MoveArgs &a, uint32_t i, uint32_t deg, double Ki, float *x) {
-    predictor_features(deg, Ki, a.feat_kept[i], a.feat_gain[i], a.moved_last[i], a.max_logk, a.iter_frac, x);
+    const float iter_frac = a.max_iterations > 0 ? (float)*a.iteration / (float)a.max_iterations : 0.0f;
+    predictor_features(deg, Ki, a.feat_kept[i], a.feat_gain[i], a.moved_last[i], a.max_logk, iter_frac, x);
 }
 
 // After a visit: record last-visit features and, for sampled visits, a trace
@@ -281,7 +282,7 @@ __device__ __forceinline__ void vertex_features(const MoveArgs &a, uint32_t i, u
 __device__ __forceinline__ void record_visit(const MoveArgs &a, uint32_t i, uint32_t deg, double Ki, double kid,
                                              double gain, double m, int moved) {
     if (!a.feat_kept) return;
-    if (a.trace_x && (hash32(i ^ a.salt) % a.trace_every) == 0) {
+    if (a.trace_x && (hash32(i ^ ((uint32_t)*a.iteration * 0x9E3779B9u + a.salt)) % a.trace_every) == 0) {
         float x[MLP_IN];
         vertex_features(a, i, deg, Ki, x);
         uint32_t slot = atomicAdd(a.trace_cnt, 1u);
@@ -289,7 +290,7 @@ __device__ __forceinline__ void record_visit(const MoveArgs &a, uint32_t i, uint
 #pragma unroll
             for (int k = 0; k < MLP_IN; k++) a.trace_x[(size_t)slot * MLP_IN + k] = x[k];
             a.trace_y[slot] = (uint8_t)moved;
-            if (a.trace_keys) a.trace_keys[slot] = a.trace_tag | i;
+            if (a.trace_keys) a.trace_keys[slot] = a.trace_tag | ((uint64_t)(*a.iteration & 0xFF) << 48) | i;
         }
     }
     float kept = Ki > 0.0 ? (float)(kid / Ki) : 0.0f;
@@ -516,7 +517,8 @@ __device__ void block_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         uint32_t deg = (uint32_t)(e - b);
         int logcap = ceil_log2(2 * deg);
         V kid = 0;
-        scan_edges<4, SYNC, V>(a.tgt, w, a.C, i, d, b, e, threadIdx.x, blockDim.x, kid,
+        constexpr int U = CAP >= 16384 ? 8 : 4;  // hubs: more gathers in flight per thread
+        scan_edges<U, SYNC, V>(a.tgt, w, a.C, i, d, b, e, threadIdx.x, blockDim.x, kid,
                                [&](uint32_t c, V wv) { smem_add<V>(keys, vals, logcap, occ, &s_nocc, c, wv); });
         kid = warp_sum(kid);
         if (lane == 0) red_k[wid] = kid;
@@ -530,7 +532,7 @@ __device__ void block_body(const MoveArgs &a, const uint32_t *__restrict__ list,
         uint32_t bestc = EMPTY;
         uint32_t nocc = s_nocc;
         uint32_t ncand = 0;
-        score_table<4, SYNC>(keys, vals, occ, nocc, threadIdx.x, blockDim.x, a.Sig, sc, best, bestc, ncand);
+        score_table<U, SYNC>(keys, vals, occ, nocc, threadIdx.x, blockDim.x, a.Sig, sc, best, bestc, ncand);
         __syncthreads();  // every slot scored before the table is emptied
         for (uint32_t k = threadIdx.x; k < nocc; k += blockDim.x) {
             uint32_t slot = occ[k];
@@ -1048,13 +1050,14 @@ __global__ void k_hub_tasks(const uint64_t *__restrict__ off, const uint32_t *__
 // --------------------------------------------------------------------------
 // Degree classes
 // --------------------------------------------------------------------------
-__device__ __forceinline__ int class_of(uint64_t deg) {
+__device__ __forceinline__ int class_of(uint64_t deg, const ClassBounds &cb) {
     if (deg <= 8) return CLS_G4;
     if (deg <= 16) return CLS_G8;
     if (deg <= 32) return CLS_G16;
-    if (deg <= 128) return CLS_G32;
-    if (deg <= 512) return CLS_W512;
-    if (deg <= 2048) return CLS_BLOCK;
+    if (deg <= cb.group_max) return CLS_G32;
+    if (deg <= cb.warp_max) return CLS_W512;
+    if (deg <= cb.block_max) return CLS_BLOCK;
+    if (deg <= cb.big_max) return CLS_BIG;
     return CLS_HUGE;
 }
 
@@ -1077,13 +1080,13 @@ __device__ __forceinline__ int wave_of(uint32_t v, int W, const uint32_t *gid, c
 }
 
 __global__ void k_classify_count(const uint64_t *__restrict__ off, uint32_t n, int W, uint32_t *counts,
-                                 const uint32_t *__restrict__ gid, const uint64_t *__restrict__ gvo) {
+                                 const uint32_t *__restrict__ gid, const uint64_t *__restrict__ gvo, ClassBounds cb) {
     __shared__ uint32_t sc[NUM_CLS * MAX_WAVES];
     for (int t = threadIdx.x; t < NUM_CLS * W; t += blockDim.x) sc[t] = 0;
     __syncthreads();
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint64_t deg = off[v + 1] - off[v];
-        if (deg) atomicAdd(&sc[class_of(deg) * W + wave_of(v, W, gid, gvo)], 1u);
+        if (deg) atomicAdd(&sc[class_of(deg, cb) * W + wave_of(v, W, gid, gvo)], 1u);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < NUM_CLS * W; t += blockDim.x)
@@ -1091,12 +1094,13 @@ __global__ void k_classify_count(const uint64_t *__restrict__ off, uint32_t n, i
 }
 
 __global__ void k_classify_fill(const uint64_t *__restrict__ off, uint32_t n, int W, uint32_t *cursor,
-                                uint32_t *list, const uint32_t *__restrict__ gid, const uint64_t *__restrict__ gvo) {
+                                uint32_t *list, const uint32_t *__restrict__ gid, const uint64_t *__restrict__ gvo,
+                                ClassBounds cb) {
     int lane = threadIdx.x & 31;
     for (uint32_t v0 = blockIdx.x * blockDim.x; v0 < n; v0 += gridDim.x * blockDim.x) {
         uint32_t v = v0 + threadIdx.x;
         uint64_t deg = (v < n) ? off[v + 1] - off[v] : 0;
-        int key = deg ? class_of(deg) * W + wave_of(v, W, gid, gvo) : -1;
+        int key = deg ? class_of(deg, cb) * W + wave_of(v, W, gid, gvo) : -1;
         uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
         int leader = __ffs(peers) - 1;
         uint32_t base = 0;
@@ -1126,7 +1130,9 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
     uint32_t *counts = arena().get<uint32_t>(2 * NK);
     GSP_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * NK, s));
     unsigned grid = grid_for(g.n, 256, sms(8));
-    k_classify_count<<<grid, 256, 0, s>>>(g.off, g.n, W, counts, gid, gvo);
+    const Tuning tn = tuning();
+    const ClassBounds cb{tn.group_max, tn.warp_max, tn.block_max, tn.big_max};
+    k_classify_count<<<grid, 256, 0, s>>>(g.off, g.n, W, counts, gid, gvo, cb);
     GSP_CHECK_LAUNCH();
     uint32_t h[NUM_CLS * MAX_WAVES];
     GSP_CUDA(cudaMemcpyAsync(h, counts, sizeof(uint32_t) * NK, cudaMemcpyDeviceToHost, s));
@@ -1136,7 +1142,7 @@ void classify_vertices(const DevGraph &g, Classes &cl, int waves, cudaStream_t s
     uint32_t *cursor = counts + NK;
     GSP_CUDA(cudaMemcpyAsync(cursor, cl.start, sizeof(uint32_t) * NK, cudaMemcpyHostToDevice, s));
     cl.list = arena().get<uint32_t>(cl.start[NK] + 1);
-    k_classify_fill<<<grid, 256, 0, s>>>(g.off, g.n, W, cursor, cl.list, gid, gvo);
+    k_classify_fill<<<grid, 256, 0, s>>>(g.off, g.n, W, cursor, cl.list, gid, gvo, cb);
     GSP_CHECK_LAUNCH();
     cl.dstart = arena().get<uint32_t>(NK + 1);
     GSP_CUDA(cudaMemcpyAsync(cl.dstart, cl.start, sizeof(uint32_t) * (NK + 1), cudaMemcpyHostToDevice, s));
@@ -1191,8 +1197,9 @@ SideStreams &side_streams() {
 
 // The class kernels of a wave touch disjoint vertices and only append to the
 // move list, so they run as parallel branches: W512 and the block class on
-// side streams 0 and 1, the hub chain on side stream 2, the group classes on
-// the main stream; all join before the wave's moves are applied.
+// side streams 0 and 1, the hub chain on side stream 2, the big-table block
+// class on side stream 3, the group classes on the main stream; all join
+// before the wave's moves are applied.
 template <typename WT, bool F64, int SYNC>
 static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t *pool_keys, void *pool_vals,
                         uint32_t *pool_occ, uint32_t *big, uint32_t *nbig, cudaStream_t main) {
@@ -1200,7 +1207,7 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
     SideStreams &ss = side_streams();
     const int f = ss.next;
     ss.next = (ss.next + 1) & 63;
-    bool used[SideStreams::N] = {false, false, false};
+    bool used[SideStreams::N] = {false, false, false, false};
     GSP_CUDA(cudaEventRecord(ss.fork_ev[f], main));
     auto on = [&](int k) -> cudaStream_t {
         if (!used[k]) {
@@ -1251,6 +1258,22 @@ static void launch_wave(const Classes &cl, const MoveArgs &a, int wave, uint32_t
         }
         k_move_block<CAP, WT, F64, SYNC><<<grid_for(nb, 1, (uint32_t)(sm * tn.block)), 256, smem, on(1)>>>(
             a, cl.list + cl.begin(CLS_BLOCK, wave), nb);
+        GSP_CHECK_LAUNCH();
+    }
+    uint32_t ng = cl.count(CLS_BIG, wave);
+    if (ng) {
+        // 2049..8192 edges: one block per vertex with a 16384-slot shared
+        // table (at most 2 x 8192 distinct keys), one block per SM
+        constexpr int CAP = 16384;
+        constexpr size_t smem = (size_t)CAP * (sizeof(uint32_t) + sizeof(V) + sizeof(uint16_t));
+        static bool attr = false;
+        if (!attr) {
+            GSP_CUDA(cudaFuncSetAttribute(k_move_block<CAP, WT, F64, SYNC>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        k_move_block<CAP, WT, F64, SYNC><<<grid_for(ng, 1, (uint32_t)sm), 256, smem, on(3)>>>(
+            a, cl.list + cl.begin(CLS_BIG, wave), ng);
         GSP_CHECK_LAUNCH();
     }
     uint32_t nh = cl.count(CLS_HUGE, wave);
@@ -1346,12 +1369,11 @@ static MoveArgs make_move_args(const DevGraph &g, const MoveBuffers &mb, bool sy
     a.trace_cnt = mb.trace_cnt;
     a.trace_cap = mb.trace_cap;
     a.trace_keys = mb.trace_keys;
-    a.trace_tag = ((uint64_t)(mb.trace_pass & 0xFF) << 56) | ((uint64_t)(iteration & 0xFF) << 48) |
-                  ((uint64_t)(mb.cur_repeat & 0xFF) << 40);
+    a.trace_tag = ((uint64_t)(mb.trace_pass & 0xFF) << 56) | ((uint64_t)(mb.cur_repeat & 0xFF) << 40);
     a.trace_every = mb.trace_every ? mb.trace_every : 1;
     a.max_logk = mb.max_logk;
-    a.iter_frac = max_iterations > 0 ? (float)iteration / (float)max_iterations : 0.0f;
-    a.salt = (uint32_t)(iteration * 0x9E3779B9u + mb.trace_salt);
+    a.max_iterations = max_iterations;
+    a.salt = mb.trace_salt;
     return a;
 }
 
@@ -1393,7 +1415,8 @@ static bool launch_persistent(const MoveArgs &a, const Classes &cl, uint32_t n, 
 
 bool sweep_persistent(const DevGraph &g, const Classes &cl, MoveBuffers &mb, bool fp64, bool rule, int iteration,
                       int max_iterations, cudaStream_t s) {
-    if (cl.cls_count(CLS_HUGE) || mb.feat_kept || mb.choice || !cl.dstart || !mb.bar) return false;
+    if (cl.cls_count(CLS_HUGE) || cl.cls_count(CLS_BIG) || mb.feat_kept || mb.choice || !cl.dstart || !mb.bar)
+        return false;
     if (g.n > tuning().persist_max_vertices) return false;
     MoveArgs a = make_move_args(g, mb, true, rule, iteration, max_iterations);
     if (g.wt == GSP_W_F32) return fp64 ? launch_persistent<float, true>(a, cl, g.n, mb, iteration, s)

@@ -221,7 +221,7 @@ static void split_lp(const DevGraph &g, const Classes &cl, const uint32_t *C, bo
     auto cnt = [&](int c) { return cl.cls_count(c); };
     auto lst = [&](int c) { return cl.list + cl.cls_begin(c); };
     const unsigned maxg = sms(8);
-    uint32_t nbig = cl.cls_count(CLS_BLOCK) + cl.cls_count(CLS_HUGE);
+    uint32_t nbig = cl.cls_count(CLS_BLOCK) + cl.cls_count(CLS_BIG) + cl.cls_count(CLS_HUGE);
     for (int it = 0; it < (1 << 30); it++) {
         GSP_CUDA(cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s));
 #define LPG(G, CLS)                                                                                  \
@@ -279,7 +279,7 @@ static void split_sv(const DevGraph &g, const Classes &cl, const uint32_t *C, ui
     auto cnt = [&](int c) { return cl.cls_count(c); };
     auto lst = [&](int c) { return cl.list + cl.cls_begin(c); };
     const unsigned maxg = sms(8);
-    const uint32_t nbig = cl.cls_count(CLS_BLOCK) + cl.cls_count(CLS_HUGE);
+    const uint32_t nbig = cl.cls_count(CLS_BLOCK) + cl.cls_count(CLS_BIG) + cl.cls_count(CLS_HUGE);
     for (int it = 0; it < (1 << 30); it++) {
         GSP_CUDA(cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s));
 #define SVG(G, CLS)                                                                                            \

@@ -1,15 +1,16 @@
 // tune.cu -- launch-geometry tuning of the local-moving kernels.
 //
 // Each degree class of local moving (Algorithm 4) runs as a grid-stride
-// kernel whose grid is capped at a number of blocks per SM.  The best caps
-// depend on the graph's degree distribution (how many vertices of each class
-// a wave holds, how unbalanced the hubs are), so gsp_autotune picks them on
-// the caller's graph: it times the first sweep of the first pass (every
-// vertex unprocessed, the heaviest sweep) under candidate caps, one class at
-// a time (two rounds of coordinate descent), restoring the start state before
-// each trial.
-// Caps change only the launch geometry: in frozen-state mode a sweep's result
-// is the same under every setting.
+// kernel whose grid is capped at a number of blocks per SM, and the degree
+// boundaries between the classes decide which kernel (table size, lanes per
+// vertex) serves a vertex.  The best choices depend on the graph's degree
+// distribution (how many vertices of each class a wave holds, how unbalanced
+// the hubs are), so gsp_autotune picks them on the caller's graph: it times
+// the first sweep of the first pass (every vertex unprocessed, the heaviest
+// sweep) under candidate caps and boundaries, one knob at a time (two rounds
+// of coordinate descent), restoring the start state before each trial.
+// Caps and boundaries change only which threads do the work: in frozen-state
+// mode a sweep's result is the same under every setting.
 #include <string.h>
 
 #include <mutex>
@@ -51,6 +52,13 @@ static void check_tuning(const gsp_tuning &t) {
                     t.block_blocks_per_sm >= 1 && t.block_blocks_per_sm <= TUNE_MAX &&
                     t.hub_blocks_per_sm >= 1 && t.hub_blocks_per_sm <= TUNE_MAX,
                 "tuning caps must be in [1, %d] blocks per SM", TUNE_MAX);
+    GSP_REQUIRE(t.group_max_degree >= 33 && t.group_max_degree <= GROUP_MAX_LIMIT &&
+                    t.warp_max_degree > t.group_max_degree && t.warp_max_degree <= WARP_MAX_LIMIT &&
+                    t.block_max_degree > t.warp_max_degree && t.block_max_degree <= BLOCK_MAX_LIMIT &&
+                    t.big_max_degree > t.block_max_degree && t.big_max_degree <= BIG_MAX_LIMIT,
+                "class boundaries must rise: 33 <= group_max <= %u < warp_max <= %u < block_max <= %u < "
+                "big_max <= %u",
+                GROUP_MAX_LIMIT, WARP_MAX_LIMIT, BLOCK_MAX_LIMIT, BIG_MAX_LIMIT);
 }
 
 static gsp_tuning to_abi(const Tuning &t) {
@@ -60,6 +68,10 @@ static gsp_tuning to_abi(const Tuning &t) {
     o.block_blocks_per_sm = t.block;
     o.hub_blocks_per_sm = t.hub;
     o.persist_max_vertices = t.persist_max_vertices;
+    o.group_max_degree = t.group_max;
+    o.warp_max_degree = t.warp_max;
+    o.block_max_degree = t.block_max;
+    o.big_max_degree = t.big_max;
     return o;
 }
 
@@ -70,6 +82,10 @@ static Tuning from_abi(const gsp_tuning &t) {
     o.block = t.block_blocks_per_sm;
     o.hub = t.hub_blocks_per_sm;
     o.persist_max_vertices = t.persist_max_vertices;
+    o.group_max = t.group_max_degree;
+    o.warp_max = t.warp_max_degree;
+    o.block_max = t.block_max_degree;
+    o.big_max = t.big_max_degree;
     return o;
 }
 
@@ -136,17 +152,31 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
         mb.K = K;
         const double m = vertex_weights(g, K, mb.m_dev, s);
         GSP_REQUIRE(m > 0.0, "gsp_autotune: the graph has no edges");
+        // the class lists and hub tables follow the class boundaries in
+        // g_tuning: rebuilt when a trial changes a boundary
         Classes cl;
-        classify_vertices(g, cl, effective_waves(o.waves, sync), s);
-        alloc_pool(mb, cl, s);
         uint32_t wave_n[MAX_WAVES];
-        for (int wv = 0; wv < cl.W; wv++) {
-            wave_n[wv] = 0;
-            for (int c = 0; c < NUM_CLS; c++) wave_n[wv] += cl.count(c, wv);
-        }
+        const size_t class_mark = arena().mark();
+        ClassBounds built{0, 0, 0, 0};
+        auto prepare = [&]() {
+            const Tuning &t = g_tuning;
+            if (built.group_max == t.group_max && built.warp_max == t.warp_max && built.block_max == t.block_max &&
+                built.big_max == t.big_max)
+                return;
+            arena().release(class_mark);
+            cl = Classes();
+            classify_vertices(g, cl, effective_waves(o.waves, sync), s);
+            alloc_pool(mb, cl, s);
+            for (int wv = 0; wv < cl.W; wv++) {
+                wave_n[wv] = 0;
+                for (int c = 0; c < NUM_CLS; c++) wave_n[wv] += cl.count(c, wv);
+            }
+            built = ClassBounds{t.group_max, t.warp_max, t.block_max, t.big_max};
+        };
         side_streams();
         cudaEvent_t e0 = pool_event(), e1 = pool_event();
         auto trial = [&]() -> float {
+            prepare();
             float best = 1e30f;
             for (int rep = 0; rep < 2; rep++) {
                 k_tune_reset<<<grid_for(n, 256), 256, 0, s>>>(mb.C, mb.Sigma, K, mb.size, mb.act, mb.mark, n);
@@ -178,12 +208,41 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
                                   {&Tuning::w512, {1, 2, 3, 4, 6}},
                                   {&Tuning::block, {2, 3, 4, 5, 8}},
                                   {&Tuning::hub, {2, 4, 8, 16, 32}}};
+            // class boundaries: each class may hand its upper half to the next
+            // (larger) kernel; a boundary only moves down from the limit its
+            // table allows
+            struct Bound {
+                uint32_t Tuning::*field;
+                uint32_t cand[2];
+            };
+            const Bound bounds[] = {{&Tuning::group_max, {GROUP_MAX_LIMIT, GROUP_MAX_LIMIT / 2}},
+                                    {&Tuning::warp_max, {WARP_MAX_LIMIT, WARP_MAX_LIMIT / 2}},
+                                    {&Tuning::block_max, {BLOCK_MAX_LIMIT, BLOCK_MAX_LIMIT / 2}},
+                                    {&Tuning::big_max, {BIG_MAX_LIMIT, BIG_MAX_LIMIT / 2}}};
+            auto valid = [](const Tuning &t) {
+                return t.group_max >= 33 && t.warp_max > t.group_max && t.block_max > t.warp_max &&
+                       t.big_max > t.block_max;
+            };
             for (int round = 0; round < 2; round++) {  // the classes share the SMs: revisit once
                 for (const Knob &k : knobs) {
                     for (int v : k.cand) {
                         if (v == best.*(k.field)) continue;
                         g_tuning = best;
                         g_tuning.*(k.field) = v;
+                        float t = trial();
+                        if (t < tb) {
+                            tb = t;
+                            best = g_tuning;
+                        }
+                    }
+                }
+                for (const Bound &b : bounds) {
+                    for (uint32_t v : b.cand) {
+                        if (v == best.*(b.field)) continue;
+                        Tuning c = best;
+                        c.*(b.field) = v;
+                        if (!valid(c)) continue;
+                        g_tuning = c;
                         float t = trial();
                         if (t < tb) {
                             tb = t;

@@ -275,7 +275,8 @@ def count_disconnected(offsets, targets, C, stream=None):
 
 
 _TUNING_FIELDS = ("groups_blocks_per_sm", "w512_blocks_per_sm", "block_blocks_per_sm", "hub_blocks_per_sm",
-                  "persist_max_vertices")
+                  "persist_max_vertices", "group_max_degree", "warp_max_degree", "block_max_degree",
+                  "big_max_degree")
 
 
 def get_tuning():

@@ -69,20 +69,27 @@ def test_invalid_arguments_rejected_on_host(lib):
 
 
 def test_tuning_roundtrip_and_validation(lib):
-    """Grid caps are host state: get/set work without a GPU and out-of-range
-    caps are rejected."""
+    """Grid caps and class boundaries are host state: get/set work without a
+    GPU and out-of-range values are rejected."""
     from paper_2402_11454_gb300._lib import GspTuning
     t = GspTuning()
     assert lib.gsp_get_tuning(ctypes.byref(t)) == 0
     assert (t.groups_blocks_per_sm, t.w512_blocks_per_sm, t.block_blocks_per_sm, t.hub_blocks_per_sm) == (8, 3, 4, 4)
     assert t.persist_max_vertices == 0
-    new = GspTuning(6, 2, 5, 8, 0)
+    assert (t.group_max_degree, t.warp_max_degree, t.block_max_degree, t.big_max_degree) == (128, 512, 2048, 8192)
+    new = GspTuning(6, 2, 5, 8, 0, 64, 256, 2048, 4096)
     assert lib.gsp_set_tuning(ctypes.byref(new)) == 0
     got = GspTuning()
     lib.gsp_get_tuning(ctypes.byref(got))
     assert (got.groups_blocks_per_sm, got.w512_blocks_per_sm, got.block_blocks_per_sm, got.hub_blocks_per_sm,
             got.persist_max_vertices) == (6, 2, 5, 8, 0)
-    for bad in (GspTuning(0, 3, 4, 4, 0), GspTuning(8, 33, 4, 4, 0), GspTuning(8, 3, -1, 4, 0)):
+    assert (got.group_max_degree, got.warp_max_degree, got.block_max_degree, got.big_max_degree) == (64, 256, 2048, 4096)
+    d = (128, 512, 2048, 8192)
+    for bad in (GspTuning(0, 3, 4, 4, 0, *d), GspTuning(8, 33, 4, 4, 0, *d), GspTuning(8, 3, -1, 4, 0, *d),
+                GspTuning(8, 3, 4, 4, 0, 256, 512, 2048, 8192),    # group table holds 128 edges at most
+                GspTuning(8, 3, 4, 4, 0, 128, 1024, 2048, 8192),   # warp table: 512
+                GspTuning(8, 3, 4, 4, 0, 128, 512, 512, 8192),     # boundaries must rise
+                GspTuning(8, 3, 4, 4, 0, 128, 512, 2048, 16384)):  # big table: 8192
         assert lib.gsp_set_tuning(ctypes.byref(bad)) == -1
     assert lib.gsp_get_tuning(None) == -1
     assert lib.gsp_set_tuning(ctypes.byref(t)) == 0  # restore the defaults

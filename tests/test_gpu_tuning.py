@@ -1,6 +1,7 @@
 """Launch-geometry tuning of local moving: in frozen-state mode the result
-must not depend on the grid caps, and the autotuner must install valid caps
-that leave results unchanged."""
+must not depend on the grid caps or on the degree boundaries between the
+kernels, and the autotuner must install valid settings that leave results
+unchanged."""
 import numpy as np
 import pytest
 
@@ -28,7 +29,11 @@ def restore(gsp):
 CAPS = [dict(groups_blocks_per_sm=1, w512_blocks_per_sm=1, block_blocks_per_sm=1, hub_blocks_per_sm=1,
              persist_max_vertices=0),
         dict(groups_blocks_per_sm=16, w512_blocks_per_sm=6, block_blocks_per_sm=8, hub_blocks_per_sm=16),
-        dict(groups_blocks_per_sm=3, w512_blocks_per_sm=32, block_blocks_per_sm=2, hub_blocks_per_sm=7)]
+        dict(groups_blocks_per_sm=3, w512_blocks_per_sm=32, block_blocks_per_sm=2, hub_blocks_per_sm=7),
+        # class boundaries moved: every class hands its upper half to the next kernel
+        dict(groups_blocks_per_sm=8, w512_blocks_per_sm=3, block_blocks_per_sm=4, hub_blocks_per_sm=4,
+             group_max_degree=64, warp_max_degree=256, block_max_degree=1024, big_max_degree=4096),
+        dict(group_max_degree=128, warp_max_degree=512, block_max_degree=2048, big_max_degree=2049)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -48,6 +53,7 @@ def test_autotune_installs_valid_caps(gsp, restore):
     caps, ms_before, ms_after = gsp.autotune(off, tgt, w)
     assert caps == gsp.get_tuning()
     assert all(1 <= v <= 32 for k, v in caps.items() if k.endswith("_per_sm"))
+    assert 33 <= caps["group_max_degree"] < caps["warp_max_degree"] < caps["block_max_degree"] < caps["big_max_degree"]
     assert 0 < ms_after <= ms_before
     C, q, _ = gsp.louvain(off, tgt, w, precision="fp64")
     assert (C == C0).all() and q == q0

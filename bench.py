@@ -193,9 +193,10 @@ def make_workload(gsp, graphgen, name):
 
 
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of all
-# local-moving launches of one R-MAT 20 step divided by that step's
-# algorithmic bytes; None when no capture of the current kernels exists.
-MOVE_TRAFFIC_RATIO = None
+# local-moving launches of one R-MAT 20 call divided by that call's
+# algorithmic bytes (profiles/dram_local_moving_rmat20.md); None when no
+# capture of the current kernels exists.
+MOVE_TRAFFIC_RATIO = 2.153
 
 
 def roofline_from(stats_list, peak_gbs, peak_kind):
@@ -212,7 +213,8 @@ def roofline_from(stats_list, peak_gbs, peak_kind):
     if MOVE_TRAFFIC_RATIO:
         r["traffic"] = round(per_step * MOVE_TRAFFIC_RATIO)
         r["traffic_basis"] = ("DRAM bytes per step: %.3f x the algorithmic bytes, ratio from an ncu capture of "
-                              "every local-moving launch of one R-MAT 20 step" % MOVE_TRAFFIC_RATIO)
+                              "every local-moving launch of one R-MAT 20 call, scaled by the algorithmic bytes "
+                              "of this workload" % MOVE_TRAFFIC_RATIO)
     return r
 
 
@@ -451,6 +453,8 @@ def main():
                     help="other workloads reported under 'configs': all, none, or a comma list of %s"
                          % ",".join(EXTRA_CONFIGS))
     ap.add_argument("--config-steps", type=int, default=3)
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the untimed float64 and disconnected-count runs (for profiling)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default grid caps instead of tuning them on the workload (untimed)")
     ap.add_argument("--caps", default=None,
@@ -560,7 +564,7 @@ def main():
         learned = learned_compare(gsp, args, off, tgt, w, kw, flush, stream, total_ms / args.steps, q, st, edges,
                                   cfg["workload"])
     gsp.release_workspace()
-    main_quality = quality(gsp, off, tgt, w, gvo, kw, q, golden, cfg)
+    main_quality = None if args.no_quality else quality(gsp, off, tgt, w, gvo, kw, q, golden, cfg)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -26,6 +26,9 @@ from .oracle import (  # noqa: F401
     louvain,
     louvain_trace,
     wave_hash,
+    refine,
+    refine_uniform,
+    splitmix64,
     TRACE_FIELDS,
     LouvainOptions,
 )

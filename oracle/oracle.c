@@ -48,6 +48,9 @@ typedef struct {
     int no_return_from;         /* frozen-state: from this iteration on no move back to the community left
                                    in the previous iteration (0: never) */
     int singleton_rule;         /* frozen-state sweeps only: singleton -> singleton moves go to lower ids */
+    int refine;                 /* 1: Leiden refinement (Section 3.5) before each aggregation (GSP-Leiden) */
+    double refine_theta;        /* randomness theta of the refinement choice (0: greedy) */
+    uint64_t seed;              /* seed of the refinement draws */
 } og_opts;
 
 typedef struct {
@@ -568,6 +571,179 @@ uint32_t og_disconnected(const og_graph *g, const uint32_t *C, uint8_t *D)
     return count;
 }
 
+/* ------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the output of the   */
+/* generator whose state has reached x, i.e. x advanced by the golden  */
+/* gamma and passed through the variant-13 mixer.                      */
+/* ------------------------------------------------------------------ */
+uint64_t og_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* Uniform draw in (0,1) for the refinement choice of vertex v among    */
+/* candidate c in a pass: SplitMix64 as a counter-based generator, the  */
+/* key (v, c) mixed into a per-pass stream of the seed.  52 random bits */
+/* plus one half, so the value is exact and never 0 or 1.               */
+double og_refine_uniform(uint64_t seed, uint32_t pass, uint32_t v, uint32_t c)
+{
+    uint64_t s = og_splitmix64(seed + 0x9e3779b97f4a7c15ull * ((uint64_t)pass + 1));
+    uint64_t r = og_splitmix64(s ^ (((uint64_t)v << 32) | c));
+    return ((double)(r >> 12) + 0.5) * 0x1.0p-52;
+}
+
+/* ------------------------------------------------------------------ */
+/* Refinement phase of the Leiden algorithm (Section 3.5), for the      */
+/* GSP-Leiden variant the conclusion mentions.  B is the bound          */
+/* membership left by local moving (ids < n); R receives the refined    */
+/* membership, each refined community named by one of its vertices.     */
+/*                                                                      */
+/* R starts from singletons.  A vertex v that is still alone in R may   */
+/* join the refined community c of a neighbour inside its own bound     */
+/* community b when                                                     */
+/*   - v is well connected to b:  E(v, b-v) >= K_v (S_b - K_v) / 2m,    */
+/*   - c is well connected to b:  E(c, b-c) >= S_c (S_b - S_c) / 2m,    */
+/*   - the gain is not negative:  g_c = E(v, c) - K_v S_c / 2m >= 0     */
+/* (g_c is m times Equation 2 for v leaving its singleton; S_b, S_c sum */
+/* K over b and c; E(x, y) is the weight between vertex sets x and y).  */
+/* With theta > 0 the choice among the eligible c and staying (gain 0)  */
+/* is random with weight exp(g / theta), drawn as the largest           */
+/* g / theta + Gumbel noise, the noise -ln(-ln u) of an independent     */
+/* uniform u per (v, candidate); theta = 0 is the greedy limit: the     */
+/* largest strictly positive gain, ties to the lowest id.               */
+/*                                                                      */
+/* Parallel form: the vertices are visited once, in the frozen-state    */
+/* waves of local moving (vertex i in wave hash(i) mod W, or i mod W);  */
+/* all decisions of a wave read the wave's start state, and a mover     */
+/* whose own singleton is another mover's target in the same wave       */
+/* stays, so that every target keeps its members.  E(c, b-c) is kept   */
+/* per refined community and updated as vertices join.  Returns the     */
+/* number of vertices that joined another refined community.            */
+/* ------------------------------------------------------------------ */
+uint32_t og_refine(const og_graph *g, const uint32_t *B, uint32_t *R, double theta, uint64_t seed, uint32_t pass,
+                   int waves, int wave_hash)
+{
+    uint32_t n = g->n;
+    size_t nn = n ? n : 1;
+    double *K = malloc(sizeof(double) * nn);
+    double *SB = calloc(nn, sizeof(double));      /* S_b per bound community */
+    double *SR = malloc(sizeof(double) * nn);     /* S_c per refined community */
+    double *ext = calloc(nn, sizeof(double));     /* E(c, b - c) per refined community */
+    double *H = calloc(nn, sizeof(double));       /* E(v, c) of the vertex being decided */
+    double *wvt = malloc(sizeof(double) * nn);    /* E(v, target) at the decision */
+    uint32_t *size = malloc(sizeof(uint32_t) * nn);
+    uint32_t *T = malloc(sizeof(uint32_t) * nn);
+    uint32_t *list = malloc(sizeof(uint32_t) * nn);
+    uint8_t *seen = calloc(nn, 1);
+    uint8_t *targeted = calloc(nn, 1);
+    uint8_t *joined = calloc(nn, 1);
+    double m = og_vertex_weights(g, K);
+    for (uint32_t v = 0; v < n; v++) {
+        SB[B[v]] += K[v];
+        R[v] = v; SR[v] = K[v]; size[v] = 1;
+    }
+    for (uint32_t v = 0; v < n; v++)
+        for (uint64_t e = g->off[v]; e < g->off[v + 1]; e++) {
+            uint32_t u = g->tgt[e];
+            if (u != v && B[u] == B[v]) ext[v] += g->w[e];
+        }
+    uint32_t moves = 0;
+    uint32_t W = waves < 1 ? 1u : (uint32_t)waves;
+    uint32_t *wstart = calloc((size_t)W + 1, sizeof(uint32_t));
+    uint32_t *wlist = malloc(sizeof(uint32_t) * nn);
+    for (uint32_t i = 0; i < n; i++) wstart[(wave_hash ? og_wave_hash(i) : i) % W + 1]++;
+    for (uint32_t k = 0; k < W; k++) wstart[k + 1] += wstart[k];
+    {
+        uint32_t *fill = malloc(sizeof(uint32_t) * ((size_t)W + 1));
+        memcpy(fill, wstart, sizeof(uint32_t) * ((size_t)W + 1));
+        for (uint32_t i = 0; i < n; i++) wlist[fill[(wave_hash ? og_wave_hash(i) : i) % W]++] = i;
+        free(fill);
+    }
+    double two_m = 2.0 * m;
+    for (uint32_t wv = 0; m > 0.0 && wv < W; wv++) {
+        /* decide, every vertex of the wave from the wave's start state */
+        for (uint32_t t = wstart[wv]; t < wstart[wv + 1]; t++) {
+            uint32_t v = wlist[t];
+            T[v] = v;
+            wvt[v] = 0.0;
+            if (size[v] != 1 || R[v] != v) continue;             /* only singletons move */
+            uint32_t b = B[v];
+            if (!(ext[v] >= K[v] * (SB[b] - K[v]) / two_m)) continue;
+            uint32_t len = 0;
+            for (uint64_t e = g->off[v]; e < g->off[v + 1]; e++) {
+                uint32_t u = g->tgt[e];
+                if (u == v || B[u] != b) continue;
+                uint32_t c = R[u];
+                if (!seen[c]) { seen[c] = 1; list[len++] = c; }
+                H[c] += g->w[e];
+            }
+            int have = 0;
+            double best = 0.0;
+            uint32_t bc = v;
+            if (theta > 0.0) { have = 1; best = -log(-log(og_refine_uniform(seed, pass, v, v))); }
+            for (uint32_t k = 0; k < len; k++) {
+                uint32_t c = list[k];
+                if (!(ext[c] >= SR[c] * (SB[b] - SR[c]) / two_m)) continue;
+                double gain = H[c] - K[v] * SR[c] / two_m;
+                double s;
+                if (theta > 0.0) {
+                    if (gain < 0.0) continue;
+                    s = gain / theta + -log(-log(og_refine_uniform(seed, pass, v, c)));
+                } else {
+                    if (!(gain > 0.0)) continue;
+                    s = gain;
+                }
+                if (!have || s > best || (s == best && c < bc)) { have = 1; best = s; bc = c; }
+            }
+            T[v] = bc;
+            if (bc != v) wvt[v] = H[bc];
+            for (uint32_t k = 0; k < len; k++) { H[list[k]] = 0.0; seen[list[k]] = 0; }
+        }
+        /* a mover whose singleton is targeted by another mover stays */
+        for (uint32_t t = wstart[wv]; t < wstart[wv + 1]; t++) {
+            uint32_t v = wlist[t];
+            if (T[v] != v) targeted[T[v]] = 1;
+        }
+        for (uint32_t t = wstart[wv]; t < wstart[wv + 1]; t++) {
+            uint32_t v = wlist[t];
+            joined[v] = (T[v] != v && !targeted[v]);
+        }
+        for (uint32_t t = wstart[wv]; t < wstart[wv + 1]; t++) {
+            uint32_t v = wlist[t];
+            if (!joined[v]) continue;
+            uint32_t c = T[v];
+            R[v] = c;
+            size[c]++; size[v] = 0;
+            SR[c] += K[v];
+            moves++;
+        }
+        /* E(c, b - c) of each target: plus the joiner's edges to the rest  */
+        /* of b, less its edges to the target's earlier members (counted   */
+        /* from both sides) and to the wave's other joiners of that target */
+        for (uint32_t t = wstart[wv]; t < wstart[wv + 1]; t++) {
+            uint32_t v = wlist[t];
+            if (!joined[v]) continue;
+            double co = 0.0;
+            for (uint64_t e = g->off[v]; e < g->off[v + 1]; e++) {
+                uint32_t u = g->tgt[e];
+                if (u != v && joined[u] && T[u] == T[v]) co += g->w[e];
+            }
+            ext[T[v]] += ext[v] - 2.0 * wvt[v] - co;
+        }
+        for (uint32_t t = wstart[wv]; t < wstart[wv + 1]; t++) {
+            uint32_t v = wlist[t];
+            targeted[T[v]] = 0;
+            joined[v] = 0;
+        }
+    }
+    free(K); free(SB); free(SR); free(ext); free(H); free(wvt); free(size); free(T); free(list);
+    free(seen); free(targeted); free(joined); free(wstart); free(wlist);
+    return moves;
+}
+
 static void run_split(const og_graph *g, const uint32_t *C, uint32_t *Cp, int mode)
 {
     if (mode == 1) og_split_lp(g, C, Cp, 0);
@@ -593,12 +769,16 @@ static uint32_t canonical_numbering(uint32_t n, uint32_t *C)
 /* ------------------------------------------------------------------ */
 /* louvain (Algorithm 1), GSP-Louvain driver.  G is the input graph;   */
 /* C receives the final membership numbered 0..k-1 by smallest vertex   */
-/* id.  Each pass: K' = Sigma' = vertexWeights(G'), C' = identity,      */
+/* id.  Each pass: K' = vertexWeights(G'), Sigma' from C' (identity),  */
 /* louvainMove, split (Split Pass), global convergence when l_i <= 1,   */
 /* low-shrink stop when |Gamma|/|V'| > tau_agg, renumber, dendrogram    */
 /* lookup, louvainAggregate, tau /= TOLERANCE_DROP.  A final lookup     */
 /* follows the loop.  With split_last the split runs once, on G and the */
-/* final membership.  Returns the number of passes.                     */
+/* final membership.  With refine (GSP-Leiden) the refined partition  */
+/* of C' (og_refine) is what the low-shrink test counts, the lookup     */
+/* follows and the aggregation merges, and each super-vertex starts   */
+/* the next pass in the bound community of its members (Section 3.5). */
+/* Returns the number of passes.                                        */
 /* ------------------------------------------------------------------ */
 static int louvain_impl(const og_graph *g, const og_opts *o, uint32_t *C, og_stats *st, og_trace *tr)
 {
@@ -612,14 +792,19 @@ static int louvain_impl(const og_graph *g, const og_opts *o, uint32_t *C, og_sta
     double *Sigma = malloc(sizeof(double) * (n ? n : 1));
     uint32_t *Cp = malloc(sizeof(uint32_t) * (n ? n : 1));
     uint32_t *Cs = malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *Rf = malloc(sizeof(uint32_t) * (n ? n : 1));
     double tau = o->tolerance;
     int passes = 0;
     int split_each_pass = (o->split != 0 && !o->split_last);
+    /* C' of the first pass is the identity; after an aggregation it is the */
+    /* identity too, or with refinement the bound community of each super- */
+    /* vertex; Sigma' sums K' over the communities of C'                    */
+    for (uint32_t i = 0; i < n; i++) Cp[i] = i;
     for (int lp = 0; lp < o->max_passes; lp++) {
         uint32_t nv = cur.n;
         double m = og_vertex_weights(&cur, K);
-        memcpy(Sigma, K, sizeof(double) * nv);
-        for (uint32_t i = 0; i < nv; i++) Cp[i] = i;
+        memset(Sigma, 0, sizeof(double) * nv);
+        for (uint32_t i = 0; i < nv; i++) Sigma[Cp[i]] += K[i];
         if (tr) {
             tr->pass = lp;
             tr->max_K = 0.0;
@@ -644,19 +829,35 @@ static int louvain_impl(const og_graph *g, const og_opts *o, uint32_t *C, og_sta
         free(tmp);
         if (st && lp < 64) { st->iterations[lp] = li; st->vertices[lp] = nv; st->communities[lp] = k; }
         if (li <= 1) break;
+        /* the partition aggregated: C' itself, or with refinement the     */
+        /* refined partition of C' (its super-vertices start the next pass */
+        /* in their bound communities)                                     */
+        uint32_t *A = Cp;
+        if (o->refine) {
+            og_refine(&cur, Cp, Rf, o->refine_theta, o->seed, (uint32_t)lp, o->waves, o->wave_hash);
+            k = og_renumber(nv, Rf);
+            A = Rf;
+        }
         if ((double)k / (double)nv > o->aggregation_tolerance) break;
-        k = og_renumber(nv, Cp);
-        og_lookup(n, C, Cp);
+        k = og_renumber(nv, A);
+        if (o->refine) og_renumber(nv, Cp);
+        og_lookup(n, C, A);
         uint64_t *noff = malloc(sizeof(uint64_t) * ((size_t)k + 1));
         uint32_t *ntgt = malloc(sizeof(uint32_t) * (cur.nnz ? cur.nnz : 1));
         double *nw = malloc(sizeof(double) * (cur.nnz ? cur.nnz : 1));
-        uint64_t nnz2 = og_aggregate(&cur, Cp, k, noff, ntgt, nw);
+        uint64_t nnz2 = og_aggregate(&cur, A, k, noff, ntgt, nw);
         free(own_off); free(own_tgt); free(own_w);
         own_off = noff; own_tgt = ntgt; own_w = nw;
         cur.n = k; cur.nnz = nnz2; cur.off = noff; cur.tgt = ntgt; cur.w = nw;
         tau = tau / o->tolerance_drop;
-        /* the pass that aggregated leaves C' as identity on the new graph */
-        for (uint32_t i = 0; i < k; i++) Cp[i] = i;
+        if (o->refine) {
+            /* super-vertex r starts in the bound community of its members */
+            for (uint32_t i = 0; i < nv; i++) Cs[Rf[i]] = Cp[i];
+            memcpy(Cp, Cs, sizeof(uint32_t) * k);
+        } else {
+            /* the pass that aggregated leaves C' as identity on the new graph */
+            for (uint32_t i = 0; i < k; i++) Cp[i] = i;
+        }
     }
     og_lookup(n, C, Cp);
     if (o->split != 0 && o->split_last) {
@@ -669,7 +870,7 @@ static int louvain_impl(const og_graph *g, const og_opts *o, uint32_t *C, og_sta
         st->final_communities = k;
         st->modularity = og_modularity(g, C);
     }
-    free(own_off); free(own_tgt); free(own_w); free(K); free(Sigma); free(Cp); free(Cs);
+    free(own_off); free(own_tgt); free(own_w); free(K); free(Sigma); free(Cp); free(Cs); free(Rf);
     return passes;
 }
 

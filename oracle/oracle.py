@@ -40,7 +40,8 @@ class _OgOpts(ctypes.Structure):
                 ("aggregation_tolerance", ctypes.c_double), ("split", ctypes.c_int),
                 ("split_last", ctypes.c_int), ("sync", ctypes.c_int), ("waves", ctypes.c_int),
                 ("wave_hash", ctypes.c_int), ("wave_repeats", ctypes.c_int), ("no_return_from", ctypes.c_int),
-                ("singleton_rule", ctypes.c_int)]
+                ("singleton_rule", ctypes.c_int), ("refine", ctypes.c_int), ("refine_theta", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
 
 
 class _OgStats(ctypes.Structure):
@@ -80,6 +81,13 @@ def _load():
         lib.og_lookup.restype = None
         lib.og_aggregate.argtypes = [G, P, ctypes.c_uint32, P, P, P]
         lib.og_aggregate.restype = ctypes.c_uint64
+        lib.og_splitmix64.argtypes = [ctypes.c_uint64]
+        lib.og_splitmix64.restype = ctypes.c_uint64
+        lib.og_refine_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+        lib.og_refine_uniform.restype = ctypes.c_double
+        lib.og_refine.argtypes = [G, P, P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                  ctypes.c_int]
+        lib.og_refine.restype = ctypes.c_uint32
         lib.og_disconnected.argtypes = [G, P, P]
         lib.og_disconnected.restype = ctypes.c_uint32
         lib.og_louvain.argtypes = [G, ctypes.POINTER(_OgOpts), P, ctypes.POINTER(_OgStats)]
@@ -216,6 +224,26 @@ def disconnected(g, C):
     return cnt, D[:g.n]
 
 
+def splitmix64(x):
+    """SplitMix64's output for generator state x (og_splitmix64)."""
+    return int(_load().og_splitmix64(int(x) & 0xFFFFFFFFFFFFFFFF))
+
+
+def refine_uniform(seed, pass_index, v, c):
+    """The uniform draw in (0,1) of the refinement choice (og_refine_uniform)."""
+    return _load().og_refine_uniform(int(seed), int(pass_index), int(v), int(c))
+
+
+def refine(g, B, theta=0.01, seed=0, pass_index=0, waves=17, wave_hash=True):
+    """Leiden refinement (Section 3.5) of the bound membership B: (refined
+    membership named by member vertex ids, number of vertices that joined)."""
+    B = _u32(B)
+    R = np.zeros(g.n, dtype=np.uint32)
+    moves = _load().og_refine(g.ref, _p(B), _p(R), float(theta), int(seed), int(pass_index), int(waves),
+                              int(bool(wave_hash)))
+    return R, int(moves)
+
+
 SPLIT_MODES = {"none": 0, "lp": 1, "lpp": 2, "bfs": 3}
 
 
@@ -234,6 +262,9 @@ class LouvainOptions:
     wave_repeats: int = 3
     no_return_from: int = 3
     singleton_rule: bool = True
+    refine: bool = False
+    refine_theta: float = 0.01
+    seed: int = 0
 
 
 def louvain(g, opts=None):
@@ -242,7 +273,7 @@ def louvain(g, opts=None):
     co = _OgOpts(o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
                  o.aggregation_tolerance, SPLIT_MODES[o.split], int(o.split_last), int(o.sync),
                  int(o.waves), int(bool(o.wave_hash)), int(o.wave_repeats), int(o.no_return_from),
-                 int(o.singleton_rule))
+                 int(o.singleton_rule), int(bool(o.refine)), float(o.refine_theta), int(o.seed))
     C = np.zeros(g.n, dtype=np.uint32)
     st = _OgStats()
     _load().og_louvain(g.ref, ctypes.byref(co), _p(C), ctypes.byref(st))
@@ -266,7 +297,7 @@ def louvain_trace(g, opts=None, capacity=1 << 20):
     co = _OgOpts(o.max_passes, o.max_iterations, o.tolerance, o.tolerance_drop,
                  o.aggregation_tolerance, SPLIT_MODES[o.split], int(o.split_last), int(o.sync),
                  int(o.waves), int(bool(o.wave_hash)), int(o.wave_repeats), int(o.no_return_from),
-                 int(o.singleton_rule))
+                 int(o.singleton_rule), int(bool(o.refine)), float(o.refine_theta), int(o.seed))
     C = np.zeros(g.n, dtype=np.uint32)
     st = _OgStats()
     rec = np.zeros((capacity, len(TRACE_FIELDS)), dtype=np.float64)

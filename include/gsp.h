@@ -123,6 +123,14 @@ typedef struct {
     float prune_threshold;          /* learned pruning: skip a vertex when P(move) < this; default 0.5 */
     int count_disconnected;         /* 1: count internally-disconnected communities of the result
                                        (Algorithm 6) into gsp_stats.disconnected; default 0 */
+    int refine;                     /* 1: GSP-Leiden -- the refinement phase of the Leiden algorithm
+                                       (Section 3.5, gsp_refine) runs after each pass's split, the
+                                       refined partition is aggregated, and each super-vertex starts
+                                       the next pass in its bound community; default 0 (gsp_louvain
+                                       only) */
+    double refine_theta;            /* randomness of the refinement's choice, >= 0 (0: greedy); default
+                                       0.01 */
+    uint64_t seed;                  /* seed of the refinement's draws; default 0 */
     void *workspace;                /* optional device scratch owned by the caller (256-byte aligned); NULL:
                                        the library's internal workspace.  With a workspace the call
                                        allocates no device memory and fails with GSP_ERR_CAPACITY when
@@ -154,6 +162,8 @@ typedef struct {
     uint32_t disconnected;          /* internally-disconnected communities of the result (Algorithm 6),
                                        GSP_NOT_COUNTED unless gsp_opts.count_disconnected is set */
     uint64_t workspace_bytes;       /* most device scratch bytes the call held at once */
+    uint32_t refined[GSP_MAX_PASS_STATS];        /* refined communities of each pass (gsp_opts.refine) */
+    float ms_refine[GSP_MAX_PASS_STATS];
 } gsp_stats;
 #define GSP_NOT_COUNTED 0xFFFFFFFFu
 
@@ -254,6 +264,29 @@ gsp_status gsp_local_move(const uint64_t *offsets, const uint32_t *targets, cons
  */
 gsp_status gsp_split(const uint64_t *offsets, const uint32_t *targets, uint32_t n, uint64_t nnz,
                      const uint32_t *C, int mode, uint32_t *labels, uint32_t *k_host, void *stream);
+
+/*
+ * Refinement phase of the Leiden algorithm (Section 3.5), the step of the
+ * GSP-Leiden variant.  B: bound membership (ids < n), e.g. local moving's
+ * result after the split.  R (output, n entries) receives the refined
+ * partition, each refined community named by one of its vertices; every
+ * refined community lies inside one bound community and is connected.
+ * Within each bound community b, R starts from singletons and every vertex
+ * is visited once, in `waves` frozen-state waves (vertex i in wave h(i) mod
+ * waves as in local moving; 0 = 17); a vertex still alone in R may join the
+ * refined community c of a neighbour in b when E(v, b-v) >= K_v (S_b - K_v)
+ * / 2m, E(c, b-c) >= S_c (S_b - S_c) / 2m and the gain g = E(v, c) - K_v S_c
+ * / 2m is >= 0 (E the weight between vertex sets, S the sum of K).  It picks
+ * among those c and staying (g = 0) with probability proportional to exp(g /
+ * theta), drawn as the largest g / theta - ln(-ln u), u a SplitMix64 draw
+ * keyed by (seed, pass, vertex, candidate); theta = 0 takes the largest g > 0
+ * (ties to the lowest id).  A mover whose own singleton is another mover's
+ * target in the same wave stays.  Scores are float64.  *moves_host (may be
+ * NULL) receives the number of vertices that joined another community.
+ */
+gsp_status gsp_refine(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
+                      uint64_t nnz, const uint32_t *B, uint32_t *R, double theta, uint64_t seed, uint32_t pass,
+                      int waves, uint32_t *moves_host, void *stream);
 
 /* Renumber communities (Algorithm 1): distinct ids of C (all < n) ranked by
  * increasing value become 0..k-1, written to C_dense; *k_host = k. */

@@ -26,6 +26,7 @@ class GspOpts(ctypes.Structure):
                 ("no_return_from", c_int), ("precision", c_int),
                 ("singleton_rule", c_int), ("prune", c_int), ("mlp_params", P),
                 ("full_sweep_every", c_int), ("prune_threshold", c_flt), ("count_disconnected", c_int),
+                ("refine", c_int), ("refine_theta", c_dbl), ("seed", c_u64),
                 ("workspace", P), ("workspace_bytes", ctypes.c_size_t), ("stream", P)]
 
 
@@ -40,7 +41,7 @@ class GspStats(ctypes.Structure):
                 ("vertices_skipped", c_u64 * _N), ("move_bytes", c_dbl * _N),
                 ("ms_move_kernels", c_flt * _N), ("final_communities", c_u32),
                 ("modularity", c_dbl), ("ms_total", c_flt), ("disconnected", c_u32),
-                ("workspace_bytes", c_u64)]
+                ("workspace_bytes", c_u64), ("refined", c_u32 * _N), ("ms_refine", c_flt * _N)]
 
 
 class GspDeviceGraph(ctypes.Structure):
@@ -68,6 +69,7 @@ _SIGS = {
                                c_int, c_int, c_int, c_int, c_int, P, P]),
     "gsp_louvain_trace": (c_int, [P, P, P, c_u32, c_u64, P, P, P, P, c_u32, c_u32, P]),
     "gsp_split": (c_int, [P, P, c_u32, c_u64, P, c_int, P, P, P]),
+    "gsp_refine": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, c_dbl, c_u64, c_u32, c_int, P, P]),
     "gsp_renumber": (c_int, [c_u32, P, P, P, P]),
     "gsp_lookup": (c_int, [c_u32, P, P, P]),
     "gsp_aggregate": (c_int, [P, P, P, c_int, c_u32, c_u64, P, c_u32, P, P, P, P, P]),

@@ -578,6 +578,7 @@ extern "C" gsp_status gsp_louvain_batched(uint32_t num_graphs, const uint64_t *g
         else gsp_default_opts(&o);
         check_opts(o);
         GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS, "batched runs support flag pruning only");
+        GSP_REQUIRE(o.refine == 0, "batched runs do not support refinement (GSP-Leiden)");
         GSP_REQUIRE(num_graphs >= 1 && graph_vertex_offsets, "need at least one graph and its vertex offsets");
         GSP_REQUIRE(graph_vertex_offsets[0] == 0 && graph_vertex_offsets[num_graphs] == n,
                     "graph_vertex_offsets must run from 0 to n");

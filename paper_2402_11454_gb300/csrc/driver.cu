@@ -684,6 +684,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
     DevGraph cur = g0;
     double tau = o.tolerance;
     const bool split_pass = o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_PASS;
+    const bool refine = o.refine != 0;
     int passes = 0;
     uint32_t *Cp = mb.C;  // membership of the current graph's vertices
     int pb = 0;
@@ -695,12 +696,18 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         const uint32_t nv = cur.n;
         size_t pass_mark = arena().mark();
         t.lap();
-        // K' = Sigma' = vertexWeights(G'), C' = [0..|V'|), all unprocessed
+        // K' = Sigma' = vertexWeights(G'), C' = [0..|V'|), all unprocessed;
+        // with refinement, after an aggregation, C' holds each super-vertex's
+        // bound community and Sigma' sums K' over it
         double m = vertex_weights(cur, K, mb.m_dev, s, lsb_cache);
-        GSP_CUDA(cudaMemcpyAsync(mb.Sigma, K, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
-        iota_u32(mb.C, nv, s);
-        k_fill_u32_<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
-        GSP_CHECK_LAUNCH();
+        if (refine && lp > 0) {
+            sigma_from_membership(mb.C, K, mb.Sigma, mb.size, nv, s);
+        } else {
+            GSP_CUDA(cudaMemcpyAsync(mb.Sigma, K, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+            iota_u32(mb.C, nv, s);
+            k_fill_u32_<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv, 1u);
+            GSP_CHECK_LAUNCH();
+        }
         reset_left(mb, nv, s);
         GSP_CUDA(cudaMemsetAsync(mb.act, 1, nv, s));
         GSP_CUDA(cudaMemsetAsync(mb.mark, 0, nv, s));
@@ -745,24 +752,40 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
             local.move_bytes[lp] = mr.bytes;
             local.ms_move_kernels[lp] = mr.ms_kernels;
         }
-        if (li <= 1) break;                                          // globally converged
+        if (li <= 1) break;  // globally converged
+        // the partition to aggregate: C' itself, or its refinement (GSP-Leiden)
+        const uint32_t *A = Cd;
+        if (refine) {
+            uint32_t *Rf = arena().get<uint32_t>(nv);
+            uint32_t *Rd = arena().get<uint32_t>(nv);
+            refine_partition(cur, cl, Cp, Rf, K, m, o.refine_theta, o.seed, (uint32_t)lp, s);
+            k = renumber(nv, Rf, Rd, s);
+            A = Rd;
+            float ms_ref = t.lap();
+            if (lp < GSP_MAX_PASS_STATS) {
+                local.refined[lp] = k;
+                local.ms_refine[lp] = ms_ref;
+            }
+        }
         if ((double)k / (double)nv > o.aggregation_tolerance) break;  // low shrink
         // renumber, dendrogram lookup, aggregate, threshold scaling
-        lookup(n0, membership, Cd, s);
+        lookup(n0, membership, A, s);
         DevGraph nxt;
         nxt.n = k;
         nxt.off = goff[pb];
         nxt.tgt = gtgt[pb];
         nxt.w = gw[pb];
         nxt.wt = GSP_W_F64;
-        nxt.nnz = aggregate(cur, Cd, k, goff[pb], gtgt[pb], gw[pb], s, /*sorted=*/false, &lsb_cache);
+        nxt.nnz = aggregate(cur, A, k, goff[pb], gtgt[pb], gw[pb], s, /*sorted=*/false, &lsb_cache);
         pb ^= 1;
         cur = nxt;
         tau = tau / o.tolerance_drop;
+        // C' on the new graph: the identity, or each super-vertex's bound community
+        if (refine) scatter_bound(A, Cd, mb.C, nv, s);
         float ms_agg = t.lap();
         if (lp < GSP_MAX_PASS_STATS) local.ms_aggregate[lp] = ms_agg;
         arena().release(pass_mark);
-        iota_u32(mb.C, cur.n, s);  // C' = identity on the new graph
+        if (!refine) iota_u32(mb.C, cur.n, s);
         Cp = mb.C;
     }
     lookup(n0, membership, Cp, s);
@@ -837,6 +860,8 @@ void check_opts(const gsp_opts &o) {
     GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS || o.prune == GSP_PRUNE_LEARNED, "unknown prune mode");
     GSP_REQUIRE(o.prune != GSP_PRUNE_LEARNED || o.mlp_params != nullptr, "learned pruning needs mlp_params");
     GSP_REQUIRE(o.workspace == nullptr || o.workspace_bytes >= 256, "workspace_bytes too small");
+    GSP_REQUIRE(o.refine == 0 || o.refine == 1, "refine must be 0 or 1");
+    GSP_REQUIRE(o.refine_theta >= 0.0, "refine_theta must be >= 0");
 }
 }  // namespace gsp
 
@@ -863,6 +888,9 @@ void gsp_default_opts(gsp_opts *o) {
     o->full_sweep_every = 4;
     o->prune_threshold = 0.5f;
     o->count_disconnected = 0;
+    o->refine = 0;
+    o->refine_theta = 0.01;
+    o->seed = 0;
     o->workspace = nullptr;
     o->workspace_bytes = 0;
     o->stream = nullptr;
@@ -1091,6 +1119,28 @@ gsp_status gsp_louvain_trace(const uint64_t *offsets, const uint32_t *targets, c
     GSP_CUDA(cudaMemcpyAsync(&rows, tr.cnt, sizeof(rows), cudaMemcpyDeviceToHost, s));
     GSP_CUDA(cudaStreamSynchronize(s));
     if (rows_host) *rows_host = std::min(rows, capacity);
+    GSP_API_END
+}
+
+gsp_status gsp_refine(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
+                      uint64_t nnz, const uint32_t *B, uint32_t *R, double theta, uint64_t seed, uint32_t pass,
+                      int waves, uint32_t *moves_host, void *stream) {
+    GSP_API_BEGIN
+    DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
+    GSP_REQUIRE(B && R, "B and R must not be NULL");
+    GSP_REQUIRE(theta >= 0.0, "theta must be >= 0");
+    GSP_REQUIRE(waves >= 0 && waves <= MAX_WAVES, "waves must be in [0, %d]", MAX_WAVES);
+    cudaStream_t s = S(stream);
+    arena().reset();
+    check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), s);
+    check_ids(B, n, n, "bound membership", s);
+    double *K = arena().get<double>(n);
+    double *m_dev = arena().get<double>(1);
+    double m = vertex_weights(g, K, m_dev, s, exact_lsb(g, s));
+    Classes cl;
+    classify_vertices(g, cl, effective_waves(waves, true), s);
+    uint32_t moves = refine_partition(g, cl, B, R, K, m, theta, seed, pass, s);
+    if (moves_host) *moves_host = moves;
     GSP_API_END
 }
 

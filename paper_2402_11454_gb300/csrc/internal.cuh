@@ -197,6 +197,20 @@ DevGraph make_graph(const uint64_t *off, const uint32_t *tgt, const void *w, int
 
 struct LouvainTimers;
 
+// Leiden refinement (Section 3.5) of the bound membership B (ids < n) into R
+// (each refined community named by one of its vertices), in the waves of
+// `cl` (built for g); returns the number of vertices that joined another
+// refined community.
+uint32_t refine_partition(const DevGraph &g, const Classes &cl, const uint32_t *B, uint32_t *R, const double *K,
+                          double m, double theta, uint64_t seed, uint32_t pass, cudaStream_t s);
+// Sigma[c] = sum of K over the vertices of community c, size[c] = their
+// count (C ids < n).
+void sigma_from_membership(const uint32_t *C, const double *K, double *Sigma, uint32_t *size, uint32_t n,
+                           cudaStream_t s);
+// C_next[R[i]] = B[i]: each super-vertex of the refined partition R (dense)
+// starts the next pass in the bound community B (dense) of its members.
+void scatter_bound(const uint32_t *R, const uint32_t *B, uint32_t *C_next, uint32_t n, cudaStream_t s);
+
 // Split (Algorithms 2, 3): labels = smallest vertex of the component.
 void split_labels(const DevGraph &g, const Classes &cl, const uint32_t *C, int mode, uint32_t *labels,
                   cudaStream_t s);

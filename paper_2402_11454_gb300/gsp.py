@@ -61,7 +61,8 @@ def _graph(off, tgt, w=None):
 def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=10.0,
               aggregation_tolerance=0.8, split="lpp", split_when="pass", move="sync", waves=0,
               wave_repeats=3, no_return_from=3, precision="mixed", singleton_rule=True, prune="flags", mlp_params=None,
-              full_sweep_every=4, prune_threshold=0.5, count_disconnected=False, workspace=None, stream=None):
+              full_sweep_every=4, prune_threshold=0.5, count_disconnected=False, refine=False, refine_theta=0.01,
+              seed=0, workspace=None, stream=None):
     o = GspOpts()
     _lib.load().gsp_default_opts(ctypes.byref(o))
     o.max_passes = max_passes
@@ -82,6 +83,9 @@ def make_opts(max_passes=10, max_iterations=20, tolerance=1e-2, tolerance_drop=1
     o.full_sweep_every = full_sweep_every
     o.prune_threshold = prune_threshold
     o.count_disconnected = int(bool(count_disconnected))
+    o.refine = int(bool(refine))
+    o.refine_theta = refine_theta
+    o.seed = seed
     if workspace is not None:
         _cuda(workspace, torch.uint8, "workspace")
         o.workspace = workspace.data_ptr()
@@ -103,7 +107,8 @@ def stats_dict(st):
                 final_communities=st.final_communities, modularity=st.modularity,
                 ms_total=st.ms_total,
                 disconnected=None if st.disconnected == _lib.GSP_NOT_COUNTED else st.disconnected,
-                workspace_bytes=st.workspace_bytes)
+                workspace_bytes=st.workspace_bytes, refined=list(st.refined[:p]),
+                ms_refine=list(st.ms_refine[:p]))
 
 
 def louvain(offsets, targets, weights, membership=None, **kw):
@@ -237,6 +242,19 @@ def split(offsets, targets, C, mode="bfs", stream=None):
     check(_lib.load().gsp_split(_p(offsets), _p(targets), n, nnz, _p(C), SPLIT[mode], _p(labels),
                                 ctypes.byref(k), _stream(stream)))
     return labels, k.value
+
+
+def refine(offsets, targets, weights, B, theta=0.01, seed=0, pass_index=0, waves=0, stream=None):
+    """Leiden refinement (Section 3.5) of the bound membership B: (refined
+    membership named by member vertex ids, number of vertices that joined)."""
+    n, nnz = _graph(offsets, targets, weights)
+    _cuda(B, torch.int32, "bound membership")
+    R = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    moves = ctypes.c_uint32()
+    check(_lib.load().gsp_refine(_p(offsets), _p(targets), _p(weights), _wt(weights), n, nnz, _p(B), _p(R),
+                                 float(theta), int(seed), int(pass_index), int(waves), ctypes.byref(moves),
+                                 _stream(stream)))
+    return R, moves.value
 
 
 def renumber(C, stream=None):

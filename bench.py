@@ -16,7 +16,10 @@ Beside the timed line the same JSON carries:
   configs  the other workloads (planted 10 K, R-MAT 22, grid 4096^2, batch
            of 4096 planted graphs), fewer steps each: edges/s, modularity,
            its error against the float64 run, against the sequential oracle
-           (stored values) and the local-moving roofline fraction.
+           (stored values) and the local-moving roofline fraction;
+  gsp_leiden  the GSP-Leiden variant (Leiden refinement after each pass's
+           split) on R-MAT 22: the same figures, and its modularity and time
+           against the GSP-Louvain run of that graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload rmat26|rmat22|planted|grid|batch|rmatNN]
@@ -235,9 +238,18 @@ def phase_rooflines(st, peak_gbs, input_wbytes=4):
             continue
         wb = input_wbytes if p == 0 else 8
         agg_b += (8.0 + wb) * E[p] + 28.0 * V[p] + 12.0 * E[p + 1] + 8.0 * V[p + 1]
+    # refinement (GSP-Leiden): per edge target 4 + weight (4 or 8) + B_u 4 +
+    # R_u 4, per vertex B, R, T 4 each, K, S_R, E(c, b-c), E(v, T) 8 each,
+    # size 4 (the passes that refined)
+    ref_b = 0.0
+    for p in range(P):
+        if st.get("ms_refine") and st["ms_refine"][p] > 0:
+            wb = input_wbytes if p == 0 else 8
+            ref_b += (12.0 + wb) * E[p] + 48.0 * V[p]
     out = {}
     for name, b, ms in (("split", split_b, sum(st["ms_split"])), ("aggregate", agg_b, sum(st["ms_aggregate"])),
-                        ("move", sum(st["move_bytes"]), sum(st["ms_move_kernels"]))):
+                        ("move", sum(st["move_bytes"]), sum(st["ms_move_kernels"])),
+                        ("refine", ref_b, sum(st.get("ms_refine") or [0.0]))):
         if ms > 0 and b > 0:
             gbs = b / (ms * 1e-3) / 1e9
             out[name] = {"bytes": b, "ms": round(ms, 3), "achieved_gbs": round(gbs, 1),
@@ -449,6 +461,8 @@ def main():
                     help="also time learned pruning against the plain run (auto: R-MAT workloads)")
     ap.add_argument("--learned-steps", type=int, default=None, help="timed steps of the learned form (default: --steps)")
     ap.add_argument("--recall", type=float, default=0.9)
+    ap.add_argument("--leiden", default="rmat22",
+                    help="workload of the GSP-Leiden line (rmat22, planted, grid, ...), or none")
     ap.add_argument("--configs", default="all",
                     help="other workloads reported under 'configs': all, none, or a comma list of %s"
                          % ",".join(EXTRA_CONFIGS))
@@ -602,6 +616,31 @@ def main():
             log("%s: %.2f ms/step, Q %.5f" % (name, summ["ms_per_step"], summ["modularity"]))
             torch.cuda.empty_cache()
         line["configs"] = configs
+    if args.leiden != "none" and ws == 1:
+        # the GSP-Leiden variant (refinement of Section 3.5) on one workload,
+        # beside the GSP-Louvain run of the same graph
+        gsp.release_workspace()
+        torch.cuda.empty_cache()
+        lkw = dict(kw, refine=True, refine_theta=0.01, seed=0)
+        summ, extra = run_workload(gsp, graphgen, args.leiden, lkw, args.config_steps, 2, flush, stream, peak, kind,
+                                   golden, autotune=not args.no_autotune and not args.caps)
+        st_l = extra[7]
+        summ["variant"] = "GSP-Leiden: refinement (Section 3.5, theta 0.01, seed 0) after each pass's split"
+        summ["refined_communities"] = st_l["refined"]
+        summ["ms_refine"] = round(sum(st_l["ms_refine"]), 3)
+        if "oracle_modularity" in summ:
+            summ["oracle_gsp_louvain_modularity"] = summ.pop("oracle_modularity")
+            if "dQ_vs_oracle" in summ:
+                summ["dQ_vs_oracle_gsp_louvain"] = summ.pop("dQ_vs_oracle")
+        plain = (line.get("configs") or {}).get(summ["config"]["workload"])
+        if plain is None and summ["config"]["workload"] == line["config"]["workload"]:
+            plain = {"modularity": q, "ms_per_step": line["ms_per_step"]}
+        if plain:
+            summ["gsp_louvain_modularity"] = plain["modularity"]
+            summ["dQ_vs_gsp_louvain"] = summ["modularity"] - plain["modularity"]
+            summ["time_vs_gsp_louvain"] = summ["ms_per_step"] / plain["ms_per_step"]
+        line["gsp_leiden"] = summ
+        log("gsp_leiden %s: %.2f ms/step, Q %.5f" % (args.leiden, summ["ms_per_step"], summ["modularity"]))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -281,12 +281,14 @@ gsp_status gsp_split(const uint64_t *offsets, const uint32_t *targets, uint32_t 
  * theta), drawn as the largest g / theta - ln(-ln u), u a SplitMix64 draw
  * keyed by (seed, pass, vertex, candidate); theta = 0 takes the largest g > 0
  * (ties to the lowest id).  A mover whose own singleton is another mover's
- * target in the same wave stays.  Scores are float64.  *moves_host (may be
- * NULL) receives the number of vertices that joined another community.
+ * target in the same wave stays.  precision (gsp_precision): FP64 computes
+ * sums, gains and scores in float64, as a sequential evaluation does; MIXED
+ * in float32 (the well-connectedness tests stay float64).  *moves_host (may
+ * be NULL) receives the number of vertices that joined another community.
  */
 gsp_status gsp_refine(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
                       uint64_t nnz, const uint32_t *B, uint32_t *R, double theta, uint64_t seed, uint32_t pass,
-                      int waves, uint32_t *moves_host, void *stream);
+                      int waves, int precision, uint32_t *moves_host, void *stream);
 
 /* Renumber communities (Algorithm 1): distinct ids of C (all < n) ranked by
  * increasing value become 0..k-1, written to C_dense; *k_host = k. */

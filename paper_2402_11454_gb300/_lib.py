@@ -69,7 +69,7 @@ _SIGS = {
                                c_int, c_int, c_int, c_int, c_int, P, P]),
     "gsp_louvain_trace": (c_int, [P, P, P, c_u32, c_u64, P, P, P, P, c_u32, c_u32, P]),
     "gsp_split": (c_int, [P, P, c_u32, c_u64, P, c_int, P, P, P]),
-    "gsp_refine": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, c_dbl, c_u64, c_u32, c_int, P, P]),
+    "gsp_refine": (c_int, [P, P, P, c_int, c_u32, c_u64, P, P, c_dbl, c_u64, c_u32, c_int, c_int, P, P]),
     "gsp_renumber": (c_int, [c_u32, P, P, P, P]),
     "gsp_lookup": (c_int, [c_u32, P, P, P]),
     "gsp_aggregate": (c_int, [P, P, P, c_int, c_u32, c_u64, P, c_u32, P, P, P, P, P]),

@@ -758,7 +758,7 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         if (refine) {
             uint32_t *Rf = arena().get<uint32_t>(nv);
             uint32_t *Rd = arena().get<uint32_t>(nv);
-            refine_partition(cur, cl, Cp, Rf, K, m, o.refine_theta, o.seed, (uint32_t)lp, s);
+            refine_partition(cur, cl, Cp, Rf, K, m, o.refine_theta, o.seed, (uint32_t)lp, fp64, s);
             k = renumber(nv, Rf, Rd, s);
             A = Rd;
             float ms_ref = t.lap();
@@ -1124,12 +1124,13 @@ gsp_status gsp_louvain_trace(const uint64_t *offsets, const uint32_t *targets, c
 
 gsp_status gsp_refine(const uint64_t *offsets, const uint32_t *targets, const void *weights, int wt, uint32_t n,
                       uint64_t nnz, const uint32_t *B, uint32_t *R, double theta, uint64_t seed, uint32_t pass,
-                      int waves, uint32_t *moves_host, void *stream) {
+                      int waves, int precision, uint32_t *moves_host, void *stream) {
     GSP_API_BEGIN
     DevGraph g = make_graph(offsets, targets, weights, wt, n, nnz);
     GSP_REQUIRE(B && R, "B and R must not be NULL");
     GSP_REQUIRE(theta >= 0.0, "theta must be >= 0");
     GSP_REQUIRE(waves >= 0 && waves <= MAX_WAVES, "waves must be in [0, %d]", MAX_WAVES);
+    GSP_REQUIRE(precision == GSP_PREC_MIXED || precision == GSP_PREC_FP64, "unknown precision");
     cudaStream_t s = S(stream);
     arena().reset();
     check_csr(offsets, targets, n, nnz, arena().get<unsigned long long>(1), s);
@@ -1139,7 +1140,7 @@ gsp_status gsp_refine(const uint64_t *offsets, const uint32_t *targets, const vo
     double m = vertex_weights(g, K, m_dev, s, exact_lsb(g, s));
     Classes cl;
     classify_vertices(g, cl, effective_waves(waves, true), s);
-    uint32_t moves = refine_partition(g, cl, B, R, K, m, theta, seed, pass, s);
+    uint32_t moves = refine_partition(g, cl, B, R, K, m, theta, seed, pass, precision == GSP_PREC_FP64, s);
     if (moves_host) *moves_host = moves;
     GSP_API_END
 }

@@ -47,6 +47,8 @@ Tuning &tuning();
 // the list holds key = class * W + wave in increasing order.
 enum { CLS_G4 = 0, CLS_G8, CLS_G16, CLS_G32, CLS_W512, CLS_BLOCK, CLS_BIG, CLS_HUGE, NUM_CLS };
 constexpr int MAX_WAVES = 64;
+// Edges of one task of the largest class (the hub task prefix of Classes).
+constexpr uint32_t HUB_CHUNK = 1024;
 constexpr int MAX_REPEATS = 8;  // repeats of a wave (gsp_opts.wave_repeats)
 
 struct Classes {
@@ -199,10 +201,10 @@ struct LouvainTimers;
 
 // Leiden refinement (Section 3.5) of the bound membership B (ids < n) into R
 // (each refined community named by one of its vertices), in the waves of
-// `cl` (built for g); returns the number of vertices that joined another
-// refined community.
+// `cl` (built for g), scores in float64 (fp64) or float32; returns the number
+// of vertices that joined another refined community.
 uint32_t refine_partition(const DevGraph &g, const Classes &cl, const uint32_t *B, uint32_t *R, const double *K,
-                          double m, double theta, uint64_t seed, uint32_t pass, cudaStream_t s);
+                          double m, double theta, uint64_t seed, uint32_t pass, bool fp64, cudaStream_t s);
 // Sigma[c] = sum of K over the vertices of community c, size[c] = their
 // count (C ids < n).
 void sigma_from_membership(const uint32_t *C, const double *K, double *Sigma, uint32_t *size, uint32_t n,

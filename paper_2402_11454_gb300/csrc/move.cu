@@ -844,7 +844,6 @@ __global__ void __launch_bounds__(256) k_sweep_persistent(MoveArgs a, const uint
 //            for the next sweep); per-block best per hub;
 //   decide:  one warp per hub reduces the block bests and decides the move.
 // --------------------------------------------------------------------------
-constexpr uint32_t HUB_CHUNK = 1024;
 constexpr int HUB_SLOG = 11;  // shared table of 2 * HUB_CHUNK slots
 
 struct HubArgs {

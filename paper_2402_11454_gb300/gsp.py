@@ -244,7 +244,7 @@ def split(offsets, targets, C, mode="bfs", stream=None):
     return labels, k.value
 
 
-def refine(offsets, targets, weights, B, theta=0.01, seed=0, pass_index=0, waves=0, stream=None):
+def refine(offsets, targets, weights, B, theta=0.01, seed=0, pass_index=0, waves=0, precision="fp64", stream=None):
     """Leiden refinement (Section 3.5) of the bound membership B: (refined
     membership named by member vertex ids, number of vertices that joined)."""
     n, nnz = _graph(offsets, targets, weights)
@@ -252,7 +252,8 @@ def refine(offsets, targets, weights, B, theta=0.01, seed=0, pass_index=0, waves
     R = torch.empty(n, dtype=torch.int32, device=offsets.device)
     moves = ctypes.c_uint32()
     check(_lib.load().gsp_refine(_p(offsets), _p(targets), _p(weights), _wt(weights), n, nnz, _p(B), _p(R),
-                                 float(theta), int(seed), int(pass_index), int(waves), ctypes.byref(moves),
+                                 float(theta), int(seed), int(pass_index), int(waves), PRECISION[precision],
+                                 ctypes.byref(moves),
                                  _stream(stream)))
     return R, moves.value
 

@@ -92,6 +92,26 @@ def test_refine_matches_oracle(gsp, name, theta, seed, waves):
     np.testing.assert_array_equal(R, Ro)
 
 
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("theta", [0.0, 0.01])
+def test_refine_mixed_precision_invariants(gsp, name, theta):
+    """Float32 sums and scores (the default mode): the refined partition
+    nests in the bound one, every target keeps its own member, refined
+    communities are connected, and the number of merges stays within 2 %
+    of the float64 evaluation's."""
+    off, tgt, w = GRAPHS[name]
+    B = BOUND[name]
+    R, moves = gsp.refine(*dev(off, tgt, w), torch.from_numpy(B.astype(np.int32)).cuda(), theta=theta, seed=3,
+                          waves=17, precision="mixed")
+    R = R.cpu().numpy().astype(np.uint32)
+    Ro, mo = oracle.refine(og(name), B, theta=theta, seed=3, waves=17, wave_hash=True)
+    assert np.all(B[R] == B)
+    assert np.all(R[R] == R)
+    assert oracle.disconnected(og(name), R)[0] == 0
+    assert moves == int((R != np.arange(len(R))).sum())
+    assert abs(moves - mo) <= max(2, 0.02 * mo)
+
+
 def test_refine_float64_weights_and_default_waves(gsp):
     """float64 weights take the same path; waves = 0 is 17."""
     off, tgt, w = GRAPHS["grid"]

@@ -479,13 +479,15 @@ gsp_status gsp_set_tuning(const gsp_tuning *t);
 
 /*
  * Pick the caps and class boundaries for this graph and install them: times
- * the first sweep of the first pass (all vertices unprocessed; opts' move
- * mode, waves and precision) under candidate caps and boundaries (each
- * boundary at its limit or half of it), one knob at a time, and keeps the
- * fastest.  Device graph as for gsp_louvain (float32 weights); the graph is
- * not modified.  *chosen receives the installed caps, *ms_default the sweep
- * time under the caps in effect at the call, *ms_tuned the time under the
- * chosen ones (host pointers, each may be NULL).  An edgeless graph is
+ * the local moving of the first pass (from singletons, sweeps until the gain
+ * falls to opts' tolerance, as a run does; opts' move mode, waves, wave
+ * repeats and precision) under candidate caps and boundaries (each boundary
+ * at its limit or half of it), one knob at a time, and keeps
+ * a candidate only when it is more than 1 % faster than the current choice.
+ * Device graph as for gsp_louvain (float32 weights); the graph is not
+ * modified.  *chosen receives the installed caps, *ms_default the time of
+ * that local moving under the caps in effect at the call, *ms_tuned under
+ * the chosen ones (host pointers, each may be NULL).  An edgeless graph is
  * GSP_ERR_INVALID.  Not safe to run concurrently with other calls.
  */
 gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const float *weights,

@@ -638,7 +638,7 @@ struct TraceSpec {
 };
 
 void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, double *modularity_out,
-                 gsp_stats *st, cudaStream_t s, const TraceSpec *trace = nullptr) {
+                 gsp_stats *st, cudaStream_t s, const TraceSpec *trace) {
     g_events.reset();
     const uint32_t n0 = g0.n;
     const bool sync = o.move == GSP_MOVE_SYNC;

@@ -199,6 +199,12 @@ DevGraph make_graph(const uint64_t *off, const uint32_t *tgt, const void *w, int
 
 struct LouvainTimers;
 
+// One GSP-Louvain run (Algorithm 1) on a validated graph, on stream s; the
+// body of gsp_louvain (trace: optional visit recording of gsp_louvain_trace).
+struct TraceSpec;
+void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, double *modularity_out,
+                 gsp_stats *st, cudaStream_t s, const TraceSpec *trace = nullptr);
+
 // Leiden refinement (Section 3.5) of the bound membership B (ids < n) into R
 // (each refined community named by one of its vertices), in the waves of
 // `cl` (built for g), scores in float64 (fp64) or float32; returns the number

@@ -194,3 +194,25 @@ def test_batched_run_rejects_refinement(gsp):
     gvo = np.array([0, len(off) - 1], dtype=np.uint64)
     with pytest.raises(RuntimeError, match="refinement"):
         gsp.louvain_batched(gvo, *dev(off, tgt, w), refine=True)
+
+
+@pytest.mark.parametrize("name", ["planted", "rmat14"])
+@pytest.mark.parametrize("variant", ["split_last", "no_split", "hooking"])
+def test_gsp_leiden_split_variants_fp64_equal_oracle(gsp, name, variant):
+    """Refinement combined with Split Last (Section 4.1), with no split at all
+    (GVE-Louvain's passes plus the refinement) and with the hooking split
+    reproduces the oracle's run of the same variant in frozen-state FP64
+    mode, the disconnected-community count included."""
+    off, tgt, w = GRAPHS[name]
+    g = og(name)
+    kw, okw = {"split_last": (dict(split="lpp", split_when="last"), dict(split="lp", split_last=True)),
+               "no_split": (dict(split="none"), dict(split="none")),
+               "hooking": (dict(split="sv"), dict(split="bfs"))}[variant]
+    C, q, st = gsp.louvain(*dev(off, tgt, w), move="sync", precision="fp64", refine=True, refine_theta=0.01, seed=2,
+                           count_disconnected=True, **kw)
+    Co, ost = oracle.louvain(g, oracle.LouvainOptions(sync=True, refine=True, refine_theta=0.01, seed=2, **okw))
+    assert st["passes"] == ost["passes"]
+    assert st["iterations"] == ost["iterations"]
+    np.testing.assert_array_equal(C.cpu().numpy().astype(np.uint32), Co)
+    assert q == pytest.approx(ost["modularity"], rel=1e-9)
+    assert st["disconnected"] == oracle.disconnected(g, Co)[0]

@@ -126,8 +126,8 @@ typedef struct {
     int refine;                     /* 1: GSP-Leiden -- the refinement phase of the Leiden algorithm
                                        (Section 3.5, gsp_refine) runs after each pass's split, the
                                        refined partition is aggregated, and each super-vertex starts
-                                       the next pass in its bound community; default 0 (gsp_louvain
-                                       only) */
+                                       the next pass in its bound community (in a batch each graph
+                                       refines as it does alone); default 0 */
     double refine_theta;            /* randomness of the refinement's choice, >= 0 (0: greedy); default
                                        0.01 */
     uint64_t seed;                  /* seed of the refinement's draws; default 0 */

@@ -333,6 +333,13 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     uint8_t *sel = arena().get<uint8_t>(G);
     uint64_t *gvo = arena().get<uint64_t>((size_t)G + 1);
     uint64_t *gvo0 = arena().get<uint64_t>((size_t)G + 1);
+    // GSP-Leiden: refined partition, its dense ids, the bound communities
+    // collapsed and dense, 2m of each graph
+    const bool refine = o.refine != 0;
+    uint32_t *Rf = refine ? arena().get<uint32_t>(n0) : nullptr;
+    uint32_t *Bl = refine ? arena().get<uint32_t>(n0) : nullptr;
+    uint32_t *Bd = refine ? arena().get<uint32_t>(n0) : nullptr;
+    double *two_m_g = refine ? arena().get<double>(G) : nullptr;
     mb.K = K;
     mb.gid = gid;
     mb.m_g = m_g;
@@ -368,8 +375,8 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
 
     std::vector<uint8_t> h_done(G, 0), h_live(G, 0), h_sel(G, 0);
     std::vector<int> h_li(G, 0);
-    std::vector<uint32_t> h_k(G, 0);
-    std::vector<double> h_m(G, 0.0), h_minv(G, 0.0);
+    std::vector<uint32_t> h_k(G, 0), h_kr(G, 0);
+    std::vector<double> h_m(G, 0.0), h_minv(G, 0.0), h_two_m(G, 0.0);
     DevGraph cur = g0;
     double tau = o.tolerance;
     const bool split_pass = o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_PASS;
@@ -398,10 +405,15 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         }
         GSP_CUDA(cudaMemcpyAsync(live, h_live.data(), G, cudaMemcpyHostToDevice, s));
         GSP_CUDA(cudaMemcpyAsync(minv_g, h_minv.data(), sizeof(double) * G, cudaMemcpyHostToDevice, s));
-        GSP_CUDA(cudaMemcpyAsync(mb.Sigma, K, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
-        iota_u32(mb.C, nv, s);
-        k_fill_ones<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv);
-        GSP_CHECK_LAUNCH();
+        if (refine && lp > 0) {
+            // each super-vertex starts in the bound community of its members
+            sigma_from_membership(mb.C, K, mb.Sigma, mb.size, nv, s);
+        } else {
+            GSP_CUDA(cudaMemcpyAsync(mb.Sigma, K, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+            iota_u32(mb.C, nv, s);
+            k_fill_ones<<<grid_for(nv, 256), 256, 0, s>>>(mb.size, nv);
+            GSP_CHECK_LAUNCH();
+        }
         reset_left(mb, nv, s);
         k_set_active<<<grid_for(nv, 256), 256, 0, s>>>(mb.act, gid, live, nv);
         GSP_CHECK_LAUNCH();
@@ -429,6 +441,29 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         GSP_CUDA(cudaMemcpyAsync(h_k.data(), k_g, sizeof(uint32_t) * G, cudaMemcpyDeviceToHost, s));
         GSP_CUDA(cudaStreamSynchronize(s));
         passes = lp + 1;
+        // GSP-Leiden: each graph's refinement of its bound communities; the
+        // low-shrink test counts refined communities
+        float ms_ref = 0.0f, ms_split_part = 0.0f;
+        if (refine) {
+            for (uint32_t gi = 0; gi < G; gi++) h_two_m[gi] = 2.0 * h_m[gi];
+            GSP_CUDA(cudaMemcpyAsync(two_m_g, h_two_m.data(), sizeof(double) * G, cudaMemcpyHostToDevice, s));
+            RefineBatch rb;
+            rb.gid = gid;
+            rb.two_m_g = two_m_g;
+            rb.gvo = gvo;
+            ms_split_part = lap();
+            refine_partition(cur, cl, Cp, Rf, K, 0.0, o.refine_theta, o.seed, (uint32_t)lp,
+                             o.precision == GSP_PREC_FP64, s, rb);
+            GSP_CUDA(cudaMemsetAsync(used, 0, nv, s));
+            GSP_CUDA(cudaMemsetAsync(k_g, 0, sizeof(uint32_t) * G, s));
+            k_mark_ids<<<grid_for(nv, 256), 256, 0, s>>>(Rf, nv, used);
+            GSP_CHECK_LAUNCH();
+            k_count_ids<<<grid_for(nv, 256), 256, 0, s>>>(used, gid, nv, k_g);
+            GSP_CHECK_LAUNCH();
+            GSP_CUDA(cudaMemcpyAsync(h_kr.data(), k_g, sizeof(uint32_t) * G, cudaMemcpyDeviceToHost, s));
+            GSP_CUDA(cudaStreamSynchronize(s));
+            ms_ref = lap();
+        }
         // per-graph convergence: l_i <= 1 (converged) or |Gamma|/|Gamma_old| > tau_agg
         uint32_t finishing = 0, k_open = 0;
         int max_li = 0;
@@ -438,16 +473,24 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
             max_li = std::max(max_li, h_li[gi]);
             k_open += h_k[gi];
             const uint64_t ng = hvo[gi + 1] - hvo[gi];
-            if (h_li[gi] <= 1 || (double)h_k[gi] / (double)ng > o.aggregation_tolerance) {
+            const uint32_t kk = refine ? h_kr[gi] : h_k[gi];
+            if (h_li[gi] <= 1 || (double)kk / (double)ng > o.aggregation_tolerance) {
                 h_sel[gi] = 1;
                 finishing++;
             }
         }
-        float ms_split = lap();
+        float ms_split = ms_split_part + lap();
         if (lp < GSP_MAX_PASS_STATS) {
             local.iterations[lp] = max_li;
             local.vertices[lp] = nv;
             local.communities[lp] = k_open;
+            if (refine) {
+                uint32_t kr_open = 0;
+                for (uint32_t gi = 0; gi < G; gi++)
+                    if (!h_done[gi]) kr_open += h_kr[gi];
+                local.refined[lp] = kr_open;
+                local.ms_refine[lp] = ms_ref;
+            }
             local.edges[lp] = cur.nnz;
             local.ms_move[lp] = ms_move;
             local.ms_split[lp] = ms_split;
@@ -469,7 +512,11 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         if (!remaining) break;
         // open graphs: renumber, lookup, aggregate, tau scaling; finished
         // graphs collapse to one super-vertex each
-        k_collapse<<<grid_for(nv, 256), 256, 0, s>>>(Cp, gid, done, gvo, nv, labels);
+        if (refine) {  // the bound communities, collapsed the same way, for the next pass's start
+            k_collapse<<<grid_for(nv, 256), 256, 0, s>>>(Cp, gid, done, gvo, nv, Bl);
+            GSP_CHECK_LAUNCH();
+        }
+        k_collapse<<<grid_for(nv, 256), 256, 0, s>>>(refine ? Rf : Cp, gid, done, gvo, nv, labels);
         GSP_CHECK_LAUNCH();
         const uint32_t k = renumber(nv, labels, Cd, s);
         k_lookup_open<<<grid_for(n0, 256), 256, 0, s>>>(membership, Cd, gid0, done, n0);
@@ -487,18 +534,22 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         std::vector<uint64_t> nvo(G + 1, 0);  // the next level's vertex ranges
         for (uint32_t gi = 0; gi < G; gi++) {
             const uint64_t ng = hvo[gi + 1] - hvo[gi];
-            nvo[gi + 1] = nvo[gi] + (h_done[gi] ? (ng ? 1 : 0) : h_k[gi]);
+            nvo[gi + 1] = nvo[gi] + (h_done[gi] ? (ng ? 1 : 0) : (refine ? h_kr[gi] : h_k[gi]));
         }
         GSP_REQUIRE(nvo[G] == k, "batched aggregation: %llu super-vertices expected, %u made",
                     (unsigned long long)nvo[G], k);
         hvo.swap(nvo);
+        if (refine) {  // super-vertex r starts the next pass in the bound community of its members
+            renumber(nv, Bl, Bd, s);
+            scatter_bound(Cd, Bd, mb.C, nv, s);
+        }
         float ms_agg = lap();
         if (lp < GSP_MAX_PASS_STATS) local.ms_aggregate[lp] = ms_agg;
         arena().release(pass_mark);
         GSP_CUDA(cudaMemcpyAsync(gvo, hvo.data(), sizeof(uint64_t) * (G + 1), cudaMemcpyHostToDevice, s));
         k_graph_of<<<grid_for(k, 256), 256, 0, s>>>(gvo, G, k, gid);
         GSP_CHECK_LAUNCH();
-        iota_u32(mb.C, cur.n, s);
+        if (!refine) iota_u32(mb.C, cur.n, s);
         Cp = mb.C;
     }
     if (remaining) {  // max_passes reached: the open graphs keep their last labels
@@ -578,7 +629,6 @@ extern "C" gsp_status gsp_louvain_batched(uint32_t num_graphs, const uint64_t *g
         else gsp_default_opts(&o);
         check_opts(o);
         GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS, "batched runs support flag pruning only");
-        GSP_REQUIRE(o.refine == 0, "batched runs do not support refinement (GSP-Leiden)");
         GSP_REQUIRE(num_graphs >= 1 && graph_vertex_offsets, "need at least one graph and its vertex offsets");
         GSP_REQUIRE(graph_vertex_offsets[0] == 0 && graph_vertex_offsets[num_graphs] == n,
                     "graph_vertex_offsets must run from 0 to n");

@@ -209,8 +209,16 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
 // (each refined community named by one of its vertices), in the waves of
 // `cl` (built for g), scores in float64 (fp64) or float32; returns the number
 // of vertices that joined another refined community.
+// Batches: graph of each vertex, 2m of each graph (device), first vertex of
+// each graph (device); all NULL for one graph.
+struct RefineBatch {
+    const uint32_t *gid = nullptr;
+    const double *two_m_g = nullptr;
+    const uint64_t *gvo = nullptr;
+};
 uint32_t refine_partition(const DevGraph &g, const Classes &cl, const uint32_t *B, uint32_t *R, const double *K,
-                          double m, double theta, uint64_t seed, uint32_t pass, bool fp64, cudaStream_t s);
+                          double m, double theta, uint64_t seed, uint32_t pass, bool fp64, cudaStream_t s,
+                          const RefineBatch &batch = RefineBatch());
 // Sigma[c] = sum of K over the vertices of community c, size[c] = their
 // count (C ids < n).
 void sigma_from_membership(const uint32_t *C, const double *K, double *Sigma, uint32_t *size, uint32_t n,

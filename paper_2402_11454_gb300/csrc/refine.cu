@@ -81,7 +81,23 @@ struct RefineState {
     double two_m;
     double theta;
     uint64_t pass_key;
+    // batches of graphs: graph of each vertex, 2m of each graph, first vertex
+    // of each graph (NULL for one graph); the draws are keyed by indices
+    // within the graph, so that a graph refines as it does alone
+    const uint32_t *gid;
+    const double *two_m_g;
+    const uint64_t *gvo;
 };
+
+// 2m of vertex v's graph.
+__device__ __forceinline__ double two_m_of(const RefineState &a, uint32_t v) {
+    return a.gid ? a.two_m_g[a.gid[v]] : a.two_m;
+}
+
+// Index of vertex v within its graph.
+__device__ __forceinline__ uint32_t local_id(const RefineState &a, uint32_t v) {
+    return a.gid ? (uint32_t)(v - a.gvo[a.gid[v]]) : v;
+}
 
 // Score arithmetic of the two precision modes.  SPAN: a bound on the spread
 // of the Gumbel noise, -ln(-ln u) for the smallest and the largest draw
@@ -93,10 +109,10 @@ template <> struct Score<double> {
     template <typename WT> __device__ static double weight(const WT *w, uint64_t e) { return wload(w, e); }
     __device__ static double kv(const RefineState &a, uint32_t v) { return a.K[v]; }
     __device__ static double gain(const RefineState &a, double Kv, uint32_t c, double H) {
-        return __dsub_rn(H, __ddiv_rn(__dmul_rn(Kv, a.SR[c]), a.two_m));
+        return __dsub_rn(H, __ddiv_rn(__dmul_rn(Kv, a.SR[c]), two_m_of(a, c)));
     }
     __device__ static double noise(const RefineState &a, uint32_t v, uint32_t c) {
-        uint64_t r = draw(a.pass_key, v, c);
+        uint64_t r = draw(a.pass_key, local_id(a, v), local_id(a, c));
         double u = __dmul_rn(__dadd_rn((double)(r >> 12), 0.5), 0x1.0p-52);
         return -log(-log(u));
     }
@@ -111,7 +127,7 @@ template <> struct Score<float> {
     __device__ static float kv(const RefineState &a, uint32_t v) { return (float)a.K[v]; }
     __device__ static float gain(const RefineState &a, float Kv, uint32_t c, float H) { return H - Kv * a.SRf[c]; }
     __device__ static float noise(const RefineState &a, uint32_t v, uint32_t c) {
-        uint64_t r = draw(a.pass_key, v, c);
+        uint64_t r = draw(a.pass_key, local_id(a, v), local_id(a, c));
         float u = ((float)(uint32_t)(r >> 41) + 0.5f) * 0x1.0p-23f;
         return -logf(-logf(u));
     }
@@ -629,8 +645,9 @@ __global__ void k_refine_wc_targets(RefineState a, Slices sl) {
         uint32_t v = sl.at(t);
         if (!a.joined[v]) continue;
         uint32_t c = a.T[v];
-        a.wc[c] = well_connected(a.ext[c], a.SR[c], a.SB[a.B[c]], a.two_m);
-        a.SRf[c] = (float)(a.SR[c] / a.two_m);
+        const double tm = two_m_of(a, c);
+        a.wc[c] = well_connected(a.ext[c], a.SR[c], a.SB[a.B[c]], tm);
+        a.SRf[c] = (float)(a.SR[c] / tm);
     }
 }
 
@@ -655,8 +672,14 @@ __global__ void k_refine_init(const uint32_t *B, const double *K, uint32_t *R, d
 // The singletons' flags: E(v, b-v) >= K_v (S_b - K_v) / 2m; and K_v / 2m.
 __global__ void k_refine_wc_init(RefineState a, uint32_t n) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        a.wc[v] = well_connected(a.ext[v], a.SR[v], a.SB[a.B[v]], a.two_m);
-        a.SRf[v] = (float)(a.SR[v] / a.two_m);
+        const double tm = two_m_of(a, v);
+        if (!(tm > 0.0)) {  // a graph without edges: nothing to join
+            a.wc[v] = 0;
+            a.SRf[v] = 0.0f;
+            continue;
+        }
+        a.wc[v] = well_connected(a.ext[v], a.SR[v], a.SB[a.B[v]], tm);
+        a.SRf[v] = (float)(a.SR[v] / tm);
     }
 }
 
@@ -738,7 +761,7 @@ template <typename K> unsigned block_grid(K kernel, size_t smem, uint32_t work) 
 
 template <typename WT, typename S>
 uint32_t refine_impl(const DevGraph &g, const Classes &cl, const uint32_t *B, uint32_t *R, const double *K, double m,
-                     double theta, uint64_t seed, uint32_t pass, cudaStream_t s) {
+                     double theta, uint64_t seed, uint32_t pass, const RefineBatch &batch, cudaStream_t s) {
     const uint32_t n = g.n;
     size_t mk = arena().mark();
     RefineState a;
@@ -760,6 +783,9 @@ uint32_t refine_impl(const DevGraph &g, const Classes &cl, const uint32_t *B, ui
     a.joined = arena().get<uint8_t>(n);
     a.moves = arena().get<unsigned long long>(1);
     a.two_m = 2.0 * m;
+    a.gid = batch.gid;
+    a.two_m_g = batch.two_m_g;
+    a.gvo = batch.gvo;
     a.theta = theta;
     a.pass_key = splitmix64(seed + GOLDEN_GAMMA * ((uint64_t)pass + 1));
     GSP_CUDA(cudaMemsetAsync(SB, 0, sizeof(double) * n, s));
@@ -768,7 +794,7 @@ uint32_t refine_impl(const DevGraph &g, const Classes &cl, const uint32_t *B, ui
     GSP_CUDA(cudaMemsetAsync(a.moves, 0, sizeof(unsigned long long), s));
     k_refine_init<<<grid_for(n, 256), 256, 0, s>>>(B, K, R, a.SR, a.size, SB, n);
     GSP_CHECK_LAUNCH();
-    if (!(m > 0.0)) {  // edgeless: every vertex stays alone
+    if (!batch.gid && !(m > 0.0)) {  // edgeless: every vertex stays alone
         arena().release(mk);
         return 0;
     }
@@ -927,14 +953,15 @@ void scatter_bound(const uint32_t *R, const uint32_t *B, uint32_t *C_next, uint3
 }
 
 uint32_t refine_partition(const DevGraph &g, const Classes &cl, const uint32_t *B, uint32_t *R, const double *K,
-                          double m, double theta, uint64_t seed, uint32_t pass, bool fp64, cudaStream_t s) {
+                          double m, double theta, uint64_t seed, uint32_t pass, bool fp64, cudaStream_t s,
+                          const RefineBatch &batch) {
     GSP_REQUIRE(theta >= 0.0 && theta == theta, "refine_theta must be >= 0");
     if (fp64) {
-        if (g.wt == GSP_W_F64) return refine_impl<double, double>(g, cl, B, R, K, m, theta, seed, pass, s);
-        return refine_impl<float, double>(g, cl, B, R, K, m, theta, seed, pass, s);
+        if (g.wt == GSP_W_F64) return refine_impl<double, double>(g, cl, B, R, K, m, theta, seed, pass, batch, s);
+        return refine_impl<float, double>(g, cl, B, R, K, m, theta, seed, pass, batch, s);
     }
-    if (g.wt == GSP_W_F64) return refine_impl<double, float>(g, cl, B, R, K, m, theta, seed, pass, s);
-    return refine_impl<float, float>(g, cl, B, R, K, m, theta, seed, pass, s);
+    if (g.wt == GSP_W_F64) return refine_impl<double, float>(g, cl, B, R, K, m, theta, seed, pass, batch, s);
+    return refine_impl<float, float>(g, cl, B, R, K, m, theta, seed, pass, batch, s);
 }
 
 }  // namespace gsp

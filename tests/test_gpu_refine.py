@@ -189,11 +189,43 @@ def test_gsp_leiden_default_mode_quality(gsp, name):
     assert q == pytest.approx(oracle.modularity(g, C.cpu().numpy().astype(np.uint32)), rel=1e-9)
 
 
-def test_batched_run_rejects_refinement(gsp):
-    off, tgt, w = GRAPHS["planted"]
-    gvo = np.array([0, len(off) - 1], dtype=np.uint64)
-    with pytest.raises(RuntimeError, match="refinement"):
-        gsp.louvain_batched(gvo, *dev(off, tgt, w), refine=True)
+def _concat(graphs):
+    offs, tgts, ws, gvo = [], [], [], [0]
+    base_v, base_e = 0, 0
+    for off, tgt, w in graphs:
+        off = np.asarray(off, dtype=np.int64)
+        offs.append(off[:-1] + base_e)
+        tgts.append(np.asarray(tgt, dtype=np.int64) + base_v)
+        ws.append(np.asarray(w))
+        base_v += len(off) - 1
+        base_e += int(off[-1])
+        gvo.append(base_v)
+    off = np.concatenate(offs + [np.array([base_e], dtype=np.int64)])
+    return off, np.concatenate(tgts), np.concatenate(ws), np.array(gvo, dtype=np.uint64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_gsp_leiden_equals_solo_runs(gsp, precision):
+    """In a batch each graph refines as it does alone (its own 2m, draws keyed
+    by its own vertex indices, waves by index within it): the batched
+    GSP-Leiden membership and modularity of every graph equal its solo run,
+    and in FP64 the oracle's."""
+    graphs = [graphgen.planted(n=3000 + 997 * k, k=8 + 5 * k, mean_degree=10 + 3 * k, p_intra=0.75, seed=20 + k)
+              for k in range(4)] + [graphgen.rmat(12, 8, seed=7), graphgen.grid(30, 40, seed=5)]
+    off, tgt, w, gvo = _concat(graphs)
+    kw = dict(move="sync", precision=precision, refine=True, refine_theta=0.01, seed=3)
+    C, qg, st = gsp.louvain_batched(gvo, *dev(off, tgt, w), **kw)
+    C = C.cpu().numpy()
+    qg = qg.cpu().numpy()
+    assert any(r > 0 for r in st["refined"])
+    for k, (o1, t1, w1) in enumerate(graphs):
+        Cs, qs, _ = gsp.louvain(*dev(o1, t1, w1), **kw)
+        np.testing.assert_array_equal(C[gvo[k]:gvo[k + 1]], Cs.cpu().numpy())
+        assert qg[k] == pytest.approx(qs, rel=1e-9)
+        if precision == "fp64":
+            Co, ost = oracle.louvain(oracle.Graph(o1, t1, w1.astype(np.float64)),
+                                     oracle.LouvainOptions(sync=True, refine=True, refine_theta=0.01, seed=3))
+            np.testing.assert_array_equal(Cs.cpu().numpy().astype(np.uint32), Co)
 
 
 @pytest.mark.parametrize("name", ["planted", "rmat14"])

@@ -3,7 +3,8 @@ technique (none = GVE-Louvain, label propagation, label propagation with
 pruning, BFS, and hooking/shortcutting (SV), which is not in the paper) and
 its placement (after every pass, or once at the end), as in the paper's
 comparison of split variants (Section 4.1) and of GSP-Louvain against the
-method without a split (Section 5).
+method without a split (Section 5); and the Leiden refinement (Section 3.5)
+with and without the split (GSP-Leiden).
 
 For every configuration it reports the device time of one gsp_louvain call,
 the modularity, the number of communities and the number of internally
@@ -17,16 +18,19 @@ import argparse
 import json
 import sys
 
+# (split technique, placement, Leiden refinement)
 VARIANTS = [
-    ("none", "pass"),   # GVE-Louvain: no split
-    ("lp", "pass"),
-    ("lpp", "pass"),
-    ("bfs", "pass"),
-    ("sv", "pass"),
-    ("lp", "last"),
-    ("lpp", "last"),
-    ("bfs", "last"),
-    ("sv", "last"),
+    ("none", "pass", False),   # GVE-Louvain: no split
+    ("lp", "pass", False),
+    ("lpp", "pass", False),
+    ("bfs", "pass", False),
+    ("sv", "pass", False),
+    ("lp", "last", False),
+    ("lpp", "last", False),
+    ("bfs", "last", False),
+    ("sv", "last", False),
+    ("none", "pass", True),    # refinement (Section 3.5) without a split
+    ("lpp", "pass", True),     # GSP-Leiden
 ]
 
 
@@ -52,8 +56,8 @@ def main(argv=None):
     for name in args.workloads.split(","):
         off, tgt, w = workload(gsp, name)
         gsp.autotune(off, tgt, w)
-        for split, when in VARIANTS:
-            kw = dict(split=split, split_when=when)
+        for split, when, refine in VARIANTS:
+            kw = dict(split=split, split_when=when, refine=refine)
             gsp.louvain(off, tgt, w, **kw)  # warm-up
             times = []
             for _ in range(args.steps):
@@ -66,6 +70,7 @@ def main(argv=None):
                 times.append(e0.elapsed_time(e1))
             dis, _ = gsp.count_disconnected(off, tgt, C)
             print(json.dumps({"workload": name, "edges": int(tgt.numel()), "split": split, "split_when": when,
+                              "refine": refine,
                               "ms": round(min(times), 3), "modularity": q,
                               "communities": st["final_communities"], "disconnected": dis,
                               "passes": st["passes"], "split_ms": round(sum(st["ms_split"]), 3)}), flush=True)

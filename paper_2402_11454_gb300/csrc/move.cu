@@ -488,7 +488,7 @@ __device__ void block_body(const MoveArgs &a, const uint32_t *__restrict__ list,
             }
         }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, claim);
-        __syncthreads();  // previous round done with s_todo
+        __syncthreads();  // the loop's previous step is done with s_todo
         if (lane == 0) s_wcnt[wid] = __popc(bal);
         __syncthreads();
         if (claim) {

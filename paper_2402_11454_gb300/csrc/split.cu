@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_lp_block(const uint64_t *__restrict__ o
             }
         }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, claim);
-        __syncthreads();  // previous round done with s_todo
+        __syncthreads();  // the loop's previous step is done with s_todo
         if (lane == 0) s_wcnt[wid] = __popc(bal);
         __syncthreads();
         if (claim) {

@@ -482,8 +482,10 @@ gsp_status gsp_set_tuning(const gsp_tuning *t);
  * the local moving of the first pass (from singletons, sweeps until the gain
  * falls to opts' tolerance, as a run does; opts' move mode, waves, wave
  * repeats and precision) under candidate caps and boundaries (each boundary
- * at its limit or half of it), one knob at a time, and keeps
- * a candidate only when it is more than 1 % faster than the current choice.
+ * at its limit or half of it), one knob at a time (each trial the better of
+ * two runs), keeps a candidate only when it is more than 1 % faster than the
+ * current choice, and finally times the pick against the settings in effect
+ * at the call once more, keeping the faster.
  * Device graph as for gsp_louvain (float32 weights); the graph is not
  * modified.  *chosen receives the installed caps, *ms_default the time of
  * that local moving under the caps in effect at the call, *ms_tuned under

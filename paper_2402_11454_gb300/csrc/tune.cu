@@ -15,6 +15,8 @@
 
 #include <mutex>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace gsp {
@@ -194,7 +196,7 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
             if (!limit) limit = before + before / 2;
             float ms = run();
             if (gsp_workspace_reserved() > before) ms = run();
-            return ms;
+            return std::min(ms, run());  // the better of two runs
         };
         std::lock_guard<std::mutex> lock(g_tuning_mu);
         const Tuning start = g_tuning;
@@ -229,7 +231,7 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
                 return t.group_max >= 33 && t.warp_max > t.group_max && t.block_max > t.warp_max &&
                        t.big_max > t.block_max;
             };
-            for (int round = 0; round < 1; round++) {
+            {
                 for (const Knob &k : knobs) {
                     for (int v : k.cand) {
                         if (v == best.*(k.field)) continue;
@@ -255,6 +257,22 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
                             best = g_tuning;
                         }
                     }
+                }
+            }
+            // the pick is the best of many noisy trials: time it against the
+            // starting settings once more and keep whichever is faster
+            if (!(best.groups == start.groups && best.w512 == start.w512 && best.block == start.block &&
+                  best.hub == start.hub && best.group_max == start.group_max && best.warp_max == start.warp_max &&
+                  best.block_max == start.block_max && best.big_max == start.big_max)) {
+                g_tuning = start;
+                const float ts = trial();
+                g_tuning = best;
+                const float tbest = trial();
+                if (ts <= tbest) {
+                    best = start;
+                    tb = ts;
+                } else {
+                    tb = tbest;
                 }
             }
         } catch (...) {

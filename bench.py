@@ -335,7 +335,7 @@ def run_workload(gsp, graphgen, name, kw, steps, warmup, flush, stream, peak, ki
 
     tuning = {"caps": gsp.get_tuning(), "autotuned": False}
     if autotune:
-        caps, ms0, ms1 = gsp.autotune(off, tgt, w, **kw)
+        caps, ms0, ms1 = gsp.autotune(off, tgt, w, graph_vertex_offsets=gvo, **kw)
         tuning = {"caps": caps, "autotuned": True, "tuning_run_ms_default": round(ms0, 3),
                   "tuning_run_ms_tuned": round(ms1, 3)}
     for _ in range(max(warmup, 0)):
@@ -527,8 +527,8 @@ def main():
         return C, st["modularity"], st
 
     tuning = {"caps": gsp.get_tuning(), "autotuned": False}
-    if not args.no_autotune and not args.caps:  # untimed: picks the local-moving grid caps for this graph
-        caps, ms0, ms1 = gsp.autotune(off, tgt, w, **kw)
+    if not args.no_autotune and not args.caps:  # untimed: picks the local-moving grid caps for this input
+        caps, ms0, ms1 = gsp.autotune(off, tgt, w, graph_vertex_offsets=gvo, **kw)
         tuning = {"caps": caps, "autotuned": True, "tuning_run_ms_default": round(ms0, 3),
                   "tuning_run_ms_tuned": round(ms1, 3)}
 

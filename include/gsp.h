@@ -479,22 +479,36 @@ gsp_status gsp_set_tuning(const gsp_tuning *t);
 
 /*
  * Pick the caps and class boundaries for this graph and install them: times
- * the local moving of the first pass (from singletons, sweeps until the gain
- * falls to opts' tolerance, as a run does; opts' move mode, waves, wave
- * repeats and precision) under candidate caps and boundaries (each boundary
- * at its limit or half of it), one knob at a time (each trial the better of
- * two runs), keeps a candidate only when it is more than 1 % faster than the
- * current choice, and finally times the pick against the settings in effect
- * at the call once more, keeping the faster.
- * Device graph as for gsp_louvain (float32 weights); the graph is not
- * modified.  *chosen receives the installed caps, *ms_default the time of
- * that local moving under the caps in effect at the call, *ms_tuned under
- * the chosen ones (host pointers, each may be NULL).  An edgeless graph is
- * GSP_ERR_INVALID.  Not safe to run concurrently with other calls.
+ * whole gsp_louvain calls on opts (its move mode, waves, wave repeats,
+ * precision, split and refinement) under candidate caps and boundaries (each
+ * boundary at its limit or half of it), one knob at a time, each trial the
+ * better of two calls; keeps a candidate only when it is more than 1 % faster
+ * than the current choice, and finally times the pick against the settings
+ * in effect at the call once more, keeping the faster.  Device graph as for
+ * gsp_louvain (float32 weights); the graph is not modified.  *chosen
+ * receives the installed settings, *ms_default the time of a call under the
+ * settings in effect at the call, *ms_tuned under the chosen ones (host
+ * pointers, each may be NULL).  The trials allocate a membership array of n
+ * entries outside the workspace and may free and rebuild the workspace.  An
+ * edgeless graph is GSP_ERR_INVALID.  Not safe to run concurrently with
+ * other calls.
  */
 gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const float *weights,
                         uint32_t n, uint64_t nnz, const gsp_opts *opts, gsp_tuning *chosen,
                         float *ms_default, float *ms_tuned);
+
+/*
+ * As gsp_autotune, timing gsp_louvain_batched calls on the batch (arguments
+ * as for gsp_louvain_batched: host graph_vertex_offsets of num_graphs + 1
+ * entries, device CSR of the concatenated graphs).  A batch stops each graph
+ * on its own gain and runs its passes over the graphs still open, so its
+ * degree mix per pass differs from that of one call on the same CSR taken
+ * as a single graph.  A batch without any edge is GSP_ERR_INVALID.
+ */
+gsp_status gsp_autotune_batched(uint32_t num_graphs, const uint64_t *graph_vertex_offsets,
+                                const uint64_t *offsets, const uint32_t *targets, const float *weights,
+                                uint32_t n, uint64_t nnz, const gsp_opts *opts, gsp_tuning *chosen,
+                                float *ms_default, float *ms_tuned);
 
 #ifdef __cplusplus
 }

@@ -82,6 +82,7 @@ _SIGS = {
     "gsp_get_tuning": (c_int, [P]),
     "gsp_set_tuning": (c_int, [P]),
     "gsp_autotune": (c_int, [P, P, P, c_u32, c_u64, P, P, P, P]),
+    "gsp_autotune_batched": (c_int, [c_u32, P, P, P, P, c_u32, c_u64, P, P, P, P]),
     "gsp_gen_rmat": (c_int, [c_u32, c_u32, c_u64, c_u64, c_u64, c_u64, P, P]),
     "gsp_gen_planted_batch": (c_int, [c_u32, P, P, P, P, P, P, P]),
     "gsp_gen_grid": (c_int, [c_u32, c_u32, c_u64, c_u64, c_flt, c_flt, c_u64, P, P]),

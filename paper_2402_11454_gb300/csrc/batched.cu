@@ -42,14 +42,42 @@ __global__ void k_graph_of(const uint64_t *__restrict__ gvo, uint32_t G, uint32_
     }
 }
 
-__global__ void k_cross_edges(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
-                              const uint32_t *__restrict__ gid, uint32_t n, unsigned long long *bad) {
+// Entries whose target lies outside the vertex range of their row's graph,
+// edge-parallel: warp w of the grid takes the contiguous entries
+// [nnz w / warps, nnz (w+1) / warps), its lanes consecutive entries.
+constexpr int CROSS_UNROLL = 4;
+__global__ void __launch_bounds__(256) k_cross_edges(const uint64_t *__restrict__ off,
+                                                     const uint32_t *__restrict__ tgt,
+                                                     const uint32_t *__restrict__ gid,
+                                                     const uint64_t *__restrict__ gvo, uint32_t n, uint64_t nnz,
+                                                     unsigned long long *bad) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t wid = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t w0 = nnz * wid / warps, w1 = nnz * (wid + 1) / warps;
+    uint32_t r = 0;
+    if (lane == 0 && w0 < w1) r = row_of(off, n, w0);
+    r = __shfl_sync(0xffffffffu, r, 0);
     unsigned long long cnt = 0;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        uint32_t g = gid[v];
-        for (uint64_t p = off[v]; p < off[v + 1]; p++) cnt += gid[tgt[p]] != g;
+    for (uint64_t p = w0 + lane; p < w1; p += 32ull * CROSS_UNROLL) {
+        uint32_t t[CROSS_UNROLL];
+#pragma unroll
+        for (int k = 0; k < CROSS_UNROLL; k++) {
+            const uint64_t q = p + 32ull * k;
+            t[k] = q < w1 ? __ldg(tgt + q) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < CROSS_UNROLL; k++) {
+            const uint64_t q = p + 32ull * k;
+            if (q < w1) {
+                r = row_from(off, n, q, r);
+                const uint32_t g = __ldg(gid + r);
+                cnt += t[k] < __ldg(gvo + g) || t[k] >= __ldg(gvo + g + 1);
+            }
+        }
     }
-    if (cnt) atomicAdd(bad, cnt);
+    cnt = warp_sum(cnt);
+    if (lane == 0 && cnt) atomicAdd(bad, cnt);
 }
 
 __global__ void k_fill_ones(uint32_t *p, uint32_t n) {
@@ -298,8 +326,8 @@ static void to_representatives(uint32_t *membership, const uint32_t *lab, uint32
     GSP_CHECK_LAUNCH();
 }
 
-static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *h_gvo0, const gsp_opts &o,
-                                uint32_t *membership, double *q_out, gsp_stats *st, cudaStream_t caller) {
+void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *h_gvo0, const gsp_opts &o,
+                         uint32_t *membership, double *q_out, gsp_stats *st, cudaStream_t caller) {
     reset_event_pool();
     cudaStream_t s = capture_stream();
     {
@@ -361,8 +389,12 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
         size_t mk = arena().mark();
         unsigned long long *bad = arena().get<unsigned long long>(1);
         GSP_CUDA(cudaMemsetAsync(bad, 0, sizeof(*bad), s));
-        k_cross_edges<<<grid_for(n0, 256), 256, 0, s>>>(g0.off, g0.tgt, gid0, n0, bad);
-        GSP_CHECK_LAUNCH();
+        if (g0.nnz) {
+            const unsigned grid = std::min(grid_for(g0.nnz, 256 * CROSS_UNROLL, sms(8)),
+                                           resident_grid((const void *)k_cross_edges, 256, 0, 8));
+            k_cross_edges<<<grid, 256, 0, s>>>(g0.off, g0.tgt, gid0, gvo0, n0, g0.nnz, bad);
+            GSP_CHECK_LAUNCH();
+        }
         unsigned long long hb = 0;
         GSP_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, s));
         GSP_CUDA(cudaStreamSynchronize(s));
@@ -615,6 +647,14 @@ static void louvain_batched_run(const DevGraph &g0, uint32_t G, const uint64_t *
     GSP_CUDA(cudaStreamWaitEvent(caller, out, 0));
 }
 
+void check_batch(uint32_t num_graphs, const uint64_t *gvo, uint32_t n, const gsp_opts &o) {
+    GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS, "batched runs support flag pruning only");
+    GSP_REQUIRE(num_graphs >= 1 && gvo, "need at least one graph and its vertex offsets");
+    GSP_REQUIRE(gvo[0] == 0 && gvo[num_graphs] == n, "graph_vertex_offsets must run from 0 to n");
+    for (uint32_t g = 0; g < num_graphs; g++)
+        GSP_REQUIRE(gvo[g + 1] >= gvo[g], "graph_vertex_offsets must not decrease");
+}
+
 }  // namespace gsp
 
 using namespace gsp;
@@ -628,13 +668,7 @@ extern "C" gsp_status gsp_louvain_batched(uint32_t num_graphs, const uint64_t *g
         if (opts) o = *opts;
         else gsp_default_opts(&o);
         check_opts(o);
-        GSP_REQUIRE(o.prune == GSP_PRUNE_FLAGS, "batched runs support flag pruning only");
-        GSP_REQUIRE(num_graphs >= 1 && graph_vertex_offsets, "need at least one graph and its vertex offsets");
-        GSP_REQUIRE(graph_vertex_offsets[0] == 0 && graph_vertex_offsets[num_graphs] == n,
-                    "graph_vertex_offsets must run from 0 to n");
-        for (uint32_t g = 0; g < num_graphs; g++)
-            GSP_REQUIRE(graph_vertex_offsets[g + 1] >= graph_vertex_offsets[g],
-                        "graph_vertex_offsets must not decrease");
+        check_batch(num_graphs, graph_vertex_offsets, n, o);
         GSP_REQUIRE(membership && modularity, "membership and modularity must not be NULL");
         DevGraph g = make_graph(offsets, targets, weights, GSP_W_F32, n, nnz);
         cudaStream_t s = static_cast<cudaStream_t>(o.stream);

@@ -74,6 +74,32 @@ inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 0) {
 }
 
 // --------------------------------------------------------- device helpers
+// Row of CSR entry p (offsets non-decreasing, off[n] > p): the
+// last row with off[row] <= p, searched forward from a row r known to have
+// off[r] <= p by doubling the step, then halving it.  Consecutive entries of
+// a thread lie a few rows apart, so the search stays in a few cached lines.
+__device__ __forceinline__ uint32_t row_from(const uint64_t *__restrict__ off, uint32_t n, uint64_t p, uint32_t r) {
+    uint64_t step = 1;
+    while ((uint64_t)r + step < n && __ldg(off + r + step) <= p) {
+        r += (uint32_t)step;
+        step <<= 1;
+    }
+    for (step >>= 1; step > 0; step >>= 1)
+        if ((uint64_t)r + step < n && __ldg(off + r + step) <= p) r += (uint32_t)step;
+    return r;
+}
+
+// The same row by bisection over all rows (a block's first entry).
+__device__ __forceinline__ uint32_t row_of(const uint64_t *__restrict__ off, uint32_t n, uint64_t p) {
+    uint32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo + 1) / 2;
+        if (__ldg(off + mid) <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ double wload(const float *w, uint64_t e) { return (double)__ldg(w + e); }
 __device__ __forceinline__ double wload(const double *w, uint64_t e) { return __ldg(w + e); }
 __device__ __forceinline__ float wloadf(const float *w, uint64_t e) { return __ldg(w + e); }

@@ -205,6 +205,13 @@ struct TraceSpec;
 void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, double *modularity_out,
                  gsp_stats *st, cudaStream_t s, const TraceSpec *trace = nullptr);
 
+// Batched GSP-Louvain on the concatenated graphs (h_gvo0: host vertex offsets
+// of the num_graphs graphs), per-graph modularity into q_out (device); the
+// body of gsp_louvain_batched.  check_batch validates its arguments.
+void check_batch(uint32_t num_graphs, const uint64_t *h_gvo0, uint32_t n, const gsp_opts &o);
+void louvain_batched_run(const DevGraph &g0, uint32_t num_graphs, const uint64_t *h_gvo0, const gsp_opts &o,
+                         uint32_t *membership, double *q_out, gsp_stats *st, cudaStream_t caller);
+
 // Leiden refinement (Section 3.5) of the bound membership B (ids < n) into R
 // (each refined community named by one of its vertices), in the waves of
 // `cl` (built for g), scores in float64 (fp64) or float32; returns the number

@@ -314,15 +314,22 @@ def set_tuning(**caps):
     return get_tuning()
 
 
-def autotune(offsets, targets, weights, **kw):
-    """Pick and install the grid caps for this graph; returns (caps, ms of the
-    first sweep before, ms after)."""
+def autotune(offsets, targets, weights, graph_vertex_offsets=None, **kw):
+    """Pick and install the grid caps and class boundaries for this graph (or,
+    with graph_vertex_offsets, for this batch through the batched call);
+    returns (settings, ms of a call before, ms after)."""
     n, nnz = _graph(offsets, targets, weights)
     o = make_opts(**kw)
     t = GspTuning()
     before, after = ctypes.c_float(), ctypes.c_float()
-    check(_lib.load().gsp_autotune(_p(offsets), _p(targets), _p(weights), n, nnz, ctypes.byref(o), ctypes.byref(t),
-                                   ctypes.byref(before), ctypes.byref(after)))
+    if graph_vertex_offsets is None:
+        check(_lib.load().gsp_autotune(_p(offsets), _p(targets), _p(weights), n, nnz, ctypes.byref(o),
+                                       ctypes.byref(t), ctypes.byref(before), ctypes.byref(after)))
+    else:
+        gvo = np.ascontiguousarray(np.asarray(graph_vertex_offsets, dtype=np.uint64))
+        check(_lib.load().gsp_autotune_batched(len(gvo) - 1, gvo.ctypes.data_as(ctypes.c_void_p), _p(offsets),
+                                               _p(targets), _p(weights), n, nnz, ctypes.byref(o),
+                                               ctypes.byref(t), ctypes.byref(before), ctypes.byref(after)))
     return {f: getattr(t, f) for f in _TUNING_FIELDS}, before.value, after.value
 
 

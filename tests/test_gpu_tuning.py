@@ -59,6 +59,42 @@ def test_autotune_installs_valid_caps(gsp, restore):
     assert (C == C0).all() and q == q0
 
 
+def test_autotune_batched_installs_valid_caps(gsp, restore):
+    # a batch of planted graphs of mixed sizes, one of them edgeless, tuned
+    # through the batched call: the settings are valid and leave every
+    # graph's result unchanged
+    rng = np.random.default_rng(7)
+    n_g = [int(x) for x in rng.integers(64, 4096, size=48)] + [8]
+    k_g = [int(rng.integers(4, 16)) for _ in n_g[:-1]] + [4]
+    e_g = [n * int(rng.integers(4, 24)) // 2 for n in n_g[:-1]] + [0]
+    off, tgt, w = gsp.gen_planted_batch(n_g, k_g, e_g, [0.8] * len(n_g), list(range(1, len(n_g) + 1)))
+    gvo = np.concatenate([[0], np.cumsum(n_g)]).astype(np.uint64)
+    C0, q0, st0 = gsp.louvain_batched(gvo, off, tgt, w, precision="fp64")
+    caps, ms_before, ms_after = gsp.autotune(off, tgt, w, graph_vertex_offsets=gvo, precision="fp64")
+    assert caps == gsp.get_tuning()
+    assert all(1 <= v <= 32 for k, v in caps.items() if k.endswith("_per_sm"))
+    assert 33 <= caps["group_max_degree"] < caps["warp_max_degree"] < caps["block_max_degree"] < caps["big_max_degree"]
+    assert 0 < ms_after <= ms_before
+    C, q, st = gsp.louvain_batched(gvo, off, tgt, w, precision="fp64")
+    assert st["iterations"] == st0["iterations"]
+    assert (C == C0).all() and (q == q0).all()
+
+
+def test_autotune_batched_rejects_bad_offsets(gsp, restore):
+    from paper_2402_11454_gb300._lib import GspError
+    off, tgt, w = gsp.gen_planted_batch([100, 100], [4, 4], [400, 400], [0.8, 0.8], [1, 2])
+    before = gsp.get_tuning()
+    for gvo in ([0, 100, 150], [0, 120, 100, 200], [1, 200]):
+        with pytest.raises(GspError):
+            gsp.autotune(off, tgt, w, graph_vertex_offsets=np.asarray(gvo, dtype=np.uint64))
+    import torch
+    params = torch.zeros(gsp.mlp_param_count(), dtype=torch.float32, device="cuda")
+    with pytest.raises(GspError):  # batches support flag pruning only
+        gsp.autotune(off, tgt, w, graph_vertex_offsets=np.asarray([0, 100, 200], dtype=np.uint64),
+                     prune="learned", mlp_params=params)
+    assert gsp.get_tuning() == before
+
+
 def test_autotune_rejects_edgeless_graph(gsp, restore):
     import torch
     from paper_2402_11454_gb300._lib import GspError

@@ -148,19 +148,19 @@ __global__ void k_community_sizes(const uint32_t *__restrict__ C, uint32_t n, ui
 }
 
 // Input checks.  Offsets: non-decreasing from 0 to nnz (checked first: the
-// row kernels below trust them).  Entries: targets < n, weights finite and
+// entry kernel below trusts them).  Entries: targets < n, weights finite and
 // > 0.  Symmetry (Section 3: G is undirected, w_ij = w_ji): every stored
 // entry (i, j, w) with i != j adds a 64-bit hash of the unordered pair and
-// the weight's bits to the "below" sums when i < j and to the "above" sums
+// the weight's bits to the "below" sum when i < j and to the "above" sum
 // when i > j.  A symmetric CSR stores the same multiset of (pair, weight) on
 // both sides, so its counts and sums agree; an asymmetric one passes only if
-// two independent 64-bit sums collide at once.  The hash is the MurmurHash3
-// 64-bit finaliser (Appleby) over the pair with the weight mixed in.
+// two 64-bit sums of hashes collide.  The hash is the MurmurHash3 64-bit
+// finaliser (Appleby) of the pair with the weight's bits mixed in by a
+// multiplication with the 64-bit golden ratio.
 struct GraphCheck {
-    unsigned long long bad;         // offset, target and weight violations
-    unsigned long long cnt[2];      // entries below / above the diagonal
-    unsigned long long fp[2][2];    // [side][hash] sums, modulo 2^64
-    uint32_t nlong;                 // rows left to the long-row kernel
+    unsigned long long bad;     // offset, target and weight violations
+    unsigned long long cnt[2];  // entries below / above the diagonal
+    unsigned long long fp[2];   // hash sums below / above, modulo 2^64
 };
 
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
@@ -173,11 +173,11 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
 }
 
 struct CheckAcc {
-    unsigned long long bad = 0, cnt[2] = {0, 0}, fp[2][2] = {{0, 0}, {0, 0}};
-    __device__ void entry(uint32_t i, uint32_t j, const float *w, uint64_t p, uint32_t n) {
+    unsigned long long bad = 0, cnt[2] = {0, 0}, fp[2] = {0, 0};
+    // entry (i, j) of weight x (has_w = 0: no weights to check)
+    __device__ void entry(uint32_t i, uint32_t j, float x, bool has_w, uint32_t n) {
         uint32_t wb = 0;
-        if (w) {
-            const float x = __ldg(w + p);
+        if (has_w) {
             if (!(x > 0.0f) || isinf(x)) bad++;
             wb = __float_as_uint(x);
         }
@@ -185,16 +185,14 @@ struct CheckAcc {
         if (i == j) return;
         const int side = i > j;
         const uint64_t key = side ? (((uint64_t)j << 32) | i) : (((uint64_t)i << 32) | j);
-        fp[side][0] += fmix64(key ^ fmix64((uint64_t)wb + 0x9E3779B97F4A7C15ull));
-        fp[side][1] += fmix64(key * 0xD6E8FEB86659FD93ull + fmix64((uint64_t)wb ^ 0xA0761D6478BD642Full));
+        fp[side] += fmix64(key ^ ((uint64_t)wb * 0x9E3779B97F4A7C15ull));
         cnt[side]++;
     }
     __device__ void flush(GraphCheck *g) {
-        unsigned long long v[7] = {bad, cnt[0], cnt[1], fp[0][0], fp[0][1], fp[1][0], fp[1][1]};
-        unsigned long long *dst[7] = {&g->bad, &g->cnt[0], &g->cnt[1], &g->fp[0][0], &g->fp[0][1], &g->fp[1][0],
-                                      &g->fp[1][1]};
+        unsigned long long v[5] = {bad, cnt[0], cnt[1], fp[0], fp[1]};
+        unsigned long long *dst[5] = {&g->bad, &g->cnt[0], &g->cnt[1], &g->fp[0], &g->fp[1]};
 #pragma unroll
-        for (int k = 0; k < 7; k++) {
+        for (int k = 0; k < 5; k++) {
             const unsigned long long t = warp_sum(v[k]);
             if ((threadIdx.x & 31) == 0 && t) atomicAdd(dst[k], t);
         }
@@ -211,42 +209,42 @@ __global__ void k_check_offsets(const uint64_t *__restrict__ off, uint32_t n, ui
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(&g->bad, b);
 }
 
-constexpr uint32_t CHECK_SHORT = 64;    // rows up to this length: one thread
-constexpr uint32_t CHECK_CHUNK = 2048;  // longer rows: tasks of this many entries, one block each
+constexpr int CHECK_UNROLL = 4;  // entries a thread loads before checking them
 
-__global__ void k_check_rows(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
-                             const float *__restrict__ w, uint32_t n, GraphCheck *g, uint32_t *longlist) {
+// Entry checks, edge-parallel: warp w of the grid takes the contiguous
+// entries [nnz w / warps, nnz (w+1) / warps), its lanes consecutive entries
+// (coalesced loads whatever the row lengths; a lane's next entry lies 32
+// entries on, so its row search moves a row or so).
+__global__ void __launch_bounds__(256) k_check_entries(const uint64_t *__restrict__ off,
+                                                       const uint32_t *__restrict__ tgt,
+                                                       const float *__restrict__ w, uint32_t n, uint64_t nnz,
+                                                       GraphCheck *g) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t wid = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t w0 = nnz * wid / warps, w1 = nnz * (wid + 1) / warps;
+    uint32_t r = 0;
+    if (lane == 0 && w0 < w1) r = row_of(off, n, w0);
+    r = __shfl_sync(0xffffffffu, r, 0);
     CheckAcc a;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint64_t b = off[i], e = off[i + 1];
-        if (e - b > CHECK_SHORT) {
-            longlist[atomicAdd(&g->nlong, 1u)] = i;
-            continue;
+    const bool has_w = w != nullptr;
+    for (uint64_t p = w0 + lane; p < w1; p += 32ull * CHECK_UNROLL) {
+        uint32_t t[CHECK_UNROLL];
+        float x[CHECK_UNROLL];
+#pragma unroll
+        for (int k = 0; k < CHECK_UNROLL; k++) {
+            const uint64_t q = p + 32ull * k;
+            t[k] = q < w1 ? __ldg(tgt + q) : 0u;
+            x[k] = (has_w && q < w1) ? __ldg(w + q) : 1.0f;
         }
-        for (uint64_t p = b; p < e; p++) a.entry(i, __ldg(tgt + p), w, p, n);
-    }
-    a.flush(g);
-}
-
-__global__ void k_check_long_tasks(const uint64_t *__restrict__ off, const uint32_t *__restrict__ longlist,
-                                   uint32_t nlong, uint64_t *ntask) {
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nlong; t += gridDim.x * blockDim.x) {
-        const uint32_t i = longlist[t];
-        ntask[t] = (off[i + 1] - off[i] + CHECK_CHUNK - 1) / CHECK_CHUNK;
-    }
-}
-
-__global__ void k_check_long(const uint64_t *__restrict__ off, const uint32_t *__restrict__ tgt,
-                             const float *__restrict__ w, uint32_t n, const uint32_t *__restrict__ longlist,
-                             const uint64_t *__restrict__ tasks, const uint32_t *__restrict__ owner,
-                             uint64_t ntasks, GraphCheck *g) {
-    CheckAcc a;
-    for (uint64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
-        const uint32_t t = owner[task];
-        const uint32_t i = longlist[t];
-        const uint64_t b = off[i] + (task - tasks[t]) * CHECK_CHUNK;
-        const uint64_t e = min(b + CHECK_CHUNK, off[i + 1]);
-        for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) a.entry(i, __ldg(tgt + p), w, p, n);
+#pragma unroll
+        for (int k = 0; k < CHECK_UNROLL; k++) {
+            const uint64_t q = p + 32ull * k;
+            if (q < w1) {
+                r = row_from(off, n, q, r);
+                a.entry(r, t[k], x[k], has_w, n);
+            }
+        }
     }
     a.flush(g);
 }
@@ -264,32 +262,16 @@ void check_graph(const uint64_t *off, const uint32_t *tgt, const float *w, uint3
     if (h.bad) arena().release(mk);
     GSP_REQUIRE(h.bad == 0, "invalid graph: offsets must rise from 0 to nnz (%llu violations)", h.bad);
     if (nnz) {
-        uint32_t *longlist = arena().get<uint32_t>(n);
-        k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(off, tgt, w, n, d, longlist);
+        const unsigned grid = std::min(grid_for(nnz, 256 * CHECK_UNROLL, sms(8)),
+                                       resident_grid((const void *)k_check_entries, 256, 0, 8));
+        k_check_entries<<<grid, 256, 0, s>>>(off, tgt, w, n, nnz, d);
         GSP_CHECK_LAUNCH();
-        GSP_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
-        GSP_CUDA(cudaStreamSynchronize(s));
-        if (h.nlong) {
-            uint64_t *ntask = arena().get<uint64_t>(h.nlong);
-            uint64_t *tasks = arena().get<uint64_t>((size_t)h.nlong + 1);
-            k_check_long_tasks<<<grid_for(h.nlong, 256), 256, 0, s>>>(off, longlist, h.nlong, ntask);
-            GSP_CHECK_LAUNCH();
-            exclusive_scan_u64(ntask, tasks, h.nlong, s);
-            uint64_t ntasks = 0;
-            GSP_CUDA(cudaMemcpyAsync(&ntasks, tasks + h.nlong, sizeof(ntasks), cudaMemcpyDeviceToHost, s));
-            GSP_CUDA(cudaStreamSynchronize(s));
-            uint32_t *owner = arena().get<uint32_t>(ntasks);
-            task_items(tasks, h.nlong, owner, s);
-            k_check_long<<<grid_for(ntasks, 1, sms(8)), 256, 0, s>>>(off, tgt, w, n, longlist, tasks, owner,
-                                                                     ntasks, d);
-            GSP_CHECK_LAUNCH();
-        }
         GSP_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
         GSP_CUDA(cudaStreamSynchronize(s));
     }
     arena().release(mk);
     GSP_REQUIRE(h.bad == 0, "invalid graph: %llu violations (targets must be < n, weights finite and > 0)", h.bad);
-    if (h.cnt[0] != h.cnt[1] || h.fp[0][0] != h.fp[1][0] || h.fp[0][1] != h.fp[1][1]) {
+    if (h.cnt[0] != h.cnt[1] || h.fp[0] != h.fp[1]) {
         set_error("graph is not symmetric: %llu entries below the diagonal, %llu above, or their (pair, weight) "
                   "multisets differ (Section 3 needs w_ij = w_ji for every stored entry)",
                   h.cnt[0], h.cnt[1]);
@@ -788,15 +770,22 @@ void louvain_run(const DevGraph &g0, const gsp_opts &o, uint32_t *membership, do
         if (!refine) iota_u32(mb.C, cur.n, s);
         Cp = mb.C;
     }
+    // Equation 1 of the result.  Aggregation keeps every weight (self-loops
+    // included), so the intra-community weight, 2m and each Sigma_c of the
+    // input graph under the looked-up membership equal those of the last
+    // level's graph under its own membership: Q is taken there, on the
+    // smaller graph, unless a last split changes the membership on the input.
+    const bool split_last = o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_LAST;
+    double q = split_last ? 0.0 : modularity(cur, Cp, s, lsb_cache);
     lookup(n0, membership, Cp, s);
-    if (o.split != GSP_SPLIT_NONE && o.split_when == GSP_SPLIT_LAST) {
+    if (split_last) {
         Classes cl;
         classify_vertices(g0, cl, 1, s);
         split_labels(g0, cl, membership, o.split, labels, s);
         GSP_CUDA(cudaMemcpyAsync(membership, labels, sizeof(uint32_t) * n0, cudaMemcpyDeviceToDevice, s));
     }
     uint32_t kf = canonical_numbering(n0, membership, s);
-    double q = modularity(g0, membership, s, lsb_cache);
+    if (split_last) q = modularity(g0, membership, s, lsb_cache);
     local.passes = passes;
     local.final_communities = kf;
     local.modularity = q;

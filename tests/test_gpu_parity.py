@@ -389,6 +389,38 @@ def test_louvain_edge_cases(gsp):
             assert q == pytest.approx(0.5, abs=1e-12)  # 2 * (12/24 - (12/24)^2)
 
 
+def test_input_check_sparse_rows_hub_and_tail(gsp):
+    """The entry check walks the entries in contiguous ranges and finds each
+    entry's row by search: a graph whose rows are mostly empty, with a hub
+    of 6000 entries and the last entries in the last row, is accepted when
+    valid, and a defect at the first entry, inside the hub or at the very last
+    entry is caught."""
+    from paper_2402_11454_gb300._lib import GspError
+    n = 60000
+    rng = np.random.default_rng(3)
+    nb = rng.choice(np.arange(10, n - 1), size=6000, replace=False)
+    u = np.concatenate([np.full(6000, 3), [0, n - 2, 17]]).astype(np.uint64)
+    v = np.concatenate([nb, [n - 1, n - 1, 18]]).astype(np.uint64)
+    off, tgt, w = graphgen.edges_to_csr(n, u, v)
+    C, q, st = gsp.louvain(*dev(off, tgt, w), precision="fp64")
+    g = oracle.Graph(off, tgt, w.astype(np.float64))
+    assert q == pytest.approx(oracle.modularity(g, C.cpu().numpy()), abs=1e-12)
+    hub = 3
+    for e, what in ((0, "first"), (int(off[hub]) + 2999, "hub"), (len(tgt) - 1, "last")):
+        t2 = tgt.copy()
+        t2[e] = n  # target out of range
+        with pytest.raises(GspError, match="violations"):
+            gsp.louvain(*dev(off, t2, w))
+        w2 = w.copy()
+        w2[e] = np.nan
+        with pytest.raises(GspError, match="violations"):
+            gsp.louvain(*dev(off, tgt, w2))
+        w3 = w.copy()
+        w3[e] = 3.0  # its mirror keeps weight 1
+        with pytest.raises(GspError, match="not symmetric"):
+            gsp.louvain(*dev(off, tgt, w3))
+
+
 def test_asymmetric_graph_rejected(gsp):
     """Section 3's graph is undirected (w_ij = w_ji): a CSR entry without its
     mirror, or with a different weight on the mirror, is GSP_ERR_NOT_SYMMETRIC
@@ -414,7 +446,7 @@ def test_asymmetric_graph_rejected(gsp):
     w3[e] = 2.0
     with pytest.raises(GspError, match="not symmetric"):
         gsp.louvain(*dev(off, tgt, w3))
-    # a long row (hub) loses an entry: the long-row kernel sees it
+    # a long row (hub) loses an entry
     hub = int(np.argmax(np.diff(off.astype(np.int64))))
     assert off[hub + 1] - off[hub] > 64
     e = int(off[hub]) + 7

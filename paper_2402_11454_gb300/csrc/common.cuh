@@ -74,11 +74,14 @@ inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 0) {
 }
 
 // --------------------------------------------------------- device helpers
-// Row of CSR entry p (offsets non-decreasing, off[n] > p): the
-// last row with off[row] <= p, searched forward from a row r known to have
-// off[r] <= p by doubling the step, then halving it.  Consecutive entries of
-// a thread lie a few rows apart, so the search stays in a few cached lines.
+// Row of CSR entry p (offsets non-decreasing, off[n] > p): the last row with
+// off[row] <= p, searched forward from a row r known to have off[r] <= p:
+// first the row itself and the next, then by doubling the step and halving
+// it.  Consecutive entries of a lane lie a row or so apart, so the search
+// mostly ends after one or two cached loads.
 __device__ __forceinline__ uint32_t row_from(const uint64_t *__restrict__ off, uint32_t n, uint64_t p, uint32_t r) {
+    if ((uint64_t)r + 1 >= n || __ldg(off + r + 1) > p) return r;
+    r += 1;
     uint64_t step = 1;
     while ((uint64_t)r + step < n && __ldg(off + r + step) <= p) {
         r += (uint32_t)step;

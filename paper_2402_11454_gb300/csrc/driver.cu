@@ -150,17 +150,18 @@ __global__ void k_community_sizes(const uint32_t *__restrict__ C, uint32_t n, ui
 // Input checks.  Offsets: non-decreasing from 0 to nnz (checked first: the
 // entry kernel below trusts them).  Entries: targets < n, weights finite and
 // > 0.  Symmetry (Section 3: G is undirected, w_ij = w_ji): every stored
-// entry (i, j, w) with i != j adds a 64-bit hash of the unordered pair and
-// the weight's bits to the "below" sum when i < j and to the "above" sum
-// when i > j.  A symmetric CSR stores the same multiset of (pair, weight) on
-// both sides, so its counts and sums agree; an asymmetric one passes only if
-// two 64-bit sums of hashes collide.  The hash is the MurmurHash3 64-bit
-// finaliser (Appleby) of the pair with the weight's bits mixed in by a
-// multiplication with the 64-bit golden ratio.
+// entry (i, j, w) with i != j hashes the unordered pair and the weight's bits
+// to 64 bits and adds the hash (and 1) when i < j, subtracts it (and 1) when
+// i > j, modulo 2^64.  A symmetric CSR stores the same multiset of (pair,
+// weight) on both sides, so both differences end at 0; an asymmetric one
+// passes only if its hash difference vanishes by chance.  The hash is the
+// MurmurHash3 64-bit finaliser (Appleby) of the pair with the weight's bits
+// mixed in by a multiplication with the 64-bit golden ratio.
 struct GraphCheck {
-    unsigned long long bad;     // offset, target and weight violations
-    unsigned long long cnt[2];  // entries below / above the diagonal
-    unsigned long long fp[2];   // hash sums below / above, modulo 2^64
+    unsigned long long bad;    // offset, target and weight violations
+    unsigned long long below;  // entries below the diagonal (i < j)
+    unsigned long long cntd;   // entries below minus above, modulo 2^64
+    unsigned long long fpd;    // hashes below minus above, modulo 2^64
 };
 
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
@@ -173,7 +174,7 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
 }
 
 struct CheckAcc {
-    unsigned long long bad = 0, cnt[2] = {0, 0}, fp[2] = {0, 0};
+    unsigned long long bad = 0, below = 0, cntd = 0, fpd = 0;
     // entry (i, j) of weight x (has_w = 0: no weights to check)
     __device__ void entry(uint32_t i, uint32_t j, float x, bool has_w, uint32_t n) {
         uint32_t wb = 0;
@@ -183,16 +184,22 @@ struct CheckAcc {
         }
         if (j >= n) { bad++; return; }
         if (i == j) return;
-        const int side = i > j;
-        const uint64_t key = side ? (((uint64_t)j << 32) | i) : (((uint64_t)i << 32) | j);
-        fp[side] += fmix64(key ^ ((uint64_t)wb * 0x9E3779B97F4A7C15ull));
-        cnt[side]++;
+        const uint64_t key = ((uint64_t)min(i, j) << 32) | max(i, j);
+        const uint64_t h = fmix64(key ^ ((uint64_t)wb * 0x9E3779B97F4A7C15ull));
+        if (i < j) {
+            fpd += h;
+            cntd++;
+            below++;
+        } else {
+            fpd -= h;
+            cntd--;
+        }
     }
     __device__ void flush(GraphCheck *g) {
-        unsigned long long v[5] = {bad, cnt[0], cnt[1], fp[0], fp[1]};
-        unsigned long long *dst[5] = {&g->bad, &g->cnt[0], &g->cnt[1], &g->fp[0], &g->fp[1]};
+        unsigned long long v[4] = {bad, below, cntd, fpd};
+        unsigned long long *dst[4] = {&g->bad, &g->below, &g->cntd, &g->fpd};
 #pragma unroll
-        for (int k = 0; k < 5; k++) {
+        for (int k = 0; k < 4; k++) {
             const unsigned long long t = warp_sum(v[k]);
             if ((threadIdx.x & 31) == 0 && t) atomicAdd(dst[k], t);
         }
@@ -215,10 +222,10 @@ constexpr int CHECK_UNROLL = 4;  // entries a thread loads before checking them
 // entries [nnz w / warps, nnz (w+1) / warps), its lanes consecutive entries
 // (coalesced loads whatever the row lengths; a lane's next entry lies 32
 // entries on, so its row search moves a row or so).
-__global__ void __launch_bounds__(256) k_check_entries(const uint64_t *__restrict__ off,
-                                                       const uint32_t *__restrict__ tgt,
-                                                       const float *__restrict__ w, uint32_t n, uint64_t nnz,
-                                                       GraphCheck *g) {
+__global__ void __launch_bounds__(256, 8) k_check_entries(const uint64_t *__restrict__ off,
+                                                          const uint32_t *__restrict__ tgt,
+                                                          const float *__restrict__ w, uint32_t n, uint64_t nnz,
+                                                          GraphCheck *g) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const uint64_t wid = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -271,10 +278,10 @@ void check_graph(const uint64_t *off, const uint32_t *tgt, const float *w, uint3
     }
     arena().release(mk);
     GSP_REQUIRE(h.bad == 0, "invalid graph: %llu violations (targets must be < n, weights finite and > 0)", h.bad);
-    if (h.cnt[0] != h.cnt[1] || h.fp[0] != h.fp[1]) {
+    if (h.cntd != 0 || h.fpd != 0) {
         set_error("graph is not symmetric: %llu entries below the diagonal, %llu above, or their (pair, weight) "
                   "multisets differ (Section 3 needs w_ij = w_ji for every stored entry)",
-                  h.cnt[0], h.cnt[1]);
+                  h.below, h.below - h.cntd);
         throw Error{GSP_ERR_NOT_SYMMETRIC};
     }
 }

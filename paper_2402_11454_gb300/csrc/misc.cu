@@ -254,7 +254,9 @@ static void row_sums(const DevGraph &g, const uint32_t *C, double *K, double *Si
     const WT *w = static_cast<const WT *>(g.w);
     k_row_sums<WT, AV><<<grid_for(g.n, 256), 256, 0, s>>>(g.off, g.tgt, w, g.n, C, K, Sig, acc, longlist, nlong, lsb);
     GSP_CHECK_LAUNCH();
-    k_row_sums_long<WT, AV><<<sms(4), 256, 0, s>>>(g.off, g.tgt, w, C, K, Sig, acc, longlist, nlong, lsb);
+    // as many warps as fit: each long row is a chain of loads per lane
+    k_row_sums_long<WT, AV><<<resident_grid((const void *)k_row_sums_long<WT, AV>, 256, 0, 8), 256, 0, s>>>(
+        g.off, g.tgt, w, C, K, Sig, acc, longlist, nlong, lsb);
     GSP_CHECK_LAUNCH();
     arena().release(mk);
 }

@@ -3,7 +3,8 @@
 The GPU run launches one process per GPU under torchrun and reduces over
 NCCL; here the same calls run as world size 2 over gloo: the max over ranks
 of the timed region, the whole-job rate, and the reference arm, which rank 0
-alone runs and prints.  The clock-log parser is checked on sample lines.
+alone runs and prints.  The clock-log parser is checked on sample lines, and
+the roofline figures on sample counters.
 """
 import json
 import os
@@ -87,3 +88,19 @@ def test_reference_arm_world_2_rank0_prints_once():
 ])
 def test_clock_log(lines, expect):
     assert bench.parse_clock_log(lines) == expect
+
+
+def test_roofline_traffic_basis():
+    """The roofline's traffic: the R-MAT 26 line takes the ratio captured at
+    that scale, other workloads the R-MAT 20 ratio, scaled and said so; the
+    fractions are algorithmic bytes (and DRAM bytes) over the kernels' time."""
+    st = [{"move_bytes": [200e9, 33.5e9], "ms_move_kernels": [500.0, 140.0]}] * 2
+    r = bench.roofline_from(st, 6784.8, "measured", "rmat26")
+    assert r["algorithmic_bytes_per_step"] == 233.5e9
+    assert r["achieved"] == round(233.5e9 / 0.64 / 1e9, 1)
+    assert r["frac"] == round(r["achieved"] / 6784.8, 4)
+    assert r["traffic"] == round(233.5e9 * 3.737) and r["traffic_basis"].find("measured") >= 0
+    assert r["dram_gbs"] == round(r["traffic"] / 0.64 / 1e9, 1)
+    s = bench.roofline_from(st, 6784.8, "measured", "grid")
+    assert s["traffic"] == round(233.5e9 * 2.153) and s["traffic_basis"].find("scaled") >= 0
+    assert bench.roofline_from([{"move_bytes": [0], "ms_move_kernels": [0.0]}], 6784.8, "measured") is None

@@ -130,7 +130,9 @@ struct TuneBuffers {
     uint32_t *membership = nullptr;
     double *q = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    TuneBuffers(uint32_t n, uint32_t num_q) {
+    // allocated after construction, so that the destructor frees what a
+    // failing later allocation leaves behind
+    void alloc(uint32_t n, uint32_t num_q) {
         GSP_CUDA(cudaMalloc(&membership, sizeof(uint32_t) * (size_t)n));
         if (num_q) GSP_CUDA(cudaMalloc(&q, sizeof(double) * (size_t)num_q));
         GSP_CUDA(cudaEventCreate(&e0));
@@ -300,7 +302,8 @@ gsp_status gsp_autotune(const uint64_t *offsets, const uint32_t *targets, const 
         check_opts(o);
         DevGraph g = make_graph(offsets, targets, weights, GSP_W_F32, n, nnz);
         cudaStream_t s = tune_prologue(g, offsets, targets, weights, o);
-        TuneBuffers buf(n, 0);
+        TuneBuffers buf;
+        buf.alloc(n, 0);
         gsp_opts ro = o;
         ro.count_disconnected = 0;
         ro.stream = s;
@@ -326,7 +329,8 @@ gsp_status gsp_autotune_batched(uint32_t num_graphs, const uint64_t *graph_verte
         check_batch(num_graphs, graph_vertex_offsets, n, o);
         DevGraph g = make_graph(offsets, targets, weights, GSP_W_F32, n, nnz);
         cudaStream_t s = tune_prologue(g, offsets, targets, weights, o);
-        TuneBuffers buf(n, num_graphs);
+        TuneBuffers buf;
+        buf.alloc(n, num_graphs);
         gsp_opts ro = o;
         ro.count_disconnected = 0;
         ro.stream = s;

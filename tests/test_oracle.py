@@ -447,6 +447,27 @@ def test_aggregate_equals_indicator_product(seed):
         oracle.modularity(g, Cd), abs=1e-12)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_modularity_kept_by_aggregation_under_any_coarser_membership(seed):
+    """Eq. 1 of a membership D of the super-vertices on the aggregated graph
+    (Algorithm 5) equals Eq. 1 of the looked-up membership D[Cd] on the
+    graph that was aggregated: aggregation keeps every weight, self-loops
+    included.  (The library takes the final modularity of a run this way, on
+    the last level's graph.)  Checked against the all-pairs brute force."""
+    rng = np.random.default_rng(650 + seed)
+    n = int(rng.integers(2, 60))
+    g, A = random_graph(rng, n, rng.uniform(0.05, 0.4))
+    C = rng.integers(0, max(1, n // 2), size=n).astype(np.uint32)
+    Cd, k = oracle.renumber(C)
+    h = oracle.aggregate(g, Cd, k)
+    for D in (np.arange(k), rng.integers(0, max(1, k // 3), size=k), np.zeros(k, np.int64)):
+        D = D.astype(np.uint32)
+        full = oracle.lookup(Cd, D)
+        q_full = brute_modularity(A, full)
+        assert oracle.modularity(g, full) == pytest.approx(q_full, abs=1e-12)
+        assert oracle.modularity(h, D) == pytest.approx(q_full, abs=1e-12)
+
+
 # --------------------------------------------------------- Algorithm 1 pins
 def brute_force_optimum(A):
     """Best Eq.1 value over all set partitions (restricted-growth strings)."""

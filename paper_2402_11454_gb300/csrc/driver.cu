@@ -218,38 +218,48 @@ __global__ void k_check_offsets(const uint64_t *__restrict__ off, uint32_t n, ui
 
 constexpr int CHECK_UNROLL = 4;  // entries a thread loads before checking them
 
-// Entry checks, edge-parallel: warp w of the grid takes the contiguous
-// entries [nnz w / warps, nnz (w+1) / warps), its lanes consecutive entries
-// (coalesced loads whatever the row lengths; a lane's next entry lies 32
-// entries on, so its row search moves a row or so).
-__global__ void __launch_bounds__(256, 8) k_check_entries(const uint64_t *__restrict__ off,
+// Entry checks, edge-parallel, in chunks of CHECK_CHUNK consecutive entries
+// whose first rows a bisection kernel finds ahead; warp w takes chunks w,
+// w + warps, ..., its lanes consecutive entries (coalesced loads whatever the
+// row lengths; a lane's next entry lies 32 entries on, so its row search
+// moves a row or so).  Dealing the chunks round the warps spreads the
+// stretches of empty rows, where the searches run longest, over all SMs.
+constexpr uint64_t CHECK_CHUNK = 1024;
+
+__global__ void k_chunk_rows(const uint64_t *__restrict__ off, uint32_t n, uint64_t nchunks, uint32_t *rows) {
+    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nchunks;
+         c += (uint64_t)gridDim.x * blockDim.x)
+        rows[c] = row_of(off, n, c * CHECK_CHUNK);
+}
+
+__global__ void __launch_bounds__(256, 6) k_check_entries(const uint64_t *__restrict__ off,
                                                           const uint32_t *__restrict__ tgt,
                                                           const float *__restrict__ w, uint32_t n, uint64_t nnz,
-                                                          GraphCheck *g) {
+                                                          const uint32_t *__restrict__ chunk_rows,
+                                                          uint64_t nchunks, GraphCheck *g) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    const uint64_t wid = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const uint64_t w0 = nnz * wid / warps, w1 = nnz * (wid + 1) / warps;
-    uint32_t r = 0;
-    if (lane == 0 && w0 < w1) r = row_of(off, n, w0);
-    r = __shfl_sync(0xffffffffu, r, 0);
     CheckAcc a;
     const bool has_w = w != nullptr;
-    for (uint64_t p = w0 + lane; p < w1; p += 32ull * CHECK_UNROLL) {
-        uint32_t t[CHECK_UNROLL];
-        float x[CHECK_UNROLL];
+    for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += warps) {
+        const uint64_t c0 = c * CHECK_CHUNK, c1 = min(c0 + CHECK_CHUNK, nnz);
+        uint32_t r = __ldg(chunk_rows + c);
+        for (uint64_t p = c0 + lane; p < c1; p += 32ull * CHECK_UNROLL) {
+            uint32_t t[CHECK_UNROLL];
+            float x[CHECK_UNROLL];
 #pragma unroll
-        for (int k = 0; k < CHECK_UNROLL; k++) {
-            const uint64_t q = p + 32ull * k;
-            t[k] = q < w1 ? __ldg(tgt + q) : 0u;
-            x[k] = (has_w && q < w1) ? __ldg(w + q) : 1.0f;
-        }
+            for (int k = 0; k < CHECK_UNROLL; k++) {
+                const uint64_t q = p + 32ull * k;
+                t[k] = q < c1 ? __ldg(tgt + q) : 0u;
+                x[k] = (has_w && q < c1) ? __ldg(w + q) : 1.0f;
+            }
 #pragma unroll
-        for (int k = 0; k < CHECK_UNROLL; k++) {
-            const uint64_t q = p + 32ull * k;
-            if (q < w1) {
-                r = row_from(off, n, q, r);
-                a.entry(r, t[k], x[k], has_w, n);
+            for (int k = 0; k < CHECK_UNROLL; k++) {
+                const uint64_t q = p + 32ull * k;
+                if (q < c1) {
+                    r = row_from(off, n, q, r);
+                    a.entry(r, t[k], x[k], has_w, n);
+                }
             }
         }
     }
@@ -269,9 +279,13 @@ void check_graph(const uint64_t *off, const uint32_t *tgt, const float *w, uint3
     if (h.bad) arena().release(mk);
     GSP_REQUIRE(h.bad == 0, "invalid graph: offsets must rise from 0 to nnz (%llu violations)", h.bad);
     if (nnz) {
-        const unsigned grid = std::min(grid_for(nnz, 256 * CHECK_UNROLL, sms(8)),
-                                       resident_grid((const void *)k_check_entries, 256, 0, 8));
-        k_check_entries<<<grid, 256, 0, s>>>(off, tgt, w, n, nnz, d);
+        const uint64_t nchunks = (nnz + CHECK_CHUNK - 1) / CHECK_CHUNK;
+        uint32_t *chunk_rows = arena().get<uint32_t>(nchunks);
+        k_chunk_rows<<<grid_for(nchunks, 256), 256, 0, s>>>(off, n, nchunks, chunk_rows);
+        GSP_CHECK_LAUNCH();
+        const unsigned grid = std::min(grid_for(nchunks, 8, sms(8)),
+                                       resident_grid((const void *)k_check_entries, 256, 0, 6));
+        k_check_entries<<<grid, 256, 0, s>>>(off, tgt, w, n, nnz, chunk_rows, nchunks, d);
         GSP_CHECK_LAUNCH();
         GSP_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
         GSP_CUDA(cudaStreamSynchronize(s));

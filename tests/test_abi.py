@@ -129,3 +129,24 @@ def test_new_defaults(lib):
     assert lib.gsp_louvain(None, None, None, 5, 0, ctypes.byref(o), None, None, None) == -1
     assert b"wave_repeats" in lib.gsp_last_error()
     assert lib.gsp_workspace_reserved() >= 0
+
+
+def test_batch_offsets_rejected_on_host(lib):
+    """Batched calls and batched tuning check the graphs' vertex offsets (host
+    array) before any device work."""
+    import numpy as np
+    from paper_2402_11454_gb300._lib import GspOpts, GspTuning
+    o = GspOpts()
+    lib.gsp_default_opts(ctypes.byref(o))
+    t = GspTuning()
+    for gvo, what in (([0, 4, 9], b"run from 0 to n"), ([1, 10], b"run from 0 to n"),
+                      ([0, 6, 4, 10], b"must not decrease")):
+        a = np.asarray(gvo, dtype=np.uint64)
+        p = a.ctypes.data_as(ctypes.c_void_p)
+        G = len(gvo) - 1
+        assert lib.gsp_louvain_batched(G, p, None, None, None, 10, 0, ctypes.byref(o), None, None, None) == -1
+        assert what in lib.gsp_last_error()
+        assert lib.gsp_autotune_batched(G, p, None, None, None, 10, 0, ctypes.byref(o), ctypes.byref(t),
+                                        None, None) == -1
+        assert what in lib.gsp_last_error()
+    assert lib.gsp_autotune_batched(0, None, None, None, None, 10, 0, None, None, None, None) == -1

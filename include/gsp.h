@@ -487,8 +487,9 @@ gsp_status gsp_set_tuning(const gsp_tuning *t);
  * in effect at the call once more, keeping the faster.  Device graph as for
  * gsp_louvain (float32 weights); the graph is not modified.  *chosen
  * receives the installed settings, *ms_default the time of a call under the
- * settings in effect at the call, *ms_tuned under the chosen ones (host
- * pointers, each may be NULL).  The trials allocate a membership array of n
+ * settings in effect at the call, *ms_tuned under the chosen ones, both from
+ * the final pair of trials when the search moved (so ms_tuned <= ms_default;
+ * host pointers, each may be NULL).  The trials allocate a membership array of n
  * entries outside the workspace and may free and rebuild the workspace.  An
  * edgeless graph is GSP_ERR_INVALID.  Not safe to run concurrently with
  * other calls.

@@ -262,7 +262,8 @@ static void autotune_search(const std::function<void()> &one_run, TuneBuffers &t
             }
         }
         // the pick is the best of many noisy trials: time it against the
-        // starting settings once more and keep whichever is faster
+        // starting settings once more and keep whichever is faster; the two
+        // times reported are then those of this last pair
         if (!(best.groups == start.groups && best.w512 == start.w512 && best.block == start.block &&
               best.hub == start.hub && best.group_max == start.group_max && best.warp_max == start.warp_max &&
               best.block_max == start.block_max && best.big_max == start.big_max)) {
@@ -270,6 +271,7 @@ static void autotune_search(const std::function<void()> &one_run, TuneBuffers &t
             const float ts = trial();
             g_tuning = best;
             const float tbest = trial();
+            t0 = ts;
             if (ts <= tbest) {
                 best = start;
                 tb = ts;
